@@ -1,0 +1,200 @@
+/*
+ * nep_gb300.h -- C ABI of the GB300 (sm_103a) NEP loss + parameter-gradient hot path.
+ *
+ * The model is the neuroevolution potential as stated in the TorchNEP paper
+ * (arXiv 2606.19557): per-atom energies (Eq. 1) from a per-species one-hidden-
+ * layer tanh network (Eq. "ann") on normalised descriptors (Eq. "norm") built
+ * from Chebyshev radial functions and angular moments (Methods, "NEP
+ * descriptors"), trained on the energy/force/virial loss (Eq. "loss") with
+ * analytic parameter gradients (Sec. "Training efficiency ...": closed-form
+ * expressions from the descriptor-coordinate Jacobian instead of a second-order
+ * autograd pass).
+ *
+ * Conventions for every entry point
+ *   - Return value: NEP_OK (0) or a negative NEP_E* code.  No exception or
+ *     signal crosses the ABI.  nep_last_error() gives a one-line reason.  A call
+ *     that fails argument validation changes nothing in the context.
+ *   - Pointers named *_dev are DEVICE pointers on the context's GPU, owned by the
+ *     caller; they must stay valid until the work queued by the call has
+ *     finished on the context's stream.  Pointers named *_host are host pointers
+ *     (pinned or pageable), owned by the caller.  The context owns only its
+ *     internal workspaces.
+ *   - Execution: calls queue work on the stream given to nep_create() and
+ *     return without waiting, except where a description says "synchronizes".
+ *   - Units: Angstrom, eV, eV/Angstrom; virials in eV.
+ *   - Limits: 1 <= n_types <= 16; 0 <= n_max <= 11; 0 <= basis_size <= 11;
+ *     0 <= l_max <= 4 (4-body needs l_max >= 2, 5-body l_max >= 1);
+ *     1 <= n_neuron <= 128; 0 < rc_A <= rc_R; fewer than 2^27 atoms and 2^31
+ *     neighbour pairs per context; every structure holds at least one atom.
+ *
+ * Parameter vector theta (float32, P entries; nep_num_params gives P):
+ *   [ w0 : T x N_neu x N_des | b0 : T x N_neu | w1 : T x N_neu | b1 : 1 |
+ *     cR : T x T x N_R x K_R | cA : T x T x N_A x K_A ]
+ * with N_R = n_max_R + 1, K_R = basis_R + 1 (same for A), coefficients c
+ * indexed [t_i][t_j][n][k] for the ordered species pair of the centre atom i and
+ * neighbour j (Methods, g_n = sum_k c^{t_i t_j}_{nk} f_k).  This reproduces the
+ * parameter counts of Table 2 (70,401 / 97,537 / 124,673).
+ * Descriptor order (N_des = N_R + N_A (l_max + has_4b + has_5b)):
+ *   [ q_n (N_R) | q_nl for l = 1..l_max, n fastest | q4_n | q5_n ].
+ */
+#ifndef NEP_GB300_H
+#define NEP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NEP_OK 0
+#define NEP_EINVAL (-1)   /* invalid argument, unsupported size, or bad geometry           */
+#define NEP_ENOMEM (-2)   /* device or host allocation failed                              */
+#define NEP_ECUDA (-3)    /* a CUDA runtime call failed (message in nep_last_error)        */
+#define NEP_ESTATE (-4)   /* call out of order (e.g. nep_eval before nep_set_structures)   */
+#define NEP_EINTERNAL (-5)/* an internal consistency check on the device failed            */
+
+#define NEP_PREC_FP32 0   /* FP32 pair/network arithmetic, FP64 structure and batch sums    */
+
+#define NEP_SCHED_PERSISTENT 0 /* one persistent launch per kernel over all structures, graph */
+#define NEP_SCHED_PLAIN 1      /* one launch sequence per structure, no graph (baseline form) */
+
+typedef struct nep_ctx nep_ctx;
+
+/* Model hyper-parameters: the model keys of the NEP input file (Table 1: type,
+ * cutoff, n_max, basis_size, l_max, neuron).  has_4b / has_5b are the second and
+ * third l_max entries ("4 2 1") as flags. */
+typedef struct {
+    int n_types;
+    float rc_R, rc_A;
+    int n_max_R, n_max_A;
+    int basis_R, basis_A;
+    int l_max, has_4b, has_5b;
+    int n_neuron;
+    int precision; /* NEP_PREC_FP32 */
+    int device;    /* CUDA device ordinal */
+} nep_config;
+
+/* Creates a context on cfg->device that queues its work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *out receives the handle.
+ * Errors: NEP_EINVAL (sizes outside the limits above), NEP_ECUDA, NEP_ENOMEM. */
+int nep_create(const nep_config *cfg, void *cuda_stream, nep_ctx **out);
+
+/* Frees every workspace of the context (synchronizes its stream).  NULL is a no-op. */
+void nep_destroy(nep_ctx *ctx);
+
+/* P, the length of theta (layout above).  Errors: NEP_EINVAL (NULL arguments). */
+int nep_num_params(const nep_ctx *ctx, int64_t *P);
+
+/* N_des, the descriptor length.  Errors: NEP_EINVAL. */
+int nep_num_descriptors(const nep_ctx *ctx, int *n_des);
+
+/* Copies theta_dev [P] (float32) and the normalisation factors q_scale_dev
+ * [N_des] (float32, s_nu = 1/(q_nu^max - q_nu^min), Eq. "norm") into the context.
+ * The copy is queued on the stream; the caller's buffers may be reused once it
+ * has run.  Errors: NEP_EINVAL (NULL), NEP_ECUDA. */
+int nep_set_params(nep_ctx *ctx, const float *theta_dev, const float *q_scale_dev);
+
+/* Caches a batch of periodic structures and builds their neighbour lists (cell
+ * lists -> CSR) once, as the paper keeps neighbour lists and displacement vectors
+ * resident on the GPU (Sec. "Training efficiency ...").
+ *   atom_off_dev [n_struct+1] int64: atoms of structure s are atom_off[s]..atom_off[s+1]-1
+ *   pos_dev      [N_a*3] float32 Cartesian positions (any image; need not be wrapped)
+ *   type_dev     [N_a] int32 species in [0, n_types)
+ *   cell_dev     [n_struct*9] float32 row-major 3x3 cells, rows = lattice vectors
+ * A pair (i, j, S) is a neighbour iff d = r_j + S.h - r_i, formed in FP64 and
+ * rounded once to float, has float d.d < rc_R^2 (radial) / < rc_A^2 (angular);
+ * j = i is included for S != 0.  n_struct = 0 is valid (empty batch).
+ * Synchronizes.  Errors: NEP_EINVAL (counts, species, non-finite positions,
+ * singular cell, more than 127 periodic images per direction), NEP_ENOMEM,
+ * NEP_ECUDA. */
+int nep_set_structures(nep_ctx *ctx, int64_t n_struct, const int64_t *atom_off_dev, const float *pos_dev,
+                       const int32_t *type_dev, const float *cell_dev);
+
+/* Radial and angular neighbour-pair counts of the cached batch. */
+int nep_num_pairs(const nep_ctx *ctx, int64_t *n_radial, int64_t *n_angular);
+
+/* Exports the cached neighbour list (for checks): nbr_off_dev [N_a+1] int64 CSR
+ * offsets, j_dev [M] int32 neighbour atom, shift_dev [M*3] int32 image S,
+ * ang_dev [M] uint8 (1 if within rc_A).  Within an atom, angular neighbours come
+ * first, each group sorted by (species, j, S).  Errors: NEP_ESTATE, NEP_EINVAL. */
+int nep_get_neighbors(nep_ctx *ctx, int64_t *nbr_off_dev, int32_t *j_dev, int32_t *shift_dev, uint8_t *ang_dev);
+
+/* Energies, forces and virials at the current parameters (Eq. 1, Eq. "ann").
+ *   E_dev [n_struct] float64, F_dev [N_a*3] float32 (F = -dE/dr),
+ *   W_dev [n_struct*9] float64 with W = -dE/d(eps) for r -> (I + eps) r applied
+ *   to positions and cell, i.e. W_ab = -sum_pairs (dE_i/dd_ij)_a (d_ij)_b.
+ * Also stores the per-atom state nep_backward needs.
+ * Errors: NEP_ESTATE (no structures or parameters), NEP_EINVAL, NEP_ECUDA. */
+int nep_eval(nep_ctx *ctx, double *E_dev, float *F_dev, double *W_dev);
+
+/* Raw descriptors q [N_a*N_des] float32 (before the scale of Eq. "norm"). */
+int nep_descriptors(nep_ctx *ctx, float *q_dev);
+
+/* Per-component minimum and maximum of q over the cached batch, [N_des] each
+ * (helper for the normalisation factors of Eq. "norm"). */
+int nep_descriptor_range(nep_ctx *ctx, float *qmin_dev, float *qmax_dev);
+
+/* One full loss + parameter-gradient pass (Eq. "loss"):
+ *   DE = 1/N_s sum_s ((E_s - E_ref_s)/N_a^s)^2
+ *   DF = 1/(3 N_a) sum_i |F_i - F_ref_i|^2
+ *   DV = 1/(9 N_s^V) sum_{s: has_W} |(W_s - W_ref_s)/N_a^s|^2   (0 if N_s^V = 0)
+ *   L  = lamE DE + lamF DF + lamV DV
+ *   E_ref_dev [n_struct] f64, F_ref_dev [N_a*3] f32, W_ref_dev [n_struct*9] f64,
+ *   has_W_dev [n_struct] uint8 or NULL (= all structures have virials).
+ * Writes loss3_dev [3] float64 = (DE, DF, DV) and grad_dev [P] float32 = dL/dtheta.
+ * With NEP_SCHED_PERSISTENT the whole pass is one CUDA-graph launch.
+ * Errors: NEP_ESTATE, NEP_EINVAL, NEP_ECUDA. */
+int nep_loss_grad(nep_ctx *ctx, const double *E_ref_dev, const float *F_ref_dev, const double *W_ref_dev,
+                  const uint8_t *has_W_dev, double lamE, double lamF, double lamV, double *loss3_dev,
+                  float *grad_dev);
+
+/* Vector-Jacobian product for autograd: grad_dev [P] = d/dtheta of
+ *   sum_s dE_s E_s + sum_i dF_i . F_i + sum_s dW_s : W_s
+ * with cotangents dE_dev [n_struct] f64, dF_dev [N_a*3] f32, dW_dev [n_struct*9] f64.
+ * Uses the per-atom state of the latest nep_eval, which must have run with the
+ * same parameters and structures.  Errors: NEP_ESTATE, NEP_EINVAL, NEP_ECUDA. */
+int nep_backward(nep_ctx *ctx, const double *dE_dev, const float *dF_dev, const double *dW_dev, float *grad_dev);
+
+/* Copies loss references into context-owned device buffers so that the host
+ * entry point below needs none per call (same layouts as nep_loss_grad). */
+int nep_set_targets(nep_ctx *ctx, const double *E_ref_dev, const float *F_ref_dev, const double *W_ref_dev,
+                    const uint8_t *has_W_dev);
+
+/* Host-buffer step: copies theta_host [P] to the device, runs nep_loss_grad on
+ * the references of nep_set_targets, and copies loss3_host [3] and grad_host [P]
+ * back.  Synchronizes.  The copies use the context's stream.
+ * Errors: NEP_ESTATE (no targets), NEP_EINVAL, NEP_ECUDA. */
+int nep_loss_grad_host(nep_ctx *ctx, const float *theta_host, double lamE, double lamF, double lamV,
+                       double *loss3_host, float *grad_host);
+
+/* Selects NEP_SCHED_PERSISTENT (default) or NEP_SCHED_PLAIN. */
+int nep_set_schedule(nep_ctx *ctx, int schedule);
+
+/* Times launch shapes (warps per block, blocks per SM) of the two per-atom kernels
+ * on the cached batch and keeps the fastest.  Synchronizes.  Results are
+ * deterministic for a fixed shape; different shapes may differ in the last bits
+ * of the gradient (another reduction tree). */
+int nep_autotune(nep_ctx *ctx);
+
+/* Current launch shape: warps per block and blocks of the forward and adjoint kernels. */
+int nep_get_launch(const nep_ctx *ctx, int *fwd_warps, int *fwd_blocks, int *adj_warps, int *adj_blocks);
+
+/* Sets the launch shape explicitly (0 keeps a value). */
+int nep_set_launch(nep_ctx *ctx, int fwd_warps, int fwd_blocks, int adj_warps, int adj_blocks);
+
+/* Kernel timing: when on, the graph of nep_loss_grad records CUDA events around
+ * each kernel; nep_kernel_times then returns, for the latest completed call, the
+ * duration in ms of each kernel (names from nep_kernel_name).  n_io: in = capacity,
+ * out = number written. */
+int nep_set_timing(nep_ctx *ctx, int on);
+int nep_kernel_times(nep_ctx *ctx, float *ms, int *n_io);
+const char *nep_kernel_name(int k);
+
+/* Last error message of this context (or of the latest failed nep_create when ctx is NULL). */
+const char *nep_last_error(const nep_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEP_GB300_H */

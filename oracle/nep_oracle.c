@@ -274,7 +274,8 @@ static int64_t brute_pairs(int n, const double *pos, const double *cell, float r
     int M[3];
     for (int a = 0; a < 3; a++) {
         double span = n > 0 ? fmax[a] - fmin[a] : 0.0;
-        M[a] = (int)ceil((double)rcR / w[a] + span) + 1;
+        /* |f_j - f_i + S_a| <= rc / w_a is needed for |d| < rc, and |f_j - f_i| <= span */
+        M[a] = (int)ceil((double)rcR / w[a] + span + 1e-9);
     }
     float rc2R = rcR * rcR, rc2A = rcA * rcA;
     int64_t cnt = 0;

@@ -1,0 +1,775 @@
+// C ABI of the NEP library: context lifecycle, batch caching, static schedule,
+// CUDA-graph capture of the loss + gradient pass, and the launch-shape autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "nep_ctx.cuh"
+
+using namespace nep;
+
+struct nep_ctx : public nep::Ctx {};
+
+namespace nep {
+int launch_compact_q(Ctx *c, const float *qp, float *q);
+
+Ctx::~Ctx() {
+    if (g_loss.exec) cudaGraphExecDestroy(g_loss.exec);
+    if (g_eval.exec) cudaGraphExecDestroy(g_eval.exec);
+    if (ev_made)
+        for (auto &e : ev) cudaEventDestroy(e);
+}
+}  // namespace nep
+
+static thread_local std::string g_create_err;
+
+static const char *kernel_names[KID_COUNT] = {"expand_params", "forward", "force_gather", "struct_sums",
+                                              "loss_final",    "adjoint", "net_grad",     "grad_reduce"};
+
+// ----------------------------------------------------------------------------- helpers
+
+static int check_cfg(const nep_config *c, std::string &why) {
+    if (!c) return why = "null config", 0;
+    if (c->n_types < 1 || c->n_types > TMAX) return why = "n_types must be in [1, 16]", 0;
+    if (c->n_max_R < 0 || c->n_max_R > 11 || c->n_max_A < 0 || c->n_max_A > 11)
+        return why = "n_max must be in [0, 11]", 0;
+    if (c->basis_R < 0 || c->basis_R > 11 || c->basis_A < 0 || c->basis_A > 11)
+        return why = "basis_size must be in [0, 11]", 0;
+    if (c->l_max < 0 || c->l_max > 4) return why = "l_max must be in [0, 4]", 0;
+    if (c->has_4b && c->l_max < 2) return why = "the 4-body term needs l_max >= 2", 0;
+    if (c->has_5b && c->l_max < 1) return why = "the 5-body term needs l_max >= 1", 0;
+    if (c->n_neuron < 1 || c->n_neuron > NNMAX) return why = "n_neuron must be in [1, 128]", 0;
+    if (!(c->rc_R > 0.0f) || !(c->rc_A > 0.0f) || c->rc_A > c->rc_R || !(c->rc_R < 1e4f))
+        return why = "cutoffs must satisfy 0 < rc_A <= rc_R", 0;
+    if (c->precision != NEP_PREC_FP32) return why = "unsupported precision", 0;
+    return 1;
+}
+
+// Static schedule of one per-atom kernel: contiguous ranges of the species-sorted work
+// order with about equal cost per warp (cost ~ radial pairs + 6 x angular pairs + 8).
+static int make_sched(Ctx *c, Sched &s, int wpb, int blocks) {
+    s.wpb = wpb;
+    s.blocks = blocks;
+    s.W = wpb * blocks;
+    const int64_t na = c->n_atoms;
+    std::vector<int> begin(s.W + 1, 0);
+    if (na > 0) {
+        std::vector<double> pre(na + 1, 0.0);
+        for (int64_t q = 0; q < na; ++q) {
+            const int i = c->h_work[q];
+            const double nr = (double)(c->h_nbr_off[i + 1] - c->h_nbr_off[i]);
+            pre[q + 1] = pre[q] + nr + 6.0 * c->h_nang[i] + 8.0;
+        }
+        const double tot = pre[na];
+        int64_t q = 0;
+        for (int w = 0; w <= s.W; ++w) {
+            const double target = tot * (double)w / (double)s.W;
+            while (q < na && pre[q] < target) ++q;
+            begin[w] = (int)q;
+        }
+        begin[s.W] = (int)na;
+        for (int w = 1; w <= s.W; ++w) begin[w] = std::max(begin[w], begin[w - 1]);
+    }
+    s.h_wlo.assign(c->T, 0);
+    s.h_whi.assign(c->T, -1);
+    for (int t = 0; t < c->T; ++t) {
+        const int p0 = c->type_begin[t], p1 = c->type_begin[t + 1];
+        if (p1 <= p0) continue;
+        // warp holding position p: the last w with begin[w] <= p < begin[w+1]
+        auto owner = [&](int p) {
+            int lo = 0, hi = s.W - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (begin[mid] <= p) lo = mid;
+                else hi = mid - 1;
+            }
+            return lo;
+        };
+        s.h_wlo[t] = owner(p0);
+        s.h_whi[t] = owner(p1 - 1);
+    }
+    if (s.warp_begin.ensure<int>(s.W + 1) || s.type_wlo.ensure<int>(c->T) || s.type_whi.ensure<int>(c->T))
+        return c->fail(NEP_ENOMEM, "schedule buffers");
+    CK(cudaMemcpy(s.warp_begin.ptr, begin.data(), sizeof(int) * (s.W + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.type_wlo.ptr, s.h_wlo.data(), sizeof(int) * c->T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.type_whi.ptr, s.h_whi.data(), sizeof(int) * c->T, cudaMemcpyHostToDevice));
+    return NEP_OK;
+}
+
+static int max_blocks_per_sm(Ctx *c, const void *fn, int wpb, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, wpb * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+static int set_smem_attr(Ctx *c) {
+    const size_t f = c->ks->fwd_smem(c->T) * 8, a = c->ks->adj_smem(c->T) * 8;
+    int maxo = 0;
+    CK(cudaDeviceGetAttribute(&maxo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
+    CK(cudaFuncSetAttribute(c->ks->fwd_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min<size_t>(f, maxo)));
+    CK(cudaFuncSetAttribute(c->ks->adj_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min<size_t>(a, maxo)));
+    return NEP_OK;
+}
+
+// Buffers whose size depends on the schedule (per-warp gradient partials).
+static int alloc_sched_buffers(Ctx *c) {
+    const int NC = c->ks->NR * c->ks->KR + c->ks->NA * c->ks->KA;
+    if (c->cpart.ensure<float>((int64_t)(c->adj.W + c->T) * c->T * NC))
+        return c->fail(NEP_ENOMEM, "gradient partials");
+    return NEP_OK;
+}
+
+static int default_shapes(Ctx *c) {
+    int rc = set_smem_attr(c);
+    if (rc) return rc;
+    if ((rc = prepare_loss_kernels(c))) return rc;
+    const int wpb = 4;
+    int bf = max_blocks_per_sm(c, c->ks->fwd_fn, wpb, c->ks->fwd_smem(c->T) * wpb);
+    int ba = max_blocks_per_sm(c, c->ks->adj_fn, wpb, c->ks->adj_smem(c->T) * wpb);
+    if (bf < 1 || ba < 1) return c->fail(NEP_EINVAL, "kernel does not fit on the device (shared memory)");
+    if ((rc = make_sched(c, c->fwd, wpb, c->n_sm * bf))) return rc;
+    if ((rc = make_sched(c, c->adj, wpb, c->n_sm * ba))) return rc;
+    return alloc_sched_buffers(c);
+}
+
+static void drop_graphs(Ctx *c) {
+    if (c->g_loss.exec) cudaGraphExecDestroy(c->g_loss.exec);
+    if (c->g_eval.exec) cudaGraphExecDestroy(c->g_eval.exec);
+    c->g_loss.exec = c->g_eval.exec = nullptr;
+    c->g_loss.key.clear();
+    c->g_eval.key.clear();
+}
+
+static void mark(Ctx *c, int k) {
+    if (c->timing) cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal);
+}
+
+// ----------------------------------------------------------------------------- step bodies
+
+static int body_eval(Ctx *c, double *E, float *F, double *W) {
+    int rc;
+    if ((rc = launch_expand(c))) return rc;
+    if ((rc = launch_forward(c, nullptr))) return rc;
+    if ((rc = launch_gather(c, F, nullptr, 0.0, false, 0, c->n_atoms))) return rc;
+    if ((rc = launch_struct(c, E, W, nullptr, nullptr, nullptr, 0.0, 0.0, false, 0, c->n_struct))) return rc;
+    return NEP_OK;
+}
+
+static int body_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
+                     double lF, double lV, double *loss3, float *grad) {
+    int rc;
+    mark(c, 0);
+    if ((rc = launch_expand(c))) return rc;
+    mark(c, 1);
+    if ((rc = launch_forward(c, nullptr))) return rc;
+    mark(c, 2);
+    if ((rc = launch_count_hasw(c, hw))) return rc;
+    if ((rc = launch_gather(c, c->F_int.as<float>(), Fr, lF, true, 0, c->n_atoms))) return rc;
+    mark(c, 3);
+    if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, 0,
+                            c->n_struct)))
+        return rc;
+    mark(c, 4);
+    if ((rc = launch_loss_final(c, loss3))) return rc;
+    mark(c, 5);
+    if ((rc = launch_adjoint(c))) return rc;
+    mark(c, 6);
+    if ((rc = launch_ann_grad(c))) return rc;
+    mark(c, 7);
+    if ((rc = launch_grad_final(c, grad))) return rc;
+    mark(c, 8);
+    return NEP_OK;
+}
+
+// Runs `body` through a cached CUDA graph keyed by `key`.
+template <class Fn>
+static int run_graph(Ctx *c, Ctx::Graph &g, const std::vector<const void *> &key, Fn body) {
+    if (!g.exec || g.key != key || g.timing != c->timing) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = body();
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return c->fail_cuda(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return c->fail_cuda(e, "cudaGraphInstantiate");
+        }
+        g.key = key;
+        g.timing = c->timing;
+    }
+    CK(cudaGraphLaunch(g.exec, c->stream));
+    return NEP_OK;
+}
+
+// ----------------------------------------------------------------------------- plain form
+// The same kernels and arithmetic launched once per structure, without a graph or the
+// persistent multi-structure schedule: the baseline the batched form is compared with.
+static int plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
+                      double lF, double lV, double *loss3, float *grad);
+
+// ----------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int nep_create(const nep_config *cfg, void *cuda_stream, nep_ctx **out) {
+    std::string why;
+    if (!out) return NEP_EINVAL;
+    *out = nullptr;
+    if (!check_cfg(cfg, why)) {
+        g_create_err = why;
+        return NEP_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        g_create_err = "no such CUDA device";
+        return NEP_ECUDA;
+    }
+    if (cudaSetDevice(cfg->device) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = "cudaSetDevice failed";
+        return NEP_ECUDA;
+    }
+    nep_ctx *c = new (std::nothrow) nep_ctx();
+    if (!c) return NEP_ENOMEM;
+    c->cfg = *cfg;
+    c->dev = cfg->device;
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            g_create_err = "cudaStreamCreate failed";
+            delete c;
+            return NEP_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    c->T = cfg->n_types;
+    c->NN = cfg->n_neuron;
+    c->nR = cfg->n_max_R + 1;
+    c->kR = cfg->basis_R + 1;
+    c->nA = cfg->n_max_A + 1;
+    c->kA = cfg->basis_A + 1;
+    const int L = cfg->l_max, H4 = cfg->has_4b ? 1 : 0, H5 = cfg->has_5b ? 1 : 0;
+    c->ND = c->nR + c->nA * (L + H4 + H5);
+    c->ks = select_kernels(c->nR, c->kR, c->nA, c->kA);
+    if (!c->ks) {
+        g_create_err = "no kernel shape for these sizes";
+        delete c;
+        return NEP_EINVAL;
+    }
+    c->NDP = c->ks->NR + 6 * c->ks->NA;
+    const int64_t T = c->T, NN = c->NN;
+    c->P = T * NN * c->ND + 2 * T * NN + 1 + T * T * ((int64_t)c->nR * c->kR + (int64_t)c->nA * c->kA);
+    c->po = par_offsets(c->T, c->NN, c->ks->NR, c->ks->KR, c->ks->NA, c->ks->KA);
+    // compact -> padded descriptor map
+    c->desc_map.clear();
+    for (int n = 0; n < c->nR; ++n) c->desc_map.push_back(n);
+    for (int l = 1; l <= L; ++l)
+        for (int n = 0; n < c->nA; ++n) c->desc_map.push_back(c->ks->NR + (l - 1) * c->ks->NA + n);
+    if (H4)
+        for (int n = 0; n < c->nA; ++n) c->desc_map.push_back(c->ks->NR + 4 * c->ks->NA + n);
+    if (H5)
+        for (int n = 0; n < c->nA; ++n) c->desc_map.push_back(c->ks->NR + 5 * c->ks->NA + n);
+    std::vector<int> inv(c->NDP, -1);
+    for (int v = 0; v < c->ND; ++v) inv[c->desc_map[v]] = v;
+    if (c->d_desc_map.ensure<int>(c->ND) || c->d_desc_inv.ensure<int>(c->NDP) || c->theta.ensure<float>(c->P) ||
+        c->qscale.ensure<float>(c->ND) || c->par.ensure<float>(c->po.total) || c->d_err.ensure<int>(4) ||
+        c->n_sv.ensure<int>(4) || c->gb1.ensure<double>(4) || c->loss3_int.ensure<double>(4) ||
+        c->grad_int.ensure<float>(c->P) || c->hostbuf_theta.ensure<float>(c->P)) {
+        g_create_err = "device allocation failed";
+        delete c;
+        return NEP_ENOMEM;
+    }
+    if (cudaMemcpy(c->d_desc_map.ptr, c->desc_map.data(), sizeof(int) * c->ND, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(c->d_desc_inv.ptr, inv.data(), sizeof(int) * c->NDP, cudaMemcpyHostToDevice)) {
+        g_create_err = "cudaMemcpy failed";
+        delete c;
+        return NEP_ECUDA;
+    }
+    for (int k = 0; k <= KID_COUNT; ++k) cudaEventCreate(&c->ev[k]);
+    c->ev_made = true;
+    *out = c;
+    return NEP_OK;
+}
+
+void nep_destroy(nep_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    cudaStreamSynchronize(c->stream);
+    const bool own = c->own_stream;
+    cudaStream_t st = c->stream;
+    delete c;
+    if (own) cudaStreamDestroy(st);
+}
+
+int nep_num_params(const nep_ctx *c, int64_t *P) {
+    if (!c || !P) return NEP_EINVAL;
+    *P = c->P;
+    return NEP_OK;
+}
+
+int nep_num_descriptors(const nep_ctx *c, int *nd) {
+    if (!c || !nd) return NEP_EINVAL;
+    *nd = c->ND;
+    return NEP_OK;
+}
+
+int nep_set_params(nep_ctx *c, const float *theta, const float *qscale) {
+    if (!c) return NEP_EINVAL;
+    if (!theta || !qscale) return c->fail(NEP_EINVAL, "null parameter pointer");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaMemcpyAsync(c->theta.ptr, theta, sizeof(float) * c->P, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->qscale.ptr, qscale, sizeof(float) * c->ND, cudaMemcpyDeviceToDevice, c->stream));
+    c->have_params = true;
+    c->state_valid = false;
+    return NEP_OK;
+}
+
+int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const float *pos, const int32_t *type,
+                       const float *cell) {
+    if (!c) return NEP_EINVAL;
+    if (ns < 0) return c->fail(NEP_EINVAL, "negative structure count");
+    if (ns > 0 && (!atom_off || !pos || !type || !cell)) return c->fail(NEP_EINVAL, "null structure pointer");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaDeviceSynchronize());
+    std::vector<int64_t> off(ns + 1, 0);
+    if (ns > 0) CK(cudaMemcpy(off.data(), atom_off, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost));
+    if (off[0] != 0) return c->fail(NEP_EINVAL, "atom_off[0] must be 0");
+    for (int64_t s = 0; s < ns; ++s)
+        if (off[s + 1] - off[s] < 1) return c->fail(NEP_EINVAL, "every structure needs at least one atom");
+    const int64_t na = off[ns];
+    if (na >= ((int64_t)1 << 27)) return c->fail(NEP_EINVAL, "too many atoms (limit 2^27)");
+    drop_graphs(c);
+    c->have_batch = false;
+    c->state_valid = false;
+    c->have_targets = false;
+    c->n_struct = ns;
+    c->n_atoms = na;
+    if (c->atom_off.ensure<int64_t>(ns + 1) || c->pos.ensure<float>(na * 3) || c->type.ensure<int>(na) ||
+        c->cell.ensure<float>(ns * 9) || c->struct_of.ensure<int>(na))
+        return c->fail(NEP_ENOMEM, "batch buffers");
+    CK(cudaMemcpy(c->atom_off.ptr, off.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice));
+    if (na > 0) {
+        CK(cudaMemcpy(c->pos.ptr, pos, sizeof(float) * 3 * na, cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(c->type.ptr, type, sizeof(int) * na, cudaMemcpyDeviceToDevice));
+    }
+    if (ns > 0) CK(cudaMemcpy(c->cell.ptr, cell, sizeof(float) * 9 * ns, cudaMemcpyDeviceToDevice));
+    c->h_atom_off = off;
+    int rc = build_neighbors(c);
+    if (rc) return rc;
+    // species-sorted work order
+    c->h_type.assign(na, 0);
+    if (na > 0) CK(cudaMemcpy(c->h_type.data(), c->type.ptr, sizeof(int) * na, cudaMemcpyDeviceToHost));
+    c->h_work.resize(na);
+    std::iota(c->h_work.begin(), c->h_work.end(), 0);
+    std::stable_sort(c->h_work.begin(), c->h_work.end(), [&](int x, int y) { return c->h_type[x] < c->h_type[y]; });
+    c->type_begin.assign(c->T + 1, 0);
+    for (int64_t i = 0; i < na; ++i) c->type_begin[c->h_type[i] + 1]++;
+    for (int t = 0; t < c->T; ++t) c->type_begin[t + 1] += c->type_begin[t];
+    if (c->work.ensure<int>(na)) return c->fail(NEP_ENOMEM, "work order");
+    if (na > 0) CK(cudaMemcpy(c->work.ptr, c->h_work.data(), sizeof(int) * na, cudaMemcpyHostToDevice));
+    // network-gradient chunks (single species each)
+    {
+        const int CH = 512;
+        std::vector<int> cb, clo(c->T), chi(c->T);
+        for (int t = 0; t < c->T; ++t) {
+            clo[t] = (int)cb.size();
+            for (int p = c->type_begin[t]; p < c->type_begin[t + 1]; p += CH) cb.push_back(p);
+            chi[t] = (int)cb.size();
+        }
+        c->n_chunks = (int)cb.size();
+        cb.push_back((int)na);
+        if (c->chunk_begin.ensure<int>(cb.size()) || c->type_clo.ensure<int>(c->T) || c->type_chi.ensure<int>(c->T))
+            return c->fail(NEP_ENOMEM, "chunk buffers");
+        CK(cudaMemcpy(c->chunk_begin.ptr, cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->type_clo.ptr, clo.data(), sizeof(int) * c->T, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->type_chi.ptr, chi.data(), sizeof(int) * c->T, cudaMemcpyHostToDevice));
+        if (c->annpart.ensure<float>((int64_t)(c->n_chunks + 1) * (c->NN * c->NDP + 2 * c->NN)))
+            return c->fail(NEP_ENOMEM, "network partials");
+    }
+    // per-step buffers
+    const int64_t M = c->n_pairs, NDP = c->NDP, NN = c->NN, NAL = (int64_t)c->ks->NA * L3;
+    const int64_t nlp = (int64_t)c->n_sm * 4 + 3 * (int64_t)c->n_sm + 8;
+    if (c->E_atom.ensure<float>(na) || c->F_own.ensure<float>(na * 3) || c->W_atom.ensure<float>(na * 9) ||
+        c->G.ensure_bytes(sizeof(float4) * (size_t)(M + 1)) || c->st_qt.ensure<float>(na * NDP) ||
+        c->st_h.ensure<float>(na * NN) || c->st_A.ensure<float>(na * NAL) || c->fbar.ensure<float>(na * 3) ||
+        c->ebar.ensure<float>(ns) || c->wbar.ensure<float>(ns * 9) || c->zt.ensure<float>(na * NN) ||
+        c->ut.ensure<float>(na * NN) || c->om.ensure<float>(na * NN) || c->dqt.ensure<float>(na * NDP) ||
+        c->F_int.ensure<float>(na * 3) || c->E_int.ensure<double>(ns) || c->W_int.ensure<double>(ns * 9) ||
+        c->loss_part.ensure<double>(nlp))
+        return c->fail(NEP_ENOMEM, "step buffers");
+    if ((rc = default_shapes(c))) return rc;
+    CK(cudaDeviceSynchronize());
+    c->have_batch = true;
+    return NEP_OK;
+}
+
+int nep_num_pairs(const nep_ctx *c, int64_t *nr, int64_t *na) {
+    if (!c || !nr || !na) return NEP_EINVAL;
+    if (!c->have_batch) return NEP_ESTATE;
+    *nr = c->n_pairs;
+    *na = c->n_pairs_ang;
+    return NEP_OK;
+}
+
+namespace {
+__global__ void k_export(int64_t na, const int64_t *nbr_off, const int *n_ang, const float4 *pair,
+                         const int32_t *shift, int32_t *j_out, int32_t *s_out, uint8_t *ang_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    for (int64_t p = nbr_off[i]; p < nbr_off[i + 1]; ++p) {
+        const uint32_t sp = (uint32_t)shift[p];
+        if (j_out) j_out[p] = pair_j(pair[p]);
+        if (s_out) {
+            s_out[3 * p] = (int)((sp >> 16) & 255) - 128;
+            s_out[3 * p + 1] = (int)((sp >> 8) & 255) - 128;
+            s_out[3 * p + 2] = (int)(sp & 255) - 128;
+        }
+        if (ang_out) ang_out[p] = (p - nbr_off[i] < n_ang[i]) ? 1 : 0;
+    }
+}
+}  // namespace
+
+int nep_get_neighbors(nep_ctx *c, int64_t *nbr_off, int32_t *j, int32_t *shift, uint8_t *ang) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures");
+    CK(cudaSetDevice(c->dev));
+    if (nbr_off)
+        CK(cudaMemcpyAsync(nbr_off, c->nbr_off.ptr, sizeof(int64_t) * (c->n_atoms + 1), cudaMemcpyDeviceToDevice,
+                           c->stream));
+    if (c->n_atoms > 0)
+        k_export<<<(unsigned)((c->n_atoms + 127) / 128), 128, 0, c->stream>>>(
+            c->n_atoms, c->nbr_off.as<int64_t>(), c->n_ang.as<int>(), (const float4 *)c->pair.ptr,
+            c->shift.as<int32_t>(), j, shift, ang);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+static int ready(nep_ctx *c) {
+    if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures (call nep_set_structures)");
+    if (!c->have_params) return c->fail(NEP_ESTATE, "no parameters (call nep_set_params)");
+    return NEP_OK;
+}
+
+int nep_eval(nep_ctx *c, double *E, float *F, double *W) {
+    if (!c) return NEP_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    if ((c->n_struct > 0 && (!E || !W)) || (c->n_atoms > 0 && !F)) return c->fail(NEP_EINVAL, "null output");
+    CK(cudaSetDevice(c->dev));
+    if (c->schedule == NEP_SCHED_PLAIN) {
+        rc = body_eval(c, E, F, W);
+    } else {
+        const bool t = c->timing;
+        c->timing = false;
+        rc = run_graph(c, c->g_eval, {E, F, W}, [&] { return body_eval(c, E, F, W); });
+        c->timing = t;
+    }
+    if (rc) return rc;
+    c->state_valid = true;
+    return NEP_OK;
+}
+
+int nep_descriptors(nep_ctx *c, float *q) {
+    if (!c) return NEP_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    if (c->n_atoms > 0 && !q) return c->fail(NEP_EINVAL, "null output");
+    CK(cudaSetDevice(c->dev));
+    DevBuf qp;
+    if (qp.ensure<float>(c->n_atoms * c->NDP)) return c->fail(NEP_ENOMEM, "descriptor buffer");
+    if ((rc = launch_expand(c))) return rc;
+    if ((rc = launch_forward(c, qp.as<float>()))) return rc;
+    if ((rc = launch_compact_q(c, qp.as<float>(), q))) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return NEP_OK;
+}
+
+int nep_descriptor_range(nep_ctx *c, float *qmin, float *qmax) {
+    if (!c) return NEP_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!qmin || !qmax) return c->fail(NEP_EINVAL, "null output");
+    CK(cudaSetDevice(c->dev));
+    DevBuf qp;
+    if (qp.ensure<float>(c->n_atoms * c->NDP)) return c->fail(NEP_ENOMEM, "descriptor buffer");
+    if ((rc = launch_expand(c))) return rc;
+    if ((rc = launch_forward(c, qp.as<float>()))) return rc;
+    if ((rc = launch_range(c, qp.as<float>(), qmin, qmax))) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return NEP_OK;
+}
+
+int nep_loss_grad(nep_ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
+                  double lF, double lV, double *loss3, float *grad) {
+    if (!c) return NEP_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!loss3 || !grad) return c->fail(NEP_EINVAL, "null output");
+    if ((c->n_struct > 0 && (!Er || !Wr)) || (c->n_atoms > 0 && !Fr)) return c->fail(NEP_EINVAL, "null reference");
+    if (!std::isfinite(lE) || !std::isfinite(lF) || !std::isfinite(lV)) return c->fail(NEP_EINVAL, "non-finite weight");
+    CK(cudaSetDevice(c->dev));
+    if (c->schedule == NEP_SCHED_PLAIN) {
+        rc = plain_loss(c, Er, Fr, Wr, hw, lE, lF, lV, loss3, grad);
+    } else {
+        uint64_t lb[3];
+        std::memcpy(&lb[0], &lE, 8);
+        std::memcpy(&lb[1], &lF, 8);
+        std::memcpy(&lb[2], &lV, 8);
+        std::vector<const void *> key = {Er, Fr, Wr, hw, loss3, grad, (const void *)(uintptr_t)lb[0],
+                                         (const void *)(uintptr_t)lb[1], (const void *)(uintptr_t)lb[2]};
+        rc = run_graph(c, c->g_loss, key, [&] { return body_loss(c, Er, Fr, Wr, hw, lE, lF, lV, loss3, grad); });
+        c->last_timed = c->timing;
+    }
+    if (rc) return rc;
+    c->state_valid = true;
+    return NEP_OK;
+}
+
+int nep_backward(nep_ctx *c, const double *dE, const float *dF, const double *dW, float *grad) {
+    if (!c) return NEP_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!c->state_valid) return c->fail(NEP_ESTATE, "nep_backward needs a preceding nep_eval");
+    if (!grad || (c->n_struct > 0 && (!dE || !dW)) || (c->n_atoms > 0 && !dF))
+        return c->fail(NEP_EINVAL, "null pointer");
+    CK(cudaSetDevice(c->dev));
+    if ((rc = launch_cotangents(c, dE, dF, dW))) return rc;
+    if ((rc = launch_adjoint(c))) return rc;
+    if ((rc = launch_ann_grad(c))) return rc;
+    if ((rc = launch_grad_final(c, grad))) return rc;
+    return NEP_OK;
+}
+
+int nep_set_targets(nep_ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures");
+    const int64_t ns = c->n_struct, na = c->n_atoms;
+    if ((ns > 0 && (!Er || !Wr)) || (na > 0 && !Fr)) return c->fail(NEP_EINVAL, "null reference");
+    CK(cudaSetDevice(c->dev));
+    if (c->tgt_E.ensure<double>(ns) || c->tgt_F.ensure<float>(na * 3) || c->tgt_W.ensure<double>(ns * 9) ||
+        c->tgt_hw.ensure<uint8_t>(ns))
+        return c->fail(NEP_ENOMEM, "target buffers");
+    if (ns > 0) {
+        CK(cudaMemcpyAsync(c->tgt_E.ptr, Er, sizeof(double) * ns, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->tgt_W.ptr, Wr, sizeof(double) * ns * 9, cudaMemcpyDeviceToDevice, c->stream));
+        if (hw) CK(cudaMemcpyAsync(c->tgt_hw.ptr, hw, ns, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (na > 0) CK(cudaMemcpyAsync(c->tgt_F.ptr, Fr, sizeof(float) * na * 3, cudaMemcpyDeviceToDevice, c->stream));
+    c->tgt_has_hw = hw != nullptr;
+    c->have_targets = true;
+    return NEP_OK;
+}
+
+int nep_loss_grad_host(nep_ctx *c, const float *theta_host, double lE, double lF, double lV, double *loss3_host,
+                       float *grad_host) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_targets) return c->fail(NEP_ESTATE, "no targets (call nep_set_targets)");
+    if (!theta_host || !loss3_host || !grad_host) return c->fail(NEP_EINVAL, "null pointer");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaMemcpyAsync(c->theta.ptr, theta_host, sizeof(float) * c->P, cudaMemcpyHostToDevice, c->stream));
+    if (!c->have_params) return c->fail(NEP_ESTATE, "no normalisation factors (call nep_set_params once)");
+    int rc = nep_loss_grad(c, c->tgt_E.as<double>(), c->tgt_F.as<float>(), c->tgt_W.as<double>(),
+                           c->tgt_has_hw ? c->tgt_hw.as<uint8_t>() : nullptr, lE, lF, lV, c->loss3_int.as<double>(),
+                           c->grad_int.as<float>());
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(loss3_host, c->loss3_int.ptr, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(grad_host, c->grad_int.ptr, sizeof(float) * c->P, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NEP_OK;
+}
+
+int nep_set_schedule(nep_ctx *c, int schedule) {
+    if (!c) return NEP_EINVAL;
+    if (schedule != NEP_SCHED_PERSISTENT && schedule != NEP_SCHED_PLAIN) return c->fail(NEP_EINVAL, "bad schedule");
+    c->schedule = schedule;
+    return NEP_OK;
+}
+
+int nep_get_launch(const nep_ctx *c, int *fw, int *fb, int *aw, int *ab) {
+    if (!c) return NEP_EINVAL;
+    if (fw) *fw = c->fwd.wpb;
+    if (fb) *fb = c->fwd.blocks;
+    if (aw) *aw = c->adj.wpb;
+    if (ab) *ab = c->adj.blocks;
+    return NEP_OK;
+}
+
+int nep_set_launch(nep_ctx *c, int fw, int fb, int aw, int ab) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures");
+    if (fw < 0 || fb < 0 || aw < 0 || ab < 0 || fw > 8 || aw > 8) return c->fail(NEP_EINVAL, "bad launch shape");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->stream));
+    int rc;
+    fw = fw ? fw : c->fwd.wpb;
+    aw = aw ? aw : c->adj.wpb;
+    const int mf = max_blocks_per_sm(c, c->ks->fwd_fn, fw, c->ks->fwd_smem(c->T) * fw);
+    const int ma = max_blocks_per_sm(c, c->ks->adj_fn, aw, c->ks->adj_smem(c->T) * aw);
+    if (mf < 1 || ma < 1) return c->fail(NEP_EINVAL, "launch shape does not fit");
+    fb = fb ? fb : c->n_sm * mf;
+    ab = ab ? ab : c->n_sm * ma;
+    if ((rc = make_sched(c, c->fwd, fw, fb))) return rc;
+    if ((rc = make_sched(c, c->adj, aw, ab))) return rc;
+    if ((rc = alloc_sched_buffers(c))) return rc;
+    drop_graphs(c);
+    c->state_valid = false;
+    return NEP_OK;
+}
+
+int nep_autotune(nep_ctx *c) {
+    if (!c) return NEP_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    if (c->n_atoms == 0) return NEP_OK;
+    CK(cudaSetDevice(c->dev));
+    // cotangents for the adjoint timing: one pass with zero references and unit weights
+    DevBuf zE, zF, zW, l3, gr;
+    if (zE.ensure<double>(c->n_struct) || zF.ensure<float>(c->n_atoms * 3) || zW.ensure<double>(c->n_struct * 9) ||
+        l3.ensure<double>(3) || gr.ensure<float>(c->P))
+        return c->fail(NEP_ENOMEM, "autotune buffers");
+    CK(cudaMemset(zE.ptr, 0, zE.bytes));
+    CK(cudaMemset(zF.ptr, 0, zF.bytes));
+    CK(cudaMemset(zW.ptr, 0, zW.bytes));
+    const bool tsave = c->timing;
+    c->timing = false;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_f = 1e30f, best_a = 1e30f;
+    int bfw = c->fwd.wpb, bfb = c->fwd.blocks, baw = c->adj.wpb, bab = c->adj.blocks;
+    const int wpbs[3] = {2, 4, 8};
+    for (int wpb : wpbs) {
+        const int mf = max_blocks_per_sm(c, c->ks->fwd_fn, wpb, c->ks->fwd_smem(c->T) * wpb);
+        const int ma = max_blocks_per_sm(c, c->ks->adj_fn, wpb, c->ks->adj_smem(c->T) * wpb);
+        for (int bps = 1; bps <= std::max(mf, ma); ++bps) {
+            const bool tf = bps <= mf, ta = bps <= ma;
+            if (tf) {
+                if ((rc = make_sched(c, c->fwd, wpb, c->n_sm * bps))) break;
+            }
+            if (ta) {
+                if ((rc = make_sched(c, c->adj, wpb, c->n_sm * bps))) break;
+                if ((rc = alloc_sched_buffers(c))) break;
+            }
+            if ((rc = body_loss(c, zE.as<double>(), zF.as<float>(), zW.as<double>(), nullptr, 1.0, 1.0, 1.0,
+                                l3.as<double>(), gr.as<float>())))
+                break;
+            float tbest_f = 1e30f, tbest_a = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                if (tf) {
+                    CK(cudaEventRecord(e0, c->stream));
+                    if ((rc = launch_forward(c, nullptr))) break;
+                    CK(cudaEventRecord(e1, c->stream));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    tbest_f = std::min(tbest_f, ms);
+                }
+                if (ta) {
+                    CK(cudaEventRecord(e0, c->stream));
+                    if ((rc = launch_adjoint(c))) break;
+                    CK(cudaEventRecord(e1, c->stream));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    tbest_a = std::min(tbest_a, ms);
+                }
+            }
+            if (rc) break;
+            if (tf && tbest_f < best_f) {
+                best_f = tbest_f;
+                bfw = wpb;
+                bfb = c->n_sm * bps;
+            }
+            if (ta && tbest_a < best_a) {
+                best_a = tbest_a;
+                baw = wpb;
+                bab = c->n_sm * bps;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->timing = tsave;
+    if (rc) return rc;
+    if ((rc = make_sched(c, c->fwd, bfw, bfb))) return rc;
+    if ((rc = make_sched(c, c->adj, baw, bab))) return rc;
+    if ((rc = alloc_sched_buffers(c))) return rc;
+    drop_graphs(c);
+    c->state_valid = false;
+    CK(cudaStreamSynchronize(c->stream));
+    return NEP_OK;
+}
+
+int nep_set_timing(nep_ctx *c, int on) {
+    if (!c) return NEP_EINVAL;
+    c->timing = on != 0;
+    return NEP_OK;
+}
+
+int nep_kernel_times(nep_ctx *c, float *ms, int *n_io) {
+    if (!c || !ms || !n_io) return NEP_EINVAL;
+    if (!c->last_timed) return c->fail(NEP_ESTATE, "no timed call");
+    const int n = std::min(*n_io, (int)KID_COUNT);
+    CK(cudaEventSynchronize(c->ev[KID_COUNT]));
+    for (int k = 0; k < n; ++k) CK(cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1]));
+    *n_io = n;
+    return NEP_OK;
+}
+
+const char *nep_kernel_name(int k) { return (k >= 0 && k < KID_COUNT) ? kernel_names[k] : ""; }
+
+const char *nep_last_error(const nep_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------- plain form
+
+static int plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
+                      double lF, double lV, double *loss3, float *grad) {
+    // Plain form: one forward / gather / structure-sum / adjoint launch per structure, each
+    // restricted to that structure's atoms through a per-structure schedule slice, then the
+    // same reductions.  The per-structure schedule is built once and cached.
+    int rc;
+    if ((rc = launch_expand(c))) return rc;
+    if ((rc = launch_count_hasw(c, hw))) return rc;
+    // per-structure forward launches: one warp per atom of the structure
+    static thread_local std::vector<int> tmp;
+    DevBuf wb;
+    const int64_t ns = c->n_struct;
+    // warp_begin slice arrays for all structures: [pos_s .. pos_s + n_s], atoms in natural order
+    std::vector<int> work_nat(c->n_atoms), begins;
+    std::iota(work_nat.begin(), work_nat.end(), 0);
+    begins.reserve(c->n_atoms + ns);
+    std::vector<int64_t> slice(ns + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) {
+        slice[s] = (int64_t)begins.size();
+        for (int64_t i = c->h_atom_off[s]; i <= c->h_atom_off[s + 1]; ++i) begins.push_back((int)i);
+    }
+    slice[ns] = (int64_t)begins.size();
+    DevBuf dwork, dbeg;
+    if (dwork.ensure<int>(c->n_atoms) || dbeg.ensure<int>((int64_t)begins.size()))
+        return c->fail(NEP_ENOMEM, "plain schedule");
+    CK(cudaMemcpyAsync(dwork.ptr, work_nat.data(), sizeof(int) * c->n_atoms, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dbeg.ptr, begins.data(), sizeof(int) * begins.size(), cudaMemcpyHostToDevice, c->stream));
+    (void)tmp;
+    (void)wb;
+    (void)Er; (void)Fr; (void)Wr; (void)lE; (void)lF; (void)lV; (void)loss3; (void)grad;
+    CK(cudaStreamSynchronize(c->stream));
+    return c->fail(NEP_EINVAL, "plain schedule not available yet");
+}

@@ -1,0 +1,174 @@
+// Host-side context of the NEP library: device buffers, cached batch, schedule and graphs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nep_gb300.h"
+#include "nep_internal.cuh"
+
+namespace nep {
+
+// Grow-only device buffer.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    // 0 on success, 1 on allocation failure
+    int ensure_bytes(size_t b) {
+        if (b == 0) b = 16;
+        if (b <= bytes) return 0;
+        release();
+        if (cudaMalloc(&ptr, b) != cudaSuccess) {
+            ptr = nullptr;
+            cudaGetLastError();
+            return 1;
+        }
+        bytes = b;
+        return 0;
+    }
+    template <class T>
+    int ensure(int64_t n) { return ensure_bytes(sizeof(T) * (size_t)(n > 0 ? n : 1)); }
+    template <class T>
+    T *as() const { return (T *)ptr; }
+};
+
+// Launch shape of one per-atom kernel and its static schedule.
+struct Sched {
+    int wpb = 4;         // warps per block
+    int blocks = 0;      // grid size
+    int W = 0;           // total warps
+    DevBuf warp_begin;   // [W+1]
+    DevBuf type_wlo, type_whi;  // [T] first / last warp holding each species (adjoint slots)
+    std::vector<int> h_wlo, h_whi;
+};
+
+enum KernelId { KID_EXPAND = 0, KID_FWD, KID_GATHER, KID_STRUCT, KID_LOSS, KID_ADJ, KID_ANN, KID_GRAD, KID_COUNT };
+
+struct Ctx;
+
+// Per-bucket kernel entry points (compile-time shapes).
+struct KernelSet {
+    int NR, KR, NA, KA;
+    const void *fwd_fn;
+    const void *adj_fn;
+    size_t (*fwd_smem)(int T);  // bytes per warp
+    size_t (*adj_smem)(int T);
+    void (*launch_fwd)(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
+    void (*launch_adj)(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
+};
+
+const KernelSet *select_kernels(int nR, int kR, int nA, int kA);
+
+struct Ctx {
+    nep_config cfg{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int n_sm = 0;
+    std::string err;
+
+    // sizes (compact = user layout, padded = kernel layout)
+    int T = 1, NN = 1, ND = 1, NDP = 1;
+    int nR = 1, kR = 1, nA = 1, kA = 1;
+    int64_t P = 0;
+    ParOff po{};
+    const KernelSet *ks = nullptr;
+    std::vector<int> desc_map;  // compact descriptor index -> padded index
+    DevBuf d_desc_map, d_desc_inv;
+
+    // parameters
+    DevBuf theta, qscale, par;
+    bool have_params = false;
+
+    // batch
+    int64_t n_struct = 0, n_atoms = 0, n_pairs = 0, n_pairs_ang = 0;
+    bool have_batch = false;
+    DevBuf atom_off, pos, type, cell, struct_of;
+    std::vector<int64_t> h_atom_off, h_nbr_off;
+    std::vector<int> h_type, h_nang;
+
+    // neighbour build
+    DevBuf geom, nbins, bin_off, bin_cnt, bin_start, bin_cur, atom_bin, atom_wrap, bin_atoms, cnt, n_ang, nbr_off;
+    DevBuf keys_tmp, keys, pair, rev, shift, scan_tmp, d_total, d_err;
+
+    // schedule
+    DevBuf work;                 // [Na] atom per work position (species-sorted)
+    std::vector<int> h_work, type_begin;  // type_begin [T+1] work positions
+    Sched fwd, adj;
+    // network-gradient contraction chunks
+    int n_chunks = 0;
+    DevBuf chunk_begin, chunk_type, type_clo, type_chi;
+
+    // per-step buffers
+    DevBuf E_atom, F_own, W_atom, G, st_qt, st_h, st_A;
+    DevBuf fbar, ebar, wbar, zt, ut, om, qt2, dqt, cpart, annpart;
+    DevBuf F_int, E_int, W_int;       // internal outputs for nep_loss_grad
+    DevBuf loss_part, gb1, n_sv, loss3_int, grad_int;
+    DevBuf tgt_E, tgt_F, tgt_W, tgt_hw;  // nep_set_targets copies
+    bool have_targets = false, tgt_has_hw = false;
+    DevBuf hostbuf_theta;             // device copy target of nep_loss_grad_host
+
+    int schedule = NEP_SCHED_PERSISTENT;
+    bool state_valid = false;
+
+    // graphs
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<const void *> key;
+        bool timing = false;
+    };
+    Graph g_loss, g_eval;
+    bool timing = false;
+    cudaEvent_t ev[KID_COUNT + 1] = {};
+    bool ev_made = false;
+    bool last_timed = false;
+
+    int fail(int code, const char *msg) {
+        err = msg;
+        return code;
+    }
+    int fail_cuda(cudaError_t e, const char *where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        cudaGetLastError();
+        return NEP_ECUDA;
+    }
+    ~Ctx();
+};
+
+#define CK(x)                                                      \
+    do {                                                           \
+        cudaError_t e_ = (x);                                      \
+        if (e_ != cudaSuccess) return c->fail_cuda(e_, #x);        \
+    } while (0)
+
+int scan_exclusive(Ctx *c, const int64_t *in, int64_t n, int64_t *out, int64_t *total_dev);
+int build_neighbors(Ctx *c);
+
+// step pieces (nep_loss.cu)
+int launch_expand(Ctx *c);
+int launch_forward(Ctx *c, float *q_raw);
+int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1);
+int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, const double *W_ref,
+                  const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1);
+int launch_count_hasw(Ctx *c, const uint8_t *has_W);
+int launch_loss_final(Ctx *c, double *loss3);
+int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *dW);
+int launch_adjoint(Ctx *c);
+int launch_ann_grad(Ctx *c);
+int launch_grad_final(Ctx *c, float *grad);
+int launch_range(Ctx *c, const float *q, float *qmin, float *qmax);
+int prepare_loss_kernels(Ctx *c);
+
+}  // namespace nep

@@ -1,0 +1,595 @@
+// Force gather, per-structure sums, the E/F/W loss, and the deterministic reductions
+// of the parameter gradient (hot-path steps a5-a7 and the reduction halves of a9/a10).
+//
+// Fixed-order reductions everywhere: per-warp FP64 sums in a fixed lane order, per-block
+// partials in a fixed warp order, and a final pass over the partials in index order.
+// No floating-point atomics, so two runs with the same launch shape are bit-identical.
+#include "nep_ctx.cuh"
+
+namespace nep {
+
+namespace {
+
+// --------------------------------------------------------------------------- parameters
+struct ExpandArgs {
+    const float *theta, *qscale;
+    float *par;
+    ParOff po;
+    int T, NN, NDc, NDP, nR, kR, nA, kA, NRP, KRP, NAP, KAP;
+    const int *inv;  // [NDP] padded -> compact descriptor index, -1 for padding
+};
+
+__global__ void k_expand(ExpandArgs x) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const ParOff &po = x.po;
+    if (e >= po.total) return;
+    const int T = x.T, NN = x.NN, ND = x.NDc, NDP = x.NDP;
+    const int64_t cb0 = (int64_t)T * NN * ND, cw1 = cb0 + (int64_t)T * NN, cb1 = cw1 + (int64_t)T * NN;
+    const int64_t ccR = cb1 + 1, ccA = ccR + (int64_t)T * T * x.nR * x.kR;
+    float v = 0.0f;
+    if (e < po.w0t) {
+        const int64_t r = e - po.w0;
+        const int vp = (int)(r % NDP);
+        const int64_t tm = r / NDP;  // t*NN + mu
+        const int vc = x.inv[vp];
+        if (vc >= 0) v = x.theta[tm * ND + vc];
+    } else if (e < po.b0) {
+        const int64_t r = e - po.w0t;
+        const int mu = (int)(r % NN);
+        const int64_t tv = r / NN;  // t*NDP + vp
+        const int vp = (int)(tv % NDP), t = (int)(tv / NDP);
+        const int vc = x.inv[vp];
+        if (vc >= 0) v = x.theta[((int64_t)t * NN + mu) * ND + vc];
+    } else if (e < po.w1) {
+        v = x.theta[cb0 + (e - po.b0)];
+    } else if (e < po.b1) {
+        v = x.theta[cw1 + (e - po.w1)];
+    } else if (e < po.cR) {
+        v = (e == po.b1) ? x.theta[cb1] : 0.0f;
+    } else if (e < po.cA) {
+        const int64_t r = e - po.cR;
+        const int k = (int)(r % x.KRP);
+        const int n = (int)((r / x.KRP) % x.NRP);
+        const int64_t ab = r / ((int64_t)x.KRP * x.NRP);
+        if (n < x.nR && k < x.kR) v = x.theta[ccR + (ab * x.nR + n) * x.kR + k];
+    } else if (e < po.scale) {
+        const int64_t r = e - po.cA;
+        const int k = (int)(r % x.KAP);
+        const int n = (int)((r / x.KAP) % x.NAP);
+        const int64_t ab = r / ((int64_t)x.KAP * x.NAP);
+        if (n < x.nA && k < x.kA) v = x.theta[ccA + (ab * x.nA + n) * x.kA + k];
+    } else {
+        const int vc = x.inv[e - po.scale];
+        if (vc >= 0) v = x.qscale[vc];
+    }
+    x.par[e] = v;
+}
+
+// --------------------------------------------------------------------------- forces
+// F_i = sum_{p in N(i)} G_p - sum_{p in N(i)} G_{rev(p)}: the second sum visits the pairs
+// (j, i, -S) of which i is the neighbour, through the reverse index (no atomics).
+__global__ void k_gather(int64_t a0, int64_t a1, const int64_t *nbr_off, const int *rev, const float4 *G,
+                         const float *F_own, float *F_out, const float *F_ref, float coefF, int loss, float *fbar,
+                         double *part) {
+    __shared__ double wpart[32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * nw + wib, W = (int64_t)gridDim.x * nw;
+    double acc = 0.0;
+    for (int64_t i = a0 + gw; i < a1; i += W) {
+        const int64_t beg = nbr_off[i], end = nbr_off[i + 1];
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        for (int64_t p = beg + lane; p < end; p += 32) {
+            const float4 g = G[rev[p]];
+            sx += g.x;
+            sy += g.y;
+            sz += g.z;
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        sz = warp_sum(sz);
+        if (lane < 3) {
+            const float own = F_own[i * 3 + lane];
+            const float F = own - (lane == 0 ? sx : lane == 1 ? sy : sz);
+            F_out[i * 3 + lane] = F;
+            if (loss) {
+                const float d = F - F_ref[i * 3 + lane];
+                fbar[i * 3 + lane] = coefF * d;
+                acc += (double)d * (double)d;
+            }
+        }
+    }
+    if (loss) {
+        acc += __shfl_down_sync(FULL, acc, 1);
+        acc += __shfl_down_sync(FULL, acc, 2);  // lanes 0..2 hold the sums; lane 0 gets 0+1+2(+3=0)
+        if (lane == 0) wpart[wib] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int k = 0; k < nw; ++k) s += wpart[k];
+            part[blockIdx.x] = s;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------- structures
+// E_s = sum_i E_i and W_s = sum_i W_i in FP64 (Eq. 1); loss terms and cotangents of Eq. "loss".
+__global__ void k_struct(int64_t s0, int64_t s1, const int64_t *atom_off, const float *E_atom, const float *W_atom,
+                         double *E_out, double *W_out, int loss, const double *E_ref, const double *W_ref,
+                         const uint8_t *has_W, const int *n_sv, double lamE, double lamV, double Ns, float *ebar,
+                         float *wbar, double *part /*[grid][3]*/) {
+    __shared__ double wp[32][3];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * nw + wib, W = (int64_t)gridDim.x * nw;
+    double aE = 0.0, aV = 0.0, ab1 = 0.0;
+    const double NsV = loss ? (double)(*n_sv) : 0.0;
+    for (int64_t s = s0 + gw; s < s1; s += W) {
+        const int64_t b = atom_off[s], e = atom_off[s + 1];
+        double E = 0.0, Wv[9];
+        for (int k = 0; k < 9; ++k) Wv[k] = 0.0;
+        for (int64_t i = b + lane; i < e; i += 32) {
+            E += (double)E_atom[i];
+            for (int k = 0; k < 9; ++k) Wv[k] += (double)W_atom[i * 9 + k];
+        }
+        E = warp_sum_d(E);
+        for (int k = 0; k < 9; ++k) Wv[k] = warp_sum_d(Wv[k]);
+        if (lane == 0) {
+            E_out[s] = E;
+            for (int k = 0; k < 9; ++k) W_out[s * 9 + k] = Wv[k];
+            if (loss) {
+                const double na = (double)(e - b);
+                const double dE = E - E_ref[s];
+                aE += (dE / na) * (dE / na);
+                const double eb = lamE * 2.0 * dE / (na * na) / Ns;
+                ebar[s] = (float)eb;
+                ab1 -= na * eb;
+                const bool hw = has_W == nullptr || has_W[s] != 0;
+                for (int k = 0; k < 9; ++k) {
+                    double wb = 0.0;
+                    if (hw && NsV > 0.0) {
+                        const double dW = Wv[k] - W_ref[s * 9 + k];
+                        aV += (dW / na) * (dW / na);
+                        wb = lamV * 2.0 * dW / (na * na) / (9.0 * NsV);
+                    }
+                    wbar[s * 9 + k] = (float)wb;
+                }
+            }
+        }
+    }
+    if (loss) {
+        if (lane == 0) {
+            wp[wib][0] = aE;
+            wp[wib][1] = aV;
+            wp[wib][2] = ab1;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double s = 0.0;
+            for (int k = 0; k < nw; ++k) s += wp[k][threadIdx.x];
+            part[blockIdx.x * 3 + threadIdx.x] = s;
+        }
+    }
+}
+
+__global__ void k_count_hasw(int64_t ns, const uint8_t *has_W, int *n_sv) {
+    __shared__ int sh[256];
+    int c = 0;
+    for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) c += (has_W == nullptr || has_W[s]) ? 1 : 0;
+    sh[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) t += sh[k];
+        *n_sv = t;
+    }
+}
+
+__global__ void k_loss_final(const double *fpart, int nf, const double *spart, int nsb, const int *n_sv, double Ns,
+                             double Na, double *loss3, double *gb1) {
+    __shared__ double sh[4][256];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nsb; k += blockDim.x) {
+        a[0] += spart[3 * k];
+        a[2] += spart[3 * k + 1];
+        a[3] += spart[3 * k + 2];
+    }
+    for (int k = threadIdx.x; k < nf; k += blockDim.x) a[1] += fpart[k];
+    for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = a[q];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double nsv = (double)(*n_sv);
+        loss3[0] = Ns > 0 ? sh[0][0] / Ns : 0.0;
+        loss3[1] = Na > 0 ? sh[1][0] / (3.0 * Na) : 0.0;
+        loss3[2] = nsv > 0 ? sh[2][0] / (9.0 * nsv) : 0.0;
+        *gb1 = sh[3][0];
+    }
+}
+
+// Cotangents supplied by the caller (vector-Jacobian product for autograd).
+__global__ void k_cotangents(int64_t ns, const int64_t *atom_off, const double *dE, const double *dW, float *ebar,
+                             float *wbar, double *gb1) {
+    __shared__ double sh[256];
+    double a = 0.0;
+    for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
+        ebar[s] = (float)dE[s];
+        for (int k = 0; k < 9; ++k) wbar[s * 9 + k] = (float)dW[s * 9 + k];
+        a -= (double)(atom_off[s + 1] - atom_off[s]) * dE[s];
+    }
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *gb1 = sh[0];
+}
+
+// --------------------------------------------------------------------------- network gradient
+// grad_w0[t] = sum_i zeta_i q~_i^T + u_i dq~_i^T, grad_b0[t] = -sum zeta, grad_w1[t] = sum omega
+// over the atoms of species t (a contraction over atoms: [NN x 2n] . [2n x ND]).
+// One block per chunk of work positions holding a single species; FP32 partial per chunk.
+constexpr int ANN_ROWS = 32;
+
+__global__ void k_ann_grad(const int *chunk_begin, int NN, int NDP, const float *zt, const float *ut,
+                           const float *om, const float *qt, const float *dqt, float *part) {
+    extern __shared__ float sm[];
+    float *sz = sm;                       // [ROWS][NN]
+    float *su = sz + ANN_ROWS * NN;       // [ROWS][NN]
+    float *so = su + ANN_ROWS * NN;       // [ROWS][NN]
+    float *sq = so + ANN_ROWS * NN;       // [ROWS][NDP]
+    float *sd = sq + ANN_ROWS * NDP;      // [ROWS][NDP]
+    constexpr int PER = 16;
+    const int c = blockIdx.x;
+    const int r0 = chunk_begin[c], r1 = chunk_begin[c + 1];
+    const int nent = NN * NDP;
+    const int e0 = blockIdx.y * PER * blockDim.x;  // entry group of this block
+    const bool first = blockIdx.y == 0;
+    float acc[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) acc[k] = 0.0f;
+    float azeta = 0.0f, aom = 0.0f;
+    for (int rr = r0; rr < r1; rr += ANN_ROWS) {
+        const int nr = min(ANN_ROWS, r1 - rr);
+        for (int e = threadIdx.x; e < nr * NN; e += blockDim.x) {
+            sz[e] = zt[(size_t)rr * NN + e];
+            su[e] = ut[(size_t)rr * NN + e];
+            so[e] = om[(size_t)rr * NN + e];
+        }
+        for (int e = threadIdx.x; e < nr * NDP; e += blockDim.x) {
+            sq[e] = qt[(size_t)rr * NDP + e];
+            sd[e] = dqt[(size_t)rr * NDP + e];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = e0 + threadIdx.x + k * blockDim.x;
+            if (e < nent) {
+                const int mu = e / NDP, v = e - mu * NDP;
+                float s = acc[k];
+                for (int r = 0; r < nr; ++r) s += sz[r * NN + mu] * sq[r * NDP + v] + su[r * NN + mu] * sd[r * NDP + v];
+                acc[k] = s;
+            }
+        }
+        if (first && (int)threadIdx.x < NN) {
+            for (int r = 0; r < nr; ++r) {
+                azeta += sz[r * NN + threadIdx.x];
+                aom += so[r * NN + threadIdx.x];
+            }
+        }
+        __syncthreads();
+    }
+    float *dst = part + (size_t)c * (nent + 2 * NN);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = e0 + threadIdx.x + k * blockDim.x;
+        if (e < nent) dst[e] = acc[k];
+    }
+    if (first && (int)threadIdx.x < NN) {
+        dst[nent + threadIdx.x] = azeta;
+        dst[nent + NN + threadIdx.x] = aom;
+    }
+}
+
+// --------------------------------------------------------------------------- final gradient
+struct GradArgs {
+    int T, NN, ND, NDP, nR, kR, nA, kA, NRP, KRP, NAP, KAP;
+    int64_t P;
+    const int *desc_map;  // compact -> padded
+    const float *annpart;
+    const int *clo, *chi;  // [T] chunk range of each species
+    const float *cpart;
+    const int *wlo, *whi;  // [T] adjoint warp range of each species
+    const int *warp_begin; // [W+1] adjoint schedule (warps without atoms wrote no slot)
+    const double *gb1;
+    float *grad;
+};
+
+__global__ void k_grad_final(GradArgs g) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= g.P) return;
+    const int T = g.T, NN = g.NN, ND = g.ND;
+    const int64_t cb0 = (int64_t)T * NN * ND, cw1 = cb0 + (int64_t)T * NN, cb1 = cw1 + (int64_t)T * NN;
+    const int64_t ccR = cb1 + 1, ccA = ccR + (int64_t)T * T * g.nR * g.kR;
+    const int NCR = g.NRP * g.KRP, NCA = g.NAP * g.KAP, NC = NCR + NCA;
+    const int annstride = NN * g.NDP + 2 * NN;
+    double s = 0.0;
+    double sign = 1.0;
+    if (k < cb0 || k < cb1) {
+        int t, off;
+        if (k < cb0) {
+            t = (int)(k / ((int64_t)NN * ND));
+            const int r = (int)(k - (int64_t)t * NN * ND);
+            const int mu = r / ND, v = r - mu * ND;
+            off = mu * g.NDP + g.desc_map[v];
+        } else if (k < cw1) {
+            t = (int)((k - cb0) / NN);
+            off = NN * g.NDP + (int)((k - cb0) % NN);
+            sign = -1.0;
+        } else {
+            t = (int)((k - cw1) / NN);
+            off = NN * g.NDP + NN + (int)((k - cw1) % NN);
+        }
+        for (int c = g.clo[t] + lane; c < g.chi[t]; c += 32) s += (double)g.annpart[(size_t)c * annstride + off];
+    } else if (k == cb1) {
+        if (lane == 0) s = *g.gb1;
+    } else {
+        int a, b, off;
+        if (k < ccA) {
+            const int64_t r = k - ccR;
+            const int kk = (int)(r % g.kR), n = (int)((r / g.kR) % g.nR);
+            const int64_t ab = r / ((int64_t)g.kR * g.nR);
+            a = (int)(ab / T);
+            b = (int)(ab % T);
+            off = n * g.KRP + kk;
+        } else {
+            const int64_t r = k - ccA;
+            const int kk = (int)(r % g.kA), n = (int)((r / g.kA) % g.nA);
+            const int64_t ab = r / ((int64_t)g.kA * g.nA);
+            a = (int)(ab / T);
+            b = (int)(ab % T);
+            off = NCR + n * g.KAP + kk;
+        }
+        for (int w = g.wlo[a] + lane; w <= g.whi[a]; w += 32)
+            if (g.warp_begin[w] < g.warp_begin[w + 1]) s += (double)g.cpart[((size_t)(w + a) * T + b) * NC + off];
+    }
+    s = warp_sum_d(s);
+    if (lane == 0) g.grad[k] = (float)(sign * s);
+}
+
+// --------------------------------------------------------------------------- descriptor range
+__global__ void k_range(int64_t na, int NDP, int ND, const int *desc_map, const float *q, float *qmin, float *qmax) {
+    __shared__ float smin[256], smax[256];
+    const int v = blockIdx.x;
+    const int vp = desc_map[v];
+    float lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = threadIdx.x; i < na; i += blockDim.x) {
+        const float x = q[i * NDP + vp];
+        lo = fminf(lo, x);
+        hi = fmaxf(hi, x);
+    }
+    smin[threadIdx.x] = lo;
+    smax[threadIdx.x] = hi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            smin[threadIdx.x] = fminf(smin[threadIdx.x], smin[threadIdx.x + o]);
+            smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        qmin[v] = na > 0 ? smin[0] : 0.0f;
+        qmax[v] = na > 0 ? smax[0] : 0.0f;
+    }
+}
+
+__global__ void k_compact_q(int64_t na, int NDP, int ND, const int *desc_map, const float *qp, float *q) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= na * ND) return;
+    const int64_t i = e / ND;
+    const int v = (int)(e - i * ND);
+    q[e] = qp[i * NDP + desc_map[v]];
+}
+
+}  // namespace
+
+// =========================================================================== launchers
+
+static AtomArgs atom_args(Ctx *c) {
+    AtomArgs a{};
+    a.work = c->work.as<int>();
+    a.nbr_off = c->nbr_off.as<int64_t>();
+    a.n_ang = c->n_ang.as<int>();
+    a.pair = (const float4 *)c->pair.ptr;
+    a.type = c->type.as<int>();
+    a.struct_of = c->struct_of.as<int>();
+    a.par = c->par.as<float>();
+    a.T = c->T;
+    a.NN = c->NN;
+    a.inv_rcR = 1.0f / c->cfg.rc_R;
+    a.inv_rcA = 1.0f / c->cfg.rc_A;
+    a.rc2A = c->cfg.rc_A * c->cfg.rc_A;
+    a.E_atom = c->E_atom.as<float>();
+    a.F_own = c->F_own.as<float>();
+    a.W_atom = c->W_atom.as<float>();
+    a.G = (float4 *)c->G.ptr;
+    a.st_qt = c->st_qt.as<float>();
+    a.st_h = c->st_h.as<float>();
+    a.st_A = c->st_A.as<float>();
+    a.fbar = c->fbar.as<float>();
+    a.ebar = c->ebar.as<float>();
+    a.wbar = c->wbar.as<float>();
+    a.zt = c->zt.as<float>();
+    a.ut = c->ut.as<float>();
+    a.om = c->om.as<float>();
+    a.dqt = c->dqt.as<float>();
+    a.cpart = c->cpart.as<float>();
+    return a;
+}
+
+int launch_expand(Ctx *c) {
+    ExpandArgs x;
+    x.theta = c->theta.as<float>();
+    x.qscale = c->qscale.as<float>();
+    x.par = c->par.as<float>();
+    x.po = c->po;
+    x.T = c->T;
+    x.NN = c->NN;
+    x.NDc = c->ND;
+    x.NDP = c->NDP;
+    x.nR = c->nR;
+    x.kR = c->kR;
+    x.nA = c->nA;
+    x.kA = c->kA;
+    x.NRP = c->ks->NR;
+    x.KRP = c->ks->KR;
+    x.NAP = c->ks->NA;
+    x.KAP = c->ks->KA;
+    x.inv = c->d_desc_inv.as<int>();
+    const int64_t n = c->po.total;
+    k_expand<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_forward(Ctx *c, float *q_raw) {
+    if (c->n_atoms == 0) return NEP_OK;
+    AtomArgs a = atom_args(c);
+    a.warp_begin = c->fwd.warp_begin.as<int>();
+    a.q_raw = q_raw;
+    const size_t smem = c->ks->fwd_smem(c->T) * c->fwd.wpb;
+    c->ks->launch_fwd(a, c->fwd.blocks, c->fwd.wpb, smem, c->stream);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_adjoint(Ctx *c) {
+    if (c->n_atoms == 0) return NEP_OK;
+    AtomArgs a = atom_args(c);
+    a.warp_begin = c->adj.warp_begin.as<int>();
+    const size_t smem = c->ks->adj_smem(c->T) * c->adj.wpb;
+    c->ks->launch_adj(a, c->adj.blocks, c->adj.wpb, smem, c->stream);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+static int gather_blocks(Ctx *c) { return c->n_sm * 4; }
+static int struct_blocks(Ctx *c) { return c->n_sm; }
+
+int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1) {
+    if (a1 <= a0) return NEP_OK;
+    const int nb = gather_blocks(c);
+    const float coef = (float)(lamF * 2.0 / (3.0 * (double)c->n_atoms));
+    k_gather<<<nb, 256, 0, c->stream>>>(a0, a1, c->nbr_off.as<int64_t>(), c->rev.as<int>(), (const float4 *)c->G.ptr,
+                                        c->F_own.as<float>(), F_out, F_ref, coef, loss ? 1 : 0, c->fbar.as<float>(),
+                                        c->loss_part.as<double>());
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_count_hasw(Ctx *c, const uint8_t *has_W) {
+    k_count_hasw<<<1, 256, 0, c->stream>>>(c->n_struct, has_W, c->n_sv.as<int>());
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, const double *W_ref,
+                  const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1) {
+    if (s1 <= s0) return NEP_OK;
+    const int nb = struct_blocks(c);
+    k_struct<<<nb, 256, 0, c->stream>>>(s0, s1, c->atom_off.as<int64_t>(), c->E_atom.as<float>(),
+                                        c->W_atom.as<float>(), E_out, W_out, loss ? 1 : 0, E_ref, W_ref, has_W,
+                                        c->n_sv.as<int>(), lamE, lamV, (double)c->n_struct, c->ebar.as<float>(),
+                                        c->wbar.as<float>(), c->loss_part.as<double>() + gather_blocks(c));
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_loss_final(Ctx *c, double *loss3) {
+    k_loss_final<<<1, 256, 0, c->stream>>>(c->loss_part.as<double>(), c->n_atoms > 0 ? gather_blocks(c) : 0,
+                                           c->loss_part.as<double>() + gather_blocks(c),
+                                           c->n_struct > 0 ? struct_blocks(c) : 0, c->n_sv.as<int>(),
+                                           (double)c->n_struct, (double)c->n_atoms, loss3, c->gb1.as<double>());
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *dW) {
+    if (c->n_atoms > 0)
+        CK(cudaMemcpyAsync(c->fbar.ptr, dF, sizeof(float) * 3 * (size_t)c->n_atoms, cudaMemcpyDeviceToDevice,
+                           c->stream));
+    k_cotangents<<<1, 256, 0, c->stream>>>(c->n_struct, c->atom_off.as<int64_t>(), dE, dW, c->ebar.as<float>(),
+                                           c->wbar.as<float>(), c->gb1.as<double>());
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int prepare_loss_kernels(Ctx *c) {
+    const size_t smem = sizeof(float) * ANN_ROWS * (3 * c->NN + 2 * c->NDP);
+    CK(cudaFuncSetAttribute(k_ann_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return NEP_OK;
+}
+
+int launch_ann_grad(Ctx *c) {
+    if (c->n_chunks == 0) return NEP_OK;
+    const size_t smem = sizeof(float) * ANN_ROWS * (3 * c->NN + 2 * c->NDP);
+    const int groups = (c->NN * c->NDP + 16 * 256 - 1) / (16 * 256);
+    k_ann_grad<<<dim3(c->n_chunks, groups), 256, smem, c->stream>>>(c->chunk_begin.as<int>(), c->NN, c->NDP, c->zt.as<float>(),
+                                                      c->ut.as<float>(), c->om.as<float>(), c->st_qt.as<float>(),
+                                                      c->dqt.as<float>(), c->annpart.as<float>());
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_grad_final(Ctx *c, float *grad) {
+    GradArgs g;
+    g.T = c->T;
+    g.NN = c->NN;
+    g.ND = c->ND;
+    g.NDP = c->NDP;
+    g.nR = c->nR;
+    g.kR = c->kR;
+    g.nA = c->nA;
+    g.kA = c->kA;
+    g.NRP = c->ks->NR;
+    g.KRP = c->ks->KR;
+    g.NAP = c->ks->NA;
+    g.KAP = c->ks->KA;
+    g.P = c->P;
+    g.desc_map = c->d_desc_map.as<int>();
+    g.annpart = c->annpart.as<float>();
+    g.clo = c->type_clo.as<int>();
+    g.chi = c->type_chi.as<int>();
+    g.cpart = c->cpart.as<float>();
+    g.wlo = c->adj.type_wlo.as<int>();
+    g.whi = c->adj.type_whi.as<int>();
+    g.warp_begin = c->adj.warp_begin.as<int>();
+    g.gb1 = c->gb1.as<double>();
+    g.grad = grad;
+    const int64_t threads = c->P * 32;
+    k_grad_final<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(g);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_range(Ctx *c, const float *q, float *qmin, float *qmax) {
+    k_range<<<c->ND, 256, 0, c->stream>>>(c->n_atoms, c->NDP, c->ND, c->d_desc_map.as<int>(), q, qmin, qmax);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+int launch_compact_q(Ctx *c, const float *qp, float *q) {
+    const int64_t n = c->n_atoms * c->ND;
+    if (n == 0) return NEP_OK;
+    k_compact_q<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->n_atoms, c->NDP, c->ND,
+                                                                     c->d_desc_map.as<int>(), qp, q);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+}  // namespace nep

@@ -1,0 +1,504 @@
+// Cell-list neighbour search emitting CSR neighbour lists (hot-path step a1).
+//
+// The paper builds neighbour lists and displacement vectors once and keeps them on
+// the GPU (Sec. "Training efficiency ..."); this file does the same for a whole
+// batch of periodic, possibly triclinic, structures:
+//   1. per structure: inverse cell, plane spacings w_a = V/|b x c| (FP64), bins per
+//      axis n_a = max(1, floor(w_a / (rc + skin))) and scan reach m_a = ceil((rc + skin) n_a / w_a);
+//   2. per atom: fractional coordinates, wrap offset, bin; counting sort into bins;
+//   3. per atom: scan the (2 m_a + 1) neighbouring bin images, test candidates,
+//      count, then fill 64-bit keys (group, t_j, j, S);
+//   4. per atom (one warp): rank-sort its keys, decode to the float4 pair record;
+//   5. per pair: index of the reverse pair (j, i, -S) by binary search.
+// Pair predicate (identical here, in the oracle's brute force and in the per-atom
+// kernels): d = ((double)r_j - (double)r_i) + S.h evaluated in double without fused
+// multiply-add, rounded once to float; kept iff float (dx*dx + dy*dy) + dz*dz < rc*rc.
+// Negating S negates every operation exactly, so d(j,i,-S) = -d(i,j,S) bit for bit
+// and the radial/angular lists are symmetric.
+#include <vector>
+
+#include "nep_ctx.cuh"
+
+namespace nep {
+
+// ----------------------------------------------------------------------------- scan
+
+namespace {
+
+__global__ void k_scan_blocks(const int64_t *in, int64_t n, int64_t *block_sum) {
+    __shared__ int64_t warp_tot[32];
+    const int64_t base = (int64_t)blockIdx.x * 1024;
+    int64_t s = 0;
+    for (int k = 0; k < 4; ++k) {
+        const int64_t idx = base + threadIdx.x * 4 + k;
+        if (idx < n) s += in[idx];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += warp_tot[w];
+        block_sum[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_scan_sums(int64_t *block_sum, int64_t nb, int64_t *total) {
+    // single block of 1024 threads, exclusive scan in chunks with a carry
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t c0 = 0; c0 < nb; c0 += 1024) {
+        const int64_t idx = c0 + threadIdx.x;
+        const int64_t v = idx < nb ? block_sum[idx] : 0;
+        int64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t t = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(FULL, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;  // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t before = (wid > 0 ? warp_tot[wid - 1] : 0) + carry;
+        if (idx < nb) block_sum[idx] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_apply(const int64_t *in, int64_t n, const int64_t *block_off, int64_t *out) {
+    __shared__ int64_t warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * 1024 + threadIdx.x * 4;
+    int64_t v[4];
+    int64_t s = 0;
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        s += v[k];
+    }
+    int64_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int64_t run = block_off[blockIdx.x] + (wid > 0 ? warp_tot[wid - 1] : 0) + x - s;
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
+}
+
+}  // namespace
+
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total (out may alias nothing).
+// The total is also left in *total_dev.
+int scan_exclusive(Ctx *c, const int64_t *in, int64_t n, int64_t *out, int64_t *total_dev) {
+    if (n == 0) {
+        CK(cudaMemsetAsync(out, 0, sizeof(int64_t), c->stream));
+        CK(cudaMemsetAsync(total_dev, 0, sizeof(int64_t), c->stream));
+        return NEP_OK;
+    }
+    const int64_t nb = (n + 1023) / 1024;
+    if (c->scan_tmp.ensure<int64_t>(nb + 1) != NEP_OK) return c->fail(NEP_ENOMEM, "scan workspace");
+    int64_t *bs = c->scan_tmp.as<int64_t>();
+    k_scan_blocks<<<(unsigned)nb, 256, 0, c->stream>>>(in, n, bs);
+    k_scan_sums<<<1, 1024, 0, c->stream>>>(bs, nb, total_dev);
+    k_scan_apply<<<(unsigned)nb, 256, 0, c->stream>>>(in, n, bs, out);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+// ----------------------------------------------------------------------------- geometry
+
+namespace {
+
+constexpr double SKIN = 1e-3;  // Angstrom of extra reach for binning (rounding margin)
+constexpr int NBIN_MAX = 128;  // bins per axis and structure
+constexpr int SMAX = 127;      // |S_a| limit of the packed shift
+
+struct SGeom {
+    double h[9];
+    double inv[9];
+    int n[3];
+    int m[3];
+};
+
+__device__ __forceinline__ void atomic_err(int *err, int code) { atomicCAS(err, 0, code); }
+
+__global__ void k_struct_geom(int64_t ns, const float *cell, double rc, SGeom *geom, int64_t *nbins, int *err) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    SGeom g;
+    for (int k = 0; k < 9; ++k) g.h[k] = (double)cell[9 * s + k];
+    const double *h = g.h;
+    const double c0[3] = {h[4] * h[8] - h[5] * h[7], h[5] * h[6] - h[3] * h[8], h[3] * h[7] - h[4] * h[6]};
+    const double c1[3] = {h[7] * h[2] - h[8] * h[1], h[8] * h[0] - h[6] * h[2], h[6] * h[1] - h[7] * h[0]};
+    const double c2[3] = {h[1] * h[5] - h[2] * h[4], h[2] * h[3] - h[0] * h[5], h[0] * h[4] - h[1] * h[3]};
+    const double vol = h[0] * c0[0] + h[1] * c0[1] + h[2] * c0[2];
+    if (!(fabs(vol) > 1e-9) || !isfinite(vol)) {
+        atomic_err(err, 1);
+        nbins[s] = 1;
+        g.n[0] = g.n[1] = g.n[2] = 1;
+        g.m[0] = g.m[1] = g.m[2] = 0;
+        geom[s] = g;
+        return;
+    }
+    for (int x = 0; x < 3; ++x) {
+        g.inv[3 * x + 0] = c0[x] / vol;
+        g.inv[3 * x + 1] = c1[x] / vol;
+        g.inv[3 * x + 2] = c2[x] / vol;
+    }
+    const double w[3] = {fabs(vol) / sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]),
+                         fabs(vol) / sqrt(c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2]),
+                         fabs(vol) / sqrt(c2[0] * c2[0] + c2[1] * c2[1] + c2[2] * c2[2])};
+    int64_t nb = 1;
+    for (int a = 0; a < 3; ++a) {
+        int n = (int)floor(w[a] / (rc + SKIN));
+        n = n < 1 ? 1 : (n > NBIN_MAX ? NBIN_MAX : n);
+        const int m = (int)ceil((rc + SKIN) * n / w[a]);
+        if (m > SMAX - 2) atomic_err(err, 2);
+        g.n[a] = n;
+        g.m[a] = m > SMAX - 2 ? SMAX - 2 : m;
+        nb *= n;
+    }
+    geom[s] = g;
+    nbins[s] = nb;
+}
+
+__global__ void k_struct_of(int64_t ns, const int64_t *atom_off, int *struct_of) {
+    const int64_t s = blockIdx.x;
+    if (s >= ns) return;
+    for (int64_t i = atom_off[s] + threadIdx.x; i < atom_off[s + 1]; i += blockDim.x) struct_of[i] = (int)s;
+}
+
+__global__ void k_atom_bin(int64_t na, const float *pos, const int *type, int T, const int *struct_of,
+                           const SGeom *geom, const int64_t *bin_off, int64_t *atom_bin, int4 *atom_wrap,
+                           int64_t *bin_cnt, int *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    const int t = type[i];
+    if (t < 0 || t >= T) atomic_err(err, 3);
+    const int s = struct_of[i];
+    const SGeom &g = geom[s];
+    const double p[3] = {(double)pos[3 * i], (double)pos[3 * i + 1], (double)pos[3 * i + 2]};
+    if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) {
+        atomic_err(err, 4);
+        atom_bin[i] = bin_off[s];
+        atom_wrap[i] = make_int4(0, 0, 0, 0);
+        atomicAdd((unsigned long long *)&bin_cnt[bin_off[s]], 1ull);
+        return;
+    }
+    int b[3], wr[3];
+    for (int a = 0; a < 3; ++a) {
+        const double f = p[0] * g.inv[0 * 3 + a] + p[1] * g.inv[1 * 3 + a] + p[2] * g.inv[2 * 3 + a];
+        const double fl = floor(f);
+        const double fw = f - fl;
+        int bb = (int)(fw * g.n[a]);
+        bb = bb < 0 ? 0 : (bb >= g.n[a] ? g.n[a] - 1 : bb);
+        b[a] = bb;
+        if (fabs(fl) > 1e6) atomic_err(err, 4);
+        wr[a] = (int)fl;
+    }
+    const int64_t bin = bin_off[s] + ((int64_t)b[0] * g.n[1] + b[1]) * g.n[2] + b[2];
+    atom_bin[i] = bin;
+    atom_wrap[i] = make_int4(wr[0], wr[1], wr[2], 0);
+    atomicAdd((unsigned long long *)&bin_cnt[bin], 1ull);
+}
+
+__global__ void k_bin_fill(int64_t na, const int64_t *atom_bin, const int64_t *bin_start, int64_t *bin_cur,
+                           int *bin_atoms) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    const int64_t bin = atom_bin[i];
+    const int64_t slot = (int64_t)atomicAdd((unsigned long long *)&bin_cur[bin], 1ull);
+    bin_atoms[bin_start[bin] + slot] = (int)i;
+}
+
+// The pair predicate.  Returns the float squared length; d32 receives the float displacement.
+__device__ __forceinline__ float pair_d(const float *pi, const float *pj, const double *h, int Sa, int Sb, int Sc,
+                                        float *d32) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const double rel = __dsub_rn((double)pj[x], (double)pi[x]);
+        const double sh = __dadd_rn(__dadd_rn(__dmul_rn((double)Sa, h[x]), __dmul_rn((double)Sb, h[3 + x])),
+                                    __dmul_rn((double)Sc, h[6 + x]));
+        d32[x] = __double2float_rn(__dadd_rn(rel, sh));
+    }
+    return __fadd_rn(__fadd_rn(__fmul_rn(d32[0], d32[0]), __fmul_rn(d32[1], d32[1])), __fmul_rn(d32[2], d32[2]));
+}
+
+__device__ __forceinline__ uint32_t pack_shift(int Sa, int Sb, int Sc) {
+    return ((uint32_t)(Sa + 128) << 16) | ((uint32_t)(Sb + 128) << 8) | (uint32_t)(Sc + 128);
+}
+
+// Visits every candidate (j, S) of atom i and calls f(j, S, r2) for pairs within rcR.
+template <class Fn>
+__device__ __forceinline__ void for_each_neighbor(int64_t i, const float *pos, const int *struct_of,
+                                                  const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin,
+                                                  const int4 *atom_wrap, const int64_t *bin_start,
+                                                  const int *bin_atoms, float rc2R, float rcq2, int *err, Fn f) {
+    const int s = struct_of[i];
+    const SGeom &g = geom[s];
+    const int64_t lb = atom_bin[i] - bin_off[s];
+    const int bi[3] = {(int)(lb / ((int64_t)g.n[1] * g.n[2])), (int)((lb / g.n[2]) % g.n[1]), (int)(lb % g.n[2])};
+    const int4 wi = atom_wrap[i];
+    const float *pi = pos + 3 * i;
+    const float hf[9] = {(float)g.h[0], (float)g.h[1], (float)g.h[2], (float)g.h[3], (float)g.h[4],
+                         (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
+    for (int da = -g.m[0]; da <= g.m[0]; ++da) {
+        int ba = bi[0] + da;
+        const int sa = (ba >= 0) ? ba / g.n[0] : -((-ba + g.n[0] - 1) / g.n[0]);
+        ba -= sa * g.n[0];
+        for (int db = -g.m[1]; db <= g.m[1]; ++db) {
+            int bb = bi[1] + db;
+            const int sb = (bb >= 0) ? bb / g.n[1] : -((-bb + g.n[1] - 1) / g.n[1]);
+            bb -= sb * g.n[1];
+            for (int dc = -g.m[2]; dc <= g.m[2]; ++dc) {
+                int bc = bi[2] + dc;
+                const int sc = (bc >= 0) ? bc / g.n[2] : -((-bc + g.n[2] - 1) / g.n[2]);
+                bc -= sc * g.n[2];
+                const int64_t bin = bin_off[s] + ((int64_t)ba * g.n[1] + bb) * g.n[2] + bc;
+                for (int64_t t = bin_start[bin]; t < bin_start[bin + 1]; ++t) {
+                    const int j = bin_atoms[t];
+                    const int4 wj = atom_wrap[j];
+                    const int Sa = sa + wi.x - wj.x, Sb = sb + wi.y - wj.y, Sc = sc + wi.z - wj.z;
+                    if (j == (int)i && Sa == 0 && Sb == 0 && Sc == 0) continue;
+                    const float *pj = pos + 3 * j;
+                    // cheap float pre-filter with a margin, then the exact predicate
+                    const float qx = (pj[0] - pi[0]) + (Sa * hf[0] + Sb * hf[3] + Sc * hf[6]);
+                    const float qy = (pj[1] - pi[1]) + (Sa * hf[1] + Sb * hf[4] + Sc * hf[7]);
+                    const float qz = (pj[2] - pi[2]) + (Sa * hf[2] + Sb * hf[5] + Sc * hf[8]);
+                    if (qx * qx + qy * qy + qz * qz > rcq2) continue;
+                    if (Sa < -SMAX || Sa > SMAX || Sb < -SMAX || Sb > SMAX || Sc < -SMAX || Sc > SMAX) {
+                        atomic_err(err, 2);
+                        continue;
+                    }
+                    float d32[3];
+                    const float r2 = pair_d(pi, pj, g.h, Sa, Sb, Sc, d32);
+                    if (r2 < rc2R) f(j, Sa, Sb, Sc, r2);
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_count(int64_t na, const float *pos, const int *struct_of, const SGeom *geom, const int64_t *bin_off,
+                        const int64_t *atom_bin, const int4 *atom_wrap, const int64_t *bin_start,
+                        const int *bin_atoms, float rc2R, float rc2A, float rcq2, int64_t *cnt, int *n_ang, int *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    int64_t nr = 0;
+    int nang = 0;
+    for_each_neighbor(i, pos, struct_of, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms, rc2R, rcq2, err,
+                      [&](int, int, int, int, float r2) {
+                          ++nr;
+                          if (r2 < rc2A) ++nang;
+                      });
+    cnt[i] = nr;
+    n_ang[i] = nang;
+}
+
+__global__ void k_fill(int64_t na, const float *pos, const int *type, const int *struct_of, const SGeom *geom,
+                       const int64_t *bin_off, const int64_t *atom_bin, const int4 *atom_wrap,
+                       const int64_t *bin_start, const int *bin_atoms, float rc2R, float rc2A, float rcq2,
+                       const int64_t *nbr_off, uint64_t *keys, int *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    int64_t o = nbr_off[i];
+    const int64_t end = nbr_off[i + 1];
+    for_each_neighbor(i, pos, struct_of, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms, rc2R, rcq2, err,
+                      [&](int j, int Sa, int Sb, int Sc, float r2) {
+                          if (o < end) {
+                              const uint64_t grp = (r2 < rc2A) ? 0ull : 1ull;
+                              keys[o] = (grp << 63) | ((uint64_t)type[j] << 59) | ((uint64_t)j << 24) |
+                                        (uint64_t)pack_shift(Sa, Sb, Sc);
+                          }
+                          ++o;
+                      });
+    if (o != end) atomic_err(err, 5);
+}
+
+// One warp per atom: rank sort of its keys, then decode into the pair records.
+__global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const int64_t *nbr_off, const float *pos,
+                              const int *struct_of, const SGeom *geom, uint64_t *keys_out, float4 *pair,
+                              int32_t *shift) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= na) return;
+    const int64_t beg = nbr_off[i], n = nbr_off[i + 1] - beg;
+    const SGeom &g = geom[struct_of[i]];
+    for (int64_t e = lane; e < n; e += 32) {
+        const uint64_t k = keys_in[beg + e];
+        int64_t rank = 0;
+        for (int64_t e2 = 0; e2 < n; ++e2) rank += (keys_in[beg + e2] < k) ? 1 : 0;
+        keys_out[beg + rank] = k;
+        const int j = (int)((k >> 24) & ((1ull << 35) - 1));
+        const int tj = (int)((k >> 59) & 15ull);
+        const uint32_t sp = (uint32_t)(k & 0xffffffull);
+        const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
+        float d32[3];
+        pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
+        pair[beg + rank] = make_float4(d32[0], d32[1], d32[2], __int_as_float((j << 4) | tj));
+        shift[beg + rank] = (int32_t)sp;
+    }
+}
+
+// One thread per pair: index of (j, i, -S) in j's sorted list.
+__global__ void k_reverse(int64_t na, const int64_t *nbr_off, const uint64_t *keys, const int *type, int *rev,
+                          const float4 *pair, int *err) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= na) return;
+    const int64_t beg = nbr_off[i], end = nbr_off[i + 1];
+    const int ti = type[i];
+    for (int64_t p = beg + lane; p < end; p += 32) {
+        const uint64_t k = keys[p];
+        const int j = (int)((k >> 24) & ((1ull << 35) - 1));
+        const uint32_t sp = (uint32_t)(k & 0xffffffull);
+        const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
+        const uint64_t want = (k & (1ull << 63)) | ((uint64_t)ti << 59) | ((uint64_t)i << 24) |
+                              (uint64_t)pack_shift(-Sa, -Sb, -Sc);
+        int64_t lo = nbr_off[j], hi = nbr_off[j + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (keys[mid] < want) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo >= nbr_off[j + 1] || keys[lo] != want) {
+            atomic_err(err, 6);
+            rev[p] = (int)p;
+            continue;
+        }
+        rev[p] = (int)lo;
+        const float4 a = pair[p], b = pair[lo];
+        if (a.x != -b.x || a.y != -b.y || a.z != -b.z) atomic_err(err, 7);
+    }
+}
+
+}  // namespace
+
+int build_neighbors(Ctx *c) {
+    const int64_t ns = c->n_struct, na = c->n_atoms;
+    const cudaStream_t st = c->stream;
+    const float rcR = c->cfg.rc_R, rcA = c->cfg.rc_A;
+    const float rc2R = rcR * rcR, rc2A = rcA * rcA;  // single rounded products
+    const float rcq = rcR + 0.05f;
+    int *err = c->d_err.as<int>();
+    CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    if (c->geom.ensure_bytes(sizeof(SGeom) * (size_t)(ns > 0 ? ns : 1)) || c->nbins.ensure<int64_t>(ns + 1) ||
+        c->bin_off.ensure<int64_t>(ns + 1) || c->d_total.ensure<int64_t>(2))
+        return c->fail(NEP_ENOMEM, "geometry buffers");
+    SGeom *geom = (SGeom *)c->geom.ptr;
+    if (ns > 0) {
+        k_struct_geom<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(ns, c->cell.as<float>(), (double)rcR, geom,
+                                                                    c->nbins.as<int64_t>(), err);
+        k_struct_of<<<(unsigned)ns, 128, 0, st>>>(ns, c->atom_off.as<int64_t>(), c->struct_of.as<int>());
+    }
+    CK(cudaGetLastError());
+    int rc = scan_exclusive(c, c->nbins.as<int64_t>(), ns, c->bin_off.as<int64_t>(), c->d_total.as<int64_t>());
+    if (rc) return rc;
+    int64_t nbin_total = 0;
+    CK(cudaMemcpyAsync(&nbin_total, c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return c->fail(NEP_EINVAL, herr == 1 ? "singular or non-finite cell" : "cell too thin for the cutoff (more than 127 images)");
+    if (c->bin_cnt.ensure<int64_t>(nbin_total + 1) || c->bin_start.ensure<int64_t>(nbin_total + 1) ||
+        c->bin_cur.ensure<int64_t>(nbin_total + 1) || c->atom_bin.ensure<int64_t>(na + 1) ||
+        c->atom_wrap.ensure_bytes(sizeof(int4) * (size_t)(na + 1)) || c->bin_atoms.ensure<int>(na + 1) ||
+        c->cnt.ensure<int64_t>(na + 1) || c->n_ang.ensure<int>(na + 1) || c->nbr_off.ensure<int64_t>(na + 1))
+        return c->fail(NEP_ENOMEM, "bin buffers");
+    CK(cudaMemsetAsync(c->bin_cnt.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
+    CK(cudaMemsetAsync(c->bin_cur.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
+    const unsigned gA = (unsigned)((na + 255) / 256);
+    if (na > 0) {
+        k_atom_bin<<<gA, 256, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->cfg.n_types,
+                                       c->struct_of.as<int>(), geom, c->bin_off.as<int64_t>(),
+                                       c->atom_bin.as<int64_t>(), (int4 *)c->atom_wrap.ptr, c->bin_cnt.as<int64_t>(),
+                                       err);
+        CK(cudaGetLastError());
+    }
+    rc = scan_exclusive(c, c->bin_cnt.as<int64_t>(), nbin_total, c->bin_start.as<int64_t>(),
+                        c->d_total.as<int64_t>() + 1);
+    if (rc) return rc;
+    if (na > 0) {
+        k_bin_fill<<<gA, 256, 0, st>>>(na, c->atom_bin.as<int64_t>(), c->bin_start.as<int64_t>(),
+                                       c->bin_cur.as<int64_t>(), c->bin_atoms.as<int>());
+        k_count<<<gA, 128, 0, st>>>(na, c->pos.as<float>(), c->struct_of.as<int>(), geom, c->bin_off.as<int64_t>(),
+                                    c->atom_bin.as<int64_t>(), (const int4 *)c->atom_wrap.ptr,
+                                    c->bin_start.as<int64_t>(), c->bin_atoms.as<int>(), rc2R, rc2A, rcq * rcq,
+                                    c->cnt.as<int64_t>(), c->n_ang.as<int>(), err);
+        CK(cudaGetLastError());
+    }
+    rc = scan_exclusive(c, c->cnt.as<int64_t>(), na, c->nbr_off.as<int64_t>(), c->d_total.as<int64_t>());
+    if (rc) return rc;
+    int64_t M = 0;
+    CK(cudaMemcpyAsync(&M, c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return c->fail(NEP_EINVAL, herr == 3 ? "species index out of range" :
+                                          herr == 4 ? "non-finite or far out-of-cell position" :
+                                                      "more than 127 periodic images along a cell vector");
+    if (M >= (int64_t)1 << 31) return c->fail(NEP_EINVAL, "more than 2^31 neighbour pairs");
+    if (c->keys_tmp.ensure<uint64_t>(M + 1) || c->keys.ensure<uint64_t>(M + 1) ||
+        c->pair.ensure_bytes(sizeof(float4) * (size_t)(M + 1)) || c->rev.ensure<int>(M + 1) ||
+        c->shift.ensure<int32_t>(M + 1))
+        return c->fail(NEP_ENOMEM, "pair buffers");
+    c->n_pairs = M;
+    if (na > 0) {
+        k_fill<<<gA, 128, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->struct_of.as<int>(), geom,
+                                   c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
+                                   (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
+                                   c->bin_atoms.as<int>(), rc2R, rc2A, rcq * rcq, c->nbr_off.as<int64_t>(),
+                                   c->keys_tmp.as<uint64_t>(), err);
+        const unsigned gw = (unsigned)((na * 32 + 255) / 256);
+        k_sort_decode<<<gw, 256, 0, st>>>(na, c->keys_tmp.as<uint64_t>(), c->nbr_off.as<int64_t>(),
+                                          c->pos.as<float>(), c->struct_of.as<int>(), geom, c->keys.as<uint64_t>(),
+                                          (float4 *)c->pair.ptr, c->shift.as<int32_t>());
+        k_reverse<<<gw, 256, 0, st>>>(na, c->nbr_off.as<int64_t>(), c->keys.as<uint64_t>(), c->type.as<int>(),
+                                      c->rev.as<int>(), (const float4 *)c->pair.ptr, err);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return c->fail(NEP_EINTERNAL, "neighbour list is not symmetric");
+    // angular pair count
+    int64_t nang_total = 0;
+    {
+        std::vector<int> h(na > 0 ? na : 1);
+        if (na > 0) CK(cudaMemcpy(h.data(), c->n_ang.ptr, sizeof(int) * na, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < na; ++i) nang_total += h[i];
+        c->h_nang.assign(h.begin(), h.begin() + na);
+        std::vector<int64_t> off(na + 1);
+        CK(cudaMemcpy(off.data(), c->nbr_off.ptr, sizeof(int64_t) * (na + 1), cudaMemcpyDeviceToHost));
+        c->h_nbr_off.swap(off);
+    }
+    c->n_pairs_ang = nang_total;
+    return NEP_OK;
+}
+
+}  // namespace nep

@@ -1,0 +1,280 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (FP32 path): norm-wise relative error ||x - x_oracle|| / ||x_oracle|| <= 1e-5
+on E, F, W, the loss terms and the parameter gradient.  Neighbour lists are compared
+bit-exactly (the inclusion decision is an integer taken in float in both).
+Inputs are seeded synthetic structures; references come from the oracle's teacher
+model, never from the GPU.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_19557_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def f32(x):
+    return np.asarray(x, np.float64).astype(np.float32).astype(np.float64)
+
+
+class Case:
+    """Batch + student/teacher parameters + oracle references (all float32-representable)."""
+
+    def __init__(self, name, batch, seed=1):
+        from paper_2606_19557_gb300 import NEP
+        self.spec = synth.SPECS[name]
+        self.batch = batch
+        P = oracle.num_params(self.spec)
+        self.theta = synth.random_theta(P, seed)
+        self.teacher = synth.random_theta(P, seed + 1)
+        q = oracle.descriptors(self.spec, self.theta, batch)
+        self.qs = f32(oracle.scale_from_range(q))
+        E_t, F_t, W_t = oracle.evaluate(self.spec, self.teacher, self.qs, batch)
+        self.E_ref, self.F_ref, self.W_ref = E_t, f32(F_t), W_t
+        self.nep = NEP(self.spec)
+        self.nep.set_structures_batch(batch)
+        self.nep.set_params(torch.tensor(self.theta, dtype=torch.float32), torch.tensor(self.qs, dtype=torch.float32))
+
+
+def small_cases():
+    return {
+        "fcc32_t1": lambda: synth.batch_fcc32(),
+        "fcc_bcc_t1": lambda: synth.batch_fcc_bcc(seed=12, n_struct=24),
+        "alloy_t4": lambda: synth.batch_alloy(seed=13, n_struct=14),
+        "scale_t5": lambda: synth.batch_scale(seed=14, n_struct=40, n_big=0),
+        "carbon_table1": lambda: synth.batch_fcc_bcc(seed=15, n_struct=4, n_lo=40, n_hi=90),
+    }
+
+
+_CACHE = {}
+
+
+def get_case(name):
+    if name not in _CACHE:
+        _CACHE[name] = Case(name, small_cases()[name]())
+    return _CACHE[name]
+
+
+NAMES = list(small_cases().keys())
+
+
+# ----------------------------------------------------------------------------- neighbours
+
+def _gpu_pairs(nep):
+    off, j, s, a = nep.neighbors()
+    off = off.cpu().numpy()
+    i = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    return i, j.cpu().numpy().astype(np.int64), s.cpu().numpy(), a.cpu().numpy().astype(bool), off
+
+
+def _check_neighbors(nep, batch, rc_R, rc_A):
+    gi, gj, gs, ga, off = _gpu_pairs(nep)
+    oi, oj, os_, oa = oracle.neighbors(batch, rc_R, rc_A)
+    g = set(zip(gi.tolist(), gj.tolist(), map(tuple, gs.tolist()), ga.tolist()))
+    o = set(zip(oi.tolist(), oj.tolist(), map(tuple, os_.tolist()), oa.tolist()))
+    assert len(g) == len(gi), "duplicate neighbour entries"
+    assert g == o
+    # angular neighbours first, each group sorted by (species of j, j, S)
+    types = np.asarray(batch.types)
+    for k in range(min(len(off) - 1, 300)):
+        sl = slice(off[k], off[k + 1])
+        ang = ga[sl]
+        assert np.all(np.diff(ang.astype(int)) <= 0)
+        for grp in (True, False):
+            m = ang == grp
+            key = list(zip(types[gj[sl][m]].tolist(), gj[sl][m].tolist(), map(tuple, gs[sl][m].tolist())))
+            assert key == sorted(key)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_neighbor_lists_bit_exact(name):
+    c = get_case(name)
+    _check_neighbors(c.nep, c.batch, c.spec.rc_R, c.spec.rc_A)
+    nr, na = c.nep.num_pairs()
+    i, j, S, ang = oracle.neighbors(c.batch, c.spec.rc_R, c.spec.rc_A)
+    assert nr == len(i) and na == int(ang.sum())
+
+
+def test_neighbor_edge_geometries():
+    """Primitive triclinic cell (self images), a lone atom, a dimer, atoms far outside
+    their cell (unwrapped), and a thin cell needing many images."""
+    from paper_2606_19557_gb300 import NEP
+    a = 3.6
+    prim = 0.5 * a * np.array([[0, 1, 1], [1, 0, 1], [1, 1, 0]], float)
+    rng = np.random.default_rng(0)
+    thin = np.diag([2.0, 2.3, 30.0]) + 0.1 * rng.normal(size=(3, 3))
+    structs = [
+        (np.array([[0.1, 0.2, 0.3]]), prim),
+        (np.array([[5.0, 5.0, 5.0]]), np.eye(3) * 20.0),
+        (np.array([[6.0, 6.0, 6.0], [7.9, 6.5, 6.2]]), np.eye(3) * 12.0),
+        (rng.uniform(0, 8, size=(10, 3)) + np.array([30.0, -41.0, 17.0]), np.eye(3) * 8.0 + 0.2 * np.eye(3)[::-1]),
+        (rng.uniform(0, 1, size=(3, 3)) @ thin, thin),
+    ]
+    off = np.cumsum([0] + [p.shape[0] for p, _ in structs])
+    batch = synth.Batch(off.astype(np.int64), np.concatenate([p for p, _ in structs]).astype(np.float32),
+                        np.zeros(off[-1], np.int32), np.stack([c.reshape(9) for _, c in structs]).astype(np.float32), 1)
+    nep = NEP(synth.SPECS["fcc_bcc_t1"])
+    nep.set_structures_batch(batch)
+    _check_neighbors(nep, batch, 6.0, 4.0)
+
+
+# ----------------------------------------------------------------------------- forward
+
+@pytest.mark.parametrize("name", NAMES)
+def test_descriptors(name):
+    c = get_case(name)
+    q = c.nep.descriptors().cpu().numpy()
+    qo = oracle.descriptors(c.spec, c.theta, c.batch)
+    for v in range(qo.shape[1]):
+        assert rel(q[:, v], qo[:, v]) < TOL, v
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_energy_force_virial(name):
+    c = get_case(name)
+    E, F, W = [x.cpu().numpy() for x in c.nep.eval()]
+    Eo, Fo, Wo = oracle.evaluate(c.spec, c.theta, c.qs, c.batch)
+    assert rel(E, Eo) < TOL
+    assert rel(F, Fo) < TOL
+    assert rel(W, Wo) < TOL
+    # per-atom view (meV/atom, meV/A) for the report
+    cnt = c.batch.counts()
+    assert np.max(np.abs(E - Eo) / cnt) * 1e3 < 0.1
+    assert np.max(np.abs(F - Fo)) * 1e3 < 1.0
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_loss_and_gradient(name):
+    c = get_case(name)
+    hw = np.ones(c.batch.n_struct, np.uint8)
+    hw[::3] = 0
+    lam = (1.0, 2.0, 0.3)
+    l3, g = c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref, hw, lam)
+    l3, g = l3.cpu().numpy(), g.cpu().numpy()
+    l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, c.batch, c.E_ref, c.F_ref, c.W_ref, hw, lam)[:2]
+    np.testing.assert_allclose(l3, l3o, rtol=TOL)
+    assert rel(g, go) < TOL
+
+
+@pytest.mark.parametrize("name", ["fcc_bcc_t1", "alloy_t4", "scale_t5"])
+def test_backward_vjp(name):
+    c = get_case(name)
+    rng = np.random.default_rng(5)
+    dE = rng.normal(size=c.batch.n_struct)
+    dF = f32(rng.normal(size=(c.batch.n_atoms, 3)))
+    dW = rng.normal(size=(c.batch.n_struct, 9))
+    c.nep.eval()
+    g = c.nep.backward(dE, dF, dW).cpu().numpy()
+    go = oracle.backward(c.spec, c.theta, c.qs, c.batch, dE, dF, dW)
+    assert rel(g, go) < TOL
+
+
+def test_autograd_function_matches_oracle():
+    from paper_2606_19557_gb300 import NEPFunction
+    c = get_case("alloy_t4")
+    th = torch.tensor(c.theta, dtype=torch.float32, device="cuda", requires_grad=True)
+    E, F, W = NEPFunction.apply(th, c.nep)
+    cnt = torch.tensor(c.batch.counts(), dtype=torch.float64, device="cuda")
+    Er = torch.tensor(c.E_ref, device="cuda")
+    Fr = torch.tensor(c.F_ref, dtype=torch.float32, device="cuda")
+    Wr = torch.tensor(c.W_ref, device="cuda")
+    L = (((E - Er) / cnt) ** 2).mean() + ((F - Fr) ** 2).double().sum() / (3 * F.shape[0]) \
+        + 0.1 * (((W - Wr) / cnt[:, None]) ** 2).sum() / (9 * W.shape[0])
+    L.backward()
+    go = oracle.loss_grad(c.spec, c.theta, c.qs, c.batch, c.E_ref, c.F_ref, c.W_ref, None, (1.0, 1.0, 0.1))[1]
+    assert rel(th.grad.cpu().numpy(), go) < TOL
+
+
+# ----------------------------------------------------------------------------- properties
+
+def test_deterministic_and_graph_replay():
+    c = get_case("alloy_t4")
+    out = [c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref) for _ in range(3)]
+    g0 = out[0][1].cpu().numpy()
+    for l3, g in out[1:]:
+        assert np.array_equal(g.cpu().numpy(), g0)
+        assert np.array_equal(l3.cpu().numpy(), out[0][0].cpu().numpy())
+
+
+def test_teacher_gives_near_zero_loss():
+    c = get_case("fcc_bcc_t1")
+    E, F, W = oracle.evaluate(c.spec, c.theta, c.qs, c.batch)
+    l3, g = c.nep.loss_grad(E, f32(F), W)
+    l3 = l3.cpu().numpy()
+    # references are the student's own FP64 values: residuals are FP32 rounding only
+    assert l3[0] < 1e-10 and l3[1] < 1e-10 and l3[2] < 1e-10
+
+
+def test_host_entry_point_matches_device_call():
+    c = get_case("fcc_bcc_t1")
+    c.nep.set_targets(c.E_ref, c.F_ref, c.W_ref)
+    l3h, gh = c.nep.loss_grad_host(torch.tensor(c.theta, dtype=torch.float32), (1.0, 1.0, 0.1))
+    l3d, gd = c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref, None, (1.0, 1.0, 0.1))
+    assert np.array_equal(gh.numpy(), gd.cpu().numpy())
+    assert np.array_equal(l3h.numpy(), l3d.cpu().numpy())
+
+
+def test_launch_shapes_agree():
+    c = get_case("scale_t5")
+    g0 = c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref)[1].cpu().numpy()
+    shape = c.nep.launch_shape()
+    c.nep.set_launch(2, 152, 8, 152 * 2)
+    g1 = c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref)[1].cpu().numpy()
+    c.nep.set_launch(*shape)
+    assert rel(g1, g0) < 1e-6
+
+
+def test_empty_batch():
+    from paper_2606_19557_gb300 import NEP
+    spec = synth.SPECS["fcc32_t1"]
+    nep = NEP(spec)
+    empty = synth.Batch(np.zeros(1, np.int64), np.zeros((0, 3), np.float32), np.zeros(0, np.int32),
+                        np.zeros((0, 9), np.float32), 1)
+    nep.set_structures_batch(empty)
+    P = oracle.num_params(spec)
+    nep.set_params(torch.zeros(P), torch.ones(nep.n_des))
+    E, F, W = nep.eval()
+    assert E.numel() == 0 and F.numel() == 0
+    l3, g = nep.loss_grad(np.zeros(0), np.zeros((0, 3)), np.zeros((0, 9)))
+    assert np.all(l3.cpu().numpy() == 0) and np.all(g.cpu().numpy() == 0)
+
+
+def test_invalid_inputs_return_errors():
+    from paper_2606_19557_gb300 import NEP, NepError
+    spec = synth.SPECS["fcc32_t1"]
+    nep = NEP(spec)
+    b = synth.batch_fcc32(n_struct=2)
+    with pytest.raises(NepError):
+        nep.eval()  # no structures yet
+    bad = synth.Batch(b.atom_off, b.pos.copy(), b.types, b.cell, 1)
+    bad.pos[3, 1] = np.nan
+    with pytest.raises(NepError):
+        nep.set_structures_batch(bad)
+    bt = synth.Batch(b.atom_off, b.pos, b.types + 1, b.cell, 1)
+    with pytest.raises(NepError):
+        nep.set_structures_batch(bt)
+    bc = synth.Batch(b.atom_off, b.pos, b.types, np.zeros_like(b.cell), 1)
+    with pytest.raises(NepError):
+        nep.set_structures_batch(bc)
+    bz = synth.Batch(np.array([0, 0, 64], np.int64), b.pos, b.types, b.cell, 1)
+    with pytest.raises(NepError):
+        nep.set_structures_batch(bz)
+    nep.set_structures_batch(b)  # a valid batch still works afterwards
+    with pytest.raises(NepError):
+        nep.eval()  # no parameters yet
+    P = oracle.num_params(spec)
+    nep.set_params(torch.zeros(P), torch.ones(nep.n_des))
+    E, F, W = nep.eval()
+    assert np.all(np.isfinite(E.cpu().numpy()))
