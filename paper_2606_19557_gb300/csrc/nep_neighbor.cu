@@ -434,7 +434,10 @@ int build_neighbors(Ctx *c) {
         return c->fail(NEP_ENOMEM, "bin buffers");
     CK(cudaMemsetAsync(c->bin_cnt.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
     CK(cudaMemsetAsync(c->bin_cur.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
-    const unsigned gA = (unsigned)((na + 255) / 256);
+    const unsigned gA = (unsigned)((na + 255) / 256);     // 256-thread blocks, one thread per atom
+    const unsigned gA128 = (unsigned)((na + 127) / 128);  // 128-thread blocks, one thread per atom
+    CK(cudaMemsetAsync(c->cnt.ptr, 0, sizeof(int64_t) * (size_t)(na + 1), st));
+    CK(cudaMemsetAsync(c->n_ang.ptr, 0, sizeof(int) * (size_t)(na + 1), st));
     if (na > 0) {
         k_atom_bin<<<gA, 256, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->cfg.n_types,
                                        c->struct_of.as<int>(), geom, c->bin_off.as<int64_t>(),
@@ -448,7 +451,7 @@ int build_neighbors(Ctx *c) {
     if (na > 0) {
         k_bin_fill<<<gA, 256, 0, st>>>(na, c->atom_bin.as<int64_t>(), c->bin_start.as<int64_t>(),
                                        c->bin_cur.as<int64_t>(), c->bin_atoms.as<int>());
-        k_count<<<gA, 128, 0, st>>>(na, c->pos.as<float>(), c->struct_of.as<int>(), geom, c->bin_off.as<int64_t>(),
+        k_count<<<gA128, 128, 0, st>>>(na, c->pos.as<float>(), c->struct_of.as<int>(), geom, c->bin_off.as<int64_t>(),
                                     c->atom_bin.as<int64_t>(), (const int4 *)c->atom_wrap.ptr,
                                     c->bin_start.as<int64_t>(), c->bin_atoms.as<int>(), rc2R, rc2A, rcq * rcq,
                                     c->cnt.as<int64_t>(), c->n_ang.as<int>(), err);
@@ -470,7 +473,7 @@ int build_neighbors(Ctx *c) {
         return c->fail(NEP_ENOMEM, "pair buffers");
     c->n_pairs = M;
     if (na > 0) {
-        k_fill<<<gA, 128, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->struct_of.as<int>(), geom,
+        k_fill<<<gA128, 128, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->struct_of.as<int>(), geom,
                                    c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
                                    (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
                                    c->bin_atoms.as<int>(), rc2R, rc2A, rcq * rcq, c->nbr_off.as<int64_t>(),
