@@ -113,7 +113,7 @@ struct Ctx {
 
     // per-step buffers
     DevBuf E_atom, F_own, W_atom, G, st_qt, st_h, st_A;
-    DevBuf fbar, ebar, wbar, zt, ut, om, qt2, dqt, cpart, annpart;
+    DevBuf fbar, ebar, wbar, zt, ut, om, dqt, cpart, annpart;
     DevBuf F_int, E_int, W_int;       // internal outputs for nep_loss_grad
     DevBuf loss_part, gb1, n_sv, loss3_int, grad_int;
     DevBuf tgt_E, tgt_F, tgt_W, tgt_hw;  // nep_set_targets copies

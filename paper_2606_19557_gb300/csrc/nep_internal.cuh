@@ -78,7 +78,7 @@ struct AtomArgs {
     const float *wbar;      // [Ns*9]  dL/dW_s
     // adjoint outputs
     float *zt, *ut, *om;    // [Na_work][NN]
-    float *qt2, *dqt;       // [Na_work][ND]
+    float *dqt;             // [Na_work][ND] normalised descriptor JVP
     float *cpart;           // [(W + T)][T][NC] per-warp c-gradient partials
     float *q_raw;           // optional [Na][ND] raw descriptors (descriptor export), may be null
 };

@@ -663,7 +663,6 @@ __global__ void __launch_bounds__(256) k_adjoint(AtomArgs a) {
             float e = 0.0f;
             for (int mu = 0; mu < NN; ++mu) e += wr[(size_t)mu * ND] * sm.zeta[mu];
             sm.ab[v] = e * scale[v];
-            a.qt2[(size_t)wi * ND + v] = sm.qt[v];
             a.dqt[(size_t)wi * ND + v] = sm.dqt[v];
         }
         __syncwarp();
