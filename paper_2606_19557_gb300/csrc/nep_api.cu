@@ -106,12 +106,15 @@ static int max_blocks_per_sm(Ctx *c, const void *fn, int wpb, size_t smem) {
     return nb;
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel (shared by every
+// context in the process), so it is raised to the device maximum, never lowered.
 static int set_smem_attr(Ctx *c) {
-    const size_t f = c->ks->fwd_smem(c->T) * 8, a = c->ks->adj_smem(c->T) * 8;
     int maxo = 0;
     CK(cudaDeviceGetAttribute(&maxo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
-    CK(cudaFuncSetAttribute(c->ks->fwd_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min<size_t>(f, maxo)));
-    CK(cudaFuncSetAttribute(c->ks->adj_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min<size_t>(a, maxo)));
+    if (c->ks->fwd_smem(c->T) > (size_t)maxo || c->ks->adj_smem(c->T) > (size_t)maxo)
+        return c->fail(NEP_EINVAL, "model too large for shared memory");
+    CK(cudaFuncSetAttribute(c->ks->fwd_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+    CK(cudaFuncSetAttribute(c->ks->adj_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     return NEP_OK;
 }
 
@@ -197,6 +200,7 @@ static int run_graph(Ctx *c, Ctx::Graph &g, const std::vector<const void *> &key
         cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         if (rc) {
             if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();  // clear the invalidated-capture status
             return rc;
         }
         if (e != cudaSuccess) return c->fail_cuda(e, "cudaStreamEndCapture");

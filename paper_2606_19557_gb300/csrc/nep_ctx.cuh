@@ -153,6 +153,13 @@ struct Ctx {
         if (e_ != cudaSuccess) return c->fail_cuda(e_, #x);        \
     } while (0)
 
+// Launch check that names the kernel in the error message.
+#define CK_LAUNCH(name)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) return c->fail_cuda(e_, "launch of " name); \
+    } while (0)
+
 int scan_exclusive(Ctx *c, const int64_t *in, int64_t n, int64_t *out, int64_t *total_dev);
 int build_neighbors(Ctx *c);
 

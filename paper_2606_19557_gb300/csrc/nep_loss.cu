@@ -6,6 +6,7 @@
 // No floating-point atomics, so two runs with the same launch shape are bit-identical.
 #include "nep_ctx.cuh"
 
+
 namespace nep {
 
 namespace {
@@ -453,7 +454,7 @@ int launch_expand(Ctx *c) {
     x.inv = c->d_desc_inv.as<int>();
     const int64_t n = c->po.total;
     k_expand<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x);
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_expand");
     return NEP_OK;
 }
 
@@ -464,7 +465,7 @@ int launch_forward(Ctx *c, float *q_raw) {
     a.q_raw = q_raw;
     const size_t smem = c->ks->fwd_smem(c->T) * c->fwd.wpb;
     c->ks->launch_fwd(a, c->fwd.blocks, c->fwd.wpb, smem, c->stream);
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_forward");
     return NEP_OK;
 }
 
@@ -474,7 +475,7 @@ int launch_adjoint(Ctx *c) {
     a.warp_begin = c->adj.warp_begin.as<int>();
     const size_t smem = c->ks->adj_smem(c->T) * c->adj.wpb;
     c->ks->launch_adj(a, c->adj.blocks, c->adj.wpb, smem, c->stream);
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_adjoint");
     return NEP_OK;
 }
 
@@ -488,13 +489,13 @@ int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool lo
     k_gather<<<nb, 256, 0, c->stream>>>(a0, a1, c->nbr_off.as<int64_t>(), c->rev.as<int>(), (const float4 *)c->G.ptr,
                                         c->F_own.as<float>(), F_out, F_ref, coef, loss ? 1 : 0, c->fbar.as<float>(),
                                         c->loss_part.as<double>());
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_gather");
     return NEP_OK;
 }
 
 int launch_count_hasw(Ctx *c, const uint8_t *has_W) {
     k_count_hasw<<<1, 256, 0, c->stream>>>(c->n_struct, has_W, c->n_sv.as<int>());
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_count_hasw");
     return NEP_OK;
 }
 
@@ -506,7 +507,7 @@ int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, con
                                         c->W_atom.as<float>(), E_out, W_out, loss ? 1 : 0, E_ref, W_ref, has_W,
                                         c->n_sv.as<int>(), lamE, lamV, (double)c->n_struct, c->ebar.as<float>(),
                                         c->wbar.as<float>(), c->loss_part.as<double>() + gather_blocks(c));
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_struct");
     return NEP_OK;
 }
 
@@ -515,7 +516,7 @@ int launch_loss_final(Ctx *c, double *loss3) {
                                            c->loss_part.as<double>() + gather_blocks(c),
                                            c->n_struct > 0 ? struct_blocks(c) : 0, c->n_sv.as<int>(),
                                            (double)c->n_struct, (double)c->n_atoms, loss3, c->gb1.as<double>());
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_loss_final");
     return NEP_OK;
 }
 
@@ -525,13 +526,14 @@ int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *d
                            c->stream));
     k_cotangents<<<1, 256, 0, c->stream>>>(c->n_struct, c->atom_off.as<int64_t>(), dE, dW, c->ebar.as<float>(),
                                            c->wbar.as<float>(), c->gb1.as<double>());
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_cotangents");
     return NEP_OK;
 }
 
 int prepare_loss_kernels(Ctx *c) {
-    const size_t smem = sizeof(float) * ANN_ROWS * (3 * c->NN + 2 * c->NDP);
-    CK(cudaFuncSetAttribute(k_ann_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int maxo = 0;
+    CK(cudaDeviceGetAttribute(&maxo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
+    CK(cudaFuncSetAttribute(k_ann_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     return NEP_OK;
 }
 
@@ -542,7 +544,7 @@ int launch_ann_grad(Ctx *c) {
     k_ann_grad<<<dim3(c->n_chunks, groups), 256, smem, c->stream>>>(c->chunk_begin.as<int>(), c->NN, c->NDP, c->zt.as<float>(),
                                                       c->ut.as<float>(), c->om.as<float>(), c->st_qt.as<float>(),
                                                       c->dqt.as<float>(), c->annpart.as<float>());
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_ann_grad");
     return NEP_OK;
 }
 
@@ -573,13 +575,13 @@ int launch_grad_final(Ctx *c, float *grad) {
     g.grad = grad;
     const int64_t threads = c->P * 32;
     k_grad_final<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(g);
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_grad_final");
     return NEP_OK;
 }
 
 int launch_range(Ctx *c, const float *q, float *qmin, float *qmax) {
     k_range<<<c->ND, 256, 0, c->stream>>>(c->n_atoms, c->NDP, c->ND, c->d_desc_map.as<int>(), q, qmin, qmax);
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_range");
     return NEP_OK;
 }
 
@@ -588,7 +590,7 @@ int launch_compact_q(Ctx *c, const float *qp, float *q) {
     if (n == 0) return NEP_OK;
     k_compact_q<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->n_atoms, c->NDP, c->ND,
                                                                      c->d_desc_map.as<int>(), qp, q);
-    CK(cudaGetLastError());
+    CK_LAUNCH("k_compact_q");
     return NEP_OK;
 }
 
