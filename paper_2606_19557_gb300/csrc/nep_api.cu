@@ -217,12 +217,6 @@ static int run_graph(Ctx *c, Ctx::Graph &g, const std::vector<const void *> &key
     return NEP_OK;
 }
 
-// ----------------------------------------------------------------------------- plain form
-// The same kernels and arithmetic launched once per structure, without a graph or the
-// persistent multi-structure schedule: the baseline the batched form is compared with.
-static int plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
-                      double lF, double lV, double *loss3, float *grad);
-
 // ----------------------------------------------------------------------------- C ABI
 
 extern "C" {
@@ -361,6 +355,7 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
     c->have_batch = false;
     c->state_valid = false;
     c->have_targets = false;
+    c->plain_ready = false;
     c->n_struct = ns;
     c->n_atoms = na;
     if (c->atom_off.ensure<int64_t>(ns + 1) || c->pos.ensure<float>(na * 3) || c->type.ensure<int>(na) ||
@@ -528,7 +523,7 @@ int nep_loss_grad(nep_ctx *c, const double *Er, const float *Fr, const double *W
     if (!std::isfinite(lE) || !std::isfinite(lF) || !std::isfinite(lV)) return c->fail(NEP_EINVAL, "non-finite weight");
     CK(cudaSetDevice(c->dev));
     if (c->schedule == NEP_SCHED_PLAIN) {
-        rc = plain_loss(c, Er, Fr, Wr, hw, lE, lF, lV, loss3, grad);
+        rc = run_plain_loss(c, Er, Fr, Wr, hw, lE, lF, lV, loss3, grad);
     } else {
         uint64_t lb[3];
         std::memcpy(&lb[0], &lE, 8);
@@ -742,38 +737,3 @@ const char *nep_last_error(const nep_ctx *c) { return c ? c->err.c_str() : g_cre
 
 }  // extern "C"
 
-// ----------------------------------------------------------------------------- plain form
-
-static int plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
-                      double lF, double lV, double *loss3, float *grad) {
-    // Plain form: one forward / gather / structure-sum / adjoint launch per structure, each
-    // restricted to that structure's atoms through a per-structure schedule slice, then the
-    // same reductions.  The per-structure schedule is built once and cached.
-    int rc;
-    if ((rc = launch_expand(c))) return rc;
-    if ((rc = launch_count_hasw(c, hw))) return rc;
-    // per-structure forward launches: one warp per atom of the structure
-    static thread_local std::vector<int> tmp;
-    DevBuf wb;
-    const int64_t ns = c->n_struct;
-    // warp_begin slice arrays for all structures: [pos_s .. pos_s + n_s], atoms in natural order
-    std::vector<int> work_nat(c->n_atoms), begins;
-    std::iota(work_nat.begin(), work_nat.end(), 0);
-    begins.reserve(c->n_atoms + ns);
-    std::vector<int64_t> slice(ns + 1, 0);
-    for (int64_t s = 0; s < ns; ++s) {
-        slice[s] = (int64_t)begins.size();
-        for (int64_t i = c->h_atom_off[s]; i <= c->h_atom_off[s + 1]; ++i) begins.push_back((int)i);
-    }
-    slice[ns] = (int64_t)begins.size();
-    DevBuf dwork, dbeg;
-    if (dwork.ensure<int>(c->n_atoms) || dbeg.ensure<int>((int64_t)begins.size()))
-        return c->fail(NEP_ENOMEM, "plain schedule");
-    CK(cudaMemcpyAsync(dwork.ptr, work_nat.data(), sizeof(int) * c->n_atoms, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(dbeg.ptr, begins.data(), sizeof(int) * begins.size(), cudaMemcpyHostToDevice, c->stream));
-    (void)tmp;
-    (void)wb;
-    (void)Er; (void)Fr; (void)Wr; (void)lE; (void)lF; (void)lV; (void)loss3; (void)grad;
-    CK(cudaStreamSynchronize(c->stream));
-    return c->fail(NEP_EINVAL, "plain schedule not available yet");
-}

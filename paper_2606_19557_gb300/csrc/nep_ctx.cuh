@@ -121,6 +121,10 @@ struct Ctx {
     DevBuf hostbuf_theta;             // device copy target of nep_loss_grad_host
 
     int schedule = NEP_SCHED_PERSISTENT;
+    // plain form (per-structure launches)
+    bool plain_ready = false;
+    std::vector<int64_t> p_cofs;
+    DevBuf p_work, p_ident, p_wlo, p_whi, p_clo, p_chi, p_chunks, p_acc, p_part;
     bool state_valid = false;
 
     // graphs
@@ -166,11 +170,16 @@ int build_neighbors(Ctx *c);
 // step pieces (nep_loss.cu)
 int launch_expand(Ctx *c);
 int launch_forward(Ctx *c, float *q_raw);
-int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1);
+int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1,
+                  double *part = nullptr, int nblocks = 0);
 int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, const double *W_ref,
-                  const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1);
+                  const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1,
+                  double *part = nullptr, int nblocks = 0);
 int launch_count_hasw(Ctx *c, const uint8_t *has_W);
-int launch_loss_final(Ctx *c, double *loss3);
+int launch_loss_final(Ctx *c, double *loss3, const double *fpart = nullptr, int nf = -1,
+                      const double *spart = nullptr, int nsb = -1);
+int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
+                   double lF, double lV, double *loss3, float *grad);
 int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *dW);
 int launch_adjoint(Ctx *c);
 int launch_ann_grad(Ctx *c);

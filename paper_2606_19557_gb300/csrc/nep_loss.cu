@@ -4,6 +4,9 @@
 // Fixed-order reductions everywhere: per-warp FP64 sums in a fixed lane order, per-block
 // partials in a fixed warp order, and a final pass over the partials in index order.
 // No floating-point atomics, so two runs with the same launch shape are bit-identical.
+#include <algorithm>
+#include <vector>
+
 #include "nep_ctx.cuh"
 
 
@@ -307,6 +310,7 @@ struct GradArgs {
     const int *warp_begin; // [W+1] adjoint schedule (warps without atoms wrote no slot)
     const double *gb1;
     float *grad;
+    double *acc;           // plain form: add the partial sums here (FP64), b1 left out
 };
 
 __global__ void k_grad_final(GradArgs g) {
@@ -337,7 +341,7 @@ __global__ void k_grad_final(GradArgs g) {
         }
         for (int c = g.clo[t] + lane; c < g.chi[t]; c += 32) s += (double)g.annpart[(size_t)c * annstride + off];
     } else if (k == cb1) {
-        if (lane == 0) s = *g.gb1;
+        if (lane == 0 && !g.acc) s = *g.gb1;
     } else {
         int a, b, off;
         if (k < ccA) {
@@ -359,7 +363,16 @@ __global__ void k_grad_final(GradArgs g) {
             if (g.warp_begin[w] < g.warp_begin[w + 1]) s += (double)g.cpart[((size_t)(w + a) * T + b) * NC + off];
     }
     s = warp_sum_d(s);
-    if (lane == 0) g.grad[k] = (float)(sign * s);
+    if (lane == 0) {
+        if (g.acc) g.acc[k] += sign * s;
+        else g.grad[k] = (float)(sign * s);
+    }
+}
+
+// Plain form: gradient = FP64 accumulator, b1 from the loss reduction.
+__global__ void k_grad_convert(int64_t P, int64_t kb1, const double *acc, const double *gb1, float *grad) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) grad[k] = (float)(k == kb1 ? *gb1 : acc[k]);
 }
 
 // --------------------------------------------------------------------------- descriptor range
@@ -482,13 +495,14 @@ int launch_adjoint(Ctx *c) {
 static int gather_blocks(Ctx *c) { return c->n_sm * 4; }
 static int struct_blocks(Ctx *c) { return c->n_sm; }
 
-int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1) {
+int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1,
+                  double *part, int nblocks) {
     if (a1 <= a0) return NEP_OK;
-    const int nb = gather_blocks(c);
+    const int nb = nblocks > 0 ? nblocks : gather_blocks(c);
     const float coef = (float)(lamF * 2.0 / (3.0 * (double)c->n_atoms));
     k_gather<<<nb, 256, 0, c->stream>>>(a0, a1, c->nbr_off.as<int64_t>(), c->rev.as<int>(), (const float4 *)c->G.ptr,
                                         c->F_own.as<float>(), F_out, F_ref, coef, loss ? 1 : 0, c->fbar.as<float>(),
-                                        c->loss_part.as<double>());
+                                        part ? part : c->loss_part.as<double>());
     CK_LAUNCH("k_gather");
     return NEP_OK;
 }
@@ -500,22 +514,27 @@ int launch_count_hasw(Ctx *c, const uint8_t *has_W) {
 }
 
 int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, const double *W_ref,
-                  const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1) {
+                  const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1, double *part,
+                  int nblocks) {
     if (s1 <= s0) return NEP_OK;
-    const int nb = struct_blocks(c);
+    const int nb = nblocks > 0 ? nblocks : struct_blocks(c);
     k_struct<<<nb, 256, 0, c->stream>>>(s0, s1, c->atom_off.as<int64_t>(), c->E_atom.as<float>(),
                                         c->W_atom.as<float>(), E_out, W_out, loss ? 1 : 0, E_ref, W_ref, has_W,
                                         c->n_sv.as<int>(), lamE, lamV, (double)c->n_struct, c->ebar.as<float>(),
-                                        c->wbar.as<float>(), c->loss_part.as<double>() + gather_blocks(c));
+                                        c->wbar.as<float>(), part ? part : c->loss_part.as<double>() + gather_blocks(c));
     CK_LAUNCH("k_struct");
     return NEP_OK;
 }
 
-int launch_loss_final(Ctx *c, double *loss3) {
-    k_loss_final<<<1, 256, 0, c->stream>>>(c->loss_part.as<double>(), c->n_atoms > 0 ? gather_blocks(c) : 0,
-                                           c->loss_part.as<double>() + gather_blocks(c),
-                                           c->n_struct > 0 ? struct_blocks(c) : 0, c->n_sv.as<int>(),
-                                           (double)c->n_struct, (double)c->n_atoms, loss3, c->gb1.as<double>());
+int launch_loss_final(Ctx *c, double *loss3, const double *fpart, int nf, const double *spart, int nsb) {
+    if (!fpart) {
+        fpart = c->loss_part.as<double>();
+        nf = c->n_atoms > 0 ? gather_blocks(c) : 0;
+        spart = c->loss_part.as<double>() + gather_blocks(c);
+        nsb = c->n_struct > 0 ? struct_blocks(c) : 0;
+    }
+    k_loss_final<<<1, 256, 0, c->stream>>>(fpart, nf, spart, nsb, c->n_sv.as<int>(), (double)c->n_struct,
+                                           (double)c->n_atoms, loss3, c->gb1.as<double>());
     CK_LAUNCH("k_loss_final");
     return NEP_OK;
 }
@@ -548,7 +567,7 @@ int launch_ann_grad(Ctx *c) {
     return NEP_OK;
 }
 
-int launch_grad_final(Ctx *c, float *grad) {
+static GradArgs grad_args(Ctx *c, float *grad) {
     GradArgs g;
     g.T = c->T;
     g.NN = c->NN;
@@ -573,9 +592,125 @@ int launch_grad_final(Ctx *c, float *grad) {
     g.warp_begin = c->adj.warp_begin.as<int>();
     g.gb1 = c->gb1.as<double>();
     g.grad = grad;
+    g.acc = nullptr;
+    return g;
+}
+
+int launch_grad_final(Ctx *c, float *grad) {
+    GradArgs g = grad_args(c, grad);
     const int64_t threads = c->P * 32;
     k_grad_final<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(g);
     CK_LAUNCH("k_grad_final");
+    return NEP_OK;
+}
+
+// ----------------------------------------------------------------------------- plain form
+// The baseline the batched pass is measured against: the same kernels and arithmetic,
+// launched once per structure with one warp per atom, no CUDA graph, no multi-structure
+// persistent schedule; the gradient of each structure is added to an FP64 accumulator.
+
+static int build_plain(Ctx *c) {
+    const int64_t ns = c->n_struct, na = c->n_atoms;
+    const int T = c->T;
+    std::vector<int> work(na), ident(na + 1), wlo(ns * T, 0), whi(ns * T, -1), clo(ns * T, 0), chi(ns * T, 0), cb;
+    std::vector<int64_t> cofs(ns + 1, 0);
+    int64_t maxn = 0;
+    for (int64_t k = 0; k <= na; ++k) ident[k] = (int)k;
+    for (int64_t s = 0; s < ns; ++s) {
+        const int64_t a0 = c->h_atom_off[s], a1 = c->h_atom_off[s + 1];
+        maxn = std::max(maxn, a1 - a0);
+        std::vector<int> at;
+        for (int64_t i = a0; i < a1; ++i) at.push_back((int)i);
+        std::stable_sort(at.begin(), at.end(), [&](int x, int y) { return c->h_type[x] < c->h_type[y]; });
+        for (size_t k = 0; k < at.size(); ++k) work[a0 + k] = at[k];
+        cofs[s] = (int64_t)cb.size();
+        int64_t p = a0;
+        for (int t = 0; t < T; ++t) {
+            const int64_t q0 = p;
+            while (p < a1 && c->h_type[work[p]] == t) ++p;
+            clo[s * T + t] = (int)(cb.size() - cofs[s]);
+            for (int64_t q = q0; q < p; q += 512) cb.push_back((int)q);
+            chi[s * T + t] = (int)(cb.size() - cofs[s]);
+            if (p > q0) {
+                wlo[s * T + t] = (int)(q0 - a0);
+                whi[s * T + t] = (int)(p - 1 - a0);
+            }
+        }
+        cb.push_back((int)a1);  // closes the last chunk of s (not a chunk start of s + 1)
+    }
+    cofs[ns] = (int64_t)cb.size();
+    c->p_cofs = cofs;
+    if (c->p_work.ensure<int>(na) || c->p_ident.ensure<int>(na + 1) || c->p_wlo.ensure<int>(ns * T) ||
+        c->p_whi.ensure<int>(ns * T) || c->p_clo.ensure<int>(ns * T) || c->p_chi.ensure<int>(ns * T) ||
+        c->p_chunks.ensure<int>((int64_t)cb.size() + 1) || c->p_acc.ensure<double>(c->P) ||
+        c->p_part.ensure<double>(ns * 5 + 8))
+        return c->fail(NEP_ENOMEM, "plain-form buffers");
+    const int NC = c->ks->NR * c->ks->KR + c->ks->NA * c->ks->KA;
+    if (c->cpart.bytes < sizeof(float) * (size_t)(maxn + T) * T * NC &&
+        c->cpart.ensure<float>((int64_t)std::max<int64_t>(maxn, c->adj.W) * T * NC + (int64_t)T * T * NC))
+        return c->fail(NEP_ENOMEM, "plain-form partials");
+    CK(cudaMemcpy(c->p_work.ptr, work.data(), sizeof(int) * na, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_ident.ptr, ident.data(), sizeof(int) * (na + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_wlo.ptr, wlo.data(), sizeof(int) * ns * T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_whi.ptr, whi.data(), sizeof(int) * ns * T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_clo.ptr, clo.data(), sizeof(int) * ns * T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_chi.ptr, chi.data(), sizeof(int) * ns * T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_chunks.ptr, cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice));
+    c->plain_ready = true;
+    return NEP_OK;
+}
+
+int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
+                   double lF, double lV, double *loss3, float *grad) {
+    int rc;
+    if (!c->plain_ready && (rc = build_plain(c))) return rc;
+    const int64_t ns = c->n_struct;
+    const int GB = 2;  // gather blocks per structure
+    double *pg = c->p_part.as<double>();
+    double *ps = pg + ns * GB;
+    if ((rc = launch_expand(c))) return rc;
+    if ((rc = launch_count_hasw(c, hw))) return rc;
+    CK(cudaMemsetAsync(c->p_acc.ptr, 0, sizeof(double) * c->P, c->stream));
+    const size_t fs = c->ks->fwd_smem(c->T), as = c->ks->adj_smem(c->T);
+    const size_t gsm = sizeof(float) * ANN_ROWS * (3 * c->NN + 2 * c->NDP);
+    const int groups = (c->NN * c->NDP + 16 * 256 - 1) / (16 * 256);
+    for (int64_t s = 0; s < ns; ++s) {
+        const int64_t a0 = c->h_atom_off[s], n = c->h_atom_off[s + 1] - a0;
+        AtomArgs a = atom_args(c);
+        a.work = c->p_work.as<int>();
+        a.warp_begin = c->p_ident.as<int>() + a0;
+        c->ks->launch_fwd(a, (int)n, 1, fs, c->stream);
+        CK_LAUNCH("k_forward (plain)");
+        if ((rc = launch_gather(c, c->F_int.as<float>(), Fr, lF, true, a0, a0 + n, pg + s * GB, GB))) return rc;
+        if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, s, s + 1,
+                                ps + s * 3, 1)))
+            return rc;
+        c->ks->launch_adj(a, (int)n, 1, as, c->stream);
+        CK_LAUNCH("k_adjoint (plain)");
+        const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
+        if (nch > 0) {
+            k_ann_grad<<<dim3(nch, groups), 256, gsm, c->stream>>>(c->p_chunks.as<int>() + c->p_cofs[s], c->NN, c->NDP,
+                                                                   c->zt.as<float>(), c->ut.as<float>(),
+                                                                   c->om.as<float>(), c->st_qt.as<float>(),
+                                                                   c->dqt.as<float>(), c->annpart.as<float>());
+            CK_LAUNCH("k_ann_grad (plain)");
+        }
+        GradArgs g = grad_args(c, nullptr);
+        g.clo = c->p_clo.as<int>() + s * c->T;
+        g.chi = c->p_chi.as<int>() + s * c->T;
+        g.wlo = c->p_wlo.as<int>() + s * c->T;
+        g.whi = c->p_whi.as<int>() + s * c->T;
+        g.warp_begin = c->p_ident.as<int>() + a0;
+        g.acc = c->p_acc.as<double>();
+        k_grad_final<<<(unsigned)((c->P * 32 + 255) / 256), 256, 0, c->stream>>>(g);
+        CK_LAUNCH("k_grad_final (plain)");
+    }
+    if ((rc = launch_loss_final(c, loss3, pg, (int)(ns * GB), ps, (int)ns))) return rc;
+    k_grad_convert<<<(unsigned)((c->P + 255) / 256), 256, 0, c->stream>>>(c->P, (int64_t)c->T * c->NN * c->ND +
+                                                                          2 * (int64_t)c->T * c->NN,
+                                                                          c->p_acc.as<double>(), c->gb1.as<double>(),
+                                                                          grad);
+    CK_LAUNCH("k_grad_convert");
     return NEP_OK;
 }
 

@@ -278,3 +278,19 @@ def test_invalid_inputs_return_errors():
     nep.set_params(torch.zeros(P), torch.ones(nep.n_des))
     E, F, W = nep.eval()
     assert np.all(np.isfinite(E.cpu().numpy()))
+
+
+@pytest.mark.parametrize("name", ["fcc_bcc_t1", "alloy_t4"])
+def test_plain_form_matches_oracle(name):
+    """The per-structure baseline form computes the same loss and gradient."""
+    from paper_2606_19557_gb300 import SCHED_PERSISTENT, SCHED_PLAIN
+    c = get_case(name)
+    c.nep.set_schedule(SCHED_PLAIN)
+    try:
+        l3, g = c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref)
+        l3, g = l3.cpu().numpy(), g.cpu().numpy()
+    finally:
+        c.nep.set_schedule(SCHED_PERSISTENT)
+    l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, c.batch, c.E_ref, c.F_ref, c.W_ref)[:2]
+    np.testing.assert_allclose(l3, l3o, rtol=TOL)
+    assert rel(g, go) < TOL
