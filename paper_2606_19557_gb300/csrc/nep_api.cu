@@ -48,7 +48,8 @@ static int check_cfg(const nep_config *c, std::string &why) {
 
 // Static schedule of one per-atom kernel: contiguous ranges of the species-sorted work
 // order with about equal cost per warp (cost ~ radial pairs + 6 x angular pairs + 8).
-static int make_sched(Ctx *c, Sched &s, int wpb, int blocks) {
+static int make_sched(Ctx *c, Sched &s, int wpb, int blocks, int var) {
+    s.var = var;
     s.wpb = wpb;
     s.blocks = blocks;
     s.W = wpb * blocks;
@@ -113,8 +114,10 @@ static int set_smem_attr(Ctx *c) {
     CK(cudaDeviceGetAttribute(&maxo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
     if (c->ks->fwd_smem(c->T) > (size_t)maxo || c->ks->adj_smem(c->T) > (size_t)maxo)
         return c->fail(NEP_EINVAL, "model too large for shared memory");
-    CK(cudaFuncSetAttribute(c->ks->fwd_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
-    CK(cudaFuncSetAttribute(c->ks->adj_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+    for (int v = 0; v < 2; ++v) {
+        CK(cudaFuncSetAttribute(c->ks->fwd_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+        CK(cudaFuncSetAttribute(c->ks->adj_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+    }
     return NEP_OK;
 }
 
@@ -131,11 +134,11 @@ static int default_shapes(Ctx *c) {
     if (rc) return rc;
     if ((rc = prepare_loss_kernels(c))) return rc;
     const int wpb = 4;
-    int bf = max_blocks_per_sm(c, c->ks->fwd_fn, wpb, c->ks->fwd_smem(c->T) * wpb);
-    int ba = max_blocks_per_sm(c, c->ks->adj_fn, wpb, c->ks->adj_smem(c->T) * wpb);
+    int bf = max_blocks_per_sm(c, c->ks->fwd_fn[0], wpb, c->ks->fwd_smem(c->T) * wpb);
+    int ba = max_blocks_per_sm(c, c->ks->adj_fn[0], wpb, c->ks->adj_smem(c->T) * wpb);
     if (bf < 1 || ba < 1) return c->fail(NEP_EINVAL, "kernel does not fit on the device (shared memory)");
-    if ((rc = make_sched(c, c->fwd, wpb, c->n_sm * bf))) return rc;
-    if ((rc = make_sched(c, c->adj, wpb, c->n_sm * ba))) return rc;
+    if ((rc = make_sched(c, c->fwd, wpb, c->n_sm * bf, 0))) return rc;
+    if ((rc = make_sched(c, c->adj, wpb, c->n_sm * ba, 0))) return rc;
     return alloc_sched_buffers(c);
 }
 
@@ -617,13 +620,14 @@ int nep_set_launch(nep_ctx *c, int fw, int fb, int aw, int ab) {
     int rc;
     fw = fw ? fw : c->fwd.wpb;
     aw = aw ? aw : c->adj.wpb;
-    const int mf = max_blocks_per_sm(c, c->ks->fwd_fn, fw, c->ks->fwd_smem(c->T) * fw);
-    const int ma = max_blocks_per_sm(c, c->ks->adj_fn, aw, c->ks->adj_smem(c->T) * aw);
+    const int vf = fw > c->ks->max_wpb[0] ? 1 : c->fwd.var, va = aw > c->ks->max_wpb[0] ? 1 : c->adj.var;
+    const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[vf], fw, c->ks->fwd_smem(c->T) * fw);
+    const int ma = max_blocks_per_sm(c, c->ks->adj_fn[va], aw, c->ks->adj_smem(c->T) * aw);
     if (mf < 1 || ma < 1) return c->fail(NEP_EINVAL, "launch shape does not fit");
     fb = fb ? fb : c->n_sm * mf;
     ab = ab ? ab : c->n_sm * ma;
-    if ((rc = make_sched(c, c->fwd, fw, fb))) return rc;
-    if ((rc = make_sched(c, c->adj, aw, ab))) return rc;
+    if ((rc = make_sched(c, c->fwd, fw, fb, vf))) return rc;
+    if ((rc = make_sched(c, c->adj, aw, ab, va))) return rc;
     if ((rc = alloc_sched_buffers(c))) return rc;
     drop_graphs(c);
     c->state_valid = false;
@@ -650,64 +654,67 @@ int nep_autotune(nep_ctx *c) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best_f = 1e30f, best_a = 1e30f;
-    int bfw = c->fwd.wpb, bfb = c->fwd.blocks, baw = c->adj.wpb, bab = c->adj.blocks;
+    int bfw = c->fwd.wpb, bfb = c->fwd.blocks, bfv = c->fwd.var, baw = c->adj.wpb, bab = c->adj.blocks, bav = c->adj.var;
     const int wpbs[3] = {2, 4, 8};
-    for (int wpb : wpbs) {
-        const int mf = max_blocks_per_sm(c, c->ks->fwd_fn, wpb, c->ks->fwd_smem(c->T) * wpb);
-        const int ma = max_blocks_per_sm(c, c->ks->adj_fn, wpb, c->ks->adj_smem(c->T) * wpb);
-        for (int bps = 1; bps <= std::max(mf, ma); ++bps) {
-            const bool tf = bps <= mf, ta = bps <= ma;
-            if (tf) {
-                if ((rc = make_sched(c, c->fwd, wpb, c->n_sm * bps))) break;
-            }
-            if (ta) {
-                if ((rc = make_sched(c, c->adj, wpb, c->n_sm * bps))) break;
-                if ((rc = alloc_sched_buffers(c))) break;
-            }
-            if ((rc = body_loss(c, zE.as<double>(), zF.as<float>(), zW.as<double>(), nullptr, 1.0, 1.0, 1.0,
-                                l3.as<double>(), gr.as<float>())))
-                break;
-            float tbest_f = 1e30f, tbest_a = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                if (tf) {
-                    CK(cudaEventRecord(e0, c->stream));
-                    if ((rc = launch_forward(c, nullptr))) break;
-                    CK(cudaEventRecord(e1, c->stream));
-                    CK(cudaEventSynchronize(e1));
-                    float ms = 0;
-                    CK(cudaEventElapsedTime(&ms, e0, e1));
-                    tbest_f = std::min(tbest_f, ms);
-                }
+    for (int var = 0; var < 2 && !rc; ++var) {
+        for (int wpb : wpbs) {
+            if (wpb > c->ks->max_wpb[var]) continue;
+            const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[var], wpb, c->ks->fwd_smem(c->T) * wpb);
+            const int ma = max_blocks_per_sm(c, c->ks->adj_fn[var], wpb, c->ks->adj_smem(c->T) * wpb);
+            for (int bps = 1; bps <= std::max(mf, ma); ++bps) {
+                const bool tf = bps <= mf, ta = bps <= ma;
+                if (tf && (rc = make_sched(c, c->fwd, wpb, c->n_sm * bps, var))) break;
                 if (ta) {
-                    CK(cudaEventRecord(e0, c->stream));
-                    if ((rc = launch_adjoint(c))) break;
-                    CK(cudaEventRecord(e1, c->stream));
-                    CK(cudaEventSynchronize(e1));
-                    float ms = 0;
-                    CK(cudaEventElapsedTime(&ms, e0, e1));
-                    tbest_a = std::min(tbest_a, ms);
+                    if ((rc = make_sched(c, c->adj, wpb, c->n_sm * bps, var))) break;
+                    if ((rc = alloc_sched_buffers(c))) break;
+                }
+                if ((rc = body_loss(c, zE.as<double>(), zF.as<float>(), zW.as<double>(), nullptr, 1.0, 1.0, 1.0,
+                                    l3.as<double>(), gr.as<float>())))
+                    break;
+                float tbest_f = 1e30f, tbest_a = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    if (tf) {
+                        CK(cudaEventRecord(e0, c->stream));
+                        if ((rc = launch_forward(c, nullptr))) break;
+                        CK(cudaEventRecord(e1, c->stream));
+                        CK(cudaEventSynchronize(e1));
+                        float ms = 0;
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        tbest_f = std::min(tbest_f, ms);
+                    }
+                    if (ta) {
+                        CK(cudaEventRecord(e0, c->stream));
+                        if ((rc = launch_adjoint(c))) break;
+                        CK(cudaEventRecord(e1, c->stream));
+                        CK(cudaEventSynchronize(e1));
+                        float ms = 0;
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        tbest_a = std::min(tbest_a, ms);
+                    }
+                }
+                if (rc) break;
+                if (tf && tbest_f < best_f) {
+                    best_f = tbest_f;
+                    bfw = wpb;
+                    bfb = c->n_sm * bps;
+                    bfv = var;
+                }
+                if (ta && tbest_a < best_a) {
+                    best_a = tbest_a;
+                    baw = wpb;
+                    bab = c->n_sm * bps;
+                    bav = var;
                 }
             }
             if (rc) break;
-            if (tf && tbest_f < best_f) {
-                best_f = tbest_f;
-                bfw = wpb;
-                bfb = c->n_sm * bps;
-            }
-            if (ta && tbest_a < best_a) {
-                best_a = tbest_a;
-                baw = wpb;
-                bab = c->n_sm * bps;
-            }
         }
-        if (rc) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->timing = tsave;
     if (rc) return rc;
-    if ((rc = make_sched(c, c->fwd, bfw, bfb))) return rc;
-    if ((rc = make_sched(c, c->adj, baw, bab))) return rc;
+    if ((rc = make_sched(c, c->fwd, bfw, bfb, bfv))) return rc;
+    if ((rc = make_sched(c, c->adj, baw, bab, bav))) return rc;
     if ((rc = alloc_sched_buffers(c))) return rc;
     drop_graphs(c);
     c->state_valid = false;

@@ -46,6 +46,7 @@ struct DevBuf {
 
 // Launch shape of one per-atom kernel and its static schedule.
 struct Sched {
+    int var = 0;         // register-budget variant of the kernel (KernelSet)
     int wpb = 4;         // warps per block
     int blocks = 0;      // grid size
     int W = 0;           // total warps
@@ -61,12 +62,13 @@ struct Ctx;
 // Per-bucket kernel entry points (compile-time shapes).
 struct KernelSet {
     int NR, KR, NA, KA;
-    const void *fwd_fn;
-    const void *adj_fn;
+    const void *fwd_fn[2];      // register-budget variants 0 (168 regs) and 1 (128 regs)
+    const void *adj_fn[2];
+    int max_wpb[2];             // largest warps per block each variant allows
     size_t (*fwd_smem)(int T);  // bytes per warp
     size_t (*adj_smem)(int T);
-    void (*launch_fwd)(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
-    void (*launch_adj)(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
+    void (*launch_fwd[2])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
+    void (*launch_adj[2])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
 };
 
 const KernelSet *select_kernels(int nR, int kR, int nA, int kA);

@@ -321,6 +321,43 @@ __device__ __forceinline__ void ylm_grad(float x, float y, float z, float *gx, f
     gz[23] = 0.0f;
 }
 
+// Calls f(lm, Y_lm, dP/dx, dP/dy, dP/dz) for lm = 0..23 with the same polynomials as
+// ylm_val / ylm_grad, one (l, m) at a time, so that callers keep only running sums live.
+template <class F>
+__device__ __forceinline__ void ylm_each(float x, float y, float z, F &&f) {
+    const float x2 = x * x, y2 = y * y, z2 = z * z;
+    const float xy = x * y, yz = y * z, xz = x * z;
+    const float a5 = 5.0f * z2 - 1.0f, b7 = 7.0f * z2 - 1.0f, c7 = 7.0f * z2 - 3.0f;
+    const float d2 = x2 - y2;
+    f(0, YlmC::c1 * y, 0.0f, YlmC::c1, 0.0f);
+    f(1, YlmC::c1 * z, 0.0f, 0.0f, YlmC::c1);
+    f(2, YlmC::c1 * x, YlmC::c1, 0.0f, 0.0f);
+    f(3, YlmC::c2a * xy, YlmC::c2a * y, YlmC::c2a * x, 0.0f);
+    f(4, YlmC::c2a * yz, 0.0f, YlmC::c2a * z, YlmC::c2a * y);
+    f(5, YlmC::c2b * (3.0f * z2 - 1.0f), 0.0f, 0.0f, YlmC::c2b * 6.0f * z);
+    f(6, YlmC::c2a * xz, YlmC::c2a * z, 0.0f, YlmC::c2a * x);
+    f(7, YlmC::c2c * d2, YlmC::c2c * 2.0f * x, -YlmC::c2c * 2.0f * y, 0.0f);
+    f(8, YlmC::c3a * y * (3.0f * x2 - y2), YlmC::c3a * 6.0f * xy, YlmC::c3a * 3.0f * d2, 0.0f);
+    f(9, YlmC::c3b * xy * z, YlmC::c3b * yz, YlmC::c3b * xz, YlmC::c3b * xy);
+    f(10, YlmC::c3c * y * a5, 0.0f, YlmC::c3c * a5, YlmC::c3c * 10.0f * yz);
+    f(11, YlmC::c3d * z * (5.0f * z2 - 3.0f), 0.0f, 0.0f, YlmC::c3d * (15.0f * z2 - 3.0f));
+    f(12, YlmC::c3c * x * a5, YlmC::c3c * a5, 0.0f, YlmC::c3c * 10.0f * xz);
+    f(13, YlmC::c3e * z * d2, YlmC::c3e * 2.0f * xz, -YlmC::c3e * 2.0f * yz, YlmC::c3e * d2);
+    f(14, YlmC::c3a * x * (x2 - 3.0f * y2), YlmC::c3a * 3.0f * d2, -YlmC::c3a * 6.0f * xy, 0.0f);
+    f(15, YlmC::c4a * xy * d2, YlmC::c4a * y * (3.0f * x2 - y2), YlmC::c4a * x * (x2 - 3.0f * y2), 0.0f);
+    f(16, YlmC::c4b * yz * (3.0f * x2 - y2), YlmC::c4b * 6.0f * xy * z, YlmC::c4b * 3.0f * z * d2,
+      YlmC::c4b * y * (3.0f * x2 - y2));
+    f(17, YlmC::c4c * xy * b7, YlmC::c4c * y * b7, YlmC::c4c * x * b7, YlmC::c4c * 14.0f * xy * z);
+    f(18, YlmC::c4d * yz * c7, 0.0f, YlmC::c4d * z * c7, YlmC::c4d * y * (21.0f * z2 - 3.0f));
+    f(19, YlmC::c4e * ((35.0f * z2 - 30.0f) * z2 + 3.0f), 0.0f, 0.0f, YlmC::c4e * (140.0f * z2 - 60.0f) * z);
+    f(20, YlmC::c4d * xz * c7, YlmC::c4d * z * c7, 0.0f, YlmC::c4d * x * (21.0f * z2 - 3.0f));
+    f(21, YlmC::c4f * d2 * b7, YlmC::c4f * 2.0f * x * b7, -YlmC::c4f * 2.0f * y * b7, YlmC::c4f * 14.0f * z * d2);
+    f(22, YlmC::c4b * xz * (x2 - 3.0f * y2), YlmC::c4b * 3.0f * z * d2, -YlmC::c4b * 6.0f * xy * z,
+      YlmC::c4b * x * (x2 - 3.0f * y2));
+    f(23, YlmC::c4g * (x2 * (x2 - 3.0f * y2) - y2 * (3.0f * x2 - y2)), YlmC::c4g * 4.0f * x * (x2 - 3.0f * y2),
+      YlmC::c4g * 4.0f * y * (y2 - 3.0f * x2), 0.0f);
+}
+
 __device__ __forceinline__ int l_of_lm(int lm) { return lm < 3 ? 1 : lm < 8 ? 2 : lm < 15 ? 3 : 4; }
 
 // 4-body scale in the real l = 2 basis.  The descriptor is the (2 2 2) Wigner-3j

@@ -477,7 +477,7 @@ int launch_forward(Ctx *c, float *q_raw) {
     a.warp_begin = c->fwd.warp_begin.as<int>();
     a.q_raw = q_raw;
     const size_t smem = c->ks->fwd_smem(c->T) * c->fwd.wpb;
-    c->ks->launch_fwd(a, c->fwd.blocks, c->fwd.wpb, smem, c->stream);
+    c->ks->launch_fwd[c->fwd.var](a, c->fwd.blocks, c->fwd.wpb, smem, c->stream);
     CK_LAUNCH("k_forward");
     return NEP_OK;
 }
@@ -487,7 +487,7 @@ int launch_adjoint(Ctx *c) {
     AtomArgs a = atom_args(c);
     a.warp_begin = c->adj.warp_begin.as<int>();
     const size_t smem = c->ks->adj_smem(c->T) * c->adj.wpb;
-    c->ks->launch_adj(a, c->adj.blocks, c->adj.wpb, smem, c->stream);
+    c->ks->launch_adj[c->adj.var](a, c->adj.blocks, c->adj.wpb, smem, c->stream);
     CK_LAUNCH("k_adjoint");
     return NEP_OK;
 }
@@ -679,13 +679,13 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         AtomArgs a = atom_args(c);
         a.work = c->p_work.as<int>();
         a.warp_begin = c->p_ident.as<int>() + a0;
-        c->ks->launch_fwd(a, (int)n, 1, fs, c->stream);
+        c->ks->launch_fwd[0](a, (int)n, 1, fs, c->stream);
         CK_LAUNCH("k_forward (plain)");
         if ((rc = launch_gather(c, c->F_int.as<float>(), Fr, lF, true, a0, a0 + n, pg + s * GB, GB))) return rc;
         if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, s, s + 1,
                                 ps + s * 3, 1)))
             return rc;
-        c->ks->launch_adj(a, (int)n, 1, as, c->stream);
+        c->ks->launch_adj[0](a, (int)n, 1, as, c->stream);
         CK_LAUNCH("k_adjoint (plain)");
         const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
         if (nch > 0) {

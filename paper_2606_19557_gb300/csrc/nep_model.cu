@@ -59,11 +59,11 @@ struct AdjSm {
 
 template <class S>
 __host__ __device__ size_t fwd_smem_bytes(int T) {
-    return ((sizeof(FwdSm<S>) + sizeof(float) * 2 * T * S::KR) + 15) & ~(size_t)15;
+    return ((sizeof(FwdSm<S>) + sizeof(float) * T * (2 * S::KR + S::NC)) + 15) & ~(size_t)15;
 }
 template <class S>
 __host__ __device__ size_t adj_smem_bytes(int T) {
-    return ((sizeof(AdjSm<S>) + sizeof(float) * T * (2 * S::KR + S::NCR + S::NCA)) + 15) & ~(size_t)15;
+    return ((sizeof(AdjSm<S>) + sizeof(float) * T * (2 * S::KR + S::NCR + S::NCA + S::NC)) + 15) & ~(size_t)15;
 }
 
 // Adds the lane-distributed totals of a reduce_scatter<V> to dst[0..K).
@@ -80,8 +80,10 @@ __device__ __forceinline__ void flush_add(float *v, float *dst, int K, int lane)
 
 // ============================================================================= forward
 
-template <class S>
-__global__ void __launch_bounds__(256) k_forward(AtomArgs a) {
+// VAR selects the register budget: 0 -> at most 128 threads x 3 blocks per SM (168
+// registers), 1 -> 256 threads x 2 blocks (128 registers); the autotuner times both.
+template <class S, int VAR>
+__global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forward(AtomArgs a) {
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int SGS = FwdSm<S>::SGS;
     constexpr int VR = pow2ceil(KR);
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(256) k_forward(AtomArgs a) {
     FwdSm<S> &sm = *reinterpret_cast<FwdSm<S> *>(base);
     float *Sr = base + sizeof(FwdSm<S>) / sizeof(float);  // [T][KR]
     float *beta = Sr + a.T * KR;                            // [T][KR]
+    float *cw = beta + a.T * KR;                            // [T][NCR] | [T][NCA] of the current species
 
     const int w = blockIdx.x * (blockDim.x >> 5) + wib;
     const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
@@ -103,14 +106,22 @@ __global__ void __launch_bounds__(256) k_forward(AtomArgs a) {
     const float *w1 = a.par + po.w1;
     const float b1 = a.par[po.b1];
     const float *scale = a.par + po.scale;
+    int cur_t = -1;
 
     for (int wi = wbeg; wi < wend; ++wi) {
         const int i = a.work[wi];
         const int ti = a.type[i];
         const int64_t beg = a.nbr_off[i], end = a.nbr_off[i + 1];
         const int64_t endA = beg + a.n_ang[i];
-        const float *cRi = a.par + po.cR + (size_t)ti * T * S::NCR;
-        const float *cAi = a.par + po.cA + (size_t)ti * T * S::NCA;
+        if (ti != cur_t) {  // species-sorted work: rare
+            __syncwarp();
+            for (int e = lane; e < T * S::NCR; e += 32) cw[e] = a.par[po.cR + (size_t)ti * T * S::NCR + e];
+            for (int e = lane; e < T * S::NCA; e += 32) cw[T * S::NCR + e] = a.par[po.cA + (size_t)ti * T * S::NCA + e];
+            cur_t = ti;
+            __syncwarp();
+        }
+        const float *cRi = cw;
+        const float *cAi = cw + T * S::NCR;
 
         // ---------------------------------------------------------------- angular moments A_nlm
         float accA[NA];
@@ -302,12 +313,8 @@ __global__ void __launch_bounds__(256) k_forward(AtomArgs a) {
                 g[n] = s0;
                 gp[n] = s1;
             }
-            float Y[L3], gx[L3], gy[L3], gz[L3];
-            ylm_val(ux, uy, uz, Y);
-            ylm_grad(ux, uy, uz, gx, gy, gz);
             float srad = 0.0f, Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
-#pragma unroll
-            for (int lm = 0; lm < L3; ++lm) {
+            ylm_each(ux, uy, uz, [&](int lm, float Y, float gx, float gy, float gz) {
                 float a1 = 0.0f, a2 = 0.0f;
 #pragma unroll
                 for (int n = 0; n < NA; ++n) {
@@ -315,11 +322,11 @@ __global__ void __launch_bounds__(256) k_forward(AtomArgs a) {
                     a1 += ah * g[n];
                     a2 += ah * gp[n];
                 }
-                srad += a2 * Y[lm];
-                Vx += a1 * gx[lm];
-                Vy += a1 * gy[lm];
-                Vz += a1 * gz[lm];
-            }
+                srad += a2 * Y;
+                Vx += a1 * gx;
+                Vy += a1 * gy;
+                Vz += a1 * gz;
+            });
             const float uv = ux * Vx + uy * Vy + uz * Vz;
             const float Gx = srad * ux + (Vx - ux * uv) * rinv;
             const float Gy = srad * uy + (Vy - uy * uv) * rinv;
@@ -383,8 +390,8 @@ __global__ void __launch_bounds__(256) k_forward(AtomArgs a) {
 
 // ============================================================================= adjoint
 
-template <class S>
-__global__ void __launch_bounds__(256) k_adjoint(AtomArgs a) {
+template <class S, int VAR>
+__global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjoint(AtomArgs a) {
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int NCR = S::NCR, NCA = S::NCA, NC = S::NC;
     constexpr int SGS = AdjSm<S>::SGS;
@@ -399,6 +406,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AtomArgs a) {
     float *Sr = base + sizeof(AdjSm<S>) / sizeof(float);  // [T][2 KR]: S^b_k | S'^b_k
     float *accR = Sr + T * 2 * KR;                          // [T][NCR]
     float *accA = accR + T * NCR;                           // [T][NCA]
+    float *cw = accA + T * NCA;                             // [T][NCR] | [T][NCA] of the current species
 
     const int w = blockIdx.x * (blockDim.x >> 5) + wib;
     const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
@@ -425,14 +433,16 @@ __global__ void __launch_bounds__(256) k_adjoint(AtomArgs a) {
             if (cur_t >= 0) flush_slot(cur_t);
             for (int e = lane; e < T * NCR; e += 32) accR[e] = 0.0f;
             for (int e = lane; e < T * NCA; e += 32) accA[e] = 0.0f;
+            for (int e = lane; e < T * NCR; e += 32) cw[e] = a.par[po.cR + (size_t)ti * T * NCR + e];
+            for (int e = lane; e < T * NCA; e += 32) cw[T * NCR + e] = a.par[po.cA + (size_t)ti * T * NCA + e];
             cur_t = ti;
             __syncwarp();
         }
         const int s = a.struct_of[i];
         const int64_t beg = a.nbr_off[i], end = a.nbr_off[i + 1];
         const int64_t endA = beg + a.n_ang[i];
-        const float *cRi = a.par + po.cR + (size_t)ti * T * NCR;
-        const float *cAi = a.par + po.cA + (size_t)ti * T * NCA;
+        const float *cRi = cw;
+        const float *cAi = cw + T * NCR;
 
         // ---------------------------------------------------------------- state of the forward pass
         for (int e = lane; e < ND; e += 32) sm.qt[e] = a.st_qt[(size_t)wi * ND + e];
@@ -519,14 +529,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AtomArgs a) {
                     sm.sg[lane * SGS + n] = s0;
                     sm.sgp[lane * SGS + n] = s1 * rl;
                 }
-                float Y[L3], gx[L3], gy[L3], gz[L3];
-                ylm_val(ux, uy, uz, Y);
-                ylm_grad(ux, uy, uz, gx, gy, gz);
-#pragma unroll
-                for (int lm = 0; lm < L3; ++lm) {
-                    sm.sY[lane * 25 + lm] = Y[lm];
-                    sm.sP[lane * 25 + lm] = gx[lm] * px + gy[lm] * py + gz[lm] * pz;
-                }
+                ylm_each(ux, uy, uz, [&](int lm, float Y, float gx, float gy, float gz) {
+                    sm.sY[lane * 25 + lm] = Y;
+                    sm.sP[lane * 25 + lm] = gx * px + gy * py + gz * pz;
+                });
             }
             __syncwarp();
             const int cnt = (int)min((int64_t)32, endA - c0);
@@ -722,19 +728,15 @@ __global__ void __launch_bounds__(256) k_adjoint(AtomArgs a) {
                     const float rl = ux * lx + uy * ly + uz * lz;
                     const float px = (lx - rl * ux) * rinv, py = (ly - rl * uy) * rinv, pz = (lz - rl * uz) * rinv;
                     basis_val_der<KA>(r, a.inv_rcA, f, fp);
-                    float Y[L3], gx[L3], gy[L3], gz[L3];
-                    ylm_val(ux, uy, uz, Y);
-                    ylm_grad(ux, uy, uz, gx, gy, gz);
-#pragma unroll
-                    for (int lm = 0; lm < L3; ++lm) {
-                        const float ps = gx[lm] * px + gy[lm] * py + gz[lm] * pz;
+                    ylm_each(ux, uy, uz, [&](int lm, float Y, float gx, float gy, float gz) {
+                        const float ps = gx * px + gy * py + gz * pz;
 #pragma unroll
                         for (int n = 0; n < NA; ++n) {
                             const float ah = sm.Ah[n * L3 + lm];
-                            al[n] += sm.Ab[n * L3 + lm] * Y[lm] + ah * ps;
-                            be[n] += ah * Y[lm];
+                            al[n] += sm.Ab[n * L3 + lm] * Y + ah * ps;
+                            be[n] += ah * Y;
                         }
-                    }
+                    });
 #pragma unroll
                     for (int n = 0; n < NA; ++n) be[n] *= rl;
                 }
@@ -768,13 +770,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AtomArgs a) {
 
 // ============================================================================= dispatch
 
-template <class S>
+template <class S, int VAR>
 void launch_fwd_t(const AtomArgs &a, int blocks, int wpb, size_t smem, cudaStream_t st) {
-    k_forward<S><<<blocks, wpb * 32, smem, st>>>(a);
+    k_forward<S, VAR><<<blocks, wpb * 32, smem, st>>>(a);
 }
-template <class S>
+template <class S, int VAR>
 void launch_adj_t(const AtomArgs &a, int blocks, int wpb, size_t smem, cudaStream_t st) {
-    k_adjoint<S><<<blocks, wpb * 32, smem, st>>>(a);
+    k_adjoint<S, VAR><<<blocks, wpb * 32, smem, st>>>(a);
 }
 
 template <int NR, int KR, int NA, int KA>
@@ -785,12 +787,18 @@ KernelSet make_set() {
     k.KR = KR;
     k.NA = NA;
     k.KA = KA;
-    k.fwd_fn = (const void *)k_forward<S>;
-    k.adj_fn = (const void *)k_adjoint<S>;
+    k.fwd_fn[0] = (const void *)k_forward<S, 0>;
+    k.fwd_fn[1] = (const void *)k_forward<S, 1>;
+    k.adj_fn[0] = (const void *)k_adjoint<S, 0>;
+    k.adj_fn[1] = (const void *)k_adjoint<S, 1>;
+    k.max_wpb[0] = 4;
+    k.max_wpb[1] = 8;
     k.fwd_smem = fwd_smem_bytes<S>;
     k.adj_smem = adj_smem_bytes<S>;
-    k.launch_fwd = launch_fwd_t<S>;
-    k.launch_adj = launch_adj_t<S>;
+    k.launch_fwd[0] = launch_fwd_t<S, 0>;
+    k.launch_fwd[1] = launch_fwd_t<S, 1>;
+    k.launch_adj[0] = launch_adj_t<S, 0>;
+    k.launch_adj[1] = launch_adj_t<S, 1>;
     return k;
 }
 
