@@ -270,7 +270,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "structures_per_gpu": batch.n_struct, "atoms_per_gpu": batch.n_atoms,
                    "radial_pairs": n_rad, "angular_pairs": n_ang, "l2": "flushed (256 MB write) between steps",
-                   "launch_shape": list(shape), "neighbor_build_ms": 1e3 * t_nbr2},
+                   "launch_shape": list(shape), "kernel_variant": list(nep.variant()),
+                   "neighbor_build_ms": 1e3 * t_nbr2},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},

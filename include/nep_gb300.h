@@ -75,7 +75,9 @@ typedef struct {
 } nep_config;
 
 /* Creates a context on cfg->device that queues its work on `cuda_stream` (a
- * cudaStream_t; NULL = the legacy default stream).  *out receives the handle.
+ * cudaStream_t).  With NULL the context creates a non-blocking stream of its own
+ * (destroyed with it); the legacy default stream cannot be used because the loss
+ * pass is captured into a CUDA graph.  *out receives the handle.
  * Errors: NEP_EINVAL (sizes outside the limits above), NEP_ECUDA, NEP_ENOMEM. */
 int nep_create(const nep_config *cfg, void *cuda_stream, nep_ctx **out);
 
@@ -178,6 +180,10 @@ int nep_autotune(nep_ctx *ctx);
 
 /* Current launch shape: warps per block and blocks of the forward and adjoint kernels. */
 int nep_get_launch(const nep_ctx *ctx, int *fwd_warps, int *fwd_blocks, int *adj_warps, int *adj_blocks);
+
+/* Kernel variant of the forward and adjoint kernels: lanes that share one atom (8 or 16)
+ * and the register budget per thread (168 or 128). */
+int nep_get_variant(const nep_ctx *ctx, int *fwd_lanes, int *fwd_regs, int *adj_lanes, int *adj_regs);
 
 /* Sets the launch shape explicitly (0 keeps a value). */
 int nep_set_launch(nep_ctx *ctx, int fwd_warps, int fwd_blocks, int adj_warps, int adj_blocks);

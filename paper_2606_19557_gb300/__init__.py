@@ -89,6 +89,7 @@ def load_library():
             "nep_autotune": (I, [P]),
             "nep_get_launch": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "nep_set_launch": (I, [P, I, I, I, I]),
+            "nep_get_variant": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "nep_set_timing": (I, [P, I]),
             "nep_kernel_times": (I, [P, P, ctypes.POINTER(I)]),
             "nep_kernel_name": (ctypes.c_char_p, [I]),
@@ -301,6 +302,12 @@ class NEP:
     def launch_shape(self):
         v = [ctypes.c_int() for _ in range(4)]
         self._check(self.lib.nep_get_launch(self.h, *[ctypes.byref(x) for x in v]))
+        return tuple(int(x.value) for x in v)
+
+    def variant(self):
+        """(forward lanes per atom, forward registers, adjoint lanes per atom, adjoint registers)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(self.lib.nep_get_variant(self.h, *[ctypes.byref(x) for x in v]))
         return tuple(int(x.value) for x in v)
 
     def set_launch(self, fwd_warps=0, fwd_blocks=0, adj_warps=0, adj_blocks=0):

@@ -112,9 +112,9 @@ static int max_blocks_per_sm(Ctx *c, const void *fn, int wpb, size_t smem) {
 static int set_smem_attr(Ctx *c) {
     int maxo = 0;
     CK(cudaDeviceGetAttribute(&maxo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
-    if (c->ks->fwd_smem(c->T) > (size_t)maxo || c->ks->adj_smem(c->T) > (size_t)maxo)
+    if (c->ks->fwd_smem[2](c->T, c->NN) > (size_t)maxo || c->ks->adj_smem[2](c->T, c->NN) > (size_t)maxo)
         return c->fail(NEP_EINVAL, "model too large for shared memory");
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < NVAR; ++v) {
         CK(cudaFuncSetAttribute(c->ks->fwd_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
         CK(cudaFuncSetAttribute(c->ks->adj_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     }
@@ -133,12 +133,12 @@ static int default_shapes(Ctx *c) {
     int rc = set_smem_attr(c);
     if (rc) return rc;
     if ((rc = prepare_loss_kernels(c))) return rc;
-    const int wpb = 4;
-    int bf = max_blocks_per_sm(c, c->ks->fwd_fn[0], wpb, c->ks->fwd_smem(c->T) * wpb);
-    int ba = max_blocks_per_sm(c, c->ks->adj_fn[0], wpb, c->ks->adj_smem(c->T) * wpb);
+    const int wpb = 4, v = 3;  // 16 lanes per atom, 128 registers, 4 warps per block
+    int bf = max_blocks_per_sm(c, c->ks->fwd_fn[v], wpb, c->ks->fwd_smem[v](c->T, c->NN) * wpb);
+    int ba = max_blocks_per_sm(c, c->ks->adj_fn[v], wpb, c->ks->adj_smem[v](c->T, c->NN) * wpb);
     if (bf < 1 || ba < 1) return c->fail(NEP_EINVAL, "kernel does not fit on the device (shared memory)");
-    if ((rc = make_sched(c, c->fwd, wpb, c->n_sm * bf, 0))) return rc;
-    if ((rc = make_sched(c, c->adj, wpb, c->n_sm * ba, 0))) return rc;
+    if ((rc = make_sched(c, c->fwd, wpb, c->n_sm * bf, v))) return rc;
+    if ((rc = make_sched(c, c->adj, wpb, c->n_sm * ba, v))) return rc;
     return alloc_sched_buffers(c);
 }
 
@@ -611,6 +611,15 @@ int nep_get_launch(const nep_ctx *c, int *fw, int *fb, int *aw, int *ab) {
     return NEP_OK;
 }
 
+int nep_get_variant(const nep_ctx *c, int *fwd_lanes, int *fwd_regs, int *adj_lanes, int *adj_regs) {
+    if (!c || !c->ks) return NEP_EINVAL;
+    if (fwd_lanes) *fwd_lanes = c->ks->sw[c->fwd.var];
+    if (fwd_regs) *fwd_regs = (c->fwd.var & 1) ? 128 : 168;
+    if (adj_lanes) *adj_lanes = c->ks->sw[c->adj.var];
+    if (adj_regs) *adj_regs = (c->adj.var & 1) ? 128 : 168;
+    return NEP_OK;
+}
+
 int nep_set_launch(nep_ctx *c, int fw, int fb, int aw, int ab) {
     if (!c) return NEP_EINVAL;
     if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures");
@@ -620,9 +629,10 @@ int nep_set_launch(nep_ctx *c, int fw, int fb, int aw, int ab) {
     int rc;
     fw = fw ? fw : c->fwd.wpb;
     aw = aw ? aw : c->adj.wpb;
-    const int vf = fw > c->ks->max_wpb[0] ? 1 : c->fwd.var, va = aw > c->ks->max_wpb[0] ? 1 : c->adj.var;
-    const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[vf], fw, c->ks->fwd_smem(c->T) * fw);
-    const int ma = max_blocks_per_sm(c, c->ks->adj_fn[va], aw, c->ks->adj_smem(c->T) * aw);
+    const int vf = (fw > c->ks->max_wpb[c->fwd.var]) ? (c->fwd.var | 1) : c->fwd.var;
+    const int va = (aw > c->ks->max_wpb[c->adj.var]) ? (c->adj.var | 1) : c->adj.var;
+    const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[vf], fw, c->ks->fwd_smem[vf](c->T, c->NN) * fw);
+    const int ma = max_blocks_per_sm(c, c->ks->adj_fn[va], aw, c->ks->adj_smem[va](c->T, c->NN) * aw);
     if (mf < 1 || ma < 1) return c->fail(NEP_EINVAL, "launch shape does not fit");
     fb = fb ? fb : c->n_sm * mf;
     ab = ab ? ab : c->n_sm * ma;
@@ -656,11 +666,11 @@ int nep_autotune(nep_ctx *c) {
     float best_f = 1e30f, best_a = 1e30f;
     int bfw = c->fwd.wpb, bfb = c->fwd.blocks, bfv = c->fwd.var, baw = c->adj.wpb, bab = c->adj.blocks, bav = c->adj.var;
     const int wpbs[3] = {2, 4, 8};
-    for (int var = 0; var < 2 && !rc; ++var) {
+    for (int var = 0; var < NVAR && !rc; ++var) {
         for (int wpb : wpbs) {
             if (wpb > c->ks->max_wpb[var]) continue;
-            const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[var], wpb, c->ks->fwd_smem(c->T) * wpb);
-            const int ma = max_blocks_per_sm(c, c->ks->adj_fn[var], wpb, c->ks->adj_smem(c->T) * wpb);
+            const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[var], wpb, c->ks->fwd_smem[var](c->T, c->NN) * wpb);
+            const int ma = max_blocks_per_sm(c, c->ks->adj_fn[var], wpb, c->ks->adj_smem[var](c->T, c->NN) * wpb);
             for (int bps = 1; bps <= std::max(mf, ma); ++bps) {
                 const bool tf = bps <= mf, ta = bps <= ma;
                 if (tf && (rc = make_sched(c, c->fwd, wpb, c->n_sm * bps, var))) break;

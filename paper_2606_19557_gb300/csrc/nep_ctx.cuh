@@ -46,7 +46,7 @@ struct DevBuf {
 
 // Launch shape of one per-atom kernel and its static schedule.
 struct Sched {
-    int var = 0;         // register-budget variant of the kernel (KernelSet)
+    int var = 0;         // kernel variant (KernelSet): lanes per atom and register budget
     int wpb = 4;         // warps per block
     int blocks = 0;      // grid size
     int W = 0;           // total warps
@@ -55,6 +55,8 @@ struct Sched {
     std::vector<int> h_wlo, h_whi;
 };
 
+constexpr int NVAR = 4;
+
 enum KernelId { KID_EXPAND = 0, KID_FWD, KID_GATHER, KID_STRUCT, KID_LOSS, KID_ADJ, KID_ANN, KID_GRAD, KID_COUNT };
 
 struct Ctx;
@@ -62,13 +64,16 @@ struct Ctx;
 // Per-bucket kernel entry points (compile-time shapes).
 struct KernelSet {
     int NR, KR, NA, KA;
-    const void *fwd_fn[2];      // register-budget variants 0 (168 regs) and 1 (128 regs)
-    const void *adj_fn[2];
-    int max_wpb[2];             // largest warps per block each variant allows
-    size_t (*fwd_smem)(int T);  // bytes per warp
-    size_t (*adj_smem)(int T);
-    void (*launch_fwd[2])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
-    void (*launch_adj[2])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
+    // variants v = 0..3: lanes per atom sw[v] (8 or 16), register budget v & 1
+    // (0: 128 threads x 3 blocks per SM, 168 registers; 1: 256 x 2, 128 registers)
+    const void *fwd_fn[NVAR];
+    const void *adj_fn[NVAR];
+    int max_wpb[NVAR];                   // largest warps per block each variant allows
+    int sw[NVAR];
+    size_t (*fwd_smem[NVAR])(int T, int NN);  // bytes per warp
+    size_t (*adj_smem[NVAR])(int T, int NN);
+    void (*launch_fwd[NVAR])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
+    void (*launch_adj[NVAR])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
 };
 
 const KernelSet *select_kernels(int nR, int kR, int nA, int kA);

@@ -145,6 +145,66 @@ __device__ __forceinline__ void reduce_scatter(float *v, int lane) {
     }
 }
 
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+// Group versions: a group is SW consecutive lanes (SW = 8, 16 or 32) aligned to SW.
+// XOR shuffles with offsets below SW stay inside the group.
+template <int V, int SW>
+struct GRS {
+    static constexpr int LSW = ilog2(SW);
+    static constexpr int LV = ilog2(V);
+    static constexpr int STEPS = LV < LSW ? LV : LSW;
+    static constexpr int OUT = V >= SW ? V / SW : 1;
+    static constexpr int DUP_MASK = (1 << (LSW - STEPS)) - 1;
+};
+
+template <int V, int SW>
+__device__ __forceinline__ int grs_base(int lane) {
+    int base = 0, h = V / 2, o = SW / 2;
+#pragma unroll
+    for (int s = 0; s < GRS<V, SW>::STEPS; ++s) {
+        if (lane & o) base += h;
+        h >>= 1;
+        o >>= 1;
+    }
+    return base;
+}
+
+// Transposing reduction of V values over the SW lanes of each group (fixed pairing).
+template <int V, int SW>
+__device__ __forceinline__ void group_reduce_scatter(float *v, int lane) {
+    int o = SW / 2;
+#pragma unroll
+    for (int h = V / 2, s = 0; s < GRS<V, SW>::STEPS; h >>= 1, ++s) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+        o >>= 1;
+    }
+#pragma unroll
+    for (int s = GRS<V, SW>::STEPS; s < GRS<V, SW>::LSW; ++s) {
+        v[0] += __shfl_xor_sync(FULL, v[0], o);
+        o >>= 1;
+    }
+}
+
+template <int SW>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = SW / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+template <int SW>
+__device__ __forceinline__ unsigned group_bits(unsigned ballot, int lane) {
+    if (SW == 32) return ballot;
+    return (ballot >> (lane & ~(SW - 1))) & ((1u << SW) - 1u);
+}
+
 __host__ __device__ constexpr int pow2ceil(int v) {
     return v <= 1 ? 1 : v <= 2 ? 2 : v <= 4 ? 4 : v <= 8 ? 8 : v <= 16 ? 16 : v <= 32 ? 32 : v <= 64 ? 64 : v <= 128 ? 128 : 256;
 }

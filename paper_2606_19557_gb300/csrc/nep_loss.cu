@@ -476,7 +476,7 @@ int launch_forward(Ctx *c, float *q_raw) {
     AtomArgs a = atom_args(c);
     a.warp_begin = c->fwd.warp_begin.as<int>();
     a.q_raw = q_raw;
-    const size_t smem = c->ks->fwd_smem(c->T) * c->fwd.wpb;
+    const size_t smem = c->ks->fwd_smem[c->fwd.var](c->T, c->NN) * c->fwd.wpb;
     c->ks->launch_fwd[c->fwd.var](a, c->fwd.blocks, c->fwd.wpb, smem, c->stream);
     CK_LAUNCH("k_forward");
     return NEP_OK;
@@ -486,7 +486,7 @@ int launch_adjoint(Ctx *c) {
     if (c->n_atoms == 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.warp_begin = c->adj.warp_begin.as<int>();
-    const size_t smem = c->ks->adj_smem(c->T) * c->adj.wpb;
+    const size_t smem = c->ks->adj_smem[c->adj.var](c->T, c->NN) * c->adj.wpb;
     c->ks->launch_adj[c->adj.var](a, c->adj.blocks, c->adj.wpb, smem, c->stream);
     CK_LAUNCH("k_adjoint");
     return NEP_OK;
@@ -671,7 +671,8 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
     if ((rc = launch_expand(c))) return rc;
     if ((rc = launch_count_hasw(c, hw))) return rc;
     CK(cudaMemsetAsync(c->p_acc.ptr, 0, sizeof(double) * c->P, c->stream));
-    const size_t fs = c->ks->fwd_smem(c->T), as = c->ks->adj_smem(c->T);
+    const int pv = 2;  // one warp per atom: lanes-per-atom 16, 168-register variant
+    const size_t fs = c->ks->fwd_smem[pv](c->T, c->NN), as = c->ks->adj_smem[pv](c->T, c->NN);
     const size_t gsm = sizeof(float) * ANN_ROWS * (3 * c->NN + 2 * c->NDP);
     const int groups = (c->NN * c->NDP + 16 * 256 - 1) / (16 * 256);
     for (int64_t s = 0; s < ns; ++s) {
@@ -679,13 +680,13 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         AtomArgs a = atom_args(c);
         a.work = c->p_work.as<int>();
         a.warp_begin = c->p_ident.as<int>() + a0;
-        c->ks->launch_fwd[0](a, (int)n, 1, fs, c->stream);
+        c->ks->launch_fwd[pv](a, (int)n, 1, fs, c->stream);
         CK_LAUNCH("k_forward (plain)");
         if ((rc = launch_gather(c, c->F_int.as<float>(), Fr, lF, true, a0, a0 + n, pg + s * GB, GB))) return rc;
         if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, s, s + 1,
                                 ps + s * 3, 1)))
             return rc;
-        c->ks->launch_adj[0](a, (int)n, 1, as, c->stream);
+        c->ks->launch_adj[pv](a, (int)n, 1, as, c->stream);
         CK_LAUNCH("k_adjoint (plain)");
         const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
         if (nch > 0) {
