@@ -215,10 +215,12 @@ __host__ __device__ constexpr int pow2ceil(int v) {
 // T_{k+1} = 2x T_k - T_{k-1},  T'_{k+1} = 2 T_k + 2x T'_k - T'_{k-1}.
 // Only called for pairs with r < rc.
 
+// The cutoff uses the hardware sine/cosine (absolute error about 2^-21 on [-pi, pi]);
+// f_c only multiplies the basis, so this stays far inside the FP32 path's tolerance.
 template <int K>
 __device__ __forceinline__ void basis_val(float r, float inv_rc, float *f) {
     const float u = r * inv_rc;
-    const float fc = 0.5f * cospif(u) + 0.5f;
+    const float fc = 0.5f * __cosf(PI_F * u) + 0.5f;
     const float y = u - 1.0f;
     const float x = 2.0f * y * y - 1.0f;
     float tm1 = 1.0f, t = x;
@@ -237,7 +239,7 @@ template <int K>
 __device__ __forceinline__ void basis_val_der(float r, float inv_rc, float *f, float *fp) {
     const float u = r * inv_rc;
     float s, c;
-    sincospif(u, &s, &c);
+    __sincosf(PI_F * u, &s, &c);
     const float fc = 0.5f * c + 0.5f;
     const float dfc = -0.5f * PI_F * inv_rc * s;
     const float y = u - 1.0f;
@@ -474,6 +476,16 @@ __device__ __forceinline__ void l2_project(const float *X, float *p) {
 
 __device__ __forceinline__ float sym_trace_prod(const float *A, const float *B) {  // tr(A B)
     return A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + 2.0f * (A[3] * B[3] + A[4] * B[4] + A[5] * B[5]);
+}
+
+// 1/|d| for a pair displacement (hardware reciprocal square root, <= 2 ulp).
+__device__ __forceinline__ float inv_norm(float r2) { return rsqrtf(r2); }
+
+// Requests the cache lines of [p, p + bytes) into L2 ahead of use.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes, int lane, int nlanes) {
+    const char *c = (const char *)((uintptr_t)p & ~(uintptr_t)127);
+    const char *e = (const char *)p + bytes;
+    for (const char *q = c + 128 * lane; q < e; q += 128 * nlanes) asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
 }
 
 __device__ __forceinline__ int pair_j(float4 p) { return __float_as_int(p.w) >> 4; }

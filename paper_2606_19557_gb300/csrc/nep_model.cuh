@@ -32,7 +32,7 @@ namespace nep {
 template <class S, int SW>
 struct FwdL {
     static constexpr int G = 32 / SW;
-    static constexpr int SGS = S::NA | 1;
+    static constexpr int SGS = (S::NA + 3) & ~3;  // rows of g_n padded to float4
     static constexpr int NLMO = (L3 + SW - 1) / SW;  // (l, m) outputs owned per lane
     struct Atom {
         float q[S::ND];
@@ -43,7 +43,7 @@ struct FwdL {
         float G4[S::NA * 5];
     };
     Atom at[G];
-    float sg[G][SW][SGS];
+    __align__(16) float sg[G][SW][SGS];
     float sY[G][SW][25];
     // runtime tail (floats): u[G][NN], Sr[G][T][KR], beta[G][T][KR], cw[T][NC]
     __host__ __device__ static size_t tail(int T, int NN) {
@@ -57,7 +57,7 @@ struct FwdL {
 template <class S, int SW>
 struct AdjL {
     static constexpr int G = 32 / SW;
-    static constexpr int SGS = S::NA | 1;
+    static constexpr int SGS = (S::NA + 3) & ~3;
     static constexpr int NLMO = (L3 + SW - 1) / SW;
     struct Atom {
         float qt[S::ND];
@@ -72,8 +72,8 @@ struct AdjL {
         float ad[S::NA];  // sum_m A_n1m dA_n1m (read by every l = 1 lane before dA is overwritten)
     };
     Atom at[G];
-    float sg[G][SW][SGS];
-    float sgp[G][SW][SGS];
+    __align__(16) float sg[G][SW][SGS];
+    __align__(16) float sgp[G][SW][SGS];
     float sY[G][SW][25];
     float sP[G][SW][25];
     // runtime tail: u[G][NN], Sr[G][T][2 KR], accR[T][NCR], accA[T][NCA], cw[T][NC]
@@ -84,6 +84,20 @@ struct AdjL {
         return ((sizeof(AdjL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
     }
 };
+
+// Loads a padded row of N floats (N a multiple of 4, 16-byte aligned) from shared memory.
+template <int N>
+__device__ __forceinline__ void load_row(const float *src, float *dst) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+        const float4 t = s4[q];
+        dst[4 * q] = t.x;
+        dst[4 * q + 1] = t.y;
+        dst[4 * q + 2] = t.z;
+        dst[4 * q + 3] = t.w;
+    }
+}
 
 // Batch of up to G consecutive work positions of one species, starting at `base`.
 __device__ __forceinline__ int batch_size(const AtomArgs &a, int base, int wend, int G, int t0) {
@@ -174,6 +188,11 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
         const int maxR = __reduce_max_sync(FULL, nRad);
         const int maxA = __reduce_max_sync(FULL, nAng);
         typename L::Atom &at = sm.at[grp];
+        if (bp + grp < wend) {  // the atoms after this batch: bring their pair records into L2
+            const int ni = a.work[bp + grp];
+            const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
+            prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
+        }
 
         // ---------------------------------------------------------------- angular moments A_nlm
         float accA[NLMO][NA];
@@ -187,7 +206,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                 const float4 pd = a.pair[beg + k];
                 const int tj = pair_t(pd);
                 const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                const float rinv = __frsqrt_rn(r2);
+                const float rinv = inv_norm(r2);
                 const float r = r2 * rinv;
                 float f[KA];
                 basis_val<KA>(r, a.inv_rcA, f);
@@ -207,13 +226,15 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
             __syncwarp();
             const int cnt = min(SW, nAng - c0);
             for (int pp = 0; pp < cnt; ++pp) {
+                float gv[SGS];
+                load_row<SGS>(sm.sg[grp][pp], gv);
 #pragma unroll
                 for (int j = 0; j < NLMO; ++j) {
                     const int lm = sl + j * SW;
                     if (lm < L3) {
                         const float y = sm.sY[grp][pp][lm];
 #pragma unroll
-                        for (int n = 0; n < NA; ++n) accA[j][n] += sm.sg[grp][pp][n] * y;
+                        for (int n = 0; n < NA; ++n) accA[j][n] += gv[n] * y;
                     }
                 }
             }
@@ -247,7 +268,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                     const float4 pd = a.pair[beg + k];
                     tj = pair_t(pd);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                    basis_val<KR>(r2 * __frsqrt_rn(r2), a.inv_rcR, f);
+                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
                 }
                 unsigned rem = group_bits<SW>(__ballot_sync(FULL, valid), lane);
                 while (__any_sync(FULL, rem != 0)) {
@@ -361,7 +382,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
             const float4 pd = a.pair[p];
             const int tj = pair_t(pd);
             const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-            const float rinv = __frsqrt_rn(r2);
+            const float rinv = inv_norm(r2);
             const float r = r2 * rinv;
             const float ux = pd.x * rinv, uy = pd.y * rinv, uz = pd.z * rinv;
             float f[KA], fp[KA];
@@ -410,7 +431,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
             const float4 pd = a.pair[p];
             const int tj = pair_t(pd);
             const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-            const float rinv = __frsqrt_rn(r2);
+            const float rinv = inv_norm(r2);
             float f[KR], fp[KR];
             basis_val_der<KR>(r2 * rinv, a.inv_rcR, f, fp);
             const float *be = beta + tj * KR;
@@ -525,6 +546,11 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         const int maxR = __reduce_max_sync(FULL, nRad);
         const int maxA = __reduce_max_sync(FULL, nAng);
         typename L::Atom &at = sm.at[grp];
+        if (bp + grp < wend) {  // the atoms after this batch: bring their pair records into L2
+            const int ni = a.work[bp + grp];
+            const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
+            prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
+        }
 
         // ---------------------------------------------------------------- state of the forward pass
         for (int e = sl; e < ND; e += SW) at.qt[e] = a.st_qt[(size_t)wi * ND + e];
@@ -592,7 +618,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     const float ly = fby - a.fbar[(size_t)j * 3 + 1] - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
                     const float lz = fbz - a.fbar[(size_t)j * 3 + 2] - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                    const float rinv = __frsqrt_rn(r2);
+                    const float rinv = inv_norm(r2);
                     const float r = r2 * rinv;
                     const float ux = pd.x * rinv, uy = pd.y * rinv, uz = pd.z * rinv;
                     const float rl = ux * lx + uy * ly + uz * lz;
@@ -619,13 +645,16 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                 __syncwarp();
                 const int cnt = min(SW, nAng - c0);
                 for (int pp = 0; pp < cnt; ++pp) {
+                    float gv[L::SGS], gpv[L::SGS];
+                    load_row<L::SGS>(sm.sg[grp][pp], gv);
+                    load_row<L::SGS>(sm.sgp[grp][pp], gpv);
 #pragma unroll
                     for (int jj = 0; jj < NLMO; ++jj) {
                         const int lm = sl + jj * SW;
                         if (lm < L3) {
                             const float y = sm.sY[grp][pp][lm], ps = sm.sP[grp][pp][lm];
 #pragma unroll
-                            for (int n = 0; n < NA; ++n) accd[jj][n] += sm.sgp[grp][pp][n] * y + sm.sg[grp][pp][n] * ps;
+                            for (int n = 0; n < NA; ++n) accd[jj][n] += gpv[n] * y + gv[n] * ps;
                         }
                     }
                 }
@@ -665,7 +694,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     const float ly = fby - a.fbar[(size_t)j * 3 + 1] - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
                     const float lz = fbz - a.fbar[(size_t)j * 3 + 2] - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                    const float rinv = __frsqrt_rn(r2);
+                    const float rinv = inv_norm(r2);
                     rl = (pd.x * lx + pd.y * ly + pd.z * lz) * rinv;
                     basis_val_der<KR>(r2 * rinv, a.inv_rcR, f, fp);
                 }
@@ -823,7 +852,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     const float ly = fby - a.fbar[(size_t)j * 3 + 1] - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
                     const float lz = fbz - a.fbar[(size_t)j * 3 + 2] - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                    const float rinv = __frsqrt_rn(r2);
+                    const float rinv = inv_norm(r2);
                     const float r = r2 * rinv;
                     const float ux = pd.x * rinv, uy = pd.y * rinv, uz = pd.z * rinv;
                     const float rl = ux * lx + uy * ly + uz * lz;
