@@ -168,7 +168,13 @@ def run_ours(args):
     nep.set_params(teacher, qs)
     E_ref, F_ref, W_ref = [x.clone() for x in nep.eval()]
     nep.set_params(theta, qs)
-    shape = nep.autotune() if args.autotune else nep.launch_shape()
+    if args.launch:
+        fv, av, fw, fb, aw, ab = [int(x) for x in args.launch.split(",")]
+        nep.set_variant(fv, av)
+        nep.set_launch(fw, fb, aw, ab)
+        shape = nep.launch_shape()
+    else:
+        shape = nep.autotune() if args.autotune else nep.launch_shape()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -298,6 +304,7 @@ def main():
     ap.add_argument("--cpu-sample", dest="cpu_sample", type=int, default=150)
     ap.add_argument("--plain-steps", dest="plain_steps", type=int, default=2)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--launch", default="", help="fixed kernel variants and shape: fv,av,fwarps,fblocks,awarps,ablocks")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

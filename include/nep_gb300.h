@@ -185,6 +185,10 @@ int nep_get_launch(const nep_ctx *ctx, int *fwd_warps, int *fwd_blocks, int *adj
  * and the register budget per thread (168 or 128). */
 int nep_get_variant(const nep_ctx *ctx, int *fwd_lanes, int *fwd_regs, int *adj_lanes, int *adj_regs);
 
+/* Selects kernel variants v in [0, 4): lanes per atom 8 (v < 2) or 16, register
+ * budget 168 (v even) or 128 (v odd); the grid is reset to the occupancy limit. */
+int nep_set_variant(nep_ctx *ctx, int fwd_var, int adj_var);
+
 /* Sets the launch shape explicitly (0 keeps a value). */
 int nep_set_launch(nep_ctx *ctx, int fwd_warps, int fwd_blocks, int adj_warps, int adj_blocks);
 

@@ -90,6 +90,7 @@ def load_library():
             "nep_get_launch": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "nep_set_launch": (I, [P, I, I, I, I]),
             "nep_get_variant": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "nep_set_variant": (I, [P, I, I]),
             "nep_set_timing": (I, [P, I]),
             "nep_kernel_times": (I, [P, P, ctypes.POINTER(I)]),
             "nep_kernel_name": (ctypes.c_char_p, [I]),
@@ -309,6 +310,10 @@ class NEP:
         v = [ctypes.c_int() for _ in range(4)]
         self._check(self.lib.nep_get_variant(self.h, *[ctypes.byref(x) for x in v]))
         return tuple(int(x.value) for x in v)
+
+    def set_variant(self, fwd_var: int, adj_var: int):
+        """Kernel variants (0-3): lanes per atom 8 for 0-1 and 16 for 2-3; odd = 128 registers."""
+        self._call(self.lib.nep_set_variant, int(fwd_var), int(adj_var))
 
     def set_launch(self, fwd_warps=0, fwd_blocks=0, adj_warps=0, adj_blocks=0):
         self._call(self.lib.nep_set_launch, int(fwd_warps), int(fwd_blocks), int(adj_warps), int(adj_blocks))

@@ -620,6 +620,25 @@ int nep_get_variant(const nep_ctx *c, int *fwd_lanes, int *fwd_regs, int *adj_la
     return NEP_OK;
 }
 
+int nep_set_variant(nep_ctx *c, int fwd_var, int adj_var) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures");
+    if (fwd_var < 0 || fwd_var >= NVAR || adj_var < 0 || adj_var >= NVAR) return c->fail(NEP_EINVAL, "bad variant");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->stream));
+    int rc;
+    const int fw = std::min(c->fwd.wpb, c->ks->max_wpb[fwd_var]), aw = std::min(c->adj.wpb, c->ks->max_wpb[adj_var]);
+    const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[fwd_var], fw, c->ks->fwd_smem[fwd_var](c->T, c->NN) * fw);
+    const int ma = max_blocks_per_sm(c, c->ks->adj_fn[adj_var], aw, c->ks->adj_smem[adj_var](c->T, c->NN) * aw);
+    if (mf < 1 || ma < 1) return c->fail(NEP_EINVAL, "variant does not fit");
+    if ((rc = make_sched(c, c->fwd, fw, c->n_sm * mf, fwd_var))) return rc;
+    if ((rc = make_sched(c, c->adj, aw, c->n_sm * ma, adj_var))) return rc;
+    if ((rc = alloc_sched_buffers(c))) return rc;
+    drop_graphs(c);
+    c->state_valid = false;
+    return NEP_OK;
+}
+
 int nep_set_launch(nep_ctx *c, int fw, int fb, int aw, int ab) {
     if (!c) return NEP_EINVAL;
     if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures");

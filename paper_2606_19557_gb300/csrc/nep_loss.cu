@@ -82,11 +82,22 @@ __global__ void k_gather(int64_t a0, int64_t a1, const int64_t *nbr_off, const i
     for (int64_t i = a0 + gw; i < a1; i += W) {
         const int64_t beg = nbr_off[i], end = nbr_off[i + 1];
         float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-        for (int64_t p = beg + lane; p < end; p += 32) {
-            const float4 g = G[rev[p]];
-            sx += g.x;
-            sy += g.y;
-            sz += g.z;
+        for (int64_t p0 = beg; p0 < end; p0 += 128) {  // 4 index loads, then 4 gathers, in flight
+            int r[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t p = p0 + lane + 32 * k;
+                r[k] = p < end ? rev[p] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (r[k] >= 0) {
+                    const float4 g = G[r[k]];
+                    sx += g.x;
+                    sy += g.y;
+                    sz += g.z;
+                }
+            }
         }
         sx = warp_sum(sx);
         sy = warp_sum(sy);
@@ -234,63 +245,78 @@ __global__ void k_cotangents(int64_t ns, const int64_t *atom_off, const double *
 
 // --------------------------------------------------------------------------- network gradient
 // grad_w0[t] = sum_i zeta_i q~_i^T + u_i dq~_i^T, grad_b0[t] = -sum zeta, grad_w1[t] = sum omega
-// over the atoms of species t (a contraction over atoms: [NN x 2n] . [2n x ND]).
-// One block per chunk of work positions holding a single species; FP32 partial per chunk.
+// over the atoms of species t: a contraction over atoms ([NN x 2n] . [2n x ND]).  One
+// block per chunk of work positions holding a single species; each thread accumulates
+// a 4 x 4 register tile of the NN x ND output; FP32 partial per chunk.
 constexpr int ANN_ROWS = 32;
+constexpr int ANN_TILES = 128;  // 4x4 tiles per block (blockIdx.y covers the rest)
 
 __global__ void k_ann_grad(const int *chunk_begin, int NN, int NDP, const float *zt, const float *ut,
                            const float *om, const float *qt, const float *dqt, float *part) {
-    extern __shared__ float sm[];
-    float *sz = sm;                       // [ROWS][NN]
-    float *su = sz + ANN_ROWS * NN;       // [ROWS][NN]
-    float *so = su + ANN_ROWS * NN;       // [ROWS][NN]
-    float *sq = so + ANN_ROWS * NN;       // [ROWS][NDP]
-    float *sd = sq + ANN_ROWS * NDP;      // [ROWS][NDP]
-    constexpr int PER = 16;
+    extern __shared__ __align__(16) float sm[];
+    const int NNP = (NN + 3) & ~3, NDQ = (NDP + 3) & ~3;
+    float *sz = sm;                      // [ROWS][NNP]
+    float *su = sz + ANN_ROWS * NNP;     // [ROWS][NNP]
+    float *sq = su + ANN_ROWS * NNP;     // [ROWS][NDQ]
+    float *sd = sq + ANN_ROWS * NDQ;     // [ROWS][NDQ]
     const int c = blockIdx.x;
     const int r0 = chunk_begin[c], r1 = chunk_begin[c + 1];
-    const int nent = NN * NDP;
-    const int e0 = blockIdx.y * PER * blockDim.x;  // entry group of this block
+    const int tn = NDQ / 4, ntiles = (NNP / 4) * tn;
+    const int tile = blockIdx.y * ANN_TILES + threadIdx.x;
+    const bool own = threadIdx.x < ANN_TILES && tile < ntiles;
+    const int mu0 = own ? 4 * (tile / tn) : 0, v0 = own ? 4 * (tile % tn) : 0;
     const bool first = blockIdx.y == 0;
-    float acc[PER];
+    float acc[4][4];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) acc[k] = 0.0f;
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
     float azeta = 0.0f, aom = 0.0f;
     for (int rr = r0; rr < r1; rr += ANN_ROWS) {
         const int nr = min(ANN_ROWS, r1 - rr);
-        for (int e = threadIdx.x; e < nr * NN; e += blockDim.x) {
-            sz[e] = zt[(size_t)rr * NN + e];
-            su[e] = ut[(size_t)rr * NN + e];
-            so[e] = om[(size_t)rr * NN + e];
+        for (int e = threadIdx.x; e < ANN_ROWS * NNP; e += blockDim.x) {
+            const int r = e / NNP, m = e - r * NNP;
+            const bool in = r < nr && m < NN;
+            sz[e] = in ? zt[(size_t)(rr + r) * NN + m] : 0.0f;
+            su[e] = in ? ut[(size_t)(rr + r) * NN + m] : 0.0f;
         }
-        for (int e = threadIdx.x; e < nr * NDP; e += blockDim.x) {
-            sq[e] = qt[(size_t)rr * NDP + e];
-            sd[e] = dqt[(size_t)rr * NDP + e];
+        for (int e = threadIdx.x; e < ANN_ROWS * NDQ; e += blockDim.x) {
+            const int r = e / NDQ, v = e - r * NDQ;
+            const bool in = r < nr && v < NDP;
+            sq[e] = in ? qt[(size_t)(rr + r) * NDP + v] : 0.0f;
+            sd[e] = in ? dqt[(size_t)(rr + r) * NDP + v] : 0.0f;
         }
         __syncthreads();
+        if (own) {
+            for (int r = 0; r < nr; ++r) {
+                const float4 z4 = *reinterpret_cast<const float4 *>(sz + r * NNP + mu0);
+                const float4 u4 = *reinterpret_cast<const float4 *>(su + r * NNP + mu0);
+                const float4 q4 = *reinterpret_cast<const float4 *>(sq + r * NDQ + v0);
+                const float4 d4 = *reinterpret_cast<const float4 *>(sd + r * NDQ + v0);
+                const float z[4] = {z4.x, z4.y, z4.z, z4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
+                const float q[4] = {q4.x, q4.y, q4.z, q4.w}, d[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = e0 + threadIdx.x + k * blockDim.x;
-            if (e < nent) {
-                const int mu = e / NDP, v = e - mu * NDP;
-                float s = acc[k];
-                for (int r = 0; r < nr; ++r) s += sz[r * NN + mu] * sq[r * NDP + v] + su[r * NN + mu] * sd[r * NDP + v];
-                acc[k] = s;
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] += z[x] * q[y] + uu[x] * d[y];
             }
         }
         if (first && (int)threadIdx.x < NN) {
             for (int r = 0; r < nr; ++r) {
-                azeta += sz[r * NN + threadIdx.x];
-                aom += so[r * NN + threadIdx.x];
+                azeta += sz[r * NNP + threadIdx.x];
+                aom += om[(size_t)(rr + r) * NN + threadIdx.x];
             }
         }
         __syncthreads();
     }
+    const int nent = NN * NDP;
     float *dst = part + (size_t)c * (nent + 2 * NN);
+    if (own) {
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int e = e0 + threadIdx.x + k * blockDim.x;
-        if (e < nent) dst[e] = acc[k];
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+                if (mu0 + x < NN && v0 + y < NDP) dst[(mu0 + x) * NDP + v0 + y] = acc[x][y];
     }
     if (first && (int)threadIdx.x < NN) {
         dst[nent + threadIdx.x] = azeta;
@@ -549,6 +575,15 @@ int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *d
     return NEP_OK;
 }
 
+static size_t ann_smem(Ctx *c) {
+    const int NNP = (c->NN + 3) & ~3, NDQ = (c->NDP + 3) & ~3;
+    return sizeof(float) * ANN_ROWS * (2 * NNP + 2 * NDQ);
+}
+static int ann_groups(Ctx *c) {
+    const int ntiles = ((c->NN + 3) / 4) * ((c->NDP + 3) / 4);
+    return (ntiles + ANN_TILES - 1) / ANN_TILES;
+}
+
 int prepare_loss_kernels(Ctx *c) {
     int maxo = 0;
     CK(cudaDeviceGetAttribute(&maxo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
@@ -558,9 +593,7 @@ int prepare_loss_kernels(Ctx *c) {
 
 int launch_ann_grad(Ctx *c) {
     if (c->n_chunks == 0) return NEP_OK;
-    const size_t smem = sizeof(float) * ANN_ROWS * (3 * c->NN + 2 * c->NDP);
-    const int groups = (c->NN * c->NDP + 16 * 256 - 1) / (16 * 256);
-    k_ann_grad<<<dim3(c->n_chunks, groups), 256, smem, c->stream>>>(c->chunk_begin.as<int>(), c->NN, c->NDP, c->zt.as<float>(),
+    k_ann_grad<<<dim3(c->n_chunks, ann_groups(c)), ANN_TILES, ann_smem(c), c->stream>>>(c->chunk_begin.as<int>(), c->NN, c->NDP, c->zt.as<float>(),
                                                       c->ut.as<float>(), c->om.as<float>(), c->st_qt.as<float>(),
                                                       c->dqt.as<float>(), c->annpart.as<float>());
     CK_LAUNCH("k_ann_grad");
@@ -673,8 +706,8 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
     CK(cudaMemsetAsync(c->p_acc.ptr, 0, sizeof(double) * c->P, c->stream));
     const int pv = 2;  // one warp per atom: lanes-per-atom 16, 168-register variant
     const size_t fs = c->ks->fwd_smem[pv](c->T, c->NN), as = c->ks->adj_smem[pv](c->T, c->NN);
-    const size_t gsm = sizeof(float) * ANN_ROWS * (3 * c->NN + 2 * c->NDP);
-    const int groups = (c->NN * c->NDP + 16 * 256 - 1) / (16 * 256);
+    const size_t gsm = ann_smem(c);
+    const int groups = ann_groups(c);
     for (int64_t s = 0; s < ns; ++s) {
         const int64_t a0 = c->h_atom_off[s], n = c->h_atom_off[s + 1] - a0;
         AtomArgs a = atom_args(c);
@@ -690,7 +723,7 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         CK_LAUNCH("k_adjoint (plain)");
         const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
         if (nch > 0) {
-            k_ann_grad<<<dim3(nch, groups), 256, gsm, c->stream>>>(c->p_chunks.as<int>() + c->p_cofs[s], c->NN, c->NDP,
+            k_ann_grad<<<dim3(nch, groups), ANN_TILES, gsm, c->stream>>>(c->p_chunks.as<int>() + c->p_cofs[s], c->NN, c->NDP,
                                                                    c->zt.as<float>(), c->ut.as<float>(),
                                                                    c->om.as<float>(), c->st_qt.as<float>(),
                                                                    c->dqt.as<float>(), c->annpart.as<float>());
