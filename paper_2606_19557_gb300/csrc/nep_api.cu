@@ -386,7 +386,7 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
     if (na > 0) CK(cudaMemcpy(c->work.ptr, c->h_work.data(), sizeof(int) * na, cudaMemcpyHostToDevice));
     // network-gradient chunks (single species each)
     {
-        const int CH = 512;
+        const int CH = 128;  // work positions per network-gradient chunk
         std::vector<int> cb, clo(c->T), chi(c->T);
         for (int t = 0; t < c->T; ++t) {
             clo[t] = (int)cb.size();
@@ -408,7 +408,7 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
     const int64_t nlp = (int64_t)c->n_sm * 4 + 3 * (int64_t)c->n_sm + 8;
     if (c->E_atom.ensure<float>(na) || c->F_own.ensure<float>(na * 3) || c->W_atom.ensure<float>(na * 9) ||
         c->G.ensure_bytes(sizeof(float4) * (size_t)(M + 1)) || c->st_qt.ensure<float>(na * NDP) ||
-        c->st_h.ensure<float>(na * NN) || c->st_A.ensure<float>(na * NAL) || c->fbar.ensure<float>(na * 3) ||
+        c->st_h.ensure<float>(na * NN) || c->st_A.ensure<float>(na * NAL) || c->fbar.ensure<float4>(na) ||
         c->ebar.ensure<float>(ns) || c->wbar.ensure<float>(ns * 9) || c->zt.ensure<float>(na * NN) ||
         c->ut.ensure<float>(na * NN) || c->om.ensure<float>(na * NN) || c->dqt.ensure<float>(na * NDP) ||
         c->F_int.ensure<float>(na * 3) || c->E_int.ensure<double>(ns) || c->W_int.ensure<double>(ns * 9) ||

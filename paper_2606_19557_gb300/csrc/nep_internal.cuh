@@ -73,7 +73,7 @@ struct AtomArgs {
     float *st_h;            // [Na_work][NN] hidden activations
     float *st_A;            // [Na_work][NA*24] angular moments
     // adjoint inputs
-    const float *fbar;      // [Na*3]  dL/dF
+    const float4 *fbar;     // [Na]    dL/dF (x, y, z, unused)
     const float *ebar;      // [Ns]    dL/dE_s
     const float *wbar;      // [Ns*9]  dL/dW_s
     // adjoint outputs

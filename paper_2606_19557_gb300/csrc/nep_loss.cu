@@ -108,7 +108,7 @@ __global__ void k_gather(int64_t a0, int64_t a1, const int64_t *nbr_off, const i
             F_out[i * 3 + lane] = F;
             if (loss) {
                 const float d = F - F_ref[i * 3 + lane];
-                fbar[i * 3 + lane] = coefF * d;
+                fbar[i * 4 + lane] = coefF * d;  // float4 rows (x, y, z, unused)
                 acc += (double)d * (double)d;
             }
         }
@@ -222,6 +222,12 @@ __global__ void k_loss_final(const double *fpart, int nf, const double *spart, i
         loss3[2] = nsv > 0 ? sh[2][0] / (9.0 * nsv) : 0.0;
         *gb1 = sh[3][0];
     }
+}
+
+// dL/dF rows into the float4 layout the adjoint gathers.
+__global__ void k_fbar_rows(int64_t na, const float *dF, float4 *fbar) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < na) fbar[i] = make_float4(dF[3 * i], dF[3 * i + 1], dF[3 * i + 2], 0.0f);
 }
 
 // Cotangents supplied by the caller (vector-Jacobian product for autograd).
@@ -461,7 +467,7 @@ static AtomArgs atom_args(Ctx *c) {
     a.st_qt = c->st_qt.as<float>();
     a.st_h = c->st_h.as<float>();
     a.st_A = c->st_A.as<float>();
-    a.fbar = c->fbar.as<float>();
+    a.fbar = c->fbar.as<float4>();
     a.ebar = c->ebar.as<float>();
     a.wbar = c->wbar.as<float>();
     a.zt = c->zt.as<float>();
@@ -566,9 +572,10 @@ int launch_loss_final(Ctx *c, double *loss3, const double *fpart, int nf, const 
 }
 
 int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *dW) {
-    if (c->n_atoms > 0)
-        CK(cudaMemcpyAsync(c->fbar.ptr, dF, sizeof(float) * 3 * (size_t)c->n_atoms, cudaMemcpyDeviceToDevice,
-                           c->stream));
+    if (c->n_atoms > 0) {
+        k_fbar_rows<<<(unsigned)((c->n_atoms + 255) / 256), 256, 0, c->stream>>>(c->n_atoms, dF, c->fbar.as<float4>());
+        CK_LAUNCH("k_fbar_rows");
+    }
     k_cotangents<<<1, 256, 0, c->stream>>>(c->n_struct, c->atom_off.as<int64_t>(), dE, dW, c->ebar.as<float>(),
                                            c->wbar.as<float>(), c->gb1.as<double>());
     CK_LAUNCH("k_cotangents");

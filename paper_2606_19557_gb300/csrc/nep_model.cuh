@@ -150,7 +150,6 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
     float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
     L &sm = *reinterpret_cast<L *>(base_ptr);
     float *tail = base_ptr + sizeof(L) / sizeof(float);
-    float *u = tail + grp * NN;                              // [NN] of this group
     float *Sr = tail + G * NN + grp * T * KR;                // [T][KR] of this group
     float *beta = tail + G * NN + G * T * KR + grp * T * KR; // [T][KR] of this group
     float *cw = tail + G * NN + 2 * G * T * KR;              // [T][NCR] | [T][NCA], current species
@@ -170,6 +169,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
         const int ti = a.type[a.work[bp]];
         const int nb = batch_size(a, bp, wend, G, ti);
         const bool act = grp < nb;
+        const int bp0 = bp;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
         const int i = a.work[wi];
@@ -325,25 +325,53 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
         __syncwarp();
 
         // ---------------------------------------------------------------- network (Eq. "ann")
-        float Epart = 0.0f;
-        for (int mu = sl; mu < NN; mu += SW) {
-            float z = -b0[ti * NN + mu];
+        // The G atoms of the batch share the species, so the layer runs as a small
+        // batched product: lanes index neurons (then descriptor components) and each
+        // weight is loaded once for all G atoms.
+        float Eg[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) Eg[g] = 0.0f;
+        for (int mu = lane; mu < NN; mu += 32) {
+            float z[G];
+            const float bz = -b0[ti * NN + mu];
+#pragma unroll
+            for (int g = 0; g < G; ++g) z[g] = bz;
             const float *wt = W0T + (size_t)ti * ND * NN + mu;
 #pragma unroll 5
-            for (int v = 0; v < ND; ++v) z += wt[(size_t)v * NN] * at.qt[v];
-            const float h = tanhf(z);
-            if (act) a.st_h[(size_t)wi * NN + mu] = h;
-            const float wv = w1[ti * NN + mu];
-            Epart += wv * h;
-            u[mu] = wv * (1.0f - h * h);
+            for (int v = 0; v < ND; ++v) {
+                const float wv = wt[(size_t)v * NN];
+#pragma unroll
+                for (int g = 0; g < G; ++g) z[g] += wv * sm.at[g].qt[v];
+            }
+            const float wo = w1[ti * NN + mu];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float h = tanhf(z[g]);
+                if (g < nb) a.st_h[(size_t)(bp0 + g) * NN + mu] = h;
+                Eg[g] += wo * h;
+                tail[g * NN + mu] = wo * (1.0f - h * h);  // u of atom g
+            }
         }
-        const float Ei = group_sum<SW>(Epart) - b1;
+        float Ei = 0.0f;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float e = warp_sum(Eg[g]);
+            if (g == grp) Ei = e - b1;
+        }
         __syncwarp();
-        for (int v = sl; v < ND; v += SW) {
+        for (int v = lane; v < ND; v += 32) {
+            float e[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) e[g] = 0.0f;
             const float *wr = W0 + (size_t)ti * NN * ND + v;
-            float e = 0.0f;
-            for (int mu = 0; mu < NN; ++mu) e += wr[(size_t)mu * ND] * u[mu];
-            at.b[v] = e * scale[v];
+            for (int mu = 0; mu < NN; ++mu) {
+                const float wv = wr[(size_t)mu * ND];
+#pragma unroll
+                for (int g = 0; g < G; ++g) e[g] += wv * tail[g * NN + mu];
+            }
+            const float sc = scale[v];
+#pragma unroll
+            for (int g = 0; g < G; ++g) sm.at[g].b[v] = e[g] * sc;
         }
         __syncwarp();
 
@@ -497,7 +525,6 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
     float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
     L &sm = *reinterpret_cast<L *>(base_ptr);
     float *tail = base_ptr + sizeof(L) / sizeof(float);
-    float *u = tail + grp * NN;                           // [NN] u, later zeta
     float *Sr = tail + G * NN + grp * T * 2 * KR;         // [T][2 KR] S^b_k | S'^b_k of this group
     float *accR = tail + G * NN + G * T * 2 * KR;         // [T][NCR] (warp)
     float *accA = accR + T * NCR;                         // [T][NCA] (warp)
@@ -524,6 +551,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         const int ti = a.type[a.work[bp]];
         const int nb = batch_size(a, bp, wend, G, ti);
         const bool act = grp < nb;
+        const int bp0 = bp;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
         const int i = a.work[wi];
@@ -555,16 +583,28 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         // ---------------------------------------------------------------- state of the forward pass
         for (int e = sl; e < ND; e += SW) at.qt[e] = a.st_qt[(size_t)wi * ND + e];
         for (int e = sl; e < NA * L3; e += SW) at.A[e] = a.st_A[(size_t)wi * NA * L3 + e];
-        for (int mu = sl; mu < NN; mu += SW) {
-            const float h = a.st_h[(size_t)wi * NN + mu];
-            u[mu] = w1[ti * NN + mu] * (1.0f - h * h);
+        for (int mu = lane; mu < NN; mu += 32) {
+            const float wo = w1[ti * NN + mu];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float h = a.st_h[(size_t)(bp0 + (g < nb ? g : 0)) * NN + mu];
+                tail[g * NN + mu] = wo * (1.0f - h * h);
+            }
         }
         __syncwarp();
-        for (int v = sl; v < ND; v += SW) {
+        for (int v = lane; v < ND; v += 32) {
+            float e[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) e[g] = 0.0f;
             const float *wr = W0 + (size_t)ti * NN * ND + v;
-            float e = 0.0f;
-            for (int mu = 0; mu < NN; ++mu) e += wr[(size_t)mu * ND] * u[mu];
-            at.b[v] = e * scale[v];
+            for (int mu = 0; mu < NN; ++mu) {
+                const float wv = wr[(size_t)mu * ND];
+#pragma unroll
+                for (int g = 0; g < G; ++g) e[g] += wv * tail[g * NN + mu];
+            }
+            const float sc = scale[v];
+#pragma unroll
+            for (int g = 0; g < G; ++g) sm.at[g].b[v] = e[g] * sc;
         }
         for (int n = sl; n < NA; n += SW) {
             const float *An = at.A + n * L3;
@@ -595,7 +635,8 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                 }
             }
         }
-        const float fbx = a.fbar[(size_t)i * 3], fby = a.fbar[(size_t)i * 3 + 1], fbz = a.fbar[(size_t)i * 3 + 2];
+        const float4 fbi = a.fbar[i];
+        const float fbx = fbi.x, fby = fbi.y, fbz = fbi.z;
         float Wb[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Wb[k] = a.wbar[(size_t)s * 9 + k];
@@ -614,9 +655,10 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                 if (k < nAng) {
                     const float4 pd = a.pair[beg + k];
                     const int j = pair_j(pd), tj = pair_t(pd);
-                    const float lx = fbx - a.fbar[(size_t)j * 3] - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
-                    const float ly = fby - a.fbar[(size_t)j * 3 + 1] - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
-                    const float lz = fbz - a.fbar[(size_t)j * 3 + 2] - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+                    const float4 fbj = a.fbar[j];
+                    const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
+                    const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
+                    const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     const float rinv = inv_norm(r2);
                     const float r = r2 * rinv;
@@ -690,9 +732,10 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     const float4 pd = a.pair[beg + k];
                     const int j = pair_j(pd);
                     tj = pair_t(pd);
-                    const float lx = fbx - a.fbar[(size_t)j * 3] - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
-                    const float ly = fby - a.fbar[(size_t)j * 3 + 1] - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
-                    const float lz = fbz - a.fbar[(size_t)j * 3 + 2] - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+                    const float4 fbj = a.fbar[j];
+                    const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
+                    const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
+                    const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     const float rinv = inv_norm(r2);
                     rl = (pd.x * lx + pd.y * ly + pd.z * lz) * rinv;
@@ -764,30 +807,54 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         __syncwarp();
 
         // ---------------------------------------------------------------- reverse through the network
-        for (int mu = sl; mu < NN; mu += SW) {
-            float v = 0.0f;
+        // ebar of every atom of the batch (one structure per atom)
+        float ebg[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) ebg[g] = __shfl_sync(FULL, eb, g * SW);
+        for (int mu = lane; mu < NN; mu += 32) {
+            float v[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) v[g] = 0.0f;
             const float *wt = W0T + (size_t)ti * ND * NN + mu;
 #pragma unroll 5
-            for (int q = 0; q < ND; ++q) v += wt[(size_t)q * NN] * at.dqt[q];
-            const float h = a.st_h[(size_t)wi * NN + mu];
-            const float hp = 1.0f - h * h;
-            const float hpp = -2.0f * h * hp;
-            const float wv = w1[ti * NN + mu];
-            const float ze = eb * wv * hp + wv * hpp * v;
-            u[mu] = ze;  // u now holds zeta
-            if (act) {
-                a.zt[(size_t)wi * NN + mu] = ze;
-                a.ut[(size_t)wi * NN + mu] = wv * hp;
-                a.om[(size_t)wi * NN + mu] = eb * h + hp * v;
+            for (int q = 0; q < ND; ++q) {
+                const float wv = wt[(size_t)q * NN];
+#pragma unroll
+                for (int g = 0; g < G; ++g) v[g] += wv * sm.at[g].dqt[q];
+            }
+            const float wo = w1[ti * NN + mu];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int wg = bp0 + (g < nb ? g : 0);
+                const float h = a.st_h[(size_t)wg * NN + mu];
+                const float hp = 1.0f - h * h;
+                const float hpp = -2.0f * h * hp;
+                const float ze = ebg[g] * wo * hp + wo * hpp * v[g];
+                tail[g * NN + mu] = ze;  // zeta of atom g
+                if (g < nb) {
+                    a.zt[(size_t)wg * NN + mu] = ze;
+                    a.ut[(size_t)wg * NN + mu] = wo * hp;
+                    a.om[(size_t)wg * NN + mu] = ebg[g] * h + hp * v[g];
+                }
             }
         }
         __syncwarp();
-        for (int v = sl; v < ND; v += SW) {
+        for (int v = lane; v < ND; v += 32) {
+            float e[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) e[g] = 0.0f;
             const float *wr = W0 + (size_t)ti * NN * ND + v;
-            float e = 0.0f;
-            for (int mu = 0; mu < NN; ++mu) e += wr[(size_t)mu * ND] * u[mu];
-            at.ab[v] = e * scale[v];
-            if (act) a.dqt[(size_t)wi * ND + v] = at.dqt[v];
+            for (int mu = 0; mu < NN; ++mu) {
+                const float wv = wr[(size_t)mu * ND];
+#pragma unroll
+                for (int g = 0; g < G; ++g) e[g] += wv * tail[g * NN + mu];
+            }
+            const float sc = scale[v];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                sm.at[g].ab[v] = e[g] * sc;
+                if (g < nb) a.dqt[(size_t)(bp0 + g) * ND + v] = sm.at[g].dqt[v];
+            }
         }
         __syncwarp();
 
@@ -848,9 +915,10 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     const float4 pd = a.pair[beg + k];
                     const int j = pair_j(pd);
                     tj = pair_t(pd);
-                    const float lx = fbx - a.fbar[(size_t)j * 3] - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
-                    const float ly = fby - a.fbar[(size_t)j * 3 + 1] - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
-                    const float lz = fbz - a.fbar[(size_t)j * 3 + 2] - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+                    const float4 fbj = a.fbar[j];
+                    const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
+                    const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
+                    const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     const float rinv = inv_norm(r2);
                     const float r = r2 * rinv;
