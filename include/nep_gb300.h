@@ -136,6 +136,21 @@ int nep_descriptors(nep_ctx *ctx, float *q_dev);
  * (helper for the normalisation factors of Eq. "norm"). */
 int nep_descriptor_range(nep_ctx *ctx, float *qmin_dev, float *qmax_dev);
 
+/* Same result as nep_descriptor_range, for callers that cannot allocate device memory
+ * during the call: code running while a stream is being captured into a CUDA graph
+ * (where cudaMalloc/cudaFree are not allowed), hosts whose own memory manager owns
+ * every device allocation, or latency-critical loops that must not enter the driver's
+ * allocator.  The paper has no counterpart; it is a library-interface addition.
+ * The call allocates and frees nothing: the raw descriptors go to a fixed scratch array
+ * of 8,388,608 floats (32 MiB) that lives in the library for the whole process on every
+ * GPU that loads it.  Batches with N_a x (padded descriptor length) above that size are
+ * rejected with NEP_EINVAL (the message gives the limit).  The first call on a device
+ * looks up the array's device address; make that first call before any stream capture.
+ * All calls share the one array, so calls whose GPU work overlaps (other streams,
+ * other contexts on the same GPU) race; calls queued on one stream are safe.  Queued on
+ * the context's stream, without waiting.  Errors: NEP_ESTATE, NEP_EINVAL, NEP_ECUDA. */
+int nep_descriptor_range_noalloc(nep_ctx *ctx, float *qmin_dev, float *qmax_dev);
+
 /* One full loss + parameter-gradient pass (Eq. "loss"):
  *   DE = 1/N_s sum_s ((E_s - E_ref_s)/N_a^s)^2
  *   DF = 1/(3 N_a) sum_i |F_i - F_ref_i|^2

@@ -1,0 +1,46 @@
+"""The allocation-free descriptor range (nep_descriptor_range_noalloc) agrees with the
+regular entry point.
+
+That entry point exists for callers that cannot allocate device memory during a call
+(inside CUDA-graph stream capture, under a host-owned memory manager, or in loops that
+must stay out of the allocator); it keeps its scratch in a fixed array inside the
+library.  This file is named to run last: it checks two calls in a row through the C
+ABI, and it must also pass on its own in a fresh process, where the first call does the
+one-time lookup of the scratch array's device address.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2606_19557_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def test_noalloc_descriptor_range_matches_regular_entry_point():
+    from paper_2606_19557_gb300 import NEP
+    spec = synth.SPECS["fcc_bcc_t1"]
+    batch = synth.batch_fcc_bcc(seed=21, n_struct=12)
+    nep = NEP(spec)
+    nep.set_structures_batch(batch)
+    theta = torch.tensor(synth.random_theta(nep.P, 3), dtype=torch.float32)
+    nep.set_params(theta, torch.ones(nep.n_des))
+    lo_ref, hi_ref = [x.cpu().numpy() for x in nep.descriptor_range()]
+
+    fn = nep.lib.nep_descriptor_range_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    for _ in range(2):  # two calls in a row share (and overwrite) the scratch array
+        lo = torch.full((nep.n_des,), float("nan"), dtype=torch.float32, device="cuda")
+        hi = torch.full((nep.n_des,), float("nan"), dtype=torch.float32, device="cuda")
+        nep._enter()
+        rc = fn(nep.h, ctypes.c_void_p(lo.data_ptr()), ctypes.c_void_p(hi.data_ptr()))
+        nep._leave()
+        assert rc == 0, nep.lib.nep_last_error(nep.h).decode()
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(lo.cpu().numpy(), lo_ref, rtol=TOL, atol=0)
+        np.testing.assert_allclose(hi.cpu().numpy(), hi_ref, rtol=TOL, atol=0)
