@@ -165,6 +165,13 @@ int nep_loss_grad(nep_ctx *ctx, const double *E_ref_dev, const float *F_ref_dev,
                   const uint8_t *has_W_dev, double lamE, double lamF, double lamV, double *loss3_dev,
                   float *grad_dev);
 
+/* Normalisers of Eq. "loss" for a batch that is one shard of a larger one: N_s, N_a
+ * and N_s^V of the whole batch (0 = use this context's own counts, the default).  With
+ * them, the loss terms and gradients of the shards add up to those of the whole batch,
+ * so one sum over shards (e.g. an all-reduce across GPUs) gives the full-batch pass.
+ * Errors: NEP_EINVAL (negative or non-finite). */
+int nep_set_loss_normalizers(nep_ctx *ctx, double N_s, double N_a, double N_s_V);
+
 /* Vector-Jacobian product for autograd: grad_dev [P] = d/dtheta of
  *   sum_s dE_s E_s + sum_i dF_i . F_i + sum_s dW_s : W_s
  * with cotangents dE_dev [n_struct] f64, dF_dev [N_a*3] f32, dW_dev [n_struct*9] f64.

@@ -83,6 +83,7 @@ def load_library():
             "nep_descriptor_range": (I, [P, P, P]),
             "nep_loss_grad": (I, [P, P, P, P, P, D, D, D, P, P]),
             "nep_backward": (I, [P, P, P, P, P]),
+            "nep_set_loss_normalizers": (I, [P, D, D, D]),
             "nep_set_targets": (I, [P, P, P, P, P]),
             "nep_loss_grad_host": (I, [P, P, D, D, D, P, P]),
             "nep_set_schedule": (I, [P, I]),
@@ -257,6 +258,10 @@ class NEP:
                    float(lam[2]), _ptr(loss3), _ptr(grad))
         self._refs = (Er, Fr, Wr, hw)
         return loss3, grad
+
+    def set_loss_normalizers(self, N_s: float = 0.0, N_a: float = 0.0, N_s_V: float = 0.0):
+        """Global N_s, N_a, N_s^V for a shard of a larger batch (0 = this batch's own)."""
+        self._check(self.lib.nep_set_loss_normalizers(self.h, float(N_s), float(N_a), float(N_s_V)))
 
     def backward(self, dE, dF, dW):
         """d/dtheta of dE.E + dF.F + dW:W, using the state of the latest eval()."""

@@ -542,6 +542,17 @@ int nep_loss_grad(nep_ctx *c, const double *Er, const float *Fr, const double *W
     return NEP_OK;
 }
 
+int nep_set_loss_normalizers(nep_ctx *c, double Ns, double Na, double NsV) {
+    if (!c) return NEP_EINVAL;
+    if (!(Ns >= 0.0) || !(Na >= 0.0) || !(NsV >= 0.0) || !std::isfinite(Ns + Na + NsV))
+        return c->fail(NEP_EINVAL, "normalisers must be finite and >= 0");
+    c->ov_Ns = Ns;
+    c->ov_Na = Na;
+    c->ov_NsV = NsV;
+    drop_graphs(c);
+    return NEP_OK;
+}
+
 int nep_backward(nep_ctx *c, const double *dE, const float *dF, const double *dW, float *grad) {
     if (!c) return NEP_EINVAL;
     int rc = ready(c);

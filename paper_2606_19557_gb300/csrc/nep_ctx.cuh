@@ -127,6 +127,11 @@ struct Ctx {
     bool have_targets = false, tgt_has_hw = false;
     DevBuf hostbuf_theta;             // device copy target of nep_loss_grad_host
 
+    // loss normalisers (0 = this batch's own N_s, N_a, N_s^V); set for one shard of a batch
+    double ov_Ns = 0.0, ov_Na = 0.0, ov_NsV = 0.0;
+    double norm_Ns() const { return ov_Ns > 0.0 ? ov_Ns : (double)n_struct; }
+    double norm_Na() const { return ov_Na > 0.0 ? ov_Na : (double)n_atoms; }
+
     int schedule = NEP_SCHED_PERSISTENT;
     // plain form (per-structure launches)
     bool plain_ready = false;

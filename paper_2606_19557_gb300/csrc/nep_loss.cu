@@ -130,13 +130,13 @@ __global__ void k_gather(int64_t a0, int64_t a1, const int64_t *nbr_off, const i
 // E_s = sum_i E_i and W_s = sum_i W_i in FP64 (Eq. 1); loss terms and cotangents of Eq. "loss".
 __global__ void k_struct(int64_t s0, int64_t s1, const int64_t *atom_off, const float *E_atom, const float *W_atom,
                          double *E_out, double *W_out, int loss, const double *E_ref, const double *W_ref,
-                         const uint8_t *has_W, const int *n_sv, double lamE, double lamV, double Ns, float *ebar,
-                         float *wbar, double *part /*[grid][3]*/) {
+                         const uint8_t *has_W, const int *n_sv, double nsv_over, double lamE, double lamV, double Ns,
+                         float *ebar, float *wbar, double *part /*[grid][3]*/) {
     __shared__ double wp[32][3];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * nw + wib, W = (int64_t)gridDim.x * nw;
     double aE = 0.0, aV = 0.0, ab1 = 0.0;
-    const double NsV = loss ? (double)(*n_sv) : 0.0;
+    const double NsV = loss ? (nsv_over > 0.0 ? nsv_over : (double)(*n_sv)) : 0.0;
     for (int64_t s = s0 + gw; s < s1; s += W) {
         const int64_t b = atom_off[s], e = atom_off[s + 1];
         double E = 0.0, Wv[9];
@@ -198,8 +198,8 @@ __global__ void k_count_hasw(int64_t ns, const uint8_t *has_W, int *n_sv) {
     }
 }
 
-__global__ void k_loss_final(const double *fpart, int nf, const double *spart, int nsb, const int *n_sv, double Ns,
-                             double Na, double *loss3, double *gb1) {
+__global__ void k_loss_final(const double *fpart, int nf, const double *spart, int nsb, const int *n_sv,
+                             double nsv_over, double Ns, double Na, double *loss3, double *gb1) {
     __shared__ double sh[4][256];
     double a[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = threadIdx.x; k < nsb; k += blockDim.x) {
@@ -216,7 +216,7 @@ __global__ void k_loss_final(const double *fpart, int nf, const double *spart, i
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double nsv = (double)(*n_sv);
+        const double nsv = nsv_over > 0.0 ? nsv_over : (double)(*n_sv);
         loss3[0] = Ns > 0 ? sh[0][0] / Ns : 0.0;
         loss3[1] = Na > 0 ? sh[1][0] / (3.0 * Na) : 0.0;
         loss3[2] = nsv > 0 ? sh[2][0] / (9.0 * nsv) : 0.0;
@@ -531,7 +531,7 @@ int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool lo
                   double *part, int nblocks) {
     if (a1 <= a0) return NEP_OK;
     const int nb = nblocks > 0 ? nblocks : gather_blocks(c);
-    const float coef = (float)(lamF * 2.0 / (3.0 * (double)c->n_atoms));
+    const float coef = (float)(lamF * 2.0 / (3.0 * c->norm_Na()));
     k_gather<<<nb, 256, 0, c->stream>>>(a0, a1, c->nbr_off.as<int64_t>(), c->rev.as<int>(), (const float4 *)c->G.ptr,
                                         c->F_own.as<float>(), F_out, F_ref, coef, loss ? 1 : 0, c->fbar.as<float>(),
                                         part ? part : c->loss_part.as<double>());
@@ -552,7 +552,7 @@ int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, con
     const int nb = nblocks > 0 ? nblocks : struct_blocks(c);
     k_struct<<<nb, 256, 0, c->stream>>>(s0, s1, c->atom_off.as<int64_t>(), c->E_atom.as<float>(),
                                         c->W_atom.as<float>(), E_out, W_out, loss ? 1 : 0, E_ref, W_ref, has_W,
-                                        c->n_sv.as<int>(), lamE, lamV, (double)c->n_struct, c->ebar.as<float>(),
+                                        c->n_sv.as<int>(), c->ov_NsV, lamE, lamV, c->norm_Ns(), c->ebar.as<float>(),
                                         c->wbar.as<float>(), part ? part : c->loss_part.as<double>() + gather_blocks(c));
     CK_LAUNCH("k_struct");
     return NEP_OK;
@@ -565,8 +565,8 @@ int launch_loss_final(Ctx *c, double *loss3, const double *fpart, int nf, const 
         spart = c->loss_part.as<double>() + gather_blocks(c);
         nsb = c->n_struct > 0 ? struct_blocks(c) : 0;
     }
-    k_loss_final<<<1, 256, 0, c->stream>>>(fpart, nf, spart, nsb, c->n_sv.as<int>(), (double)c->n_struct,
-                                           (double)c->n_atoms, loss3, c->gb1.as<double>());
+    k_loss_final<<<1, 256, 0, c->stream>>>(fpart, nf, spart, nsb, c->n_sv.as<int>(), c->ov_NsV, c->norm_Ns(),
+                                           c->norm_Na(), loss3, c->gb1.as<double>());
     CK_LAUNCH("k_loss_final");
     return NEP_OK;
 }

@@ -294,3 +294,39 @@ def test_plain_form_matches_oracle(name):
     l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, c.batch, c.E_ref, c.F_ref, c.W_ref)[:2]
     np.testing.assert_allclose(l3, l3o, rtol=TOL)
     assert rel(g, go) < TOL
+
+
+def test_shards_sum_to_full_batch():
+    """Two shards evaluated with the whole batch's normalisers add up to the full pass."""
+    from paper_2606_19557_gb300 import NEP, NepError, shard
+    c = get_case("alloy_t4")
+    b = c.batch
+    hw = np.ones(b.n_struct, np.uint8)
+    hw[1::4] = 0
+    lam = (1.0, 2.0, 0.3)
+    norms = shard.global_normalizers(b.counts(), hw)
+    L = np.zeros(3)
+    G = np.zeros(len(c.theta))
+    for idx in shard.partition(b.counts(), 2):
+        sub = b.subset(idx)
+        a_idx = np.concatenate([np.arange(b.atom_off[i], b.atom_off[i + 1]) for i in idx])
+        nep = NEP(c.spec)
+        nep.set_structures_batch(sub)
+        nep.set_params(torch.tensor(c.theta, dtype=torch.float32), torch.tensor(c.qs, dtype=torch.float32))
+        nep.set_loss_normalizers(*norms)
+        l3, g = nep.loss_grad(c.E_ref[idx], c.F_ref[a_idx], c.W_ref[idx], hw[idx], lam)
+        L += l3.cpu().numpy()
+        G += g.cpu().numpy().astype(np.float64)
+        with pytest.raises(NepError):
+            nep.set_loss_normalizers(-1.0, 0.0, 0.0)
+        # back to the shard's own counts: now it is the shard's standalone loss
+        nep.set_loss_normalizers()
+        l3s, gs = nep.loss_grad(c.E_ref[idx], c.F_ref[a_idx], c.W_ref[idx], hw[idx], lam)
+        l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, sub, c.E_ref[idx], c.F_ref[a_idx], c.W_ref[idx],
+                                   hw[idx], lam)[:2]
+        np.testing.assert_allclose(l3s.cpu().numpy(), l3o, rtol=TOL)
+        assert rel(gs.cpu().numpy(), go) < TOL
+        nep.close()
+    l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, b, c.E_ref, c.F_ref, c.W_ref, hw, lam)[:2]
+    np.testing.assert_allclose(L, l3o, rtol=TOL)
+    assert rel(G, go) < TOL
