@@ -488,6 +488,12 @@ __device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes, int lan
     for (const char *q = c + 128 * lane; q < e; q += 128 * nlanes) asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
 }
 
+// Record k of a pair list of length n through the read-only path, or a zero record past
+// the end: pair loops load the record of their next iteration one iteration ahead.
+__device__ __forceinline__ float4 pair_or_zero(const float4 *pr, int k, int n) {
+    return k < n ? __ldg(pr + k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
 __device__ __forceinline__ int pair_j(float4 p) { return __float_as_int(p.w) >> 4; }
 __device__ __forceinline__ int pair_t(float4 p) { return __float_as_int(p.w) & 15; }
 

@@ -60,7 +60,6 @@ struct AdjL {
     static constexpr int SGS = (S::NA + 3) & ~3;
     static constexpr int NLMO = (L3 + SW - 1) / SW;
     struct Atom {
-        float qt[S::ND];
         float b[S::ND];
         float ab[S::ND];
         float dqt[S::ND];
@@ -200,10 +199,13 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
         for (int j = 0; j < NLMO; ++j)
 #pragma unroll
             for (int n = 0; n < NA; ++n) accA[j][n] = 0.0f;
+        const float4 *prs = a.pair + beg;
+        float4 nxt = pair_or_zero(prs, sl, nAng);
         for (int c0 = 0; c0 < maxA; c0 += SW) {
             const int k = c0 + sl;
+            const float4 pd = nxt;
+            nxt = pair_or_zero(prs, k + SW, nAng);
             if (k < nAng) {
-                const float4 pd = a.pair[beg + k];
                 const int tj = pair_t(pd);
                 const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                 const float rinv = inv_norm(r2);
@@ -257,15 +259,17 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
 #pragma unroll
             for (int k = 0; k < VR; ++k) v[k] = 0.0f;
             int bcur = -1;
+            float4 nxr = pair_or_zero(prs, sl, nRad);
             for (int c0 = 0; c0 < maxR; c0 += SW) {
                 const int k = c0 + sl;
                 const bool valid = k < nRad;
+                const float4 pd = nxr;
+                nxr = pair_or_zero(prs, k + SW, nRad);
                 int tj = -1;
                 float f[KR];
 #pragma unroll
                 for (int kk = 0; kk < KR; ++kk) f[kk] = 0.0f;
                 if (valid) {
-                    const float4 pd = a.pair[beg + k];
                     tj = pair_t(pd);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
@@ -405,9 +409,12 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
         float W9[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) W9[k] = 0.0f;
+        // angular neighbours: angular and radial parts of G_p together
+        float4 nxf = pair_or_zero(prs, sl, nAng);
         for (int k = sl; k < nAng; k += SW) {
             const int64_t p = beg + k;
-            const float4 pd = a.pair[p];
+            const float4 pd = nxf;
+            nxf = pair_or_zero(prs, k + SW, nAng);
             const int tj = pair_t(pd);
             const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
             const float rinv = inv_norm(r2);
@@ -442,6 +449,13 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                 Vy += a1 * gy;
                 Vz += a1 * gz;
             });
+            {
+                float fr[KR], fpr[KR];
+                basis_val_der<KR>(r, a.inv_rcR, fr, fpr);
+                const float *be = beta + tj * KR;
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) srad += be[kk] * fpr[kk];
+            }
             const float uv = ux * Vx + uy * Vy + uz * Vz;
             const float Gx = srad * ux + (Vx - ux * uv) * rinv;
             const float Gy = srad * uy + (Vy - uy * uv) * rinv;
@@ -454,9 +468,12 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
             W9[3] -= Gy * pd.x; W9[4] -= Gy * pd.y; W9[5] -= Gy * pd.z;
             W9[6] -= Gz * pd.x; W9[7] -= Gz * pd.y; W9[8] -= Gz * pd.z;
         }
-        for (int k = sl; k < nRad; k += SW) {
+        // radial-only neighbours
+        nxf = pair_or_zero(prs, nAng + sl, nRad);
+        for (int k = nAng + sl; k < nRad; k += SW) {
             const int64_t p = beg + k;
-            const float4 pd = a.pair[p];
+            const float4 pd = nxf;
+            nxf = pair_or_zero(prs, k + SW, nRad);
             const int tj = pair_t(pd);
             const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
             const float rinv = inv_norm(r2);
@@ -468,14 +485,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
             for (int kk = 0; kk < KR; ++kk) s2 += be[kk] * fp[kk];
             s2 *= rinv;
             const float Gx = s2 * pd.x, Gy = s2 * pd.y, Gz = s2 * pd.z;
-            float4 gt = make_float4(Gx, Gy, Gz, 0.0f);
-            if (k < nAng) {
-                const float4 g0 = a.G[p];  // angular part, written by this lane above
-                gt.x += g0.x;
-                gt.y += g0.y;
-                gt.z += g0.z;
-            }
-            a.G[p] = gt;
+            a.G[p] = make_float4(Gx, Gy, Gz, 0.0f);
             Fx += Gx;
             Fy += Gy;
             Fz += Gz;
@@ -581,7 +591,6 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         }
 
         // ---------------------------------------------------------------- state of the forward pass
-        for (int e = sl; e < ND; e += SW) at.qt[e] = a.st_qt[(size_t)wi * ND + e];
         for (int e = sl; e < NA * L3; e += SW) at.A[e] = a.st_A[(size_t)wi * NA * L3 + e];
         for (int mu = lane; mu < NN; mu += 32) {
             const float wo = w1[ti * NN + mu];
@@ -635,6 +644,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                 }
             }
         }
+        const float4 *prs = a.pair + beg;
         const float4 fbi = a.fbar[i];
         const float fbx = fbi.x, fby = fbi.y, fbz = fbi.z;
         float Wb[9];
@@ -650,10 +660,12 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
             for (int j = 0; j < NLMO; ++j)
 #pragma unroll
                 for (int n = 0; n < NA; ++n) accd[j][n] = 0.0f;
+            float4 nxt = pair_or_zero(prs, sl, nAng);
             for (int c0 = 0; c0 < maxA; c0 += SW) {
                 const int k = c0 + sl;
+                const float4 pd = nxt;
+                nxt = pair_or_zero(prs, k + SW, nAng);
                 if (k < nAng) {
-                    const float4 pd = a.pair[beg + k];
                     const int j = pair_j(pd), tj = pair_t(pd);
                     const float4 fbj = a.fbar[j];
                     const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
@@ -720,16 +732,18 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
             for (int k = 0; k < VR2; ++k) v[k] = 0.0f;
             int bcur = -1;
+            float4 nxt = pair_or_zero(prs, sl, nRad);
             for (int c0 = 0; c0 < maxR; c0 += SW) {
                 const int k = c0 + sl;
                 const bool valid = k < nRad;
+                const float4 pd = nxt;
+                nxt = pair_or_zero(prs, k + SW, nRad);
                 int tj = -1;
                 float f[KR], fp[KR];
 #pragma unroll
                 for (int kk = 0; kk < KR; ++kk) f[kk] = fp[kk] = 0.0f;
                 float rl = 0.0f;
                 if (valid) {
-                    const float4 pd = a.pair[beg + k];
                     const int j = pair_j(pd);
                     tj = pair_t(pd);
                     const float4 fbj = a.fbar[j];
@@ -902,9 +916,12 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
             for (int e = 0; e < VA; ++e) X[e] = 0.0f;
             int bcur = -1;
+            float4 nxt = pair_or_zero(prs, sl, nAng);
             for (int c0 = 0; c0 < maxA; c0 += SW) {
                 const int k = c0 + sl;
                 const bool valid = k < nAng;
+                const float4 pd = nxt;
+                nxt = pair_or_zero(prs, k + SW, nAng);
                 int tj = -1;
                 float f[KA], fp[KA], al[NA], be[NA];
 #pragma unroll
@@ -912,7 +929,6 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
                 for (int n = 0; n < NA; ++n) al[n] = be[n] = 0.0f;
                 if (valid) {
-                    const float4 pd = a.pair[beg + k];
                     const int j = pair_j(pd);
                     tj = pair_t(pd);
                     const float4 fbj = a.fbar[j];
