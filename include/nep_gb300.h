@@ -191,6 +191,83 @@ int nep_set_targets(nep_ctx *ctx, const double *E_ref_dev, const float *F_ref_de
 int nep_loss_grad_host(nep_ctx *ctx, const float *theta_host, double lamE, double lamF, double lamV,
                        double *loss3_host, float *grad_host);
 
+/* ---------------------------------------------------------------- training loop
+ * Optimiser of Sec. "Training": Adam with the AMSGrad variant that keeps the maximum
+ * of the BIAS-CORRECTED second moment,
+ *   m_t = b1 m + (1-b1) g,  v_t = b2 v + (1-b2) g^2,  m^ = m_t/(1-b1^t),  v^ = v_t/(1-b2^t),
+ *   v^max = max(v^max, v^),  theta -= eta m^ / (sqrt(v^max) + eps),
+ * applied to the context's own parameter copy (set by nep_set_params), and the
+ * epoch-level plateau schedule eta <- max(factor eta, lr_min) after `patience`
+ * consecutive epochs whose mean loss L_e fails L_e < best (1 - threshold).
+ * Parameters stay FP32; moments and update arithmetic are FP64 on the device.  All
+ * state lives on the device, so steps need no host round trip. */
+typedef struct {
+    double lr;        /* eta at the start (and after nep_optim_set_lr), > 0 */
+    double beta1;     /* [0, 1), paper: 0.9 */
+    double beta2;     /* [0, 1), paper: 0.999 */
+    double eps;       /* >= 0, paper: 1e-8 */
+    double factor;    /* plateau reduction gamma, (0, 1) */
+    int patience;     /* p >= 1 consecutive epochs without improvement */
+    double lr_min;    /* floor of eta, >= 0 */
+    double threshold; /* relative improvement threshold tau, [0, 1) */
+} nep_optim_config;
+
+/* Zeroes the moments, sets t = 0 and eta = cfg->lr, forgets the best loss.
+ * Errors: NEP_EINVAL (a value out of range), NEP_ENOMEM, NEP_ECUDA. */
+int nep_optim_init(nep_ctx *ctx, const nep_optim_config *cfg);
+
+/* One optimiser step on the context's parameters with gradient grad_dev [P] f32
+ * (device).  loss_dev (device, 1 double, or NULL) is added to the epoch's loss sum.
+ * Asynchronous on the context's stream.  Errors: NEP_ESTATE (no nep_optim_init). */
+int nep_optim_step(nep_ctx *ctx, const float *grad_dev, const double *loss_dev);
+
+/* One training step on the whole cached batch: nep_loss_grad at the current
+ * parameters against the references of nep_set_targets (weights lamE, lamF, lamV),
+ * then the optimiser step; the step's loss L = lamE DE + lamF DF + lamV DV joins the
+ * epoch sum.  One CUDA graph.  loss3_dev (device [3] or NULL) receives DE, DF, DV
+ * at the parameters BEFORE the update.  Errors: NEP_ESTATE, NEP_EINVAL, NEP_ECUDA. */
+int nep_train_step(nep_ctx *ctx, double lamE, double lamF, double lamV, double *loss3_dev);
+
+/* Epoch boundary: mean loss of the steps since the previous boundary, improvement
+ * test and, after `patience` bad epochs, the rate reduction (all on the device). */
+int nep_optim_epoch_end(nep_ctx *ctx);
+
+/* Start of a stage of the two-stage protocol: eta = lr and the plateau schedule
+ * restarts (best loss forgotten); moments and t are kept.  Errors: NEP_EINVAL. */
+int nep_optim_set_lr(nep_ctx *ctx, double lr);
+
+/* Optimiser state, copied to the host (synchronizes): out_host[6] = t, eta, best
+ * epoch loss, bad epochs, latest epoch loss (NaN before the first), reductions. */
+int nep_optim_state(nep_ctx *ctx, double *out_host);
+
+/* Copies the context's current parameters into theta_dev [P] f32 (device). */
+int nep_get_params(nep_ctx *ctx, float *theta_dev);
+
+/* ---------------------------------------------------------------- mini-batch mode
+ * Sec. "Training": every optimisation step uses a mini-batch of structures while the
+ * geometry (neighbour lists, pair records) of the whole cached batch is built once.
+ * nep_minibatch_setup splits the cached batch into groups of batch_size CONSECUTIVE
+ * structures (the last group may be smaller; shuffle the structures before
+ * nep_set_structures to randomise the composition) and builds each group's kernel
+ * schedule on the host, once.  *n_batches (may be NULL) receives the group count.
+ * Invalidated by nep_set_structures.  Errors: NEP_ESTATE, NEP_EINVAL, NEP_ENOMEM. */
+int nep_minibatch_setup(nep_ctx *ctx, int batch_size, int64_t *n_batches);
+
+/* Loss and gradient of group m alone (normalisers N_s, N_a, N_s^V of the group)
+ * against the references of nep_set_targets; outputs as nep_loss_grad (device). */
+int nep_minibatch_loss_grad(nep_ctx *ctx, int64_t m, double lamE, double lamF, double lamV, double *loss3_dev,
+                            float *grad_dev);
+
+/* nep_minibatch_loss_grad of group m followed by the optimiser step; the group's
+ * weighted loss joins the epoch sum.  loss3_dev: device [3] or NULL. */
+int nep_minibatch_train_step(nep_ctx *ctx, int64_t m, double lamE, double lamF, double lamV, double *loss3_dev);
+
+/* One epoch driven by the library: training steps on the groups order_host[0..n_steps)
+ * in that order, then nep_optim_epoch_end.  Asynchronous (no host synchronisation).
+ * Errors: NEP_EINVAL (an index out of range: nothing is launched). */
+int nep_minibatch_epoch(nep_ctx *ctx, const int64_t *order_host, int64_t n_steps, double lamE, double lamF,
+                        double lamV);
+
 /* Selects NEP_SCHED_PERSISTENT (default) or NEP_SCHED_PLAIN. */
 int nep_set_schedule(nep_ctx *ctx, int schedule);
 

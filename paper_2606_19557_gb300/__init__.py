@@ -39,6 +39,13 @@ class NepError(RuntimeError):
         self.code = code
 
 
+class OptimConfig(ctypes.Structure):
+    """nep_optim_config: AMSGrad (paper defaults beta1 0.9, beta2 0.999, eps 1e-8) and the plateau schedule."""
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("factor", ctypes.c_double), ("patience", ctypes.c_int),
+                ("lr_min", ctypes.c_double), ("threshold", ctypes.c_double)]
+
+
 class _Config(ctypes.Structure):
     _fields_ = [("n_types", ctypes.c_int), ("rc_R", ctypes.c_float), ("rc_A", ctypes.c_float),
                 ("n_max_R", ctypes.c_int), ("n_max_A", ctypes.c_int), ("basis_R", ctypes.c_int),
@@ -86,6 +93,17 @@ def load_library():
             "nep_set_loss_normalizers": (I, [P, D, D, D]),
             "nep_set_targets": (I, [P, P, P, P, P]),
             "nep_loss_grad_host": (I, [P, P, D, D, D, P, P]),
+            "nep_optim_init": (I, [P, ctypes.POINTER(OptimConfig)]),
+            "nep_optim_step": (I, [P, P, P]),
+            "nep_train_step": (I, [P, D, D, D, P]),
+            "nep_optim_epoch_end": (I, [P]),
+            "nep_optim_set_lr": (I, [P, D]),
+            "nep_optim_state": (I, [P, P]),
+            "nep_get_params": (I, [P, P]),
+            "nep_minibatch_setup": (I, [P, I, ctypes.POINTER(I64)]),
+            "nep_minibatch_loss_grad": (I, [P, I64, D, D, D, P, P]),
+            "nep_minibatch_train_step": (I, [P, I64, D, D, D, P]),
+            "nep_minibatch_epoch": (I, [P, P, I64, D, D, D]),
             "nep_set_schedule": (I, [P, I]),
             "nep_autotune": (I, [P]),
             "nep_get_launch": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -298,6 +316,79 @@ class NEP:
         return loss3_host, grad_host
 
     # ------------------------------------------------------------------ scheduling
+    # ---------------------------------------------------------------- training loop (Sec. "Training")
+    def optim_init(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                   factor: float = 0.5, patience: int = 5, lr_min: float = 0.0, threshold: float = 0.0):
+        """AMSGrad state (moments zeroed, t = 0) and the plateau schedule, on the device."""
+        cfg = OptimConfig(float(lr), float(beta1), float(beta2), float(eps), float(factor), int(patience),
+                          float(lr_min), float(threshold))
+        self._call(self.lib.nep_optim_init, ctypes.byref(cfg))
+
+    def optim_step(self, grad, loss=None):
+        """One AMSGrad step on the context's parameters; ``loss`` (device scalar) joins the epoch mean."""
+        t = self.torch
+        g = self._dev(grad, t.float32).reshape(-1)
+        lo = None if loss is None else self._dev(loss, t.float64).reshape(-1)
+        self._call(self.lib.nep_optim_step, _ptr(g), _ptr(lo))
+        self._opt_refs = (g, lo)
+
+    def train_step(self, lam: Sequence[float] = (1.0, 1.0, 0.1), loss3=None):
+        """Loss + gradient at the current parameters, then the AMSGrad step (one graph).
+        Returns loss3 (DE, DF, DV before the update), a float64 device tensor."""
+        t = self.torch
+        if loss3 is None:
+            loss3 = t.empty(3, dtype=t.float64, device=self.device)
+        self._call(self.lib.nep_train_step, float(lam[0]), float(lam[1]), float(lam[2]), _ptr(loss3))
+        return loss3
+
+    def optim_epoch_end(self):
+        self._call(self.lib.nep_optim_epoch_end)
+
+    def optim_set_lr(self, lr: float):
+        """Stage start: learning rate set, plateau schedule restarted (moments kept)."""
+        self._call(self.lib.nep_optim_set_lr, float(lr))
+
+    def optim_state(self) -> dict:
+        out = (ctypes.c_double * 6)()
+        self._check(self.lib.nep_optim_state(self.h, out))
+        keys = ("t", "lr", "best", "bad_epochs", "last_epoch_loss", "reductions")
+        return {k: float(v) for k, v in zip(keys, out)}
+
+    def get_params(self):
+        t = self.torch
+        th = t.empty(self.P, dtype=t.float32, device=self.device)
+        self._call(self.lib.nep_get_params, _ptr(th))
+        return th
+
+    # ---------------------------------------------------------------- mini-batch mode
+    def minibatch_setup(self, batch_size: int) -> int:
+        """Groups of ``batch_size`` consecutive cached structures; returns the group count."""
+        n = ctypes.c_int64()
+        self._call(self.lib.nep_minibatch_setup, int(batch_size), ctypes.byref(n))
+        self.n_minibatches = int(n.value)
+        return self.n_minibatches
+
+    def minibatch_loss_grad(self, m: int, lam: Sequence[float] = (1.0, 1.0, 0.1)):
+        t = self.torch
+        loss3 = t.empty(3, dtype=t.float64, device=self.device)
+        grad = t.empty(self.P, dtype=t.float32, device=self.device)
+        self._call(self.lib.nep_minibatch_loss_grad, int(m), float(lam[0]), float(lam[1]), float(lam[2]),
+                   _ptr(loss3), _ptr(grad))
+        return loss3, grad
+
+    def minibatch_train_step(self, m: int, lam: Sequence[float] = (1.0, 1.0, 0.1), loss3=None):
+        self._call(self.lib.nep_minibatch_train_step, int(m), float(lam[0]), float(lam[1]), float(lam[2]),
+                   _ptr(loss3))
+        return loss3
+
+    def minibatch_epoch(self, order, lam: Sequence[float] = (1.0, 1.0, 0.1)):
+        """One epoch over the groups in ``order`` (host sequence of indices), then the
+        epoch boundary of the schedule; runs asynchronously on the context's stream."""
+        import numpy as np
+        o = np.ascontiguousarray(np.asarray(order, dtype=np.int64).reshape(-1))
+        self._call(self.lib.nep_minibatch_epoch, o.ctypes.data_as(ctypes.c_void_p), int(o.size), float(lam[0]),
+                   float(lam[1]), float(lam[2]))
+
     def set_schedule(self, mode: int):
         self._check(self.lib.nep_set_schedule(self.h, int(mode)))
 

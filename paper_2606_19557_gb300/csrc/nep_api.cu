@@ -143,11 +143,11 @@ static int default_shapes(Ctx *c) {
 }
 
 static void drop_graphs(Ctx *c) {
-    if (c->g_loss.exec) cudaGraphExecDestroy(c->g_loss.exec);
-    if (c->g_eval.exec) cudaGraphExecDestroy(c->g_eval.exec);
-    c->g_loss.exec = c->g_eval.exec = nullptr;
-    c->g_loss.key.clear();
-    c->g_eval.key.clear();
+    for (Ctx::Graph *g : {&c->g_loss, &c->g_eval, &c->g_train}) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+        g->key.clear();
+    }
 }
 
 static void mark(Ctx *c, int k) {
@@ -359,6 +359,8 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
     c->state_valid = false;
     c->have_targets = false;
     c->plain_ready = false;
+    c->mb.clear();
+    c->mb_B = 0;
     c->n_struct = ns;
     c->n_atoms = na;
     if (c->atom_off.ensure<int64_t>(ns + 1) || c->pos.ensure<float>(na * 3) || c->type.ensure<int>(na) ||
@@ -604,6 +606,182 @@ int nep_loss_grad_host(nep_ctx *c, const float *theta_host, double lE, double lF
     CK(cudaMemcpyAsync(grad_host, c->grad_int.ptr, sizeof(float) * c->P, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return NEP_OK;
+}
+
+int nep_optim_init(nep_ctx *c, const nep_optim_config *o) {
+    if (!c) return NEP_EINVAL;
+    if (!o) return c->fail(NEP_EINVAL, "null optimiser configuration");
+    const bool ok = std::isfinite(o->lr) && o->lr > 0.0 && o->beta1 >= 0.0 && o->beta1 < 1.0 && o->beta2 >= 0.0 &&
+                    o->beta2 < 1.0 && std::isfinite(o->eps) && o->eps >= 0.0 && o->factor > 0.0 && o->factor < 1.0 &&
+                    o->patience >= 1 && std::isfinite(o->lr_min) && o->lr_min >= 0.0 && o->threshold >= 0.0 &&
+                    o->threshold < 1.0;
+    if (!ok) return c->fail(NEP_EINVAL, "optimiser configuration out of range");
+    CK(cudaSetDevice(c->dev));
+    if (c->opt_m.ensure<double>(c->P) || c->opt_v.ensure<double>(c->P) || c->opt_vmax.ensure<double>(c->P) ||
+        c->opt_st.ensure<double>(OPT_NST))
+        return c->fail(NEP_ENOMEM, "optimiser state");
+    c->ocfg = *o;
+    int rc = launch_opt_reset(c);
+    if (rc) return rc;
+    c->have_opt = true;
+    drop_graphs(c);  // the training graph bakes in the optimiser constants
+    return NEP_OK;
+}
+
+int nep_optim_step(nep_ctx *c, const float *grad, const double *loss) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_opt) return c->fail(NEP_ESTATE, "no optimiser (call nep_optim_init)");
+    if (!c->have_params) return c->fail(NEP_ESTATE, "no parameters (call nep_set_params)");
+    if (!grad) return c->fail(NEP_EINVAL, "null gradient");
+    CK(cudaSetDevice(c->dev));
+    int rc = launch_opt_step(c, grad, nullptr, 0.0, 0.0, 0.0, loss);
+    if (rc) return rc;
+    c->state_valid = false;
+    return NEP_OK;
+}
+
+static int body_train(Ctx *c, double lE, double lF, double lV, double *loss3) {
+    int rc = body_loss(c, c->tgt_E.as<double>(), c->tgt_F.as<float>(), c->tgt_W.as<double>(),
+                       c->tgt_has_hw ? c->tgt_hw.as<uint8_t>() : nullptr, lE, lF, lV, loss3, c->grad_int.as<float>());
+    if (rc) return rc;
+    return launch_opt_step(c, c->grad_int.as<float>(), loss3, lE, lF, lV, nullptr);
+}
+
+int nep_train_step(nep_ctx *c, double lE, double lF, double lV, double *loss3) {
+    if (!c) return NEP_EINVAL;
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!c->have_targets) return c->fail(NEP_ESTATE, "no targets (call nep_set_targets)");
+    if (!c->have_opt) return c->fail(NEP_ESTATE, "no optimiser (call nep_optim_init)");
+    if (!std::isfinite(lE) || !std::isfinite(lF) || !std::isfinite(lV)) return c->fail(NEP_EINVAL, "non-finite weight");
+    CK(cudaSetDevice(c->dev));
+    double *l3 = loss3 ? loss3 : c->loss3_int.as<double>();
+    if (c->schedule == NEP_SCHED_PLAIN) {
+        rc = run_plain_loss(c, c->tgt_E.as<double>(), c->tgt_F.as<float>(), c->tgt_W.as<double>(),
+                            c->tgt_has_hw ? c->tgt_hw.as<uint8_t>() : nullptr, lE, lF, lV, l3, c->grad_int.as<float>());
+        if (!rc) rc = launch_opt_step(c, c->grad_int.as<float>(), l3, lE, lF, lV, nullptr);
+    } else {
+        uint64_t lb[3];
+        std::memcpy(&lb[0], &lE, 8);
+        std::memcpy(&lb[1], &lF, 8);
+        std::memcpy(&lb[2], &lV, 8);
+        std::vector<const void *> key = {l3, (const void *)(uintptr_t)lb[0], (const void *)(uintptr_t)lb[1],
+                                         (const void *)(uintptr_t)lb[2]};
+        rc = run_graph(c, c->g_train, key, [&] { return body_train(c, lE, lF, lV, l3); });
+        c->last_timed = c->timing;
+    }
+    if (rc) return rc;
+    c->state_valid = false;
+    return NEP_OK;
+}
+
+int nep_optim_epoch_end(nep_ctx *c) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_opt) return c->fail(NEP_ESTATE, "no optimiser (call nep_optim_init)");
+    CK(cudaSetDevice(c->dev));
+    return launch_opt_epoch(c);
+}
+
+int nep_optim_set_lr(nep_ctx *c, double lr) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_opt) return c->fail(NEP_ESTATE, "no optimiser (call nep_optim_init)");
+    if (!std::isfinite(lr) || !(lr > 0.0)) return c->fail(NEP_EINVAL, "learning rate must be finite and > 0");
+    CK(cudaSetDevice(c->dev));
+    return launch_opt_set_lr(c, lr);
+}
+
+int nep_optim_state(nep_ctx *c, double *out) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_opt) return c->fail(NEP_ESTATE, "no optimiser (call nep_optim_init)");
+    if (!out) return c->fail(NEP_EINVAL, "null output");
+    CK(cudaSetDevice(c->dev));
+    double st[OPT_NST];
+    CK(cudaMemcpyAsync(st, c->opt_st.ptr, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out[0] = st[OPT_T];
+    out[1] = st[OPT_LR];
+    out[2] = st[OPT_BEST];
+    out[3] = st[OPT_BAD];
+    out[4] = st[OPT_LAST];
+    out[5] = st[OPT_NRED];
+    return NEP_OK;
+}
+
+int nep_get_params(nep_ctx *c, float *theta) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_params) return c->fail(NEP_ESTATE, "no parameters (call nep_set_params)");
+    if (!theta) return c->fail(NEP_EINVAL, "null output");
+    CK(cudaSetDevice(c->dev));
+    if (c->P > 0) CK(cudaMemcpyAsync(theta, c->theta.ptr, sizeof(float) * c->P, cudaMemcpyDeviceToDevice, c->stream));
+    return NEP_OK;
+}
+
+int nep_minibatch_setup(nep_ctx *c, int batch_size, int64_t *n_batches) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures (call nep_set_structures)");
+    if (batch_size < 1) return c->fail(NEP_EINVAL, "batch size must be >= 1");
+    CK(cudaSetDevice(c->dev));
+    int rc = build_minibatches(c, batch_size);
+    if (rc) return rc;
+    if (n_batches) *n_batches = (int64_t)c->mb.size();
+    return NEP_OK;
+}
+
+static int mb_ready(nep_ctx *c, int64_t m) {
+    int rc = ready(c);
+    if (rc) return rc;
+    if (c->mb_B < 1) return c->fail(NEP_ESTATE, "no mini-batches (call nep_minibatch_setup)");
+    if (!c->have_targets) return c->fail(NEP_ESTATE, "no targets (call nep_set_targets)");
+    if (m < 0 || m >= (int64_t)c->mb.size()) return c->fail(NEP_EINVAL, "mini-batch index out of range");
+    return NEP_OK;
+}
+
+int nep_minibatch_loss_grad(nep_ctx *c, int64_t m, double lE, double lF, double lV, double *loss3, float *grad) {
+    if (!c) return NEP_EINVAL;
+    int rc = mb_ready(c, m);
+    if (rc) return rc;
+    if (!loss3 || !grad) return c->fail(NEP_EINVAL, "null output");
+    if (!std::isfinite(lE) || !std::isfinite(lF) || !std::isfinite(lV)) return c->fail(NEP_EINVAL, "non-finite weight");
+    CK(cudaSetDevice(c->dev));
+    if ((rc = run_minibatch_loss(c, m, lE, lF, lV, loss3, grad))) return rc;
+    c->state_valid = false;  // the per-atom state now holds one group only
+    return NEP_OK;
+}
+
+static int mb_train_step(nep_ctx *c, int64_t m, double lE, double lF, double lV, double *loss3) {
+    double *l3 = loss3 ? loss3 : c->loss3_int.as<double>();
+    int rc = run_minibatch_loss(c, m, lE, lF, lV, l3, c->grad_int.as<float>());
+    if (rc) return rc;
+    return launch_opt_step(c, c->grad_int.as<float>(), l3, lE, lF, lV, nullptr);
+}
+
+int nep_minibatch_train_step(nep_ctx *c, int64_t m, double lE, double lF, double lV, double *loss3) {
+    if (!c) return NEP_EINVAL;
+    int rc = mb_ready(c, m);
+    if (rc) return rc;
+    if (!c->have_opt) return c->fail(NEP_ESTATE, "no optimiser (call nep_optim_init)");
+    if (!std::isfinite(lE) || !std::isfinite(lF) || !std::isfinite(lV)) return c->fail(NEP_EINVAL, "non-finite weight");
+    CK(cudaSetDevice(c->dev));
+    if ((rc = mb_train_step(c, m, lE, lF, lV, loss3))) return rc;
+    c->state_valid = false;
+    return NEP_OK;
+}
+
+int nep_minibatch_epoch(nep_ctx *c, const int64_t *order, int64_t n_steps, double lE, double lF, double lV) {
+    if (!c) return NEP_EINVAL;
+    int rc = mb_ready(c, 0);
+    if (rc) return rc;
+    if (!c->have_opt) return c->fail(NEP_ESTATE, "no optimiser (call nep_optim_init)");
+    if (n_steps < 0 || (n_steps > 0 && !order)) return c->fail(NEP_EINVAL, "bad step list");
+    if (!std::isfinite(lE) || !std::isfinite(lF) || !std::isfinite(lV)) return c->fail(NEP_EINVAL, "non-finite weight");
+    for (int64_t k = 0; k < n_steps; ++k)
+        if (order[k] < 0 || order[k] >= (int64_t)c->mb.size())
+            return c->fail(NEP_EINVAL, "mini-batch index out of range");
+    CK(cudaSetDevice(c->dev));
+    for (int64_t k = 0; k < n_steps; ++k)
+        if ((rc = mb_train_step(c, order[k], lE, lF, lV, nullptr))) return rc;
+    c->state_valid = false;
+    return launch_opt_epoch(c);
 }
 
 int nep_set_schedule(nep_ctx *c, int schedule) {

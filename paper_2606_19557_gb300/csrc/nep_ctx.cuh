@@ -132,6 +132,24 @@ struct Ctx {
     double norm_Ns() const { return ov_Ns > 0.0 ? ov_Ns : (double)n_struct; }
     double norm_Na() const { return ov_Na > 0.0 ? ov_Na : (double)n_atoms; }
 
+    // optimiser (AMSGrad + plateau schedule); state slots OPT_*
+    bool have_opt = false;
+    nep_optim_config ocfg{};
+    DevBuf opt_m, opt_v, opt_vmax, opt_st;
+
+    // mini-batch mode: groups of consecutive structures, each with its own schedule
+    struct MiniBatch {
+        int64_t s0, s1, a0, a1;  // structure and atom ranges (work positions = [a0, a1))
+        int Wf, Wa;              // warps of the forward / adjoint launch (multiples of wpb)
+        int64_t wf_off, wa_off;  // offsets of the warp_begin slices in mb_wbf / mb_wba
+        int64_t ck_off;          // offset of the chunk list in mb_chunks (n_ck + 1 entries)
+        int n_ck;
+    };
+    int mb_B = 0;
+    int mb_key[6] = {-1, -1, -1, -1, -1, -1};  // launch shapes the schedules were built for
+    std::vector<MiniBatch> mb;
+    DevBuf mb_work, mb_wbf, mb_wba, mb_wlo, mb_whi, mb_chunks, mb_clo, mb_chi;
+
     int schedule = NEP_SCHED_PERSISTENT;
     // plain form (per-structure launches)
     bool plain_ready = false;
@@ -145,7 +163,7 @@ struct Ctx {
         std::vector<const void *> key;
         bool timing = false;
     };
-    Graph g_loss, g_eval;
+    Graph g_loss, g_eval, g_train;
     bool timing = false;
     cudaEvent_t ev[KID_COUNT + 1] = {};
     bool ev_made = false;
@@ -182,12 +200,18 @@ int build_neighbors(Ctx *c);
 // step pieces (nep_loss.cu)
 int launch_expand(Ctx *c);
 int launch_forward(Ctx *c, float *q_raw);
+// explicit schedules (mini-batch mode)
+int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks);
+int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks);
+int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks);
+int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi, const int *wlo, const int *whi,
+                            const int *warp_begin);
 int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1,
                   double *part = nullptr, int nblocks = 0);
 int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, const double *W_ref,
                   const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1,
                   double *part = nullptr, int nblocks = 0);
-int launch_count_hasw(Ctx *c, const uint8_t *has_W);
+int launch_count_hasw(Ctx *c, const uint8_t *has_W, int64_t s0 = 0, int64_t s1 = -1);
 int launch_loss_final(Ctx *c, double *loss3, const double *fpart = nullptr, int nf = -1,
                       const double *spart = nullptr, int nsb = -1);
 int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
@@ -197,6 +221,18 @@ int launch_adjoint(Ctx *c);
 int launch_ann_grad(Ctx *c);
 int launch_grad_final(Ctx *c, float *grad);
 int launch_range(Ctx *c, const float *q, float *qmin, float *qmax);
+
+// optimiser (nep_optim.cu); device state slots
+enum { OPT_T, OPT_B1T, OPT_B2T, OPT_LR, OPT_BEST, OPT_BAD, OPT_ACC, OPT_NACC, OPT_LAST, OPT_NRED, OPT_NST };
+int launch_opt_reset(Ctx *c);
+int launch_opt_set_lr(Ctx *c, double lr);
+int launch_opt_step(Ctx *c, const float *grad, const double *loss3, double lE, double lF, double lV,
+                    const double *loss1);
+int launch_opt_epoch(Ctx *c);
+
+// mini-batch mode (nep_minibatch.cu)
+int build_minibatches(Ctx *c, int batch_size);
+int run_minibatch_loss(Ctx *c, int64_t m, double lE, double lF, double lV, double *loss3, float *grad);
 int prepare_loss_kernels(Ctx *c);
 
 }  // namespace nep

@@ -524,6 +524,28 @@ int launch_adjoint(Ctx *c) {
     return NEP_OK;
 }
 
+int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks) {
+    if (blocks <= 0) return NEP_OK;
+    AtomArgs a = atom_args(c);
+    a.work = work;
+    a.warp_begin = warp_begin;
+    const size_t smem = c->ks->fwd_smem[c->fwd.var](c->T, c->NN) * c->fwd.wpb;
+    c->ks->launch_fwd[c->fwd.var](a, blocks, c->fwd.wpb, smem, c->stream);
+    CK_LAUNCH("k_forward");
+    return NEP_OK;
+}
+
+int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks) {
+    if (blocks <= 0) return NEP_OK;
+    AtomArgs a = atom_args(c);
+    a.work = work;
+    a.warp_begin = warp_begin;
+    const size_t smem = c->ks->adj_smem[c->adj.var](c->T, c->NN) * c->adj.wpb;
+    c->ks->launch_adj[c->adj.var](a, blocks, c->adj.wpb, smem, c->stream);
+    CK_LAUNCH("k_adjoint");
+    return NEP_OK;
+}
+
 static int gather_blocks(Ctx *c) { return c->n_sm * 4; }
 static int struct_blocks(Ctx *c) { return c->n_sm; }
 
@@ -539,8 +561,9 @@ int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool lo
     return NEP_OK;
 }
 
-int launch_count_hasw(Ctx *c, const uint8_t *has_W) {
-    k_count_hasw<<<1, 256, 0, c->stream>>>(c->n_struct, has_W, c->n_sv.as<int>());
+int launch_count_hasw(Ctx *c, const uint8_t *has_W, int64_t s0, int64_t s1) {
+    if (s1 < 0) s1 = c->n_struct;
+    k_count_hasw<<<1, 256, 0, c->stream>>>(s1 - s0, has_W ? has_W + s0 : nullptr, c->n_sv.as<int>());
     CK_LAUNCH("k_count_hasw");
     return NEP_OK;
 }
@@ -607,6 +630,15 @@ int launch_ann_grad(Ctx *c) {
     return NEP_OK;
 }
 
+int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks) {
+    if (n_chunks <= 0) return NEP_OK;
+    k_ann_grad<<<dim3(n_chunks, ann_groups(c)), ANN_TILES, ann_smem(c), c->stream>>>(
+        chunks, c->NN, c->NDP, c->zt.as<float>(), c->ut.as<float>(), c->om.as<float>(), c->st_qt.as<float>(),
+        c->dqt.as<float>(), c->annpart.as<float>());
+    CK_LAUNCH("k_ann_grad");
+    return NEP_OK;
+}
+
 static GradArgs grad_args(Ctx *c, float *grad) {
     GradArgs g;
     g.T = c->T;
@@ -634,6 +666,19 @@ static GradArgs grad_args(Ctx *c, float *grad) {
     g.grad = grad;
     g.acc = nullptr;
     return g;
+}
+
+int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi, const int *wlo, const int *whi,
+                            const int *warp_begin) {
+    GradArgs g = grad_args(c, grad);
+    g.clo = clo;
+    g.chi = chi;
+    g.wlo = wlo;
+    g.whi = whi;
+    g.warp_begin = warp_begin;
+    k_grad_final<<<(unsigned)((c->P * 32 + 255) / 256), 256, 0, c->stream>>>(g);
+    CK_LAUNCH("k_grad_final");
+    return NEP_OK;
 }
 
 int launch_grad_final(Ctx *c, float *grad) {

@@ -1,0 +1,194 @@
+// Mini-batch mode (Sec. "Training": each optimisation step uses a mini-batch of
+// structures; the geometry-dependent data are built once and kept on the GPU).
+//
+// The cached batch is split into groups of `batch_size` consecutive structures.  A
+// group is a contiguous range of structures and atoms, so the neighbour lists, the
+// pair records and the per-atom buffers of the whole batch serve every group as they
+// are: only the schedules differ.  For each group the host builds, once:
+//   * its work order (its atoms sorted by species, at work positions [a0, a1));
+//   * cost-balanced warp ranges for the forward and adjoint kernels, with as many warps
+//     as the group fills (one batch of atoms per warp when it is small);
+//   * the species runs of the adjoint warps and the network-gradient chunks.
+// A step then launches the same kernels as the whole-batch pass on those slices, with
+// the group's own normalisers N_s, N_a and N_s^V in Eq. "loss".
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "nep_ctx.cuh"
+
+namespace nep {
+
+namespace {
+
+// Cost-balanced split of the positions [p0, p1) (prefix costs pre, relative to p0) over W
+// warps; returns W + 1 global boundaries.
+std::vector<int> split_warps(const std::vector<double> &pre, int p0, int W) {
+    const int n = (int)pre.size() - 1;
+    std::vector<int> begin(W + 1, p0 + n);
+    const double tot = pre[n];
+    int q = 0;
+    for (int w = 0; w < W; ++w) {
+        const double target = tot * (double)w / (double)W;
+        while (q < n && pre[q] < target) ++q;
+        begin[w] = p0 + q;
+    }
+    for (int w = 1; w <= W; ++w) begin[w] = std::max(begin[w], begin[w - 1]);
+    return begin;
+}
+
+// First and last warp (relative to the launch) holding positions of each species.
+void species_warps(const std::vector<int> &begin, const std::vector<int> &tb /*[T+1] global*/, int T, int *wlo,
+                   int *whi) {
+    const int W = (int)begin.size() - 1;
+    auto owner = [&](int p) {
+        int lo = 0, hi = W - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (begin[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    for (int t = 0; t < T; ++t) {
+        wlo[t] = 0;
+        whi[t] = -1;
+        if (tb[t + 1] > tb[t]) {
+            wlo[t] = owner(tb[t]);
+            whi[t] = owner(tb[t + 1] - 1);
+        }
+    }
+}
+
+void shape_key(const Ctx *c, int *key) {
+    key[0] = c->fwd.var;
+    key[1] = c->fwd.wpb;
+    key[2] = c->fwd.W;
+    key[3] = c->adj.var;
+    key[4] = c->adj.wpb;
+    key[5] = c->adj.W;
+}
+
+}  // namespace
+
+int build_minibatches(Ctx *c, int B) {
+    const int64_t ns = c->n_struct, na = c->n_atoms;
+    const int T = c->T;
+    const int gf = 32 / c->ks->sw[c->fwd.var], ga = 32 / c->ks->sw[c->adj.var];
+    const int CH = 128;  // work positions per network-gradient chunk
+    std::vector<int> work(na);
+    std::vector<int> wbf, wba, wlo, whi, chunks, clo, chi;
+    std::vector<Ctx::MiniBatch> mbs;
+    for (int64_t s0 = 0; s0 < ns; s0 += B) {
+        Ctx::MiniBatch m{};
+        m.s0 = s0;
+        m.s1 = std::min<int64_t>(ns, s0 + B);
+        m.a0 = c->h_atom_off[m.s0];
+        m.a1 = c->h_atom_off[m.s1];
+        const int p0 = (int)m.a0, n = (int)(m.a1 - m.a0);
+        // work order: the group's atoms by species (stable)
+        for (int k = 0; k < n; ++k) work[p0 + k] = p0 + k;
+        std::stable_sort(work.begin() + p0, work.begin() + p0 + n,
+                         [&](int x, int y) { return c->h_type[x] < c->h_type[y]; });
+        std::vector<int> tb(T + 1, p0);
+        for (int k = 0; k < n; ++k) tb[c->h_type[work[p0 + k]] + 1]++;
+        for (int t = 0; t < T; ++t) tb[t + 1] += tb[t] - p0;
+        std::vector<double> pre(n + 1, 0.0);
+        for (int k = 0; k < n; ++k) {
+            const int i = work[p0 + k];
+            pre[k + 1] = pre[k] + (double)(c->h_nbr_off[i + 1] - c->h_nbr_off[i]) + 6.0 * c->h_nang[i] + 8.0;
+        }
+        // warps: one batch of atoms each for a small group, at most the full persistent grid
+        auto warps = [&](int g, const Sched &s) {
+            int W = std::max(1, (n + g - 1) / g);
+            W = std::min(W, s.W);
+            return (W + s.wpb - 1) / s.wpb * s.wpb;
+        };
+        m.Wf = warps(gf, c->fwd);
+        m.Wa = warps(ga, c->adj);
+        const std::vector<int> bf = split_warps(pre, p0, m.Wf), ba = split_warps(pre, p0, m.Wa);
+        m.wf_off = (int64_t)wbf.size();
+        wbf.insert(wbf.end(), bf.begin(), bf.end());
+        m.wa_off = (int64_t)wba.size();
+        wba.insert(wba.end(), ba.begin(), ba.end());
+        const size_t tofs = wlo.size();
+        wlo.resize(tofs + T);
+        whi.resize(tofs + T);
+        species_warps(ba, tb, T, wlo.data() + tofs, whi.data() + tofs);
+        // network-gradient chunks of one species each
+        m.ck_off = (int64_t)chunks.size();
+        clo.resize(tofs + T);
+        chi.resize(tofs + T);
+        for (int t = 0; t < T; ++t) {
+            clo[tofs + t] = (int)(chunks.size() - m.ck_off);
+            for (int p = tb[t]; p < tb[t + 1]; p += CH) chunks.push_back(p);
+            chi[tofs + t] = (int)(chunks.size() - m.ck_off);
+        }
+        m.n_ck = (int)(chunks.size() - m.ck_off);
+        chunks.push_back((int)m.a1);
+        mbs.push_back(m);
+    }
+    const int64_t nm = (int64_t)mbs.size();
+    if (c->mb_work.ensure<int>(std::max<int64_t>(na, 1)) || c->mb_wbf.ensure<int>((int64_t)wbf.size() + 1) ||
+        c->mb_wba.ensure<int>((int64_t)wba.size() + 1) || c->mb_wlo.ensure<int>(nm * T + 1) ||
+        c->mb_whi.ensure<int>(nm * T + 1) || c->mb_chunks.ensure<int>((int64_t)chunks.size() + 1) ||
+        c->mb_clo.ensure<int>(nm * T + 1) || c->mb_chi.ensure<int>(nm * T + 1))
+        return c->fail(NEP_ENOMEM, "mini-batch schedules");
+    auto up = [&](DevBuf &d, const std::vector<int> &h) {
+        return h.empty() ? cudaSuccess : cudaMemcpy(d.ptr, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+    };
+    CK(up(c->mb_work, work));
+    CK(up(c->mb_wbf, wbf));
+    CK(up(c->mb_wba, wba));
+    CK(up(c->mb_wlo, wlo));
+    CK(up(c->mb_whi, whi));
+    CK(up(c->mb_chunks, chunks));
+    CK(up(c->mb_clo, clo));
+    CK(up(c->mb_chi, chi));
+    c->mb = std::move(mbs);
+    c->mb_B = B;
+    shape_key(c, c->mb_key);
+    return NEP_OK;
+}
+
+// Loss and gradient of group m against the references of nep_set_targets.
+int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, double *loss3, float *grad) {
+    int key[6];
+    shape_key(c, key);
+    if (!std::equal(key, key + 6, c->mb_key)) {
+        int rc = build_minibatches(c, c->mb_B);  // the launch shape changed since the setup
+        if (rc) return rc;
+    }
+    const Ctx::MiniBatch &m = c->mb[mi];
+    const int T = c->T;
+    const uint8_t *hw = c->tgt_has_hw ? c->tgt_hw.as<uint8_t>() : nullptr;
+    // the group's own normalisers (restored below: they only enter launch arguments)
+    const double sNs = c->ov_Ns, sNa = c->ov_Na, sNsV = c->ov_NsV;
+    c->ov_Ns = (double)(m.s1 - m.s0);
+    c->ov_Na = (double)(m.a1 - m.a0);
+    c->ov_NsV = 0.0;
+    int rc = NEP_OK;
+    do {
+        if ((rc = launch_expand(c))) break;
+        if ((rc = launch_forward_sched(c, c->mb_work.as<int>(), c->mb_wbf.as<int>() + m.wf_off, m.Wf / c->fwd.wpb)))
+            break;
+        if ((rc = launch_count_hasw(c, hw, m.s0, m.s1))) break;
+        if ((rc = launch_gather(c, c->F_int.as<float>(), c->tgt_F.as<float>(), lF, true, m.a0, m.a1))) break;
+        if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), c->tgt_E.as<double>(),
+                                c->tgt_W.as<double>(), hw, lE, lV, true, m.s0, m.s1)))
+            break;
+        if ((rc = launch_loss_final(c, loss3))) break;
+        if ((rc = launch_adjoint_sched(c, c->mb_work.as<int>(), c->mb_wba.as<int>() + m.wa_off, m.Wa / c->adj.wpb)))
+            break;
+        if ((rc = launch_ann_grad_chunks(c, c->mb_chunks.as<int>() + m.ck_off, m.n_ck))) break;
+        rc = launch_grad_final_sched(c, grad, c->mb_clo.as<int>() + mi * T, c->mb_chi.as<int>() + mi * T,
+                                     c->mb_wlo.as<int>() + mi * T, c->mb_whi.as<int>() + mi * T,
+                                     c->mb_wba.as<int>() + m.wa_off);
+    } while (0);
+    c->ov_Ns = sNs;
+    c->ov_Na = sNa;
+    c->ov_NsV = sNsV;
+    return rc;
+}
+
+}  // namespace nep
