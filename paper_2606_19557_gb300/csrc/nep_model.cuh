@@ -98,11 +98,26 @@ __device__ __forceinline__ void load_row(const float *src, float *dst) {
     }
 }
 
-// Batch of up to G consecutive work positions of one species, starting at `base`.
-__device__ __forceinline__ int batch_size(const AtomArgs &a, int base, int wend, int G, int t0) {
-    int nb = 1;
-    while (nb < G && base + nb < wend && a.type[a.work[base + nb]] == t0) ++nb;
-    return nb;
+// Batch of up to G = 32/SW consecutive work positions of one species, starting at `base`
+// (< wend): group g reads position base + g, so the loads of all groups are in flight
+// together.  Returns the species ti, the batch size nb and this group's atom i (the
+// batch's first atom for groups beyond nb).
+template <int SW>
+__device__ __forceinline__ void load_batch(const AtomArgs &a, int base, int wend, int lane, int &ti, int &nb,
+                                           int &i) {
+    constexpr int G = 32 / SW;
+    const int grp = lane / SW;
+    const int q = base + grp;
+    const int iq = (grp < G && q < wend) ? a.work[q] : -1;
+    const int tq = iq >= 0 ? a.type[iq] : -1;
+    ti = __shfl_sync(FULL, tq, 0);
+    const unsigned same = __ballot_sync(FULL, tq == ti);
+    unsigned gm = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) gm |= ((same >> (g * SW)) & 1u) << g;
+    nb = min(G, __ffs(~gm) - 1);
+    const int i0 = __shfl_sync(FULL, iq, 0);
+    i = grp < nb ? iq : i0;
 }
 
 // Reduce-scatter the V-vector of every group and add the totals of group `grp` into
@@ -165,13 +180,12 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
     int cur_t = -1;
 
     for (int bp = wbeg; bp < wend;) {
-        const int ti = a.type[a.work[bp]];
-        const int nb = batch_size(a, bp, wend, G, ti);
+        int ti, nb, i;
+        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
         const bool act = grp < nb;
         const int bp0 = bp;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
-        const int i = a.work[wi];
         if (ti != cur_t) {  // species-sorted work: rare
             __syncwarp();
             for (int e = lane; e < T * S::NCR; e += 32) cw[e] = a.par[po.cR + (size_t)ti * T * S::NCR + e];
@@ -274,6 +288,13 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
                 }
+                if (T == 1) {  // one species: no runs to track
+                    if (valid) {
+#pragma unroll
+                        for (int kk = 0; kk < KR; ++kk) v[kk] += f[kk];
+                    }
+                    continue;
+                }
                 unsigned rem = group_bits<SW>(__ballot_sync(FULL, valid), lane);
                 while (__any_sync(FULL, rem != 0)) {
                     const bool has = rem != 0;
@@ -292,6 +313,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                     }
                 }
             }
+            if (T == 1 && nRad > 0) bcur = 0;
             if (__any_sync(FULL, bcur >= 0)) flush_groups<VR, SW>(v, Sr + (bcur >= 0 ? bcur : 0) * KR, KR, bcur >= 0, lane, false);
         }
         __syncwarp();
@@ -341,7 +363,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
 #pragma unroll
             for (int g = 0; g < G; ++g) z[g] = bz;
             const float *wt = W0T + (size_t)ti * ND * NN + mu;
-#pragma unroll 5
+#pragma unroll
             for (int v = 0; v < ND; ++v) {
                 const float wv = wt[(size_t)v * NN];
 #pragma unroll
@@ -368,6 +390,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
 #pragma unroll
             for (int g = 0; g < G; ++g) e[g] = 0.0f;
             const float *wr = W0 + (size_t)ti * NN * ND + v;
+#pragma unroll 10
             for (int mu = 0; mu < NN; ++mu) {
                 const float wv = wr[(size_t)mu * ND];
 #pragma unroll
@@ -558,13 +581,12 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
     };
 
     for (int bp = wbeg; bp < wend;) {
-        const int ti = a.type[a.work[bp]];
-        const int nb = batch_size(a, bp, wend, G, ti);
+        int ti, nb, i;
+        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
         const bool act = grp < nb;
         const int bp0 = bp;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
-        const int i = a.work[wi];
         if (ti != cur_t) {
             __syncwarp();
             if (cur_t >= 0) flush_slot(cur_t);
@@ -591,6 +613,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         }
 
         // ---------------------------------------------------------------- state of the forward pass
+#pragma unroll
         for (int e = sl; e < NA * L3; e += SW) at.A[e] = a.st_A[(size_t)wi * NA * L3 + e];
         for (int mu = lane; mu < NN; mu += 32) {
             const float wo = w1[ti * NN + mu];
@@ -606,6 +629,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
             for (int g = 0; g < G; ++g) e[g] = 0.0f;
             const float *wr = W0 + (size_t)ti * NN * ND + v;
+#pragma unroll 10
             for (int mu = 0; mu < NN; ++mu) {
                 const float wv = wr[(size_t)mu * ND];
 #pragma unroll
@@ -755,6 +779,16 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     rl = (pd.x * lx + pd.y * ly + pd.z * lz) * rinv;
                     basis_val_der<KR>(r2 * rinv, a.inv_rcR, f, fp);
                 }
+                if (T == 1) {  // one species: no runs to track
+                    if (valid) {
+#pragma unroll
+                        for (int kk = 0; kk < KR; ++kk) {
+                            v[kk] += f[kk];
+                            v[KR + kk] += rl * fp[kk];
+                        }
+                    }
+                    continue;
+                }
                 unsigned rem = group_bits<SW>(__ballot_sync(FULL, valid), lane);
                 while (__any_sync(FULL, rem != 0)) {
                     const bool has = rem != 0;
@@ -776,6 +810,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     }
                 }
             }
+            if (T == 1 && nRad > 0) bcur = 0;
             if (__any_sync(FULL, bcur >= 0))
                 flush_groups<VR2, SW>(v, Sr + (bcur >= 0 ? bcur : 0) * 2 * KR, 2 * KR, bcur >= 0, lane, false);
         }
@@ -830,7 +865,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
             for (int g = 0; g < G; ++g) v[g] = 0.0f;
             const float *wt = W0T + (size_t)ti * ND * NN + mu;
-#pragma unroll 5
+#pragma unroll
             for (int q = 0; q < ND; ++q) {
                 const float wv = wt[(size_t)q * NN];
 #pragma unroll
@@ -858,6 +893,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
             for (int g = 0; g < G; ++g) e[g] = 0.0f;
             const float *wr = W0 + (size_t)ti * NN * ND + v;
+#pragma unroll 10
             for (int mu = 0; mu < NN; ++mu) {
                 const float wv = wr[(size_t)mu * ND];
 #pragma unroll
@@ -954,6 +990,15 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
                     for (int n = 0; n < NA; ++n) be[n] *= rl;
                 }
+                if (T == 1) {  // one species: no runs to track
+                    if (valid) {
+#pragma unroll
+                        for (int n = 0; n < NA; ++n)
+#pragma unroll
+                            for (int kk = 0; kk < KA; ++kk) X[n * KA + kk] += al[n] * f[kk] + be[n] * fp[kk];
+                    }
+                    continue;
+                }
                 unsigned rem = group_bits<SW>(__ballot_sync(FULL, valid), lane);
                 while (__any_sync(FULL, rem != 0)) {
                     const bool has = rem != 0;
@@ -974,6 +1019,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     }
                 }
             }
+            if (T == 1 && nAng > 0) bcur = 0;
             if (__any_sync(FULL, bcur >= 0))
                 flush_groups<VA, SW>(X, accA + (bcur >= 0 ? bcur : 0) * NCA, NCA, bcur >= 0, lane, true);
         }
