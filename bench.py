@@ -32,6 +32,26 @@ WORKLOAD = "fcc_bcc_t1: 1000 structures x U{64..256} atoms, FCC/BCC, strain 3%, 
            "1 species, rc 6/4 A, n_max 4/4, basis 8/8, l_max 4 + 4-body, 30 neurons"
 LAM = (1.0, 1.0, 0.1)
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per atom of the per-atom
+# kernels, from one ncu capture of the first 200 structures of this workload at the bench's
+# launch shape (profiles/forward_adjoint_gather_ann_fcc_bcc_200.md), scaled to a launch by
+# its atoms.  Valid only for the kernel sources with this SHA-256; otherwise null.
+KERNEL_SOURCES = ("paper_2606_19557_gb300/csrc/nep_model.cuh", "paper_2606_19557_gb300/csrc/nep_internal.cuh")
+TRAFFIC = {"sha256": "07e1680e57821aee0670bc7346dc44bab6ab630955a732aebf27ab8e4ed78638",
+           "bytes_per_atom": {"forward": (38.189568e6 + 10.1248e6) / 32546,
+                              "adjoint": (58.17472e6 + 1.142272e6) / 32546}}
+
+
+def kernel_traffic(kernel: str, n_atoms: int):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != TRAFFIC["sha256"] or kernel not in TRAFFIC["bytes_per_atom"]:
+        return None
+    return TRAFFIC["bytes_per_atom"][kernel] * n_atoms
+
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -129,6 +149,50 @@ def cpu_baseline(spec, batch, n_sample: int):
     dt = time.perf_counter() - t0
     return {"value": sample.n_atoms / dt, "unit": "atoms/s", "cores": oracle.threads(), "kind": "oracle",
             "sample": f"first {sample.n_struct} structures ({sample.n_atoms} atoms), one loss+grad pass, {dt:.1f} s"}
+
+
+def md_eval(steps: int, device: int):
+    """Ten 10,000-atom FCC cells (5 species; n_max 6/6, basis 10/10, l_max 4 + 4- and 5-body,
+    50 neurons): per step new positions, neighbour rebuild (nep_update_positions) and
+    nep_eval.  Inputs are generated on the device before the timed region."""
+    import torch
+
+    from paper_2606_19557_gb300 import NEP, synth
+    spec = synth.SPECS["scale_t5"]
+    b = synth.batch_scale(seed=5, n_struct=0, n_big=10)
+    nep = NEP(spec, device=device)
+    nep.set_structures_batch(b)
+    P = nep.P
+    nep.set_params(torch.tensor(synth.random_theta(P, 5), dtype=torch.float32), torch.ones(nep.n_des))
+    lo, hi = nep.descriptor_range()
+    span = (hi - lo).double()
+    qs = torch.where(span > 0, 1.0 / torch.where(span > 0, span, torch.ones_like(span)), torch.ones_like(span))
+    nep.set_params(torch.tensor(synth.random_theta(P, 5), dtype=torch.float32), qs.float())
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    pos0 = torch.tensor(b.pos, dtype=torch.float32, device="cuda")
+    poss = [pos0 + 0.02 * torch.randn(pos0.shape, generator=gen, device="cuda") for _ in range(steps + 1)]
+    nep.update_positions(poss[0])
+    nep.eval()
+    torch.cuda.synchronize()
+    wall, ev_ms = [], []
+    for k in range(steps):
+        t0 = time.perf_counter()
+        nep.update_positions(poss[k + 1])
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(nep.stream)
+        nep.eval()
+        e.record(nep.stream)
+        e.synchronize()
+        wall.append(time.perf_counter() - t0)
+        ev_ms.append(s.elapsed_time(e))
+    n_rad, n_ang = nep.num_pairs()
+    step_s = sum(wall) / steps
+    return {"workload": "10 FCC cells x 10,000 atoms, 5 species, rc 6/4 A, n_max 6/6, basis 10/10, "
+                        "l_max 4 + 4-body + 5-body, 50 neurons; positions jittered 0.02 A per step",
+            "atoms": b.n_atoms, "radial_pairs": n_rad, "angular_pairs": n_ang, "steps": steps,
+            "ms_per_step": 1e3 * step_s, "atoms_per_s": b.n_atoms / step_s,
+            "eval_ms": sum(ev_ms) / steps, "eval_atoms_per_s": b.n_atoms / (sum(ev_ms) / steps / 1e3),
+            "neighbor_rebuild_ms": 1e3 * step_s - sum(ev_ms) / steps}
 
 
 def run_ours(args):
@@ -286,6 +350,14 @@ def run_ours(args):
         except Exception as ex:  # reported, not hidden
             mbe = {"unavailable": str(ex).splitlines()[0]}
 
+    # MD-style evaluation of large cells (E, F, W only), neighbour lists rebuilt every step
+    md = None
+    if args.md_steps > 0 and rank == 0:
+        try:
+            md = md_eval(args.md_steps, local)
+        except Exception as ex:  # reported, not hidden
+            md = {"unavailable": str(ex).splitlines()[0]}
+
     kavg = {k: sum(v) / len(v) for k, v in kt.items()}
     fl = flops.per_kernel(spec, batch.n_atoms, n_rad, n_ang)
     dom = max(("forward", "adjoint"), key=lambda k: kavg.get(k, 0.0))
@@ -304,7 +376,7 @@ def run_ours(args):
                    "launch_shape": list(shape), "kernel_variant": list(nep.variant()),
                    "neighbor_build_ms": 1e3 * t_nbr2},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": kernel_traffic(dom, batch.n_atoms), "traffic_unit": "bytes",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "kernel_ms": kavg,
         "e2e": {"value": e2e_value, "unit": "atoms/s", "h2d_bytes_per_step": 4 * P, "d2h_bytes_per_step": 24 + 4 * P},
@@ -313,6 +385,7 @@ def run_ours(args):
         "cpu_baseline": cb,
         "plain_form": plain,
         "minibatch_epoch": mbe,
+        "md_eval": md,
         "wall_s": wall,
     }
     print(json.dumps(res))
@@ -332,6 +405,7 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--mb-epochs", dest="mb_epochs", type=int, default=2)
     ap.add_argument("--mb-size", dest="mb_size", type=int, default=16)
+    ap.add_argument("--md-steps", dest="md_steps", type=int, default=5)
     ap.add_argument("--launch", default="", help="fixed kernel variants and shape: fv,av,fwarps,fblocks,awarps,ablocks")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

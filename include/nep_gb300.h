@@ -112,6 +112,14 @@ int nep_set_params(nep_ctx *ctx, const float *theta_dev, const float *q_scale_de
 int nep_set_structures(nep_ctx *ctx, int64_t n_struct, const int64_t *atom_off_dev, const float *pos_dev,
                        const int32_t *type_dev, const float *cell_dev);
 
+/* New positions (and optionally cells) for the cached batch: same structures, atom
+ * counts and species.  pos_dev [N_a*3] f32 (device); cell_dev [n_struct*9] f32 (device)
+ * or NULL to keep the cells.  Rebuilds the neighbour lists on the device (step a1, as an
+ * MD-style evaluation needs every step) and keeps the kernel schedules; synchronizes.
+ * Errors: NEP_ESTATE (no batch), NEP_EINVAL (bad geometry: the batch is then unusable
+ * until the next successful call), NEP_ENOMEM, NEP_ECUDA. */
+int nep_update_positions(nep_ctx *ctx, const float *pos_dev, const float *cell_dev);
+
 /* Radial and angular neighbour-pair counts of the cached batch. */
 int nep_num_pairs(const nep_ctx *ctx, int64_t *n_radial, int64_t *n_angular);
 

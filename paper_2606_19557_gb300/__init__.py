@@ -84,6 +84,7 @@ def load_library():
             "nep_set_params": (I, [P, P, P]),
             "nep_set_structures": (I, [P, I64, P, P, P, P]),
             "nep_num_pairs": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+            "nep_update_positions": (I, [P, P, P]),
             "nep_get_neighbors": (I, [P, P, P, P, P]),
             "nep_eval": (I, [P, P, P, P]),
             "nep_descriptors": (I, [P, P]),
@@ -219,6 +220,15 @@ class NEP:
     def set_structures_batch(self, batch):
         """set_structures from an object with atom_off, pos, types and cell arrays."""
         self.set_structures(batch.atom_off, batch.pos, batch.types, batch.cell)
+
+    def update_positions(self, pos, cell=None):
+        """New positions (and cells) for the cached structures; rebuilds the neighbour lists."""
+        t = self.torch
+        p = self._dev(pos, t.float32).reshape(-1)
+        cl = None if cell is None else self._dev(cell, t.float32).reshape(-1)
+        if p.numel() != 3 * self.n_atoms or (cl is not None and cl.numel() != 9 * self.n_struct):
+            raise ValueError("positions [N_a, 3] and cells [n_struct, 9] of the cached batch expected")
+        self._call(self.lib.nep_update_positions, _ptr(p), _ptr(cl))
 
     def num_pairs(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()

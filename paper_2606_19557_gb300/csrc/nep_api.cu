@@ -422,6 +422,33 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
     return NEP_OK;
 }
 
+int nep_update_positions(nep_ctx *c, const float *pos, const float *cell) {
+    if (!c) return NEP_EINVAL;
+    if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures (call nep_set_structures)");
+    if (c->n_atoms > 0 && !pos) return c->fail(NEP_EINVAL, "null positions");
+    CK(cudaSetDevice(c->dev));
+    const void *before[5] = {c->pair.ptr, c->rev.ptr, c->G.ptr, c->nbr_off.ptr, c->n_ang.ptr};
+    if (c->n_atoms > 0)
+        CK(cudaMemcpyAsync(c->pos.ptr, pos, sizeof(float) * 3 * c->n_atoms, cudaMemcpyDeviceToDevice, c->stream));
+    if (cell && c->n_struct > 0)
+        CK(cudaMemcpyAsync(c->cell.ptr, cell, sizeof(float) * 9 * c->n_struct, cudaMemcpyDeviceToDevice, c->stream));
+    c->have_batch = false;  // until the lists are rebuilt
+    c->state_valid = false;
+    int rc = build_neighbors(c);
+    if (rc) return rc;
+    if (c->G.ensure_bytes(sizeof(float4) * (size_t)(c->n_pairs + 1))) return c->fail(NEP_ENOMEM, "pair gradients");
+    // re-balance the kernel schedules for the new neighbour counts (same sizes, same
+    // buffers): the result is then the one a fresh context computes, bit for bit
+    if ((rc = make_sched(c, c->fwd, c->fwd.wpb, c->fwd.blocks, c->fwd.var))) return rc;
+    if ((rc = make_sched(c, c->adj, c->adj.wpb, c->adj.blocks, c->adj.var))) return rc;
+    if (c->mb_B > 0 && (rc = build_minibatches(c, c->mb_B))) return rc;
+    const void *after[5] = {c->pair.ptr, c->rev.ptr, c->G.ptr, c->nbr_off.ptr, c->n_ang.ptr};
+    if (!std::equal(before, before + 5, after)) drop_graphs(c);  // graphs hold the old addresses
+    c->plain_ready = false;
+    c->have_batch = true;
+    return NEP_OK;
+}
+
 int nep_num_pairs(const nep_ctx *c, int64_t *nr, int64_t *na) {
     if (!c || !nr || !na) return NEP_EINVAL;
     if (!c->have_batch) return NEP_ESTATE;

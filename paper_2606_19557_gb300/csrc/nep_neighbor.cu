@@ -255,20 +255,71 @@ __device__ __forceinline__ uint32_t pack_shift(int Sa, int Sb, int Sc) {
     return ((uint32_t)(Sa + 128) << 16) | ((uint32_t)(Sb + 128) << 8) | (uint32_t)(Sc + 128);
 }
 
-// Visits every candidate (j, S) of atom i and calls f(j, S, r2) for pairs within rcR.
+// Warp-cooperative candidate scan of atom i (one warp per atom).  Calls hit(j, Sa, Sb, Sc, r2)
+// for every pair within rcR, from any lane, in no particular order (the lists are sorted
+// afterwards).  Two ways to enumerate candidates, chosen per structure:
+//   * a structure held in one bin per axis (a cell narrower than 2 rc): the lanes take the
+//     structure's atoms j and each enumerates only the periodic images S that can lie
+//     within the cutoff of i, the box |d.b_a| <= rcq |b_a| around the nearest image
+//     (b_a the reciprocal vectors, so |d.b_a| <= |d| |b_a|);
+//   * otherwise the (2m+1)^3 neighbouring bins, the lanes taking the atoms of each bin.
+// Both apply the same float pre-filter and the exact predicate as the thread-per-atom scan.
 template <class Fn>
-__device__ __forceinline__ void for_each_neighbor(int64_t i, const float *pos, const int *struct_of,
-                                                  const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin,
-                                                  const int4 *atom_wrap, const int64_t *bin_start,
-                                                  const int *bin_atoms, float rc2R, float rcq2, int *err, Fn f) {
+__device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float *pos, const int *struct_of,
+                                               const int64_t *atom_off, const SGeom *geom, const int64_t *bin_off,
+                                               const int64_t *atom_bin, const int4 *atom_wrap,
+                                               const int64_t *bin_start, const int *bin_atoms, float rc2R,
+                                               float rcq2, float rcq, int *err, Fn hit) {
     const int s = struct_of[i];
     const SGeom &g = geom[s];
-    const int64_t lb = atom_bin[i] - bin_off[s];
-    const int bi[3] = {(int)(lb / ((int64_t)g.n[1] * g.n[2])), (int)((lb / g.n[2]) % g.n[1]), (int)(lb % g.n[2])};
-    const int4 wi = atom_wrap[i];
     const float *pi = pos + 3 * i;
     const float hf[9] = {(float)g.h[0], (float)g.h[1], (float)g.h[2], (float)g.h[3], (float)g.h[4],
                          (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
+    auto test = [&](int j, int Sa, int Sb, int Sc) {
+        if (j == (int)i && Sa == 0 && Sb == 0 && Sc == 0) return;
+        const float *pj = pos + 3 * j;
+        const float qx = (pj[0] - pi[0]) + (Sa * hf[0] + Sb * hf[3] + Sc * hf[6]);
+        const float qy = (pj[1] - pi[1]) + (Sa * hf[1] + Sb * hf[4] + Sc * hf[7]);
+        const float qz = (pj[2] - pi[2]) + (Sa * hf[2] + Sb * hf[5] + Sc * hf[8]);
+        if (qx * qx + qy * qy + qz * qz > rcq2) return;
+        if (Sa < -SMAX || Sa > SMAX || Sb < -SMAX || Sb > SMAX || Sc < -SMAX || Sc > SMAX) {
+            atomic_err(err, 2);
+            return;
+        }
+        float d32[3];
+        const float r2 = pair_d(pi, pj, g.h, Sa, Sb, Sc, d32);
+        if (r2 < rc2R) hit(j, Sa, Sb, Sc, r2);
+    };
+    if (g.n[0] == 1 && g.n[1] == 1 && g.n[2] == 1) {
+        double R[3];  // rcq |b_a|
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            R[a] = (double)rcq * sqrt(g.inv[a] * g.inv[a] + g.inv[3 + a] * g.inv[3 + a] + g.inv[6 + a] * g.inv[6 + a]);
+        const double pid[3] = {(double)pi[0], (double)pi[1], (double)pi[2]};
+        for (int64_t j = atom_off[s] + lane; j < atom_off[s + 1]; j += 32) {
+            const float *pj = pos + 3 * j;
+            const double d0[3] = {(double)pj[0] - pid[0], (double)pj[1] - pid[1], (double)pj[2] - pid[2]};
+            int lo[3], hi[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double f = d0[0] * g.inv[a] + d0[1] * g.inv[3 + a] + d0[2] * g.inv[6 + a];
+                lo[a] = (int)ceil(-f - R[a]);
+                hi[a] = (int)floor(-f + R[a]);
+                if (lo[a] < -SMAX - 1 || hi[a] > SMAX + 1) {  // beyond the packed shift range
+                    atomic_err(err, 2);
+                    lo[a] = 1;
+                    hi[a] = 0;
+                }
+            }
+            for (int Sa = lo[0]; Sa <= hi[0]; ++Sa)
+                for (int Sb = lo[1]; Sb <= hi[1]; ++Sb)
+                    for (int Sc = lo[2]; Sc <= hi[2]; ++Sc) test((int)j, Sa, Sb, Sc);
+        }
+        return;
+    }
+    const int64_t lb = atom_bin[i] - bin_off[s];
+    const int bi[3] = {(int)(lb / ((int64_t)g.n[1] * g.n[2])), (int)((lb / g.n[2]) % g.n[1]), (int)(lb % g.n[2])};
+    const int4 wi = atom_wrap[i];
     for (int da = -g.m[0]; da <= g.m[0]; ++da) {
         int ba = bi[0] + da;
         const int sa = (ba >= 0) ? ba / g.n[0] : -((-ba + g.n[0] - 1) / g.n[0]);
@@ -282,79 +333,84 @@ __device__ __forceinline__ void for_each_neighbor(int64_t i, const float *pos, c
                 const int sc = (bc >= 0) ? bc / g.n[2] : -((-bc + g.n[2] - 1) / g.n[2]);
                 bc -= sc * g.n[2];
                 const int64_t bin = bin_off[s] + ((int64_t)ba * g.n[1] + bb) * g.n[2] + bc;
-                for (int64_t t = bin_start[bin]; t < bin_start[bin + 1]; ++t) {
+                for (int64_t t = bin_start[bin] + lane; t < bin_start[bin + 1]; t += 32) {
                     const int j = bin_atoms[t];
                     const int4 wj = atom_wrap[j];
-                    const int Sa = sa + wi.x - wj.x, Sb = sb + wi.y - wj.y, Sc = sc + wi.z - wj.z;
-                    if (j == (int)i && Sa == 0 && Sb == 0 && Sc == 0) continue;
-                    const float *pj = pos + 3 * j;
-                    // cheap float pre-filter with a margin, then the exact predicate
-                    const float qx = (pj[0] - pi[0]) + (Sa * hf[0] + Sb * hf[3] + Sc * hf[6]);
-                    const float qy = (pj[1] - pi[1]) + (Sa * hf[1] + Sb * hf[4] + Sc * hf[7]);
-                    const float qz = (pj[2] - pi[2]) + (Sa * hf[2] + Sb * hf[5] + Sc * hf[8]);
-                    if (qx * qx + qy * qy + qz * qz > rcq2) continue;
-                    if (Sa < -SMAX || Sa > SMAX || Sb < -SMAX || Sb > SMAX || Sc < -SMAX || Sc > SMAX) {
-                        atomic_err(err, 2);
-                        continue;
-                    }
-                    float d32[3];
-                    const float r2 = pair_d(pi, pj, g.h, Sa, Sb, Sc, d32);
-                    if (r2 < rc2R) f(j, Sa, Sb, Sc, r2);
+                    test(j, sa + wi.x - wj.x, sb + wi.y - wj.y, sc + wi.z - wj.z);
                 }
             }
         }
     }
 }
 
-__global__ void k_count(int64_t na, const float *pos, const int *struct_of, const SGeom *geom, const int64_t *bin_off,
-                        const int64_t *atom_bin, const int4 *atom_wrap, const int64_t *bin_start,
-                        const int *bin_atoms, float rc2R, float rc2A, float rcq2, int64_t *cnt, int *n_ang, int *err) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Pair counts per atom (one warp per atom).
+__global__ void k_count_w(int64_t na, const float *pos, const int *struct_of, const int64_t *atom_off,
+                          const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin, const int4 *atom_wrap,
+                          const int64_t *bin_start, const int *bin_atoms, float rc2R, float rc2A, float rcq,
+                          int64_t *cnt, int *n_ang, int *err) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= na) return;
-    int64_t nr = 0;
-    int nang = 0;
-    for_each_neighbor(i, pos, struct_of, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms, rc2R, rcq2, err,
-                      [&](int, int, int, int, float r2) {
-                          ++nr;
-                          if (r2 < rc2A) ++nang;
-                      });
-    cnt[i] = nr;
-    n_ang[i] = nang;
+    int nr = 0, nang = 0;
+    scan_atom_warp(i, lane, pos, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms, rc2R,
+                   rcq * rcq, rcq, err, [&](int, int, int, int, float r2) {
+                       ++nr;
+                       if (r2 < rc2A) ++nang;
+                   });
+    nr = __reduce_add_sync(FULL, nr);
+    nang = __reduce_add_sync(FULL, nang);
+    if (lane == 0) {
+        cnt[i] = nr;
+        n_ang[i] = nang;
+    }
 }
 
-__global__ void k_fill(int64_t na, const float *pos, const int *type, const int *struct_of, const SGeom *geom,
-                       const int64_t *bin_off, const int64_t *atom_bin, const int4 *atom_wrap,
-                       const int64_t *bin_start, const int *bin_atoms, float rc2R, float rc2A, float rcq2,
-                       const int64_t *nbr_off, uint64_t *keys, int *err) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Sort keys of every pair (one warp per atom); slots taken through a shared counter.
+__global__ void k_fill_w(int64_t na, const float *pos, const int *type, const int *struct_of, const int64_t *atom_off,
+                         const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin, const int4 *atom_wrap,
+                         const int64_t *bin_start, const int *bin_atoms, float rc2R, float rc2A, float rcq,
+                         const int64_t *nbr_off, uint64_t *keys, int *err) {
+    __shared__ int slot[32];
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (i >= na) return;
-    int64_t o = nbr_off[i];
-    const int64_t end = nbr_off[i + 1];
-    for_each_neighbor(i, pos, struct_of, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms, rc2R, rcq2, err,
-                      [&](int j, int Sa, int Sb, int Sc, float r2) {
-                          if (o < end) {
-                              const uint64_t grp = (r2 < rc2A) ? 0ull : 1ull;
-                              keys[o] = (grp << 63) | ((uint64_t)type[j] << 59) | ((uint64_t)j << 24) |
-                                        (uint64_t)pack_shift(Sa, Sb, Sc);
-                          }
-                          ++o;
-                      });
-    if (o != end) atomic_err(err, 5);
+    if (lane == 0) slot[wib] = 0;
+    __syncwarp();
+    const int64_t o = nbr_off[i], n = nbr_off[i + 1] - o;
+    scan_atom_warp(i, lane, pos, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms, rc2R,
+                   rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, float r2) {
+                       const int k = atomicAdd(&slot[wib], 1);
+                       if (k < n) {
+                           const uint64_t grp = (r2 < rc2A) ? 0ull : 1ull;
+                           keys[o + k] = (grp << 63) | ((uint64_t)type[j] << 59) | ((uint64_t)j << 24) |
+                                         (uint64_t)pack_shift(Sa, Sb, Sc);
+                       }
+                   });
+    __syncwarp();
+    if (lane == 0 && slot[wib] != n) atomic_err(err, 5);
 }
 
 // One warp per atom: rank sort of its keys, then decode into the pair records.
 __global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const int64_t *nbr_off, const float *pos,
                               const int *struct_of, const SGeom *geom, uint64_t *keys_out, float4 *pair,
                               int32_t *shift) {
+    constexpr int STAGE = 256;  // keys per warp staged in shared memory
+    __shared__ uint64_t sk[8][STAGE];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (i >= na) return;
     const int64_t beg = nbr_off[i], n = nbr_off[i + 1] - beg;
     const SGeom &g = geom[struct_of[i]];
+    const uint64_t *src = keys_in + beg;
+    if (n <= STAGE) {  // the rank sort reads every key n times: from shared memory when it fits
+        for (int64_t e = lane; e < n; e += 32) sk[wib][e] = src[e];
+        __syncwarp();
+        src = sk[wib];
+    }
     for (int64_t e = lane; e < n; e += 32) {
-        const uint64_t k = keys_in[beg + e];
+        const uint64_t k = src[e];
         int64_t rank = 0;
-        for (int64_t e2 = 0; e2 < n; ++e2) rank += (keys_in[beg + e2] < k) ? 1 : 0;
+        for (int64_t e2 = 0; e2 < n; ++e2) rank += (src[e2] < k) ? 1 : 0;
         keys_out[beg + rank] = k;
         const int j = (int)((k >> 24) & ((1ull << 35) - 1));
         const int tj = (int)((k >> 59) & 15ull);
@@ -435,7 +491,7 @@ int build_neighbors(Ctx *c) {
     CK(cudaMemsetAsync(c->bin_cnt.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
     CK(cudaMemsetAsync(c->bin_cur.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
     const unsigned gA = (unsigned)((na + 255) / 256);     // 256-thread blocks, one thread per atom
-    const unsigned gA128 = (unsigned)((na + 127) / 128);  // 128-thread blocks, one thread per atom
+    const unsigned gW = (unsigned)((na * 32 + 255) / 256);  // 256-thread blocks, one warp per atom
     CK(cudaMemsetAsync(c->cnt.ptr, 0, sizeof(int64_t) * (size_t)(na + 1), st));
     CK(cudaMemsetAsync(c->n_ang.ptr, 0, sizeof(int) * (size_t)(na + 1), st));
     if (na > 0) {
@@ -451,10 +507,11 @@ int build_neighbors(Ctx *c) {
     if (na > 0) {
         k_bin_fill<<<gA, 256, 0, st>>>(na, c->atom_bin.as<int64_t>(), c->bin_start.as<int64_t>(),
                                        c->bin_cur.as<int64_t>(), c->bin_atoms.as<int>());
-        k_count<<<gA128, 128, 0, st>>>(na, c->pos.as<float>(), c->struct_of.as<int>(), geom, c->bin_off.as<int64_t>(),
-                                    c->atom_bin.as<int64_t>(), (const int4 *)c->atom_wrap.ptr,
-                                    c->bin_start.as<int64_t>(), c->bin_atoms.as<int>(), rc2R, rc2A, rcq * rcq,
-                                    c->cnt.as<int64_t>(), c->n_ang.as<int>(), err);
+        k_count_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
+                                      c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
+                                      (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
+                                      c->bin_atoms.as<int>(), rc2R, rc2A, rcq, c->cnt.as<int64_t>(),
+                                      c->n_ang.as<int>(), err);
         CK(cudaGetLastError());
     }
     rc = scan_exclusive(c, c->cnt.as<int64_t>(), na, c->nbr_off.as<int64_t>(), c->d_total.as<int64_t>());
@@ -473,11 +530,11 @@ int build_neighbors(Ctx *c) {
         return c->fail(NEP_ENOMEM, "pair buffers");
     c->n_pairs = M;
     if (na > 0) {
-        k_fill<<<gA128, 128, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->struct_of.as<int>(), geom,
-                                   c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
-                                   (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
-                                   c->bin_atoms.as<int>(), rc2R, rc2A, rcq * rcq, c->nbr_off.as<int64_t>(),
-                                   c->keys_tmp.as<uint64_t>(), err);
+        k_fill_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->struct_of.as<int>(),
+                                     c->atom_off.as<int64_t>(), geom, c->bin_off.as<int64_t>(),
+                                     c->atom_bin.as<int64_t>(), (const int4 *)c->atom_wrap.ptr,
+                                     c->bin_start.as<int64_t>(), c->bin_atoms.as<int>(), rc2R, rc2A, rcq,
+                                     c->nbr_off.as<int64_t>(), c->keys_tmp.as<uint64_t>(), err);
         const unsigned gw = (unsigned)((na * 32 + 255) / 256);
         k_sort_decode<<<gw, 256, 0, st>>>(na, c->keys_tmp.as<uint64_t>(), c->nbr_off.as<int64_t>(),
                                           c->pos.as<float>(), c->struct_of.as<int>(), geom, c->keys.as<uint64_t>(),

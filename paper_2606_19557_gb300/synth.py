@@ -125,6 +125,8 @@ def _close_atoms(pos: np.ndarray, cell: np.ndarray, dmin: float) -> np.ndarray:
     2 dmin wide, so rounding fractional differences finds the nearest image."""
     n = pos.shape[0]
     frac = pos @ np.linalg.inv(cell)
+    if n > 300:
+        return _close_atoms_tree(frac, cell, dmin)
     bad = np.zeros(n, bool)
     chunk = max(1, 4_000_000 // max(1, n))
     for i0 in range(0, n, chunk):
@@ -137,6 +139,24 @@ def _close_atoms(pos: np.ndarray, cell: np.ndarray, dmin: float) -> np.ndarray:
         d2[idx - i0, idx] = np.inf
         bad[i0:i1] |= (d2 < dmin * dmin).any(axis=1)
     return np.nonzero(bad)[0]
+
+
+def _close_atoms_tree(frac: np.ndarray, cell: np.ndarray, dmin: float) -> np.ndarray:
+    """Same result as the all-pairs check, for large cells: candidate pairs from a periodic
+    k-d tree on the unstrained box (radius 1.2 dmin covers the few per cent of strain),
+    then the exact minimum-image distance of each candidate."""
+    from scipy.spatial import cKDTree
+    f = frac - np.floor(frac)
+    L = np.linalg.norm(cell, axis=1)
+    x = np.minimum(f * L, np.nextafter(L, 0))
+    pairs = cKDTree(x, boxsize=L).query_pairs(r=1.2 * dmin, output_type="ndarray")
+    if pairs.size == 0:
+        return np.zeros(0, np.int64)
+    df = f[pairs[:, 1]] - f[pairs[:, 0]]
+    df -= np.round(df)
+    d = df @ cell
+    close = pairs[np.einsum("ij,ij->i", d, d) < dmin * dmin]
+    return np.unique(close.ravel())
 
 
 def make_structure(rng: np.random.Generator, n: int, kind: str, strain: float, sigma: float,
