@@ -137,18 +137,49 @@ def run_reference(args):
 
 
 def cpu_baseline(spec, batch, n_sample: int):
+    """Times the oracle on a sample of the workload; also returns its inputs and results,
+    against which the GPU path's errors are reported."""
     import oracle
     from paper_2606_19557_gb300 import synth
     sample = batch.subset(range(min(n_sample, batch.n_struct)))
     P = oracle.num_params(spec)
     theta = synth.random_theta(P, 1)
-    qs = oracle.scale_from_range(oracle.descriptors(spec, theta, sample))
+    qs = oracle.scale_from_range(oracle.descriptors(spec, theta, sample)).astype(np.float32).astype(np.float64)
     Er, Fr, Wr = synth.random_targets(sample, 3)
     t0 = time.perf_counter()
-    oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
+    loss3, grad, E, F, W = oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
     dt = time.perf_counter() - t0
-    return {"value": sample.n_atoms / dt, "unit": "atoms/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"first {sample.n_struct} structures ({sample.n_atoms} atoms), one loss+grad pass, {dt:.1f} s"}
+    cb = {"value": sample.n_atoms / dt, "unit": "atoms/s", "cores": oracle.threads(), "kind": "oracle",
+          "sample": f"first {sample.n_struct} structures ({sample.n_atoms} atoms), one loss+grad pass, {dt:.1f} s"}
+    ref = {"sample": sample, "theta": theta, "qs": qs, "targets": (Er, Fr, Wr),
+           "out": {"loss3": loss3, "grad": grad, "E": E, "F": F, "W": W}}
+    return cb, ref
+
+
+def errors_vs_oracle(spec, ref, device: int):
+    """The GPU path on the oracle's sample and inputs; norm-wise relative errors per
+    quantity plus the largest per-atom energy and force errors."""
+    import torch
+
+    from paper_2606_19557_gb300 import NEP
+    s = ref["sample"]
+    nep = NEP(spec, device=device)
+    nep.set_structures_batch(s)
+    nep.set_params(torch.tensor(ref["theta"], dtype=torch.float32), torch.tensor(ref["qs"], dtype=torch.float32))
+    Er, Fr, Wr = ref["targets"]
+    l3, g = [x.cpu().numpy().astype(np.float64) for x in nep.loss_grad(Er, Fr, Wr, None, LAM)]
+    E, F, W = [x.cpu().numpy().astype(np.float64) for x in nep.eval()]
+    o = ref["out"]
+
+    def rel(a, b):
+        return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(np.asarray(b).ravel()), 1e-300))
+
+    nat = s.counts().astype(np.float64)
+    return {"E_rel": rel(E, o["E"]), "F_rel": rel(F, o["F"]), "W_rel": rel(W, o["W"]),
+            "loss_rel": rel(l3, o["loss3"]), "grad_rel": rel(g, o["grad"]),
+            "E_meV_per_atom_max": float(np.max(np.abs(E - o["E"]) / nat) * 1e3),
+            "F_meV_per_A_max": float(np.max(np.abs(F - o["F"])) * 1e3),
+            "sample": f"first {s.n_struct} structures ({s.n_atoms} atoms), oracle-computed inputs"}
 
 
 def md_eval(steps: int, device: int):
@@ -208,7 +239,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     spec, batch = build_workload(rank, args.n_struct)
     # the CPU baseline runs before any GPU work of this process
-    cb = cpu_baseline(spec, batch, args.cpu_sample) if (rank == 0 and ws == 1 and args.cpu_sample > 0) else None
+    cb, ref = cpu_baseline(spec, batch, args.cpu_sample) if (rank == 0 and ws == 1 and args.cpu_sample > 0) \
+        else (None, None)
 
     nep = NEP(spec, device=local)
     t0 = time.perf_counter()
@@ -358,6 +390,13 @@ def run_ours(args):
         except Exception as ex:  # reported, not hidden
             md = {"unavailable": str(ex).splitlines()[0]}
 
+    err = None
+    if ref is not None:
+        try:
+            err = errors_vs_oracle(spec, ref, local)
+        except Exception as ex:  # reported, not hidden
+            err = {"unavailable": str(ex).splitlines()[0]}
+
     kavg = {k: sum(v) / len(v) for k, v in kt.items()}
     fl = flops.per_kernel(spec, batch.n_atoms, n_rad, n_ang)
     dom = max(("forward", "adjoint"), key=lambda k: kavg.get(k, 0.0))
@@ -383,6 +422,7 @@ def run_ours(args):
         "gpu_launches": 9 * args.steps,
         "clocks": clocks,
         "cpu_baseline": cb,
+        "err_vs_oracle": err,
         "plain_form": plain,
         "minibatch_epoch": mbe,
         "md_eval": md,

@@ -407,7 +407,7 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
     }
     // per-step buffers
     const int64_t M = c->n_pairs, NDP = c->NDP, NN = c->NN, NAL = (int64_t)c->ks->NA * L3;
-    const int64_t nlp = (int64_t)c->n_sm * 4 + 3 * (int64_t)c->n_sm + 8;
+    const int64_t nlp = (int64_t)c->n_sm * 4 + 3 * ns + 8;  // gather blocks + 3 per structure
     if (c->E_atom.ensure<float>(na) || c->F_own.ensure<float>(na * 3) || c->W_atom.ensure<float>(na * 9) ||
         c->G.ensure_bytes(sizeof(float4) * (size_t)(M + 1)) || c->st_qt.ensure<float>(na * NDP) ||
         c->st_h.ensure<float>(na * NN) || c->st_A.ensure<float>(na * NAL) || c->fbar.ensure<float4>(na) ||

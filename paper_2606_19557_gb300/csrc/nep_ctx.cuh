@@ -109,6 +109,7 @@ struct Ctx {
     // neighbour build
     DevBuf geom, nbins, bin_off, bin_cnt, bin_start, bin_cur, atom_bin, atom_wrap, bin_atoms, cnt, n_ang, nbr_off;
     DevBuf keys_tmp, keys, pair, rev, shift, scan_tmp, d_total, d_err;
+    DevBuf pos4, nbr_scratch, d_flag;  // float4 positions, per-atom key scratch, overflow flag
 
     // schedule
     DevBuf work;                 // [Na] atom per work position (species-sorted)
@@ -129,6 +130,7 @@ struct Ctx {
 
     // loss normalisers (0 = this batch's own N_s, N_a, N_s^V); set for one shard of a batch
     double ov_Ns = 0.0, ov_Na = 0.0, ov_NsV = 0.0;
+    int64_t struct_parts = 0;  // loss partials written by the latest k_struct launch (one per structure)
     double norm_Ns() const { return ov_Ns > 0.0 ? ov_Ns : (double)n_struct; }
     double norm_Na() const { return ov_Na > 0.0 ? ov_Na : (double)n_atoms; }
 

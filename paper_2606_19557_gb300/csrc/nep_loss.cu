@@ -128,61 +128,62 @@ __global__ void k_gather(int64_t a0, int64_t a1, const int64_t *nbr_off, const i
 
 // --------------------------------------------------------------------------- structures
 // E_s = sum_i E_i and W_s = sum_i W_i in FP64 (Eq. 1); loss terms and cotangents of Eq. "loss".
+// One block per structure: its threads stride over the structure's atoms, then a fixed-order
+// reduction (lanes, then warps in order), so a 10,000-atom cell is summed by 256 threads.
+// The block size (~4 atoms per thread, from the launch's mean structure size) fixes the
+// summation order.  part[3 * (s - s0) + q]: the structure's loss terms.
 __global__ void k_struct(int64_t s0, int64_t s1, const int64_t *atom_off, const float *E_atom, const float *W_atom,
                          double *E_out, double *W_out, int loss, const double *E_ref, const double *W_ref,
                          const uint8_t *has_W, const int *n_sv, double nsv_over, double lamE, double lamV, double Ns,
-                         float *ebar, float *wbar, double *part /*[grid][3]*/) {
-    __shared__ double wp[32][3];
+                         float *ebar, float *wbar, double *part /*[s1 - s0][3]*/) {
+    __shared__ double red[32][10];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * nw + wib, W = (int64_t)gridDim.x * nw;
-    double aE = 0.0, aV = 0.0, ab1 = 0.0;
-    const double NsV = loss ? (nsv_over > 0.0 ? nsv_over : (double)(*n_sv)) : 0.0;
-    for (int64_t s = s0 + gw; s < s1; s += W) {
-        const int64_t b = atom_off[s], e = atom_off[s + 1];
-        double E = 0.0, Wv[9];
-        for (int k = 0; k < 9; ++k) Wv[k] = 0.0;
-        for (int64_t i = b + lane; i < e; i += 32) {
-            E += (double)E_atom[i];
-            for (int k = 0; k < 9; ++k) Wv[k] += (double)W_atom[i * 9 + k];
-        }
-        E = warp_sum_d(E);
-        for (int k = 0; k < 9; ++k) Wv[k] = warp_sum_d(Wv[k]);
-        if (lane == 0) {
-            E_out[s] = E;
-            for (int k = 0; k < 9; ++k) W_out[s * 9 + k] = Wv[k];
-            if (loss) {
-                const double na = (double)(e - b);
-                const double dE = E - E_ref[s];
-                aE += (dE / na) * (dE / na);
-                const double eb = lamE * 2.0 * dE / (na * na) / Ns;
-                ebar[s] = (float)eb;
-                ab1 -= na * eb;
-                const bool hw = has_W == nullptr || has_W[s] != 0;
-                for (int k = 0; k < 9; ++k) {
-                    double wb = 0.0;
-                    if (hw && NsV > 0.0) {
-                        const double dW = Wv[k] - W_ref[s * 9 + k];
-                        aV += (dW / na) * (dW / na);
-                        wb = lamV * 2.0 * dW / (na * na) / (9.0 * NsV);
-                    }
-                    wbar[s * 9 + k] = (float)wb;
-                }
-            }
-        }
+    const int64_t s = s0 + blockIdx.x;
+    if (s >= s1) return;
+    const int64_t b = atom_off[s], e = atom_off[s + 1];
+    double v[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v[k] = 0.0;
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+        v[0] += (double)E_atom[i];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) v[1 + k] += (double)W_atom[i * 9 + k];
     }
-    if (loss) {
-        if (lane == 0) {
-            wp[wib][0] = aE;
-            wp[wib][1] = aV;
-            wp[wib][2] = ab1;
-        }
-        __syncthreads();
-        if (threadIdx.x < 3) {
-            double s = 0.0;
-            for (int k = 0; k < nw; ++k) s += wp[k][threadIdx.x];
-            part[blockIdx.x * 3 + threadIdx.x] = s;
-        }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v[k] = warp_sum_d(v[k]);
+    if (lane == 0)
+        for (int k = 0; k < 10; ++k) red[wib][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double E = 0.0, Wv[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < nw; ++w) {
+        E += red[w][0];
+        for (int k = 0; k < 9; ++k) Wv[k] += red[w][1 + k];
     }
+    E_out[s] = E;
+    for (int k = 0; k < 9; ++k) W_out[s * 9 + k] = Wv[k];
+    if (!loss) return;
+    const double NsV = nsv_over > 0.0 ? nsv_over : (double)(*n_sv);
+    const double na = (double)(e - b);
+    const double dE = E - E_ref[s];
+    const double aE = (dE / na) * (dE / na);
+    const double eb = lamE * 2.0 * dE / (na * na) / Ns;
+    ebar[s] = (float)eb;
+    const double ab1 = -na * eb;
+    double aV = 0.0;
+    const bool hw = has_W == nullptr || has_W[s] != 0;
+    for (int k = 0; k < 9; ++k) {
+        double wb = 0.0;
+        if (hw && NsV > 0.0) {
+            const double dW = Wv[k] - W_ref[s * 9 + k];
+            aV += (dW / na) * (dW / na);
+            wb = lamV * 2.0 * dW / (na * na) / (9.0 * NsV);
+        }
+        wbar[s * 9 + k] = (float)wb;
+    }
+    part[3 * (s - s0) + 0] = aE;
+    part[3 * (s - s0) + 1] = aV;
+    part[3 * (s - s0) + 2] = ab1;
 }
 
 __global__ void k_count_hasw(int64_t ns, const uint8_t *has_W, int *n_sv) {
@@ -547,7 +548,7 @@ int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blo
 }
 
 static int gather_blocks(Ctx *c) { return c->n_sm * 4; }
-static int struct_blocks(Ctx *c) { return c->n_sm; }
+
 
 int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1,
                   double *part, int nblocks) {
@@ -568,12 +569,21 @@ int launch_count_hasw(Ctx *c, const uint8_t *has_W, int64_t s0, int64_t s1) {
     return NEP_OK;
 }
 
+static int64_t pow2ceil_host(int64_t n) {
+    int64_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
 int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, const double *W_ref,
                   const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1, double *part,
                   int nblocks) {
     if (s1 <= s0) return NEP_OK;
-    const int nb = nblocks > 0 ? nblocks : struct_blocks(c);
-    k_struct<<<nb, 256, 0, c->stream>>>(s0, s1, c->atom_off.as<int64_t>(), c->E_atom.as<float>(),
+    (void)nblocks;  // one block per structure, ~4 atoms per thread (32 to 256 threads)
+    c->struct_parts = s1 - s0;
+    const int64_t mean = (c->h_atom_off[s1] - c->h_atom_off[s0]) / (s1 - s0);
+    const int threads = (int)std::min<int64_t>(256, std::max<int64_t>(32, pow2ceil_host(mean / 4)));
+    k_struct<<<(unsigned)(s1 - s0), threads, 0, c->stream>>>(s0, s1, c->atom_off.as<int64_t>(), c->E_atom.as<float>(),
                                         c->W_atom.as<float>(), E_out, W_out, loss ? 1 : 0, E_ref, W_ref, has_W,
                                         c->n_sv.as<int>(), c->ov_NsV, lamE, lamV, c->norm_Ns(), c->ebar.as<float>(),
                                         c->wbar.as<float>(), part ? part : c->loss_part.as<double>() + gather_blocks(c));
@@ -586,7 +596,7 @@ int launch_loss_final(Ctx *c, double *loss3, const double *fpart, int nf, const 
         fpart = c->loss_part.as<double>();
         nf = c->n_atoms > 0 ? gather_blocks(c) : 0;
         spart = c->loss_part.as<double>() + gather_blocks(c);
-        nsb = c->n_struct > 0 ? struct_blocks(c) : 0;
+        nsb = c->n_struct > 0 ? (int)c->struct_parts : 0;
     }
     k_loss_final<<<1, 256, 0, c->stream>>>(fpart, nf, spart, nsb, c->n_sv.as<int>(), c->ov_NsV, c->norm_Ns(),
                                            c->norm_Na(), loss3, c->gb1.as<double>());

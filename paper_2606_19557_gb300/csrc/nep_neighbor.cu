@@ -6,8 +6,10 @@
 //   1. per structure: inverse cell, plane spacings w_a = V/|b x c| (FP64), bins per
 //      axis n_a = max(1, floor(w_a / (rc + skin))) and scan reach m_a = ceil((rc + skin) n_a / w_a);
 //   2. per atom: fractional coordinates, wrap offset, bin; counting sort into bins;
-//   3. per atom: scan the (2 m_a + 1) neighbouring bin images, test candidates,
-//      count, then fill 64-bit keys (group, t_j, j, S);
+//   3. per atom (one warp): scan the candidates, either the (2 m_a + 1) neighbouring
+//      bin images or, for a structure held in one bin per axis, each atom's own box of
+//      periodic images; count the pairs and keep the 64-bit keys (group, t_j, j, S) of
+//      up to `cap` of them (a second scan writes the keys only if some atom has more);
 //   4. per atom (one warp): rank-sort its keys, decode to the float4 pair record;
 //   5. per pair: index of the reverse pair (j, i, -S) by binary search.
 // Pair predicate (identical here, in the oracle's brute force and in the per-atom
@@ -15,6 +17,7 @@
 // multiply-add, rounded once to float; kept iff float (dx*dx + dy*dy) + dz*dz < rc*rc.
 // Negating S negates every operation exactly, so d(j,i,-S) = -d(i,j,S) bit for bit
 // and the radial/angular lists are symmetric.
+#include <algorithm>
 #include <vector>
 
 #include "nep_ctx.cuh"
@@ -197,9 +200,10 @@ __global__ void k_struct_of(int64_t ns, const int64_t *atom_off, int *struct_of)
 
 __global__ void k_atom_bin(int64_t na, const float *pos, const int *type, int T, const int *struct_of,
                            const SGeom *geom, const int64_t *bin_off, int64_t *atom_bin, int4 *atom_wrap,
-                           int64_t *bin_cnt, int *err) {
+                           int64_t *bin_cnt, float4 *pos4, int *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= na) return;
+    pos4[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], 0.0f);
     const int t = type[i];
     if (t < 0 || t >= T) atomic_err(err, 3);
     const int s = struct_of[i];
@@ -265,7 +269,8 @@ __device__ __forceinline__ uint32_t pack_shift(int Sa, int Sb, int Sc) {
 //   * otherwise the (2m+1)^3 neighbouring bins, the lanes taking the atoms of each bin.
 // Both apply the same float pre-filter and the exact predicate as the thread-per-atom scan.
 template <class Fn>
-__device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float *pos, const int *struct_of,
+__device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float *pos, const float4 *pos4,
+                                               const int *struct_of,
                                                const int64_t *atom_off, const SGeom *geom, const int64_t *bin_off,
                                                const int64_t *atom_bin, const int4 *atom_wrap,
                                                const int64_t *bin_start, const int *bin_atoms, float rc2R,
@@ -277,11 +282,12 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
                          (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
     auto test = [&](int j, int Sa, int Sb, int Sc) {
         if (j == (int)i && Sa == 0 && Sb == 0 && Sc == 0) return;
-        const float *pj = pos + 3 * j;
-        const float qx = (pj[0] - pi[0]) + (Sa * hf[0] + Sb * hf[3] + Sc * hf[6]);
-        const float qy = (pj[1] - pi[1]) + (Sa * hf[1] + Sb * hf[4] + Sc * hf[7]);
-        const float qz = (pj[2] - pi[2]) + (Sa * hf[2] + Sb * hf[5] + Sc * hf[8]);
+        const float4 pj4 = pos4[j];
+        const float qx = (pj4.x - pi[0]) + (Sa * hf[0] + Sb * hf[3] + Sc * hf[6]);
+        const float qy = (pj4.y - pi[1]) + (Sa * hf[1] + Sb * hf[4] + Sc * hf[7]);
+        const float qz = (pj4.z - pi[2]) + (Sa * hf[2] + Sb * hf[5] + Sc * hf[8]);
         if (qx * qx + qy * qy + qz * qz > rcq2) return;
+        const float *pj = pos + 3 * j;
         if (Sa < -SMAX || Sa > SMAX || Sb < -SMAX || Sb > SMAX || Sc < -SMAX || Sc > SMAX) {
             atomic_err(err, 2);
             return;
@@ -297,8 +303,8 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
             R[a] = (double)rcq * sqrt(g.inv[a] * g.inv[a] + g.inv[3 + a] * g.inv[3 + a] + g.inv[6 + a] * g.inv[6 + a]);
         const double pid[3] = {(double)pi[0], (double)pi[1], (double)pi[2]};
         for (int64_t j = atom_off[s] + lane; j < atom_off[s + 1]; j += 32) {
-            const float *pj = pos + 3 * j;
-            const double d0[3] = {(double)pj[0] - pid[0], (double)pj[1] - pid[1], (double)pj[2] - pid[2]};
+            const float4 pj = pos4[j];
+            const double d0[3] = {(double)pj.x - pid[0], (double)pj.y - pid[1], (double)pj.z - pid[2]};
             int lo[3], hi[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -343,30 +349,46 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
     }
 }
 
-// Pair counts per atom (one warp per atom).
-__global__ void k_count_w(int64_t na, const float *pos, const int *struct_of, const int64_t *atom_off,
-                          const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin, const int4 *atom_wrap,
-                          const int64_t *bin_start, const int *bin_atoms, float rc2R, float rc2A, float rcq,
-                          int64_t *cnt, int *n_ang, int *err) {
+__device__ __forceinline__ uint64_t pair_key(float r2, float rc2A, int tj, int j, int Sa, int Sb, int Sc) {
+    const uint64_t grp = (r2 < rc2A) ? 0ull : 1ull;  // angular neighbours first
+    return (grp << 63) | ((uint64_t)tj << 59) | ((uint64_t)j << 24) | (uint64_t)pack_shift(Sa, Sb, Sc);
+}
+
+// Pair counts per atom (one warp per atom), and the sort keys of the first `cap` pairs
+// of each atom in scratch[i * cap ...] (unordered): when no atom has more, the keys need
+// no second scan.  *overflow is set when some atom has more than cap pairs.
+__global__ void k_count_w(int64_t na, const float *pos, const float4 *pos4, const int *type, const int *struct_of,
+                          const int64_t *atom_off, const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin,
+                          const int4 *atom_wrap, const int64_t *bin_start, const int *bin_atoms, float rc2R,
+                          float rc2A, float rcq, int64_t *cnt, int *n_ang, uint64_t *scratch, int cap, int *overflow,
+                          int *err) {
+    __shared__ int slot[32];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (i >= na) return;
-    int nr = 0, nang = 0;
-    scan_atom_warp(i, lane, pos, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms, rc2R,
-                   rcq * rcq, rcq, err, [&](int, int, int, int, float r2) {
-                       ++nr;
+    if (lane == 0) slot[wib] = 0;
+    __syncwarp();
+    int nang = 0;
+    uint64_t *dst = scratch + i * (int64_t)cap;
+    scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms,
+                   rc2R, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, float r2) {
+                       const int k = atomicAdd(&slot[wib], 1);
+                       if (k < cap) dst[k] = pair_key(r2, rc2A, type[j], j, Sa, Sb, Sc);
                        if (r2 < rc2A) ++nang;
                    });
-    nr = __reduce_add_sync(FULL, nr);
     nang = __reduce_add_sync(FULL, nang);
+    __syncwarp();
     if (lane == 0) {
+        const int nr = slot[wib];
         cnt[i] = nr;
         n_ang[i] = nang;
+        if (nr > cap) atomicOr(overflow, 1);
     }
 }
 
 // Sort keys of every pair (one warp per atom); slots taken through a shared counter.
-__global__ void k_fill_w(int64_t na, const float *pos, const int *type, const int *struct_of, const int64_t *atom_off,
+__global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const int *type, const int *struct_of,
+                         const int64_t *atom_off,
                          const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin, const int4 *atom_wrap,
                          const int64_t *bin_start, const int *bin_atoms, float rc2R, float rc2A, float rcq,
                          const int64_t *nbr_off, uint64_t *keys, int *err) {
@@ -377,21 +399,18 @@ __global__ void k_fill_w(int64_t na, const float *pos, const int *type, const in
     if (lane == 0) slot[wib] = 0;
     __syncwarp();
     const int64_t o = nbr_off[i], n = nbr_off[i + 1] - o;
-    scan_atom_warp(i, lane, pos, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms, rc2R,
-                   rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, float r2) {
+    scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms,
+                   rc2R, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, float r2) {
                        const int k = atomicAdd(&slot[wib], 1);
-                       if (k < n) {
-                           const uint64_t grp = (r2 < rc2A) ? 0ull : 1ull;
-                           keys[o + k] = (grp << 63) | ((uint64_t)type[j] << 59) | ((uint64_t)j << 24) |
-                                         (uint64_t)pack_shift(Sa, Sb, Sc);
-                       }
+                       if (k < n) keys[o + k] = pair_key(r2, rc2A, type[j], j, Sa, Sb, Sc);
                    });
     __syncwarp();
     if (lane == 0 && slot[wib] != n) atomic_err(err, 5);
 }
 
 // One warp per atom: rank sort of its keys, then decode into the pair records.
-__global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const int64_t *nbr_off, const float *pos,
+__global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const uint64_t *scratch, int cap,
+                              const int64_t *nbr_off, const float *pos,
                               const int *struct_of, const SGeom *geom, uint64_t *keys_out, float4 *pair,
                               int32_t *shift) {
     constexpr int STAGE = 256;  // keys per warp staged in shared memory
@@ -401,7 +420,7 @@ __global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const int64_t
     if (i >= na) return;
     const int64_t beg = nbr_off[i], n = nbr_off[i + 1] - beg;
     const SGeom &g = geom[struct_of[i]];
-    const uint64_t *src = keys_in + beg;
+    const uint64_t *src = scratch ? scratch + i * (int64_t)cap : keys_in + beg;
     if (n <= STAGE) {  // the rank sort reads every key n times: from shared memory when it fits
         for (int64_t e = lane; e < n; e += 32) sk[wib][e] = src[e];
         __syncwarp();
@@ -486,8 +505,13 @@ int build_neighbors(Ctx *c) {
     if (c->bin_cnt.ensure<int64_t>(nbin_total + 1) || c->bin_start.ensure<int64_t>(nbin_total + 1) ||
         c->bin_cur.ensure<int64_t>(nbin_total + 1) || c->atom_bin.ensure<int64_t>(na + 1) ||
         c->atom_wrap.ensure_bytes(sizeof(int4) * (size_t)(na + 1)) || c->bin_atoms.ensure<int>(na + 1) ||
-        c->cnt.ensure<int64_t>(na + 1) || c->n_ang.ensure<int>(na + 1) || c->nbr_off.ensure<int64_t>(na + 1))
+        c->cnt.ensure<int64_t>(na + 1) || c->n_ang.ensure<int>(na + 1) || c->nbr_off.ensure<int64_t>(na + 1) ||
+        c->pos4.ensure<float4>(na + 1) || c->d_flag.ensure<int>(1))
         return c->fail(NEP_ENOMEM, "bin buffers");
+    // keys of up to `cap` pairs per atom are kept from the counting scan (at most 8 GB)
+    const int cap = (int)std::min<int64_t>(128, (int64_t)8e9 / (8 * std::max<int64_t>(na, 1)));
+    if (c->nbr_scratch.ensure<uint64_t>(na * (int64_t)cap + 1)) return c->fail(NEP_ENOMEM, "neighbour scratch");
+    CK(cudaMemsetAsync(c->d_flag.ptr, 0, sizeof(int), st));
     CK(cudaMemsetAsync(c->bin_cnt.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
     CK(cudaMemsetAsync(c->bin_cur.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
     const unsigned gA = (unsigned)((na + 255) / 256);     // 256-thread blocks, one thread per atom
@@ -498,7 +522,7 @@ int build_neighbors(Ctx *c) {
         k_atom_bin<<<gA, 256, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->cfg.n_types,
                                        c->struct_of.as<int>(), geom, c->bin_off.as<int64_t>(),
                                        c->atom_bin.as<int64_t>(), (int4 *)c->atom_wrap.ptr, c->bin_cnt.as<int64_t>(),
-                                       err);
+                                       c->pos4.as<float4>(), err);
         CK(cudaGetLastError());
     }
     rc = scan_exclusive(c, c->bin_cnt.as<int64_t>(), nbin_total, c->bin_start.as<int64_t>(),
@@ -507,36 +531,43 @@ int build_neighbors(Ctx *c) {
     if (na > 0) {
         k_bin_fill<<<gA, 256, 0, st>>>(na, c->atom_bin.as<int64_t>(), c->bin_start.as<int64_t>(),
                                        c->bin_cur.as<int64_t>(), c->bin_atoms.as<int>());
-        k_count_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
+        k_count_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(), c->type.as<int>(),
+                                      c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
                                       c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
                                       (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
                                       c->bin_atoms.as<int>(), rc2R, rc2A, rcq, c->cnt.as<int64_t>(),
-                                      c->n_ang.as<int>(), err);
+                                      c->n_ang.as<int>(), c->nbr_scratch.as<uint64_t>(), cap, c->d_flag.as<int>(), err);
         CK(cudaGetLastError());
     }
     rc = scan_exclusive(c, c->cnt.as<int64_t>(), na, c->nbr_off.as<int64_t>(), c->d_total.as<int64_t>());
     if (rc) return rc;
     int64_t M = 0;
+    int overflow = 0;
     CK(cudaMemcpyAsync(&M, c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&overflow, c->d_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr) return c->fail(NEP_EINVAL, herr == 3 ? "species index out of range" :
                                           herr == 4 ? "non-finite or far out-of-cell position" :
                                                       "more than 127 periodic images along a cell vector");
     if (M >= (int64_t)1 << 31) return c->fail(NEP_EINVAL, "more than 2^31 neighbour pairs");
-    if (c->keys_tmp.ensure<uint64_t>(M + 1) || c->keys.ensure<uint64_t>(M + 1) ||
+    if ((overflow && c->keys_tmp.ensure<uint64_t>(M + 1)) || c->keys.ensure<uint64_t>(M + 1) ||
         c->pair.ensure_bytes(sizeof(float4) * (size_t)(M + 1)) || c->rev.ensure<int>(M + 1) ||
         c->shift.ensure<int32_t>(M + 1))
         return c->fail(NEP_ENOMEM, "pair buffers");
     c->n_pairs = M;
     if (na > 0) {
-        k_fill_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->struct_of.as<int>(),
-                                     c->atom_off.as<int64_t>(), geom, c->bin_off.as<int64_t>(),
-                                     c->atom_bin.as<int64_t>(), (const int4 *)c->atom_wrap.ptr,
-                                     c->bin_start.as<int64_t>(), c->bin_atoms.as<int>(), rc2R, rc2A, rcq,
-                                     c->nbr_off.as<int64_t>(), c->keys_tmp.as<uint64_t>(), err);
+        if (overflow)  // some atom has more than `cap` pairs: a second scan writes the keys
+            k_fill_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(), c->type.as<int>(),
+                                         c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
+                                         c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
+                                         (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
+                                         c->bin_atoms.as<int>(), rc2R, rc2A, rcq, c->nbr_off.as<int64_t>(),
+                                         c->keys_tmp.as<uint64_t>(), err);
         const unsigned gw = (unsigned)((na * 32 + 255) / 256);
-        k_sort_decode<<<gw, 256, 0, st>>>(na, c->keys_tmp.as<uint64_t>(), c->nbr_off.as<int64_t>(),
+        k_sort_decode<<<gw, 256, 0, st>>>(na, c->keys_tmp.as<uint64_t>(),
+                                          overflow ? nullptr : c->nbr_scratch.as<uint64_t>(), cap,
+                                          c->nbr_off.as<int64_t>(),
                                           c->pos.as<float>(), c->struct_of.as<int>(), geom, c->keys.as<uint64_t>(),
                                           (float4 *)c->pair.ptr, c->shift.as<int32_t>());
         k_reverse<<<gw, 256, 0, st>>>(na, c->nbr_off.as<int64_t>(), c->keys.as<uint64_t>(), c->type.as<int>(),
