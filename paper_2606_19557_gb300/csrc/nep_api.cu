@@ -17,6 +17,8 @@ int launch_compact_q(Ctx *c, const float *qp, float *q);
 Ctx::~Ctx() {
     if (g_loss.exec) cudaGraphExecDestroy(g_loss.exec);
     if (g_eval.exec) cudaGraphExecDestroy(g_eval.exec);
+    if (g_train.exec) cudaGraphExecDestroy(g_train.exec);
+    drop_minibatch_graphs(this);
     if (ev_made)
         for (auto &e : ev) cudaEventDestroy(e);
 }
@@ -148,6 +150,7 @@ static void drop_graphs(Ctx *c) {
         g->exec = nullptr;
         g->key.clear();
     }
+    drop_minibatch_graphs(c);
 }
 
 static void mark(Ctx *c, int k) {
@@ -805,8 +808,39 @@ int nep_minibatch_epoch(nep_ctx *c, const int64_t *order, int64_t n_steps, doubl
         if (order[k] < 0 || order[k] >= (int64_t)c->mb.size())
             return c->fail(NEP_EINVAL, "mini-batch index out of range");
     CK(cudaSetDevice(c->dev));
-    for (int64_t k = 0; k < n_steps; ++k)
-        if ((rc = mb_train_step(c, order[k], lE, lF, lV, nullptr))) return rc;
+    // every group's training step is one cached graph, captured on its first step
+    if ((rc = minibatch_shape_check(c))) return rc;
+    uint64_t lb[3];
+    std::memcpy(&lb[0], &lE, 8);
+    std::memcpy(&lb[1], &lF, 8);
+    std::memcpy(&lb[2], &lV, 8);
+    if (c->mb_gkey != std::vector<uint64_t>(lb, lb + 3)) {
+        drop_minibatch_graphs(c);
+        c->mb_gkey.assign(lb, lb + 3);
+    }
+    if (c->mb_graphs.size() != c->mb.size()) c->mb_graphs.assign(c->mb.size(), nullptr);
+    for (int64_t k = 0; k < n_steps; ++k) {
+        cudaGraphExec_t &g = c->mb_graphs[order[k]];
+        if (!g) {
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            rc = mb_train_step(c, order[k], lE, lF, lV, nullptr);
+            const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return rc;
+            }
+            if (e != cudaSuccess) return c->fail_cuda(e, "cudaStreamEndCapture (mini-batch step)");
+            const cudaError_t ei = cudaGraphInstantiate(&g, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                g = nullptr;
+                return c->fail_cuda(ei, "cudaGraphInstantiate (mini-batch step)");
+            }
+        }
+        CK(cudaGraphLaunch(g, c->stream));
+    }
     c->state_valid = false;
     return launch_opt_epoch(c);
 }

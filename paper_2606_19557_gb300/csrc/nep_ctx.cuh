@@ -151,6 +151,8 @@ struct Ctx {
     int mb_key[6] = {-1, -1, -1, -1, -1, -1};  // launch shapes the schedules were built for
     std::vector<MiniBatch> mb;
     DevBuf mb_work, mb_wbf, mb_wba, mb_wlo, mb_whi, mb_chunks, mb_clo, mb_chi;
+    std::vector<cudaGraphExec_t> mb_graphs;  // per group: training step, captured on first use
+    std::vector<uint64_t> mb_gkey;           // loss weights the graphs were captured with
 
     int schedule = NEP_SCHED_PERSISTENT;
     // plain form (per-structure launches)
@@ -234,6 +236,8 @@ int launch_opt_epoch(Ctx *c);
 
 // mini-batch mode (nep_minibatch.cu)
 int build_minibatches(Ctx *c, int batch_size);
+int minibatch_shape_check(Ctx *c);  // rebuilds the schedules if the launch shape changed
+void drop_minibatch_graphs(Ctx *c);
 int run_minibatch_loss(Ctx *c, int64_t m, double lE, double lF, double lV, double *loss3, float *grad);
 int prepare_loss_kernels(Ctx *c);
 

@@ -258,14 +258,56 @@ __global__ void k_cotangents(int64_t ns, const int64_t *atom_off, const double *
 constexpr int ANN_ROWS = 32;
 constexpr int ANN_TILES = 128;  // 4x4 tiles per block (blockIdx.y covers the rest)
 
+// Asynchronous 4-byte global -> shared copy (zero fill when !pred), so that the next rows
+// of a chunk load while the current ones are contracted.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct AnnTile {  // one buffer of ANN_ROWS staged rows
+    float *z, *u, *o, *q, *d;
+};
+
+__device__ __forceinline__ AnnTile ann_tile(float *base, int NNP, int NDQ) {
+    AnnTile t;
+    t.z = base;
+    t.u = t.z + ANN_ROWS * NNP;
+    t.o = t.u + ANN_ROWS * NNP;
+    t.q = t.o + ANN_ROWS * NNP;
+    t.d = t.q + ANN_ROWS * NDQ;
+    return t;
+}
+
+__device__ __forceinline__ void ann_stage(const AnnTile &t, int rr, int nr, int NN, int NDP, int NNP, int NDQ,
+                                          const float *zt, const float *ut, const float *om, const float *qt,
+                                          const float *dqt) {
+    for (int e = threadIdx.x; e < ANN_ROWS * NNP; e += blockDim.x) {
+        const int r = e / NNP, m = e - r * NNP;
+        const bool in = r < nr && m < NN;
+        const size_t g = in ? (size_t)(rr + r) * NN + m : 0;
+        cp_async4(t.z + e, zt + g, in);
+        cp_async4(t.u + e, ut + g, in);
+        cp_async4(t.o + e, om + g, in);
+    }
+    for (int e = threadIdx.x; e < ANN_ROWS * NDQ; e += blockDim.x) {
+        const int r = e / NDQ, v = e - r * NDQ;
+        const bool in = r < nr && v < NDP;
+        const size_t g = in ? (size_t)(rr + r) * NDP + v : 0;
+        cp_async4(t.q + e, qt + g, in);
+        cp_async4(t.d + e, dqt + g, in);
+    }
+    cp_async_commit();
+}
+
 __global__ void k_ann_grad(const int *chunk_begin, int NN, int NDP, const float *zt, const float *ut,
                            const float *om, const float *qt, const float *dqt, float *part) {
     extern __shared__ __align__(16) float sm[];
     const int NNP = (NN + 3) & ~3, NDQ = (NDP + 3) & ~3;
-    float *sz = sm;                      // [ROWS][NNP]
-    float *su = sz + ANN_ROWS * NNP;     // [ROWS][NNP]
-    float *sq = su + ANN_ROWS * NNP;     // [ROWS][NDQ]
-    float *sd = sq + ANN_ROWS * NDQ;     // [ROWS][NDQ]
+    const int tile_floats = ANN_ROWS * (3 * NNP + 2 * NDQ);
+    const AnnTile buf[2] = {ann_tile(sm, NNP, NDQ), ann_tile(sm + tile_floats, NNP, NDQ)};
     const int c = blockIdx.x;
     const int r0 = chunk_begin[c], r1 = chunk_begin[c + 1];
     const int tn = NDQ / 4, ntiles = (NNP / 4) * tn;
@@ -279,27 +321,22 @@ __global__ void k_ann_grad(const int *chunk_begin, int NN, int NDP, const float 
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
     float azeta = 0.0f, aom = 0.0f;
+    if (r0 < r1) ann_stage(buf[0], r0, min(ANN_ROWS, r1 - r0), NN, NDP, NNP, NDQ, zt, ut, om, qt, dqt);
+    int cur = 0;
     for (int rr = r0; rr < r1; rr += ANN_ROWS) {
         const int nr = min(ANN_ROWS, r1 - rr);
-        for (int e = threadIdx.x; e < ANN_ROWS * NNP; e += blockDim.x) {
-            const int r = e / NNP, m = e - r * NNP;
-            const bool in = r < nr && m < NN;
-            sz[e] = in ? zt[(size_t)(rr + r) * NN + m] : 0.0f;
-            su[e] = in ? ut[(size_t)(rr + r) * NN + m] : 0.0f;
-        }
-        for (int e = threadIdx.x; e < ANN_ROWS * NDQ; e += blockDim.x) {
-            const int r = e / NDQ, v = e - r * NDQ;
-            const bool in = r < nr && v < NDP;
-            sq[e] = in ? qt[(size_t)(rr + r) * NDP + v] : 0.0f;
-            sd[e] = in ? dqt[(size_t)(rr + r) * NDP + v] : 0.0f;
-        }
-        __syncthreads();
+        cp_async_wait_all();
+        __syncthreads();  // rows rr.. are in buf[cur]; every thread is done with buf[cur ^ 1]
+        if (rr + ANN_ROWS < r1)
+            ann_stage(buf[cur ^ 1], rr + ANN_ROWS, min(ANN_ROWS, r1 - rr - ANN_ROWS), NN, NDP, NNP, NDQ, zt, ut, om,
+                      qt, dqt);
+        const AnnTile &t = buf[cur];
         if (own) {
             for (int r = 0; r < nr; ++r) {
-                const float4 z4 = *reinterpret_cast<const float4 *>(sz + r * NNP + mu0);
-                const float4 u4 = *reinterpret_cast<const float4 *>(su + r * NNP + mu0);
-                const float4 q4 = *reinterpret_cast<const float4 *>(sq + r * NDQ + v0);
-                const float4 d4 = *reinterpret_cast<const float4 *>(sd + r * NDQ + v0);
+                const float4 z4 = *reinterpret_cast<const float4 *>(t.z + r * NNP + mu0);
+                const float4 u4 = *reinterpret_cast<const float4 *>(t.u + r * NNP + mu0);
+                const float4 q4 = *reinterpret_cast<const float4 *>(t.q + r * NDQ + v0);
+                const float4 d4 = *reinterpret_cast<const float4 *>(t.d + r * NDQ + v0);
                 const float z[4] = {z4.x, z4.y, z4.z, z4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
                 const float q[4] = {q4.x, q4.y, q4.z, q4.w}, d[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
@@ -310,11 +347,11 @@ __global__ void k_ann_grad(const int *chunk_begin, int NN, int NDP, const float 
         }
         if (first && (int)threadIdx.x < NN) {
             for (int r = 0; r < nr; ++r) {
-                azeta += sz[r * NNP + threadIdx.x];
-                aom += om[(size_t)(rr + r) * NN + threadIdx.x];
+                azeta += t.z[r * NNP + threadIdx.x];
+                aom += t.o[r * NNP + threadIdx.x];
             }
         }
-        __syncthreads();
+        cur ^= 1;
     }
     const int nent = NN * NDP;
     float *dst = part + (size_t)c * (nent + 2 * NN);
@@ -346,10 +383,15 @@ struct GradArgs {
     double *acc;           // plain form: add the partial sums here (FP64), b1 left out
 };
 
+// One block per 32 consecutive parameters (threadIdx.x) with GF_RG row groups (threadIdx.y):
+// the threads of a warp read 32 neighbouring parameters of one partial row (coalesced),
+// each row group sums every GF_RG-th row, and the row groups are added in a fixed order.
+constexpr int GF_RG = 32;
+
 __global__ void k_grad_final(GradArgs g) {
-    const int lane = threadIdx.x & 31;
-    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (k >= g.P) return;
+    __shared__ double red[GF_RG][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * 32 + tx;
     const int T = g.T, NN = g.NN, ND = g.ND;
     const int64_t cb0 = (int64_t)T * NN * ND, cw1 = cb0 + (int64_t)T * NN, cb1 = cw1 + (int64_t)T * NN;
     const int64_t ccR = cb1 + 1, ccA = ccR + (int64_t)T * T * g.nR * g.kR;
@@ -357,49 +399,60 @@ __global__ void k_grad_final(GradArgs g) {
     const int annstride = NN * g.NDP + 2 * NN;
     double s = 0.0;
     double sign = 1.0;
-    if (k < cb0 || k < cb1) {
-        int t, off;
-        if (k < cb0) {
-            t = (int)(k / ((int64_t)NN * ND));
-            const int r = (int)(k - (int64_t)t * NN * ND);
-            const int mu = r / ND, v = r - mu * ND;
-            off = mu * g.NDP + g.desc_map[v];
-        } else if (k < cw1) {
-            t = (int)((k - cb0) / NN);
-            off = NN * g.NDP + (int)((k - cb0) % NN);
-            sign = -1.0;
+    if (k < g.P) {
+        if (k < cb1) {
+            int t, off;
+            if (k < cb0) {
+                t = (int)(k / ((int64_t)NN * ND));
+                const int r = (int)(k - (int64_t)t * NN * ND);
+                const int mu = r / ND, v = r - mu * ND;
+                off = mu * g.NDP + g.desc_map[v];
+            } else if (k < cw1) {
+                t = (int)((k - cb0) / NN);
+                off = NN * g.NDP + (int)((k - cb0) % NN);
+                sign = -1.0;
+            } else {
+                t = (int)((k - cw1) / NN);
+                off = NN * g.NDP + NN + (int)((k - cw1) % NN);
+            }
+            double s4[4] = {0.0, 0.0, 0.0, 0.0};  // four independent chains keep four loads in flight
+            int q = 0;
+            for (int c = g.clo[t] + ty; c < g.chi[t]; c += GF_RG, q = (q + 1) & 3)
+                s4[q] += (double)g.annpart[(size_t)c * annstride + off];
+            s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+        } else if (k == cb1) {
+            if (ty == 0 && !g.acc) s = *g.gb1;
         } else {
-            t = (int)((k - cw1) / NN);
-            off = NN * g.NDP + NN + (int)((k - cw1) % NN);
+            int a, b, off;
+            if (k < ccA) {
+                const int64_t r = k - ccR;
+                const int kk = (int)(r % g.kR), n = (int)((r / g.kR) % g.nR);
+                const int64_t ab = r / ((int64_t)g.kR * g.nR);
+                a = (int)(ab / T);
+                b = (int)(ab % T);
+                off = n * g.KRP + kk;
+            } else {
+                const int64_t r = k - ccA;
+                const int kk = (int)(r % g.kA), n = (int)((r / g.kA) % g.nA);
+                const int64_t ab = r / ((int64_t)g.kA * g.nA);
+                a = (int)(ab / T);
+                b = (int)(ab % T);
+                off = NCR + n * g.KAP + kk;
+            }
+            double s4[4] = {0.0, 0.0, 0.0, 0.0};
+            int q = 0;
+            for (int w = g.wlo[a] + ty; w <= g.whi[a]; w += GF_RG, q = (q + 1) & 3)
+                if (g.warp_begin[w] < g.warp_begin[w + 1]) s4[q] += (double)g.cpart[((size_t)(w + a) * T + b) * NC + off];
+            s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         }
-        for (int c = g.clo[t] + lane; c < g.chi[t]; c += 32) s += (double)g.annpart[(size_t)c * annstride + off];
-    } else if (k == cb1) {
-        if (lane == 0 && !g.acc) s = *g.gb1;
-    } else {
-        int a, b, off;
-        if (k < ccA) {
-            const int64_t r = k - ccR;
-            const int kk = (int)(r % g.kR), n = (int)((r / g.kR) % g.nR);
-            const int64_t ab = r / ((int64_t)g.kR * g.nR);
-            a = (int)(ab / T);
-            b = (int)(ab % T);
-            off = n * g.KRP + kk;
-        } else {
-            const int64_t r = k - ccA;
-            const int kk = (int)(r % g.kA), n = (int)((r / g.kA) % g.nA);
-            const int64_t ab = r / ((int64_t)g.kA * g.nA);
-            a = (int)(ab / T);
-            b = (int)(ab % T);
-            off = NCR + n * g.KAP + kk;
-        }
-        for (int w = g.wlo[a] + lane; w <= g.whi[a]; w += 32)
-            if (g.warp_begin[w] < g.warp_begin[w + 1]) s += (double)g.cpart[((size_t)(w + a) * T + b) * NC + off];
     }
-    s = warp_sum_d(s);
-    if (lane == 0) {
-        if (g.acc) g.acc[k] += sign * s;
-        else g.grad[k] = (float)(sign * s);
-    }
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty != 0 || k >= g.P) return;
+    double tot = 0.0;
+    for (int r = 0; r < GF_RG; ++r) tot += red[r][tx];
+    if (g.acc) g.acc[k] += sign * tot;
+    else g.grad[k] = (float)(sign * tot);
 }
 
 // Plain form: gradient = FP64 accumulator, b1 from the loss reduction.
@@ -615,9 +668,9 @@ int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *d
     return NEP_OK;
 }
 
-static size_t ann_smem(Ctx *c) {
+static size_t ann_smem(Ctx *c) {  // two buffers of staged rows
     const int NNP = (c->NN + 3) & ~3, NDQ = (c->NDP + 3) & ~3;
-    return sizeof(float) * ANN_ROWS * (2 * NNP + 2 * NDQ);
+    return 2 * sizeof(float) * ANN_ROWS * (3 * NNP + 2 * NDQ);
 }
 static int ann_groups(Ctx *c) {
     const int ntiles = ((c->NN + 3) / 4) * ((c->NDP + 3) / 4);
@@ -686,15 +739,14 @@ int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi,
     g.wlo = wlo;
     g.whi = whi;
     g.warp_begin = warp_begin;
-    k_grad_final<<<(unsigned)((c->P * 32 + 255) / 256), 256, 0, c->stream>>>(g);
+    k_grad_final<<<(unsigned)((c->P + 31) / 32), dim3(32, GF_RG), 0, c->stream>>>(g);
     CK_LAUNCH("k_grad_final");
     return NEP_OK;
 }
 
 int launch_grad_final(Ctx *c, float *grad) {
     GradArgs g = grad_args(c, grad);
-    const int64_t threads = c->P * 32;
-    k_grad_final<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(g);
+    k_grad_final<<<(unsigned)((c->P + 31) / 32), dim3(32, GF_RG), 0, c->stream>>>(g);
     CK_LAUNCH("k_grad_final");
     return NEP_OK;
 }
@@ -798,7 +850,7 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         g.whi = c->p_whi.as<int>() + s * c->T;
         g.warp_begin = c->p_ident.as<int>() + a0;
         g.acc = c->p_acc.as<double>();
-        k_grad_final<<<(unsigned)((c->P * 32 + 255) / 256), 256, 0, c->stream>>>(g);
+        k_grad_final<<<(unsigned)((c->P + 31) / 32), dim3(32, GF_RG), 0, c->stream>>>(g);
         CK_LAUNCH("k_grad_final (plain)");
     }
     if ((rc = launch_loss_final(c, loss3, pg, (int)(ns * GB), ps, (int)ns))) return rc;

@@ -71,7 +71,21 @@ void shape_key(const Ctx *c, int *key) {
 
 }  // namespace
 
+void drop_minibatch_graphs(Ctx *c) {
+    for (cudaGraphExec_t g : c->mb_graphs)
+        if (g) cudaGraphExecDestroy(g);
+    c->mb_graphs.clear();
+    c->mb_gkey.clear();
+}
+
+int minibatch_shape_check(Ctx *c) {
+    int key[6];
+    shape_key(c, key);
+    return std::equal(key, key + 6, c->mb_key) ? NEP_OK : build_minibatches(c, c->mb_B);
+}
+
 int build_minibatches(Ctx *c, int B) {
+    drop_minibatch_graphs(c);  // the graphs hold the old schedules
     const int64_t ns = c->n_struct, na = c->n_atoms;
     const int T = c->T;
     const int gf = 32 / c->ks->sw[c->fwd.var], ga = 32 / c->ks->sw[c->adj.var];
@@ -153,12 +167,8 @@ int build_minibatches(Ctx *c, int B) {
 
 // Loss and gradient of group m against the references of nep_set_targets.
 int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, double *loss3, float *grad) {
-    int key[6];
-    shape_key(c, key);
-    if (!std::equal(key, key + 6, c->mb_key)) {
-        int rc = build_minibatches(c, c->mb_B);  // the launch shape changed since the setup
-        if (rc) return rc;
-    }
+    int rc0 = minibatch_shape_check(c);  // the launch shape may have changed since the setup
+    if (rc0) return rc0;
     const Ctx::MiniBatch &m = c->mb[mi];
     const int T = c->T;
     const uint8_t *hw = c->tgt_has_hw ? c->tgt_hw.as<uint8_t>() : nullptr;
