@@ -293,7 +293,8 @@ int nep_create(const nep_config *cfg, void *cuda_stream, nep_ctx **out) {
     if (c->d_desc_map.ensure<int>(c->ND) || c->d_desc_inv.ensure<int>(c->NDP) || c->theta.ensure<float>(c->P) ||
         c->qscale.ensure<float>(c->ND) || c->par.ensure<float>(c->po.total) || c->d_err.ensure<int>(4) ||
         c->n_sv.ensure<int>(4) || c->gb1.ensure<double>(4) || c->loss3_int.ensure<double>(4) ||
-        c->grad_int.ensure<float>(c->P) || c->hostbuf_theta.ensure<float>(c->P)) {
+        c->grad_int.ensure<float>(c->P) || c->hostbuf_theta.ensure<float>(c->P) ||
+        c->gpart.ensure<double>(8 * c->P)) {
         g_create_err = "device allocation failed";
         delete c;
         return NEP_ENOMEM;

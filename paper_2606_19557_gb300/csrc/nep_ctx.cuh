@@ -110,6 +110,7 @@ struct Ctx {
     DevBuf geom, nbins, bin_off, bin_cnt, bin_start, bin_cur, atom_bin, atom_wrap, bin_atoms, cnt, n_ang, nbr_off;
     DevBuf keys_tmp, keys, pair, rev, shift, scan_tmp, d_total, d_err;
     DevBuf pos4, nbr_scratch, d_flag;  // float4 positions, per-atom key scratch, overflow flag
+    DevBuf bin_pos, bin_wrap;          // atoms in bin order: (x, y, z, bits(j)) and wrap offsets
 
     // schedule
     DevBuf work;                 // [Na] atom per work position (species-sorted)
@@ -124,6 +125,7 @@ struct Ctx {
     DevBuf fbar, ebar, wbar, zt, ut, om, dqt, cpart, annpart;
     DevBuf F_int, E_int, W_int;       // internal outputs for nep_loss_grad
     DevBuf loss_part, gb1, n_sv, loss3_int, grad_int;
+    DevBuf gpart;                     // [8][P] FP64 segment sums of the gradient reduction
     DevBuf tgt_E, tgt_F, tgt_W, tgt_hw;  // nep_set_targets copies
     bool have_targets = false, tgt_has_hw = false;
     DevBuf hostbuf_theta;             // device copy target of nep_loss_grad_host

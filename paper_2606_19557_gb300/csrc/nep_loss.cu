@@ -383,66 +383,96 @@ struct GradArgs {
     double *acc;           // plain form: add the partial sums here (FP64), b1 left out
 };
 
-// One block per 32 consecutive parameters (threadIdx.x) with GF_RG row groups (threadIdx.y):
-// the threads of a warp read 32 neighbouring parameters of one partial row (coalesced),
-// each row group sums every GF_RG-th row, and the row groups are added in a fixed order.
+// Two passes.  k_grad_part: one block per (32 consecutive parameters, row segment), with
+// GF_RG row groups (threadIdx.y); the threads of a warp read 32 neighbouring parameters of
+// one partial row (coalesced), each thread keeps four FP64 chains, the row groups are added
+// in a fixed order and each segment's sum goes to gpart[seg][k].  k_grad_sum adds the
+// GF_SEG segments of each parameter in order.  Spreading the rows over segments keeps
+// every SM busy with the FP64 additions.
 constexpr int GF_RG = 32;
+constexpr int GF_SEG = 8;
 
-__global__ void k_grad_final(GradArgs g) {
-    __shared__ double red[GF_RG][33];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t k = (int64_t)blockIdx.x * 32 + tx;
+struct GradSource {  // where parameter k's partials live
+    bool net;         // network parameter: rows = chunks [lo, hi) of annpart
+    bool b1;          // the shared output bias (from the loss reduction)
+    int lo, hi;       // row range (c-parameters: adjoint warps [lo, hi), slot w + a)
+    int a, b, off;    // species pair of a c-parameter, column in the partial row
+    double sign;
+};
+
+__device__ __forceinline__ GradSource grad_source(const GradArgs &g, int64_t k) {
+    GradSource r{};
+    r.sign = 1.0;
     const int T = g.T, NN = g.NN, ND = g.ND;
     const int64_t cb0 = (int64_t)T * NN * ND, cw1 = cb0 + (int64_t)T * NN, cb1 = cw1 + (int64_t)T * NN;
     const int64_t ccR = cb1 + 1, ccA = ccR + (int64_t)T * T * g.nR * g.kR;
-    const int NCR = g.NRP * g.KRP, NCA = g.NAP * g.KAP, NC = NCR + NCA;
-    const int annstride = NN * g.NDP + 2 * NN;
+    const int NCR = g.NRP * g.KRP;
+    if (k < cb1) {
+        int t;
+        r.net = true;
+        if (k < cb0) {
+            t = (int)(k / ((int64_t)NN * ND));
+            const int rr = (int)(k - (int64_t)t * NN * ND);
+            const int mu = rr / ND, v = rr - mu * ND;
+            r.off = mu * g.NDP + g.desc_map[v];
+        } else if (k < cw1) {
+            t = (int)((k - cb0) / NN);
+            r.off = NN * g.NDP + (int)((k - cb0) % NN);
+            r.sign = -1.0;
+        } else {
+            t = (int)((k - cw1) / NN);
+            r.off = NN * g.NDP + NN + (int)((k - cw1) % NN);
+        }
+        r.lo = g.clo[t];
+        r.hi = g.chi[t];
+    } else if (k == cb1) {
+        r.b1 = true;
+    } else {
+        int64_t rr;
+        int kk, n;
+        if (k < ccA) {
+            rr = k - ccR;
+            kk = (int)(rr % g.kR);
+            n = (int)((rr / g.kR) % g.nR);
+            rr /= (int64_t)g.kR * g.nR;
+            r.off = n * g.KRP + kk;
+        } else {
+            rr = k - ccA;
+            kk = (int)(rr % g.kA);
+            n = (int)((rr / g.kA) % g.nA);
+            rr /= (int64_t)g.kA * g.nA;
+            r.off = NCR + n * g.KAP + kk;
+        }
+        r.a = (int)(rr / T);
+        r.b = (int)(rr % T);
+        r.lo = g.wlo[r.a];
+        r.hi = g.whi[r.a] + 1;
+    }
+    return r;
+}
+
+__global__ void k_grad_part(GradArgs g, double *gpart /*[GF_SEG][P]*/) {
+    __shared__ double red[GF_RG][33];
+    const int tx = threadIdx.x, ty = threadIdx.y, seg = blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * 32 + tx;
+    const int T = g.T, NC = g.NRP * g.KRP + g.NAP * g.KAP;
+    const int annstride = g.NN * g.NDP + 2 * g.NN;
     double s = 0.0;
-    double sign = 1.0;
     if (k < g.P) {
-        if (k < cb1) {
-            int t, off;
-            if (k < cb0) {
-                t = (int)(k / ((int64_t)NN * ND));
-                const int r = (int)(k - (int64_t)t * NN * ND);
-                const int mu = r / ND, v = r - mu * ND;
-                off = mu * g.NDP + g.desc_map[v];
-            } else if (k < cw1) {
-                t = (int)((k - cb0) / NN);
-                off = NN * g.NDP + (int)((k - cb0) % NN);
-                sign = -1.0;
-            } else {
-                t = (int)((k - cw1) / NN);
-                off = NN * g.NDP + NN + (int)((k - cw1) % NN);
-            }
+        const GradSource r = grad_source(g, k);
+        if (!r.b1) {
+            const int len = (r.hi - r.lo + GF_SEG - 1) / GF_SEG;
+            const int lo = r.lo + seg * len, hi = min(r.hi, lo + len);
             double s4[4] = {0.0, 0.0, 0.0, 0.0};  // four independent chains keep four loads in flight
             int q = 0;
-            for (int c = g.clo[t] + ty; c < g.chi[t]; c += GF_RG, q = (q + 1) & 3)
-                s4[q] += (double)g.annpart[(size_t)c * annstride + off];
-            s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-        } else if (k == cb1) {
-            if (ty == 0 && !g.acc) s = *g.gb1;
-        } else {
-            int a, b, off;
-            if (k < ccA) {
-                const int64_t r = k - ccR;
-                const int kk = (int)(r % g.kR), n = (int)((r / g.kR) % g.nR);
-                const int64_t ab = r / ((int64_t)g.kR * g.nR);
-                a = (int)(ab / T);
-                b = (int)(ab % T);
-                off = n * g.KRP + kk;
+            if (r.net) {
+                for (int c = lo + ty; c < hi; c += GF_RG, q = (q + 1) & 3)
+                    s4[q] += (double)g.annpart[(size_t)c * annstride + r.off];
             } else {
-                const int64_t r = k - ccA;
-                const int kk = (int)(r % g.kA), n = (int)((r / g.kA) % g.nA);
-                const int64_t ab = r / ((int64_t)g.kA * g.nA);
-                a = (int)(ab / T);
-                b = (int)(ab % T);
-                off = NCR + n * g.KAP + kk;
+                for (int w = lo + ty; w < hi; w += GF_RG, q = (q + 1) & 3)
+                    if (g.warp_begin[w] < g.warp_begin[w + 1])
+                        s4[q] += (double)g.cpart[((size_t)(w + r.a) * T + r.b) * NC + r.off];
             }
-            double s4[4] = {0.0, 0.0, 0.0, 0.0};
-            int q = 0;
-            for (int w = g.wlo[a] + ty; w <= g.whi[a]; w += GF_RG, q = (q + 1) & 3)
-                if (g.warp_begin[w] < g.warp_begin[w + 1]) s4[q] += (double)g.cpart[((size_t)(w + a) * T + b) * NC + off];
             s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         }
     }
@@ -450,9 +480,19 @@ __global__ void k_grad_final(GradArgs g) {
     __syncthreads();
     if (ty != 0 || k >= g.P) return;
     double tot = 0.0;
-    for (int r = 0; r < GF_RG; ++r) tot += red[r][tx];
-    if (g.acc) g.acc[k] += sign * tot;
-    else g.grad[k] = (float)(sign * tot);
+    for (int rr = 0; rr < GF_RG; ++rr) tot += red[rr][tx];
+    gpart[(size_t)seg * g.P + k] = tot;
+}
+
+__global__ void k_grad_sum(GradArgs g, const double *gpart) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.P) return;
+    const GradSource r = grad_source(g, k);
+    double tot = 0.0;
+    for (int seg = 0; seg < GF_SEG; ++seg) tot += gpart[(size_t)seg * g.P + k];
+    if (r.b1) tot = g.acc ? 0.0 : *g.gb1;
+    if (g.acc) g.acc[k] += r.sign * tot;
+    else g.grad[k] = (float)(r.sign * tot);
 }
 
 // Plain form: gradient = FP64 accumulator, b1 from the loss reduction.
@@ -702,6 +742,15 @@ int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks) {
     return NEP_OK;
 }
 
+static int run_grad_final(Ctx *c, const GradArgs &g) {
+    double *gp = c->gpart.as<double>();
+    k_grad_part<<<dim3((unsigned)((c->P + 31) / 32), GF_SEG), dim3(32, GF_RG), 0, c->stream>>>(g, gp);
+    CK_LAUNCH("k_grad_part");
+    k_grad_sum<<<(unsigned)((c->P + 255) / 256), 256, 0, c->stream>>>(g, gp);
+    CK_LAUNCH("k_grad_sum");
+    return NEP_OK;
+}
+
 static GradArgs grad_args(Ctx *c, float *grad) {
     GradArgs g;
     g.T = c->T;
@@ -739,16 +788,12 @@ int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi,
     g.wlo = wlo;
     g.whi = whi;
     g.warp_begin = warp_begin;
-    k_grad_final<<<(unsigned)((c->P + 31) / 32), dim3(32, GF_RG), 0, c->stream>>>(g);
-    CK_LAUNCH("k_grad_final");
-    return NEP_OK;
+    return run_grad_final(c, g);
 }
 
 int launch_grad_final(Ctx *c, float *grad) {
     GradArgs g = grad_args(c, grad);
-    k_grad_final<<<(unsigned)((c->P + 31) / 32), dim3(32, GF_RG), 0, c->stream>>>(g);
-    CK_LAUNCH("k_grad_final");
-    return NEP_OK;
+    return run_grad_final(c, g);
 }
 
 // ----------------------------------------------------------------------------- plain form
@@ -850,8 +895,7 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         g.whi = c->p_whi.as<int>() + s * c->T;
         g.warp_begin = c->p_ident.as<int>() + a0;
         g.acc = c->p_acc.as<double>();
-        k_grad_final<<<(unsigned)((c->P + 31) / 32), dim3(32, GF_RG), 0, c->stream>>>(g);
-        CK_LAUNCH("k_grad_final (plain)");
+        if ((rc = run_grad_final(c, g))) return rc;
     }
     if ((rc = launch_loss_final(c, loss3, pg, (int)(ns * GB), ps, (int)ns))) return rc;
     k_grad_convert<<<(unsigned)((c->P + 255) / 256), 256, 0, c->stream>>>(c->P, (int64_t)c->T * c->NN * c->ND +

@@ -242,6 +242,18 @@ __global__ void k_bin_fill(int64_t na, const int64_t *atom_bin, const int64_t *b
     bin_atoms[bin_start[bin] + slot] = (int)i;
 }
 
+// The atoms of every bin in bin order: (x, y, z, bits(j)) and the wrap offsets, so that the
+// lanes scanning a bin read consecutive entries.
+__global__ void k_bin_pack(int64_t na, const int *bin_atoms, const float4 *pos4, const int4 *atom_wrap,
+                           float4 *bin_pos, int4 *bin_wrap) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= na) return;
+    const int j = bin_atoms[t];
+    const float4 p = pos4[j];
+    bin_pos[t] = make_float4(p.x, p.y, p.z, __int_as_float(j));
+    bin_wrap[t] = atom_wrap[j];
+}
+
 // The pair predicate.  Returns the float squared length; d32 receives the float displacement.
 __device__ __forceinline__ float pair_d(const float *pi, const float *pj, const double *h, int Sa, int Sb, int Sc,
                                         float *d32) {
@@ -273,16 +285,15 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
                                                const int *struct_of,
                                                const int64_t *atom_off, const SGeom *geom, const int64_t *bin_off,
                                                const int64_t *atom_bin, const int4 *atom_wrap,
-                                               const int64_t *bin_start, const int *bin_atoms, float rc2R,
-                                               float rcq2, float rcq, int *err, Fn hit) {
+                                               const int64_t *bin_start, const float4 *bin_pos, const int4 *bin_wrap,
+                                               float rc2R, float rcq2, float rcq, int *err, Fn hit) {
     const int s = struct_of[i];
     const SGeom &g = geom[s];
     const float *pi = pos + 3 * i;
     const float hf[9] = {(float)g.h[0], (float)g.h[1], (float)g.h[2], (float)g.h[3], (float)g.h[4],
                          (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
-    auto test = [&](int j, int Sa, int Sb, int Sc) {
+    auto test = [&](int j, int Sa, int Sb, int Sc, float4 pj4) {
         if (j == (int)i && Sa == 0 && Sb == 0 && Sc == 0) return;
-        const float4 pj4 = pos4[j];
         const float qx = (pj4.x - pi[0]) + (Sa * hf[0] + Sb * hf[3] + Sc * hf[6]);
         const float qy = (pj4.y - pi[1]) + (Sa * hf[1] + Sb * hf[4] + Sc * hf[7]);
         const float qz = (pj4.z - pi[2]) + (Sa * hf[2] + Sb * hf[5] + Sc * hf[8]);
@@ -319,7 +330,7 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
             }
             for (int Sa = lo[0]; Sa <= hi[0]; ++Sa)
                 for (int Sb = lo[1]; Sb <= hi[1]; ++Sb)
-                    for (int Sc = lo[2]; Sc <= hi[2]; ++Sc) test((int)j, Sa, Sb, Sc);
+                    for (int Sc = lo[2]; Sc <= hi[2]; ++Sc) test((int)j, Sa, Sb, Sc, pj);
         }
         return;
     }
@@ -340,9 +351,9 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
                 bc -= sc * g.n[2];
                 const int64_t bin = bin_off[s] + ((int64_t)ba * g.n[1] + bb) * g.n[2] + bc;
                 for (int64_t t = bin_start[bin] + lane; t < bin_start[bin + 1]; t += 32) {
-                    const int j = bin_atoms[t];
-                    const int4 wj = atom_wrap[j];
-                    test(j, sa + wi.x - wj.x, sb + wi.y - wj.y, sc + wi.z - wj.z);
+                    const float4 bp = bin_pos[t];  // the bin's atoms in bin order: coalesced
+                    const int4 wj = bin_wrap[t];
+                    test(__float_as_int(bp.w), sa + wi.x - wj.x, sb + wi.y - wj.y, sc + wi.z - wj.z, bp);
                 }
             }
         }
@@ -359,7 +370,8 @@ __device__ __forceinline__ uint64_t pair_key(float r2, float rc2A, int tj, int j
 // no second scan.  *overflow is set when some atom has more than cap pairs.
 __global__ void k_count_w(int64_t na, const float *pos, const float4 *pos4, const int *type, const int *struct_of,
                           const int64_t *atom_off, const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin,
-                          const int4 *atom_wrap, const int64_t *bin_start, const int *bin_atoms, float rc2R,
+                          const int4 *atom_wrap, const int64_t *bin_start, const float4 *bin_pos,
+                          const int4 *bin_wrap, float rc2R,
                           float rc2A, float rcq, int64_t *cnt, int *n_ang, uint64_t *scratch, int cap, int *overflow,
                           int *err) {
     __shared__ int slot[32];
@@ -370,7 +382,7 @@ __global__ void k_count_w(int64_t na, const float *pos, const float4 *pos4, cons
     __syncwarp();
     int nang = 0;
     uint64_t *dst = scratch + i * (int64_t)cap;
-    scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms,
+    scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_pos, bin_wrap,
                    rc2R, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, float r2) {
                        const int k = atomicAdd(&slot[wib], 1);
                        if (k < cap) dst[k] = pair_key(r2, rc2A, type[j], j, Sa, Sb, Sc);
@@ -390,7 +402,8 @@ __global__ void k_count_w(int64_t na, const float *pos, const float4 *pos4, cons
 __global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const int *type, const int *struct_of,
                          const int64_t *atom_off,
                          const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin, const int4 *atom_wrap,
-                         const int64_t *bin_start, const int *bin_atoms, float rc2R, float rc2A, float rcq,
+                         const int64_t *bin_start, const float4 *bin_pos, const int4 *bin_wrap, float rc2R,
+                         float rc2A, float rcq,
                          const int64_t *nbr_off, uint64_t *keys, int *err) {
     __shared__ int slot[32];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -399,7 +412,7 @@ __global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const
     if (lane == 0) slot[wib] = 0;
     __syncwarp();
     const int64_t o = nbr_off[i], n = nbr_off[i + 1] - o;
-    scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_atoms,
+    scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_pos, bin_wrap,
                    rc2R, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, float r2) {
                        const int k = atomicAdd(&slot[wib], 1);
                        if (k < n) keys[o + k] = pair_key(r2, rc2A, type[j], j, Sa, Sb, Sc);
@@ -506,7 +519,8 @@ int build_neighbors(Ctx *c) {
         c->bin_cur.ensure<int64_t>(nbin_total + 1) || c->atom_bin.ensure<int64_t>(na + 1) ||
         c->atom_wrap.ensure_bytes(sizeof(int4) * (size_t)(na + 1)) || c->bin_atoms.ensure<int>(na + 1) ||
         c->cnt.ensure<int64_t>(na + 1) || c->n_ang.ensure<int>(na + 1) || c->nbr_off.ensure<int64_t>(na + 1) ||
-        c->pos4.ensure<float4>(na + 1) || c->d_flag.ensure<int>(1))
+        c->pos4.ensure<float4>(na + 1) || c->d_flag.ensure<int>(1) || c->bin_pos.ensure<float4>(na + 1) ||
+        c->bin_wrap.ensure_bytes(sizeof(int4) * (size_t)(na + 1)))
         return c->fail(NEP_ENOMEM, "bin buffers");
     // keys of up to `cap` pairs per atom are kept from the counting scan (at most 8 GB)
     const int cap = (int)std::min<int64_t>(128, (int64_t)8e9 / (8 * std::max<int64_t>(na, 1)));
@@ -531,11 +545,15 @@ int build_neighbors(Ctx *c) {
     if (na > 0) {
         k_bin_fill<<<gA, 256, 0, st>>>(na, c->atom_bin.as<int64_t>(), c->bin_start.as<int64_t>(),
                                        c->bin_cur.as<int64_t>(), c->bin_atoms.as<int>());
+        k_bin_pack<<<gA, 256, 0, st>>>(na, c->bin_atoms.as<int>(), c->pos4.as<float4>(),
+                                       (const int4 *)c->atom_wrap.ptr, c->bin_pos.as<float4>(),
+                                       (int4 *)c->bin_wrap.ptr);
         k_count_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(), c->type.as<int>(),
                                       c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
                                       c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
                                       (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
-                                      c->bin_atoms.as<int>(), rc2R, rc2A, rcq, c->cnt.as<int64_t>(),
+                                      c->bin_pos.as<float4>(), (const int4 *)c->bin_wrap.ptr, rc2R, rc2A, rcq,
+                                      c->cnt.as<int64_t>(),
                                       c->n_ang.as<int>(), c->nbr_scratch.as<uint64_t>(), cap, c->d_flag.as<int>(), err);
         CK(cudaGetLastError());
     }
@@ -562,7 +580,8 @@ int build_neighbors(Ctx *c) {
                                          c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
                                          c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
                                          (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
-                                         c->bin_atoms.as<int>(), rc2R, rc2A, rcq, c->nbr_off.as<int64_t>(),
+                                         c->bin_pos.as<float4>(), (const int4 *)c->bin_wrap.ptr, rc2R, rc2A, rcq,
+                                         c->nbr_off.as<int64_t>(),
                                          c->keys_tmp.as<uint64_t>(), err);
         const unsigned gw = (unsigned)((na * 32 + 255) / 256);
         k_sort_decode<<<gw, 256, 0, st>>>(na, c->keys_tmp.as<uint64_t>(),
