@@ -163,21 +163,24 @@ __global__ void k_struct(int64_t s0, int64_t s1, const int64_t *atom_off, const 
     E_out[s] = E;
     for (int k = 0; k < 9; ++k) W_out[s * 9 + k] = Wv[k];
     if (!loss) return;
+    // FP64 division is slow on this part: one reciprocal per structure, coefficients once
     const double NsV = nsv_over > 0.0 ? nsv_over : (double)(*n_sv);
     const double na = (double)(e - b);
+    const double inv_na = 1.0 / na, inv_na2 = inv_na * inv_na;
     const double dE = E - E_ref[s];
-    const double aE = (dE / na) * (dE / na);
-    const double eb = lamE * 2.0 * dE / (na * na) / Ns;
+    const double aE = (dE * inv_na) * (dE * inv_na);
+    const double eb = (lamE * 2.0 / Ns) * dE * inv_na2;
     ebar[s] = (float)eb;
     const double ab1 = -na * eb;
     double aV = 0.0;
     const bool hw = has_W == nullptr || has_W[s] != 0;
+    const double cV = NsV > 0.0 ? lamV * 2.0 / (9.0 * NsV) : 0.0;
     for (int k = 0; k < 9; ++k) {
         double wb = 0.0;
         if (hw && NsV > 0.0) {
             const double dW = Wv[k] - W_ref[s * 9 + k];
-            aV += (dW / na) * (dW / na);
-            wb = lamV * 2.0 * dW / (na * na) / (9.0 * NsV);
+            aV += (dW * inv_na) * (dW * inv_na);
+            wb = cV * dW * inv_na2;
         }
         wbar[s * 9 + k] = (float)wb;
     }
