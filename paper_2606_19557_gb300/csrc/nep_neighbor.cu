@@ -271,22 +271,28 @@ __device__ __forceinline__ uint32_t pack_shift(int Sa, int Sb, int Sc) {
     return ((uint32_t)(Sa + 128) << 16) | ((uint32_t)(Sb + 128) << 8) | (uint32_t)(Sc + 128);
 }
 
-// Warp-cooperative candidate scan of atom i (one warp per atom).  Calls hit(j, Sa, Sb, Sc, r2)
-// for every pair within rcR, from any lane, in no particular order (the lists are sorted
-// afterwards).  Two ways to enumerate candidates, chosen per structure:
+// Warp-cooperative candidate scan of atom i (one warp per atom).  Calls hit(j, Sa, Sb, Sc, ang)
+// for every pair within rcR (ang: also within rcA), from any lane, in no particular order
+// (the lists are sorted afterwards).  Two ways to enumerate candidates, chosen per structure:
 //   * a structure held in one bin per axis (a cell narrower than 2 rc): the lanes take the
 //     structure's atoms j and each enumerates only the periodic images S that can lie
 //     within the cutoff of i, the box |d.b_a| <= rcq |b_a| around the nearest image
 //     (b_a the reciprocal vectors, so |d.b_a| <= |d| |b_a|);
 //   * otherwise the (2m+1)^3 neighbouring bins, the lanes taking the atoms of each bin.
-// Both apply the same float pre-filter and the exact predicate as the thread-per-atom scan.
+// Each candidate is first evaluated in FP32 with explicit rounding: q = (p_j - p_i) + S.h and
+// r2q = |q|^2.  Every FP32 step is within half an ulp, so |q_x - d_x| <= 7 2^-24 B_x with
+// B_x = |p_j,x| + |p_i,x| + sum_k |S_k h_k,x| (d the predicate's displacement); the band
+// uses 2^-20 B_x, more than twice that, and bounds |r2q - r2| by M (below).  Only a candidate
+// whose r2q lies within M of rc^2 (rcR or rcA) takes the exact FP64 predicate, so the
+// slow FP64 units see a tiny fraction of the candidates and every decision is the
+// predicate's.
 template <class Fn>
 __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float *pos, const float4 *pos4,
                                                const int *struct_of,
                                                const int64_t *atom_off, const SGeom *geom, const int64_t *bin_off,
                                                const int64_t *atom_bin, const int4 *atom_wrap,
                                                const int64_t *bin_start, const float4 *bin_pos, const int4 *bin_wrap,
-                                               float rc2R, float rcq2, float rcq, int *err, Fn hit) {
+                                               float rc2R, float rc2A, float rcq2, float rcq, int *err, Fn hit) {
     const int s = struct_of[i];
     const SGeom &g = geom[s];
     const float *pi = pos + 3 * i;
@@ -294,18 +300,40 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
                          (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
     auto test = [&](int j, int Sa, int Sb, int Sc, float4 pj4) {
         if (j == (int)i && Sa == 0 && Sb == 0 && Sc == 0) return;
-        const float qx = (pj4.x - pi[0]) + (Sa * hf[0] + Sb * hf[3] + Sc * hf[6]);
-        const float qy = (pj4.y - pi[1]) + (Sa * hf[1] + Sb * hf[4] + Sc * hf[7]);
-        const float qz = (pj4.z - pi[2]) + (Sa * hf[2] + Sb * hf[5] + Sc * hf[8]);
-        if (qx * qx + qy * qy + qz * qz > rcq2) return;
-        const float *pj = pos + 3 * j;
+        const float fa = (float)Sa, fb = (float)Sb, fc = (float)Sc;
+        float q[3], B[3];
+        const float pjv[3] = {pj4.x, pj4.y, pj4.z};
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            const float ta = __fmul_rn(fa, hf[x]), tb = __fmul_rn(fb, hf[3 + x]), tc = __fmul_rn(fc, hf[6 + x]);
+            q[x] = __fadd_rn(__fsub_rn(pjv[x], pi[x]), __fadd_rn(__fadd_rn(ta, tb), tc));
+            B[x] = fabsf(pjv[x]) + fabsf(pi[x]) + fabsf(ta) + fabsf(tb) + fabsf(tc);
+        }
+        const float r2q = __fadd_rn(__fadd_rn(__fmul_rn(q[0], q[0]), __fmul_rn(q[1], q[1])), __fmul_rn(q[2], q[2]));
+        if (r2q > rcq2) return;
         if (Sa < -SMAX || Sa > SMAX || Sb < -SMAX || Sb > SMAX || Sc < -SMAX || Sc > SMAX) {
             atomic_err(err, 2);
             return;
         }
-        float d32[3];
-        const float r2 = pair_d(pi, pj, g.h, Sa, Sb, Sc, d32);
-        if (r2 < rc2R) hit(j, Sa, Sb, Sc, r2);
+        constexpr float EPS = 9.5367431640625e-07f;  // 2^-20
+        float M = EPS * r2q;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            const float dx = EPS * B[x];
+            M += 2.0f * fabsf(q[x]) * dx + dx * dx;
+        }
+        const float lo = r2q - M, hi = r2q + M;
+        bool inR, inA;
+        if ((hi < rc2R || lo >= rc2R) && (hi < rc2A || lo >= rc2A)) {
+            inR = hi < rc2R;
+            inA = hi < rc2A;
+        } else {  // within the error band of a cutoff: the exact predicate
+            float d32[3];
+            const float r2 = pair_d(pi, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
+            inR = r2 < rc2R;
+            inA = r2 < rc2A;
+        }
+        if (inR) hit(j, Sa, Sb, Sc, inA);
     };
     if (g.n[0] == 1 && g.n[1] == 1 && g.n[2] == 1) {
         double R[3];  // rcq |b_a|
@@ -360,8 +388,8 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
     }
 }
 
-__device__ __forceinline__ uint64_t pair_key(float r2, float rc2A, int tj, int j, int Sa, int Sb, int Sc) {
-    const uint64_t grp = (r2 < rc2A) ? 0ull : 1ull;  // angular neighbours first
+__device__ __forceinline__ uint64_t pair_key(bool ang, int tj, int j, int Sa, int Sb, int Sc) {
+    const uint64_t grp = ang ? 0ull : 1ull;  // angular neighbours first
     return (grp << 63) | ((uint64_t)tj << 59) | ((uint64_t)j << 24) | (uint64_t)pack_shift(Sa, Sb, Sc);
 }
 
@@ -383,10 +411,10 @@ __global__ void k_count_w(int64_t na, const float *pos, const float4 *pos4, cons
     int nang = 0;
     uint64_t *dst = scratch + i * (int64_t)cap;
     scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_pos, bin_wrap,
-                   rc2R, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, float r2) {
+                   rc2R, rc2A, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, bool ang) {
                        const int k = atomicAdd(&slot[wib], 1);
-                       if (k < cap) dst[k] = pair_key(r2, rc2A, type[j], j, Sa, Sb, Sc);
-                       if (r2 < rc2A) ++nang;
+                       if (k < cap) dst[k] = pair_key(ang, type[j], j, Sa, Sb, Sc);
+                       if (ang) ++nang;
                    });
     nang = __reduce_add_sync(FULL, nang);
     __syncwarp();
@@ -413,9 +441,9 @@ __global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const
     __syncwarp();
     const int64_t o = nbr_off[i], n = nbr_off[i + 1] - o;
     scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_pos, bin_wrap,
-                   rc2R, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, float r2) {
+                   rc2R, rc2A, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, bool ang) {
                        const int k = atomicAdd(&slot[wib], 1);
-                       if (k < n) keys[o + k] = pair_key(r2, rc2A, type[j], j, Sa, Sb, Sc);
+                       if (k < n) keys[o + k] = pair_key(ang, type[j], j, Sa, Sb, Sc);
                    });
     __syncwarp();
     if (lane == 0 && slot[wib] != n) atomic_err(err, 5);
