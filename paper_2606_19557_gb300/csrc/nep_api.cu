@@ -752,8 +752,11 @@ int nep_minibatch_setup(nep_ctx *c, int batch_size, int64_t *n_batches) {
     if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures (call nep_set_structures)");
     if (batch_size < 1) return c->fail(NEP_EINVAL, "batch size must be >= 1");
     CK(cudaSetDevice(c->dev));
+    c->mb_var[0] = c->mb_var[1] = -1;
     int rc = build_minibatches(c, batch_size);
     if (rc) return rc;
+    if ((rc = minibatch_tune(c))) return rc;
+    c->state_valid = false;
     if (n_batches) *n_batches = (int64_t)c->mb.size();
     return NEP_OK;
 }

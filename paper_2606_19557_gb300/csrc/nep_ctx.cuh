@@ -150,6 +150,8 @@ struct Ctx {
         int n_ck;
     };
     int mb_B = 0;
+    int mb_var[2] = {-1, -1};  // forward / adjoint variants of the groups (-1: the batch's own)
+    int mb_used[4] = {0, 0, 0, 0};  // variants and warps per block the schedules use
     int mb_key[6] = {-1, -1, -1, -1, -1, -1};  // launch shapes the schedules were built for
     std::vector<MiniBatch> mb;
     DevBuf mb_work, mb_wbf, mb_wba, mb_wlo, mb_whi, mb_chunks, mb_clo, mb_chi;
@@ -207,8 +209,8 @@ int build_neighbors(Ctx *c);
 int launch_expand(Ctx *c);
 int launch_forward(Ctx *c, float *q_raw);
 // explicit schedules (mini-batch mode)
-int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks);
-int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks);
+int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb);
+int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb);
 int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks);
 int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi, const int *wlo, const int *whi,
                             const int *warp_begin);
@@ -239,6 +241,7 @@ int launch_opt_epoch(Ctx *c);
 // mini-batch mode (nep_minibatch.cu)
 int build_minibatches(Ctx *c, int batch_size);
 int minibatch_shape_check(Ctx *c);  // rebuilds the schedules if the launch shape changed
+int minibatch_tune(Ctx *c);         // picks the kernel variants of the group steps by timing
 void drop_minibatch_graphs(Ctx *c);
 int run_minibatch_loss(Ctx *c, int64_t m, double lE, double lF, double lV, double *loss3, float *grad);
 int prepare_loss_kernels(Ctx *c);

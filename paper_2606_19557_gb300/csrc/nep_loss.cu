@@ -621,24 +621,24 @@ int launch_adjoint(Ctx *c) {
     return NEP_OK;
 }
 
-int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks) {
+int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb) {
     if (blocks <= 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.work = work;
     a.warp_begin = warp_begin;
-    const size_t smem = c->ks->fwd_smem[c->fwd.var](c->T, c->NN) * c->fwd.wpb;
-    c->ks->launch_fwd[c->fwd.var](a, blocks, c->fwd.wpb, smem, c->stream);
+    const size_t smem = c->ks->fwd_smem[var](c->T, c->NN) * wpb;
+    c->ks->launch_fwd[var](a, blocks, wpb, smem, c->stream);
     CK_LAUNCH("k_forward");
     return NEP_OK;
 }
 
-int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks) {
+int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb) {
     if (blocks <= 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.work = work;
     a.warp_begin = warp_begin;
-    const size_t smem = c->ks->adj_smem[c->adj.var](c->T, c->NN) * c->adj.wpb;
-    c->ks->launch_adj[c->adj.var](a, blocks, c->adj.wpb, smem, c->stream);
+    const size_t smem = c->ks->adj_smem[var](c->T, c->NN) * wpb;
+    c->ks->launch_adj[var](a, blocks, wpb, smem, c->stream);
     CK_LAUNCH("k_adjoint");
     return NEP_OK;
 }

@@ -67,6 +67,25 @@ void shape_key(const Ctx *c, int *key) {
     key[3] = c->adj.var;
     key[4] = c->adj.wpb;
     key[5] = c->adj.W;
+    key[0] += 16 * (c->mb_var[0] + 1);  // the group variants, when set, change the schedules too
+    key[3] += 16 * (c->mb_var[1] + 1);
+}
+
+// Variant and warps per block of the group launches: the chosen group variant with the
+// largest block its launch bounds allow, else the batch's own shape.
+void group_launch(const Ctx *c, int which, int &var, int &wpb, int &wcap) {
+    const Sched &s = which == 0 ? c->fwd : c->adj;
+    const int v = c->mb_var[which];
+    if (v < 0) {
+        var = s.var;
+        wpb = s.wpb;
+        wcap = s.W;
+    } else {
+        var = v;
+        wpb = c->ks->max_wpb[v];
+        // adjoint warps write per-warp gradient slots sized for the batch's adjoint grid
+        wcap = which == 0 ? c->n_sm * 16 : c->adj.W / wpb * wpb;
+    }
 }
 
 }  // namespace
@@ -88,7 +107,10 @@ int build_minibatches(Ctx *c, int B) {
     drop_minibatch_graphs(c);  // the graphs hold the old schedules
     const int64_t ns = c->n_struct, na = c->n_atoms;
     const int T = c->T;
-    const int gf = 32 / c->ks->sw[c->fwd.var], ga = 32 / c->ks->sw[c->adj.var];
+    int fvar, fwpb, fcap, avar, awpb, acap;
+    group_launch(c, 0, fvar, fwpb, fcap);
+    group_launch(c, 1, avar, awpb, acap);
+    const int gf = 32 / c->ks->sw[fvar], ga = 32 / c->ks->sw[avar];
     const int CH = 128;  // work positions per network-gradient chunk
     std::vector<int> work(na);
     std::vector<int> wbf, wba, wlo, whi, chunks, clo, chi;
@@ -113,13 +135,13 @@ int build_minibatches(Ctx *c, int B) {
             pre[k + 1] = pre[k] + (double)(c->h_nbr_off[i + 1] - c->h_nbr_off[i]) + 6.0 * c->h_nang[i] + 8.0;
         }
         // warps: one batch of atoms each for a small group, at most the full persistent grid
-        auto warps = [&](int g, const Sched &s) {
+        auto warps = [&](int g, int wpb, int cap) {
             int W = std::max(1, (n + g - 1) / g);
-            W = std::min(W, s.W);
-            return (W + s.wpb - 1) / s.wpb * s.wpb;
+            W = std::min(W, cap);
+            return (W + wpb - 1) / wpb * wpb;
         };
-        m.Wf = warps(gf, c->fwd);
-        m.Wa = warps(ga, c->adj);
+        m.Wf = warps(gf, fwpb, fcap);
+        m.Wa = warps(ga, awpb, acap);
         const std::vector<int> bf = split_warps(pre, p0, m.Wf), ba = split_warps(pre, p0, m.Wa);
         m.wf_off = (int64_t)wbf.size();
         wbf.insert(wbf.end(), bf.begin(), bf.end());
@@ -161,8 +183,51 @@ int build_minibatches(Ctx *c, int B) {
     CK(up(c->mb_chi, chi));
     c->mb = std::move(mbs);
     c->mb_B = B;
+    c->mb_used[0] = fvar;
+    c->mb_used[1] = fwpb;
+    c->mb_used[2] = avar;
+    c->mb_used[3] = awpb;
     shape_key(c, c->mb_key);
     return NEP_OK;
+}
+
+// Small groups leave most of the GPU idle, and the fastest kernel variant is then often not
+// the batch's one (16 lanes per atom halve the atoms, so the latency, of a warp's batch):
+// time a loss + gradient pass over the first groups for a few variant pairs, keep the
+// fastest.  Needs parameters and targets; otherwise the batch's own variants stay.
+int minibatch_tune(Ctx *c) {
+    if (!c->have_targets || !c->have_params || c->mb.empty()) return NEP_OK;
+    const int cand[][2] = {{-1, -1}, {2, 2}, {3, 2}, {3, 3}, {0, 0}};
+    const int ng = (int)std::min<size_t>(8, c->mb.size());
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bi = 0, rc = NEP_OK;
+    for (int k = 0; k < 5 && !rc; ++k) {
+        c->mb_var[0] = cand[k][0];
+        c->mb_var[1] = cand[k][1];
+        if ((rc = build_minibatches(c, c->mb_B))) break;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && !rc; ++rep) {  // the first repetition warms up
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess) rc = c->fail(NEP_ECUDA, "event record");
+            for (int m = 0; m < ng && !rc; ++m)
+                rc = run_minibatch_loss(c, m, 1.0, 1.0, 0.1, c->loss3_int.as<double>(), c->grad_int.as<float>());
+            if (!rc && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = c->fail(NEP_ECUDA, "event timing");
+        }
+        if (!rc && ms < best) {
+            best = ms;
+            bi = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    c->mb_var[0] = cand[bi][0];
+    c->mb_var[1] = cand[bi][1];
+    return build_minibatches(c, c->mb_B);
 }
 
 // Loss and gradient of group m against the references of nep_set_targets.
@@ -180,7 +245,8 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
     int rc = NEP_OK;
     do {
         if ((rc = launch_expand(c))) break;
-        if ((rc = launch_forward_sched(c, c->mb_work.as<int>(), c->mb_wbf.as<int>() + m.wf_off, m.Wf / c->fwd.wpb)))
+        if ((rc = launch_forward_sched(c, c->mb_work.as<int>(), c->mb_wbf.as<int>() + m.wf_off, m.Wf / c->mb_used[1],
+                                       c->mb_used[0], c->mb_used[1])))
             break;
         if ((rc = launch_count_hasw(c, hw, m.s0, m.s1))) break;
         if ((rc = launch_gather(c, c->F_int.as<float>(), c->tgt_F.as<float>(), lF, true, m.a0, m.a1))) break;
@@ -188,7 +254,8 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
                                 c->tgt_W.as<double>(), hw, lE, lV, true, m.s0, m.s1)))
             break;
         if ((rc = launch_loss_final(c, loss3))) break;
-        if ((rc = launch_adjoint_sched(c, c->mb_work.as<int>(), c->mb_wba.as<int>() + m.wa_off, m.Wa / c->adj.wpb)))
+        if ((rc = launch_adjoint_sched(c, c->mb_work.as<int>(), c->mb_wba.as<int>() + m.wa_off, m.Wa / c->mb_used[3],
+                                       c->mb_used[2], c->mb_used[3])))
             break;
         if ((rc = launch_ann_grad_chunks(c, c->mb_chunks.as<int>() + m.ck_off, m.n_ck))) break;
         rc = launch_grad_final_sched(c, grad, c->mb_clo.as<int>() + mi * T, c->mb_chi.as<int>() + mi * T,
