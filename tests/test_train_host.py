@@ -1,6 +1,6 @@
 """Host-side sequencing of the two-stage protocol (paper_2606_19557_gb300.train), on CPU:
 a stand-in context records the calls and keeps its schedule with the oracle's plateau
-rule, so the driver's stage starts, epoch boundaries and log are checked without a GPU."""
+rule, so the protocol's stage starts, epoch boundaries and log are checked without a GPU."""
 import math
 
 import pytest
