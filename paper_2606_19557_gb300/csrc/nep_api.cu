@@ -135,12 +135,17 @@ static int default_shapes(Ctx *c) {
     int rc = set_smem_attr(c);
     if (rc) return rc;
     if ((rc = prepare_loss_kernels(c))) return rc;
-    const int wpb = 4, v = 3;  // 16 lanes per atom, 128 registers, 4 warps per block
-    int bf = max_blocks_per_sm(c, c->ks->fwd_fn[v], wpb, c->ks->fwd_smem[v](c->T, c->NN) * wpb);
-    int ba = max_blocks_per_sm(c, c->ks->adj_fn[v], wpb, c->ks->adj_smem[v](c->T, c->NN) * wpb);
+    // 16 lanes per atom, 128 registers; 4 warps per block, fewer when a large model's
+    // shared-memory tail (it grows with the species count) does not fit
+    const int v = 3;
+    int wf = 0, wa = 0, bf = 0, ba = 0;
+    for (int w = 4; w >= 1 && bf < 1; w /= 2)
+        if ((bf = max_blocks_per_sm(c, c->ks->fwd_fn[v], w, c->ks->fwd_smem[v](c->T, c->NN) * w)) >= 1) wf = w;
+    for (int w = 4; w >= 1 && ba < 1; w /= 2)
+        if ((ba = max_blocks_per_sm(c, c->ks->adj_fn[v], w, c->ks->adj_smem[v](c->T, c->NN) * w)) >= 1) wa = w;
     if (bf < 1 || ba < 1) return c->fail(NEP_EINVAL, "kernel does not fit on the device (shared memory)");
-    if ((rc = make_sched(c, c->fwd, wpb, c->n_sm * bf, v))) return rc;
-    if ((rc = make_sched(c, c->adj, wpb, c->n_sm * ba, v))) return rc;
+    if ((rc = make_sched(c, c->fwd, wf, c->n_sm * bf, v))) return rc;
+    if ((rc = make_sched(c, c->adj, wa, c->n_sm * ba, v))) return rc;
     return alloc_sched_buffers(c);
 }
 

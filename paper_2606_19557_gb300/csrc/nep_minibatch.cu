@@ -82,7 +82,18 @@ void group_launch(const Ctx *c, int which, int &var, int &wpb, int &wcap) {
         wcap = s.W;
     } else {
         var = v;
-        wpb = c->ks->max_wpb[v];
+        // the largest block the launch bounds allow that fits the shared-memory budget
+        const void *fn = which == 0 ? c->ks->fwd_fn[v] : c->ks->adj_fn[v];
+        wpb = 1;
+        for (int w = c->ks->max_wpb[v]; w >= 1; w /= 2) {
+            const size_t sm = (which == 0 ? c->ks->fwd_smem[v] : c->ks->adj_smem[v])(c->T, c->NN) * w;
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, w * 32, sm) != cudaSuccess) cudaGetLastError();
+            if (nb >= 1) {
+                wpb = w;
+                break;
+            }
+        }
         // adjoint warps write per-warp gradient slots sized for the batch's adjoint grid
         wcap = which == 0 ? c->n_sm * 16 : c->adj.W / wpb * wpb;
     }
@@ -209,15 +220,21 @@ int minibatch_tune(Ctx *c) {
         c->mb_var[1] = cand[k][1];
         if ((rc = build_minibatches(c, c->mb_B))) break;
         float ms = 0.0f;
-        for (int rep = 0; rep < 2 && !rc; ++rep) {  // the first repetition warms up
-            if (cudaEventRecord(e0, c->stream) != cudaSuccess) rc = c->fail(NEP_ECUDA, "event record");
-            for (int m = 0; m < ng && !rc; ++m)
-                rc = run_minibatch_loss(c, m, 1.0, 1.0, 0.1, c->loss3_int.as<double>(), c->grad_int.as<float>());
-            if (!rc && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                rc = c->fail(NEP_ECUDA, "event timing");
+        int trc = NEP_OK;  // a candidate that cannot launch (too large a model) is skipped
+        for (int rep = 0; rep < 2 && !trc; ++rep) {  // the first repetition warms up
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess) trc = NEP_ECUDA;
+            for (int m = 0; m < ng && !trc; ++m)
+                trc = run_minibatch_loss(c, m, 1.0, 1.0, 0.1, c->loss3_int.as<double>(), c->grad_int.as<float>());
+            if (!trc && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                trc = NEP_ECUDA;
         }
-        if (!rc && ms < best) {
+        if (trc) {
+            cudaStreamSynchronize(c->stream);
+            cudaGetLastError();
+            continue;
+        }
+        if (ms < best) {
             best = ms;
             bi = k;
         }

@@ -239,6 +239,10 @@ SPECS = {
     "scale_t5": ModelSpec(5, 6.0, 4.0, 6, 6, 10, 10, 4, 1, 1, 50),
     # Table 1 carbon input: cutoff 4.2 3.7, n_max 10 8, basis 10 8, l_max 4 2 1, 100 neurons
     "carbon_table1": ModelSpec(1, 4.2, 3.7, 10, 8, 10, 8, 4, 1, 1, 100),
+    # Table 2 16-element models NEP44 / NEP88 (70,401 / 124,673 parameters); the cutoffs are
+    # not printed with them, 6 / 4 A as in the other configurations
+    "nep44_t16": ModelSpec(16, 6.0, 4.0, 4, 4, 8, 8, 4, 1, 1, 80),
+    "nep88_t16": ModelSpec(16, 6.0, 4.0, 8, 8, 8, 8, 4, 1, 1, 80),
 }
 
 

@@ -367,3 +367,30 @@ def test_update_positions_matches_fresh_context():
     l3o, go = oracle.loss_grad(spec, theta, qs, b2, Er, Fr, Wr)[:2]
     np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
     assert rel(g.cpu().numpy(), go) < TOL
+
+
+@pytest.mark.parametrize("name", ["nep44_t16", "nep88_t16"])
+def test_table2_sixteen_species_models(name):
+    """The paper's 16-element models (Table 2 sizes; 80 neurons, 4- and 5-body terms) on a
+    16-species alloy batch: E/F/W, loss and gradient against the oracle."""
+    from paper_2606_19557_gb300 import NEP
+    spec = synth.SPECS[name]
+    b = synth.batch_alloy(seed=61, n_struct=6, n_types=16, n_lo=24, n_hi=90)
+    P = oracle.num_params(spec)
+    theta = synth.random_theta(P, 61)
+    qs = f32(oracle.scale_from_range(oracle.descriptors(spec, theta, b)))
+    nep = NEP(spec)
+    nep.set_structures_batch(b)
+    nep.set_params(torch.tensor(theta, dtype=torch.float32), torch.tensor(qs, dtype=torch.float32))
+    E, F, W = [x.cpu().numpy() for x in nep.eval()]
+    Eo, Fo, Wo = oracle.evaluate(spec, theta, qs, b)
+    assert rel(E, Eo) < TOL and rel(F, Fo) < TOL and rel(W, Wo) < TOL
+    Er, Fr, Wr = synth.random_targets(b, 62)
+    lam = (1.0, 2.0, 0.3)
+    l3, g = nep.loss_grad(Er, Fr, Wr, None, lam)
+    l3o, go = oracle.loss_grad(spec, theta, qs, b, Er, Fr, Wr, None, lam)[:2]
+    np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
+    assert rel(g.cpu().numpy(), go) < TOL
+    nep.autotune()  # every variant that fits the 16-species shared-memory tail
+    g2 = nep.loss_grad(Er, Fr, Wr, None, lam)[1].cpu().numpy()
+    assert rel(g2, go) < TOL
