@@ -149,11 +149,47 @@ def cpu_baseline(spec, batch, n_sample: int):
     t0 = time.perf_counter()
     loss3, grad, E, F, W = oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
     dt = time.perf_counter() - t0
-    cb = {"value": sample.n_atoms / dt, "unit": "atoms/s", "cores": oracle.threads(), "kind": "oracle",
-          "sample": f"first {sample.n_struct} structures ({sample.n_atoms} atoms), one loss+grad pass, {dt:.1f} s"}
+    cores = oracle.threads()
+    cb = {"value": sample.n_atoms / dt, "unit": "atoms/s", "cores": cores, "kind": "oracle",
+          "sample": f"first {sample.n_struct} structures ({sample.n_atoms} atoms), one loss+grad pass, {dt:.1f} s",
+          "cpu_model": _cpu_model()}
+    # the same oracle on one core, on a smaller sample
+    small = batch.subset(range(min(max(1, n_sample // 8), batch.n_struct)))
+    Es, Fs, Ws = synth.random_targets(small, 3)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.loss_grad(spec, theta, qs, small, Es, Fs, Ws, None, LAM)
+        d1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(0)
+    cb["single_core"] = {"value": small.n_atoms / d1, "unit": "atoms/s",
+                         "sample": f"first {small.n_struct} structures ({small.n_atoms} atoms), {d1:.1f} s"}
     ref = {"sample": sample, "theta": theta, "qs": qs, "targets": (Er, Fr, Wr),
            "out": {"loss3": loss3, "grad": grad, "E": E, "F": F, "W": W}}
     return cb, ref
+
+
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "Model name", "CPU part"):
+            for line in txt.splitlines():
+                if line.startswith(key):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def errors_vs_oracle(spec, ref, device: int):

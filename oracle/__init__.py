@@ -105,6 +105,14 @@ def threads() -> int:
     return int(_load().orc_threads())
 
 
+def set_threads(n: int) -> None:
+    """Threads for the following calls; n <= 0 restores one per host core."""
+    lib = _load()
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
+    lib.orc_set_threads.restype = None
+    lib.orc_set_threads(int(n))
+
+
 def num_params(spec) -> int:
     return int(_load().orc_num_params(ctypes.byref(_cfg(spec))))
 

@@ -714,6 +714,16 @@ static int threads_used(void) {
 }
 int orc_threads(void) { return threads_used(); }
 
+/* Threads for the following calls (timing single-core against all-core); n <= 0 restores
+ * one per host core.  Changes no arithmetic. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
 /* E [Ns], F [Na*3], W [Ns*9], q [Na*ND] (optional) at theta (FP64). */
 int orc_eval(const orc_cfg *cfg, const double *theta, const double *qscale, int64_t n_struct,
              const int64_t *atom_off, const double *pos, const int32_t *type, const double *cell,
