@@ -125,9 +125,24 @@ def test_neighbor_edge_geometries():
     off = np.cumsum([0] + [p.shape[0] for p, _ in structs])
     batch = synth.Batch(off.astype(np.int64), np.concatenate([p for p, _ in structs]).astype(np.float32),
                         np.zeros(off[-1], np.int32), np.stack([c.reshape(9) for _, c in structs]).astype(np.float32), 1)
-    nep = NEP(synth.SPECS["fcc_bcc_t1"])
+    spec = synth.SPECS["fcc_bcc_t1"]
+    nep = NEP(spec)
     nep.set_structures_batch(batch)
     _check_neighbors(nep, batch, 6.0, 4.0)
+    # the degenerate environments (no neighbour at all, one neighbour, self images only)
+    # through the whole pass
+    P = oracle.num_params(spec)
+    theta = synth.random_theta(P, 70)
+    qs = f32(oracle.scale_from_range(oracle.descriptors(spec, theta, batch)))
+    nep.set_params(torch.tensor(theta, dtype=torch.float32), torch.tensor(qs, dtype=torch.float32))
+    E, F, W = [x.cpu().numpy() for x in nep.eval()]
+    Eo, Fo, Wo = oracle.evaluate(spec, theta, qs, batch)
+    assert rel(E, Eo) < TOL and rel(F, Fo) < TOL and rel(W, Wo) < TOL
+    Er, Fr, Wr = synth.random_targets(batch, 71)
+    l3, g = nep.loss_grad(Er, Fr, Wr, None, (1.0, 2.0, 0.3))
+    l3o, go = oracle.loss_grad(spec, theta, qs, batch, Er, Fr, Wr, None, (1.0, 2.0, 0.3))[:2]
+    np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
+    assert rel(g.cpu().numpy(), go) < TOL
 
 
 # ----------------------------------------------------------------------------- forward
