@@ -409,3 +409,41 @@ def test_table2_sixteen_species_models(name):
     nep.autotune()  # every variant that fits the 16-species shared-memory tail
     g2 = nep.loss_grad(Er, Fr, Wr, None, lam)[1].cpu().numpy()
     assert rel(g2, go) < TOL
+
+
+
+MODEL_VARIANTS = {
+    # largest model the kernels take: n_max = basis = 11, l_max 4 with 4- and 5-body, 128 neurons
+    "maximum": (synth.ModelSpec(3, 6.0, 4.5, 11, 11, 11, 11, 4, 1, 1, 128), 3),
+    # smallest: one radial and one angular function of one basis term, l_max 0, one neuron
+    "minimum": (synth.ModelSpec(2, 5.0, 4.0, 0, 0, 0, 0, 0, 0, 0, 1), 2),
+    # l_max 1 with the 5-body term only
+    "l1_5body": (synth.ModelSpec(2, 5.5, 4.0, 3, 2, 5, 4, 1, 0, 1, 16), 2),
+    # l_max 2 with the 4-body term, angular cutoff equal to the radial one
+    "l2_4body_equal_cutoffs": (synth.ModelSpec(2, 5.0, 5.0, 5, 3, 6, 5, 2, 1, 0, 20), 2),
+}
+
+
+@pytest.mark.parametrize("name", list(MODEL_VARIANTS))
+def test_model_variants(name):
+    """Corners of the model limits (n_max, basis_size, l_max, 4-/5-body flags, neurons,
+    r_c^A = r_c^R) through E/F/W, the loss and the gradient."""
+    from paper_2606_19557_gb300 import NEP
+    spec, T = MODEL_VARIANTS[name]
+    b = synth.batch_alloy(seed=81, n_struct=5, n_types=T, n_lo=20, n_hi=70)
+    P = oracle.num_params(spec)
+    theta = synth.random_theta(P, 81)
+    qs = f32(oracle.scale_from_range(oracle.descriptors(spec, theta, b)))
+    nep = NEP(spec)
+    nep.set_structures_batch(b)
+    _check_neighbors(nep, b, spec.rc_R, spec.rc_A)
+    nep.set_params(torch.tensor(theta, dtype=torch.float32), torch.tensor(qs, dtype=torch.float32))
+    E, F, W = [x.cpu().numpy() for x in nep.eval()]
+    Eo, Fo, Wo = oracle.evaluate(spec, theta, qs, b)
+    assert rel(E, Eo) < TOL and rel(F, Fo) < TOL and rel(W, Wo) < TOL
+    Er, Fr, Wr = synth.random_targets(b, 82)
+    l3, g = nep.loss_grad(Er, Fr, Wr, None, (1.0, 1.0, 0.1))
+    l3o, go = oracle.loss_grad(spec, theta, qs, b, Er, Fr, Wr, None, (1.0, 1.0, 0.1))[:2]
+    np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
+    assert rel(g.cpu().numpy(), go) < TOL
+    nep.close()
