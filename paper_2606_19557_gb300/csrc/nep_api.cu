@@ -51,6 +51,8 @@ static int check_cfg(const nep_config *c, std::string &why) {
 // Static schedule of one per-atom kernel: contiguous ranges of the species-sorted work
 // order with about equal cost per warp (cost ~ radial pairs + 6 x angular pairs + 8).
 static int make_sched(Ctx *c, Sched &s, int wpb, int blocks, int var) {
+    int rc = fetch_host_lists(c);
+    if (rc) return rc;
     s.var = var;
     s.wpb = wpb;
     s.blocks = blocks;
@@ -74,8 +76,7 @@ static int make_sched(Ctx *c, Sched &s, int wpb, int blocks, int var) {
         begin[s.W] = (int)na;
         for (int w = 1; w <= s.W; ++w) begin[w] = std::max(begin[w], begin[w - 1]);
     }
-    s.h_wlo.assign(c->T, 0);
-    s.h_whi.assign(c->T, -1);
+    std::vector<int> wlo(c->T, 0), whi(c->T, -1);
     for (int t = 0; t < c->T; ++t) {
         const int p0 = c->type_begin[t], p1 = c->type_begin[t + 1];
         if (p1 <= p0) continue;
@@ -89,14 +90,101 @@ static int make_sched(Ctx *c, Sched &s, int wpb, int blocks, int var) {
             }
             return lo;
         };
-        s.h_wlo[t] = owner(p0);
-        s.h_whi[t] = owner(p1 - 1);
+        wlo[t] = owner(p0);
+        whi[t] = owner(p1 - 1);
     }
     if (s.warp_begin.ensure<int>(s.W + 1) || s.type_wlo.ensure<int>(c->T) || s.type_whi.ensure<int>(c->T))
         return c->fail(NEP_ENOMEM, "schedule buffers");
     CK(cudaMemcpy(s.warp_begin.ptr, begin.data(), sizeof(int) * (s.W + 1), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(s.type_wlo.ptr, s.h_wlo.data(), sizeof(int) * c->T, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(s.type_whi.ptr, s.h_whi.data(), sizeof(int) * c->T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.type_wlo.ptr, wlo.data(), sizeof(int) * c->T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.type_whi.ptr, whi.data(), sizeof(int) * c->T, cudaMemcpyHostToDevice));
+    return NEP_OK;
+}
+
+// The same schedules built on the device from the current lists, without copying them to
+// the host (used when only the positions changed).  The costs are integers, so their
+// prefix is exact in int64 and in the host's doubles alike (below 2^53); the split targets
+// take the same double operations, so the warp ranges equal those of make_sched.
+namespace {
+__global__ void k_sched_cost(int64_t na, const int *work, const int64_t *nbr_off, const int *n_ang, int64_t *cost) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= na) return;
+    const int i = work[q];
+    cost[q] = (nbr_off[i + 1] - nbr_off[i]) + 6 * (int64_t)n_ang[i] + 8;
+}
+
+// begin[w] = first work position q with pre[q] >= tot * w / W (na if none); begin[W] = na
+__global__ void k_sched_split(int64_t na, const int64_t *pre, int W, int *begin) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w > W) return;
+    if (w == W) {
+        begin[W] = (int)na;
+        return;
+    }
+    const double target = (double)pre[na] * (double)w / (double)W;
+    int64_t lo = 0, hi = na;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if ((double)pre[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    begin[w] = (int)lo;
+}
+
+struct TypeRanges {
+    int begin[TMAX + 1];  // work positions of each species
+};
+
+// first / last warp holding each species: the last w with begin[w] <= p
+__global__ void k_sched_types(int T, TypeRanges tr, const int *begin, int W, int *wlo, int *whi) {
+    const int t = threadIdx.x;
+    if (t >= T) return;
+    const int p0 = tr.begin[t], p1 = tr.begin[t + 1];
+    if (p1 <= p0) {
+        wlo[t] = 0;
+        whi[t] = -1;
+        return;
+    }
+    auto owner = [&](int p) {
+        int lo = 0, hi = W - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (begin[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    wlo[t] = owner(p0);
+    whi[t] = owner(p1 - 1);
+}
+}  // namespace
+
+static int make_scheds_device(Ctx *c) {
+    const int64_t na = c->n_atoms;
+    if (na == 0 || c->T > TMAX) {
+        int rc = make_sched(c, c->fwd, c->fwd.wpb, c->fwd.blocks, c->fwd.var);
+        return rc ? rc : make_sched(c, c->adj, c->adj.wpb, c->adj.blocks, c->adj.var);
+    }
+    if (c->sched_cost.ensure<int64_t>(na + 1) || c->sched_pre.ensure<int64_t>(na + 1))
+        return c->fail(NEP_ENOMEM, "schedule workspace");
+    const cudaStream_t st = c->stream;
+    k_sched_cost<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(na, c->work.as<int>(), c->nbr_off.as<int64_t>(),
+                                                              c->n_ang.as<int>(), c->sched_cost.as<int64_t>());
+    CK(cudaGetLastError());
+    int rc = scan_exclusive(c, c->sched_cost.as<int64_t>(), na, c->sched_pre.as<int64_t>(), c->d_total.as<int64_t>() + 2);
+    if (rc) return rc;
+    TypeRanges tr{};
+    for (int t = 0; t <= c->T; ++t) tr.begin[t] = c->type_begin[t];
+    for (Sched *s : {&c->fwd, &c->adj}) {
+        s->W = s->wpb * s->blocks;
+        if (s->warp_begin.ensure<int>(s->W + 1) || s->type_wlo.ensure<int>(c->T) || s->type_whi.ensure<int>(c->T))
+            return c->fail(NEP_ENOMEM, "schedule buffers");
+        k_sched_split<<<(unsigned)((s->W + 256) / 256), 256, 0, st>>>(na, c->sched_pre.as<int64_t>(), s->W,
+                                                                       s->warp_begin.as<int>());
+        k_sched_types<<<1, 32, 0, st>>>(c->T, tr, s->warp_begin.as<int>(), s->W, s->type_wlo.as<int>(),
+                                        s->type_whi.as<int>());
+        CK(cudaGetLastError());
+    }
     return NEP_OK;
 }
 
@@ -443,14 +531,20 @@ int nep_update_positions(nep_ctx *c, const float *pos, const float *cell) {
         CK(cudaMemcpyAsync(c->cell.ptr, cell, sizeof(float) * 9 * c->n_struct, cudaMemcpyDeviceToDevice, c->stream));
     c->have_batch = false;  // until the lists are rebuilt
     c->state_valid = false;
-    int rc = build_neighbors(c);
+    // the mini-batch schedules are built on the host from host copies of the lists
+    const bool host_lists = c->mb_B > 0;
+    int rc = build_neighbors(c, cell == nullptr, host_lists);
     if (rc) return rc;
     if (c->G.ensure_bytes(sizeof(float4) * (size_t)(c->n_pairs + 1))) return c->fail(NEP_ENOMEM, "pair gradients");
     // re-balance the kernel schedules for the new neighbour counts (same sizes, same
     // buffers): the result is then the one a fresh context computes, bit for bit
-    if ((rc = make_sched(c, c->fwd, c->fwd.wpb, c->fwd.blocks, c->fwd.var))) return rc;
-    if ((rc = make_sched(c, c->adj, c->adj.wpb, c->adj.blocks, c->adj.var))) return rc;
-    if (c->mb_B > 0 && (rc = build_minibatches(c, c->mb_B))) return rc;
+    if (host_lists) {
+        if ((rc = make_sched(c, c->fwd, c->fwd.wpb, c->fwd.blocks, c->fwd.var))) return rc;
+        if ((rc = make_sched(c, c->adj, c->adj.wpb, c->adj.blocks, c->adj.var))) return rc;
+        if ((rc = build_minibatches(c, c->mb_B))) return rc;
+    } else if ((rc = make_scheds_device(c))) {
+        return rc;
+    }
     const void *after[5] = {c->pair.ptr, c->rev.ptr, c->G.ptr, c->nbr_off.ptr, c->n_ang.ptr};
     if (!std::equal(before, before + 5, after)) drop_graphs(c);  // graphs hold the old addresses
     c->plain_ready = false;

@@ -52,7 +52,6 @@ struct Sched {
     int W = 0;           // total warps
     DevBuf warp_begin;   // [W+1]
     DevBuf type_wlo, type_whi;  // [T] first / last warp holding each species (adjoint slots)
-    std::vector<int> h_wlo, h_whi;
 };
 
 constexpr int NVAR = 4;
@@ -105,17 +104,21 @@ struct Ctx {
     DevBuf atom_off, pos, type, cell, struct_of;
     std::vector<int64_t> h_atom_off, h_nbr_off;
     std::vector<int> h_type, h_nang;
+    bool h_lists_ok = false;  // h_nbr_off / h_nang hold the current lists (fetch_host_lists)
 
     // neighbour build
     DevBuf geom, nbins, bin_off, bin_cnt, bin_start, bin_cur, atom_bin, atom_wrap, bin_atoms, cnt, n_ang, nbr_off;
     DevBuf keys_tmp, keys, pair, rev, shift, scan_tmp, d_total, d_err;
     DevBuf pos4, nbr_scratch, d_flag;  // float4 positions, per-atom key scratch, overflow flag
     DevBuf bin_pos, bin_wrap;          // atoms in bin order: (x, y, z, bits(j)) and wrap offsets
+    int64_t nbin_total = 0;            // bins of the current cells
+    bool geom_ok = false;              // geom / nbins / bin_off / struct_of hold the current cells
 
     // schedule
     DevBuf work;                 // [Na] atom per work position (species-sorted)
     std::vector<int> h_work, type_begin;  // type_begin [T+1] work positions
     Sched fwd, adj;
+    DevBuf sched_cost, sched_pre;  // [Na + 1] work cost per position and its exclusive prefix
     // network-gradient contraction chunks
     int n_chunks = 0;
     DevBuf chunk_begin, chunk_type, type_clo, type_chi;
@@ -203,7 +206,10 @@ struct Ctx {
     } while (0)
 
 int scan_exclusive(Ctx *c, const int64_t *in, int64_t n, int64_t *out, int64_t *total_dev);
-int build_neighbors(Ctx *c);
+// same_cells: the cells are those of the previous successful build (geometry kept);
+// host_lists: copy the per-atom counts and offsets to h_nang / h_nbr_off.
+int build_neighbors(Ctx *c, bool same_cells = false, bool host_lists = true);
+int fetch_host_lists(Ctx *c);
 
 // step pieces (nep_loss.cu)
 int launch_expand(Ctx *c);

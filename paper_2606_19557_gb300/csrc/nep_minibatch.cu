@@ -116,6 +116,7 @@ int minibatch_shape_check(Ctx *c) {
 
 int build_minibatches(Ctx *c, int B) {
     drop_minibatch_graphs(c);  // the graphs hold the old schedules
+    if (int rc = fetch_host_lists(c)) return rc;
     const int64_t ns = c->n_struct, na = c->n_atoms;
     const int T = c->T;
     int fvar, fwpb, fcap, avar, awpb, acap;

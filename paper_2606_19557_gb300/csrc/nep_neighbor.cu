@@ -515,9 +515,18 @@ __global__ void k_reverse(int64_t na, const int64_t *nbr_off, const uint64_t *ke
     }
 }
 
+// out += sum of v[0..n) (integer atomics: the total does not depend on the order)
+__global__ void k_sum_int(int64_t n, const int *v, int64_t *out) {
+    long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += v[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0) atomicAdd((unsigned long long *)out, (unsigned long long)s);
+}
+
 }  // namespace
 
-int build_neighbors(Ctx *c) {
+int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
     const int64_t ns = c->n_struct, na = c->n_atoms;
     const cudaStream_t st = c->stream;
     const float rcR = c->cfg.rc_R, rcA = c->cfg.rc_A;
@@ -526,23 +535,29 @@ int build_neighbors(Ctx *c) {
     int *err = c->d_err.as<int>();
     CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     if (c->geom.ensure_bytes(sizeof(SGeom) * (size_t)(ns > 0 ? ns : 1)) || c->nbins.ensure<int64_t>(ns + 1) ||
-        c->bin_off.ensure<int64_t>(ns + 1) || c->d_total.ensure<int64_t>(2))
+        c->bin_off.ensure<int64_t>(ns + 1) || c->d_total.ensure<int64_t>(4))
         return c->fail(NEP_ENOMEM, "geometry buffers");
     SGeom *geom = (SGeom *)c->geom.ptr;
-    if (ns > 0) {
-        k_struct_geom<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(ns, c->cell.as<float>(), (double)rcR, geom,
-                                                                    c->nbins.as<int64_t>(), err);
-        k_struct_of<<<(unsigned)ns, 128, 0, st>>>(ns, c->atom_off.as<int64_t>(), c->struct_of.as<int>());
+    int rc = 0, herr = 0;
+    if (!(same_cells && c->geom_ok)) {  // per-structure bin grids (depend on the cells only)
+        c->geom_ok = false;
+        if (ns > 0) {
+            k_struct_geom<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(ns, c->cell.as<float>(), (double)rcR, geom,
+                                                                        c->nbins.as<int64_t>(), err);
+            k_struct_of<<<(unsigned)ns, 128, 0, st>>>(ns, c->atom_off.as<int64_t>(), c->struct_of.as<int>());
+        }
+        CK(cudaGetLastError());
+        rc = scan_exclusive(c, c->nbins.as<int64_t>(), ns, c->bin_off.as<int64_t>(), c->d_total.as<int64_t>());
+        if (rc) return rc;
+        int64_t nbt = 0;
+        CK(cudaMemcpyAsync(&nbt, c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) return c->fail(NEP_EINVAL, herr == 1 ? "singular or non-finite cell" : "cell too thin for the cutoff (more than 127 images)");
+        c->nbin_total = nbt;
+        c->geom_ok = true;
     }
-    CK(cudaGetLastError());
-    int rc = scan_exclusive(c, c->nbins.as<int64_t>(), ns, c->bin_off.as<int64_t>(), c->d_total.as<int64_t>());
-    if (rc) return rc;
-    int64_t nbin_total = 0;
-    CK(cudaMemcpyAsync(&nbin_total, c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    int herr = 0;
-    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (herr) return c->fail(NEP_EINVAL, herr == 1 ? "singular or non-finite cell" : "cell too thin for the cutoff (more than 127 images)");
+    const int64_t nbin_total = c->nbin_total;
     if (c->bin_cnt.ensure<int64_t>(nbin_total + 1) || c->bin_start.ensure<int64_t>(nbin_total + 1) ||
         c->bin_cur.ensure<int64_t>(nbin_total + 1) || c->atom_bin.ensure<int64_t>(na + 1) ||
         c->atom_wrap.ensure_bytes(sizeof(int4) * (size_t)(na + 1)) || c->bin_atoms.ensure<int>(na + 1) ||
@@ -621,21 +636,33 @@ int build_neighbors(Ctx *c) {
                                       c->rev.as<int>(), (const float4 *)c->pair.ptr, err);
         CK(cudaGetLastError());
     }
-    CK(cudaStreamSynchronize(st));
-    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (herr) return c->fail(NEP_EINTERNAL, "neighbour list is not symmetric");
-    // angular pair count
+    // angular pair count (an integer sum: exact in any order)
+    int64_t *nang_dev = c->d_total.as<int64_t>() + 3;
+    CK(cudaMemsetAsync(nang_dev, 0, sizeof(int64_t), st));
+    if (na > 0) k_sum_int<<<(unsigned)std::min<int64_t>((na + 255) / 256, 1024), 256, 0, st>>>(na, c->n_ang.as<int>(), nang_dev);
+    CK(cudaGetLastError());
     int64_t nang_total = 0;
-    {
-        std::vector<int> h(na > 0 ? na : 1);
-        if (na > 0) CK(cudaMemcpy(h.data(), c->n_ang.ptr, sizeof(int) * na, cudaMemcpyDeviceToHost));
-        for (int64_t i = 0; i < na; ++i) nang_total += h[i];
-        c->h_nang.assign(h.begin(), h.begin() + na);
-        std::vector<int64_t> off(na + 1);
-        CK(cudaMemcpy(off.data(), c->nbr_off.ptr, sizeof(int64_t) * (na + 1), cudaMemcpyDeviceToHost));
-        c->h_nbr_off.swap(off);
-    }
+    CK(cudaMemcpyAsync(&nang_total, nang_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) return c->fail(NEP_EINTERNAL, "neighbour list is not symmetric");
     c->n_pairs_ang = nang_total;
+    c->h_lists_ok = false;
+    return host_lists ? fetch_host_lists(c) : NEP_OK;
+}
+
+// Host copies of the per-atom angular counts and CSR offsets (used by the host-side
+// schedule builders); copied only when the lists changed since the last copy.
+int fetch_host_lists(Ctx *c) {
+    if (c->h_lists_ok) return NEP_OK;
+    const int64_t na = c->n_atoms;
+    c->h_nang.assign(na, 0);
+    c->h_nbr_off.assign(na + 1, 0);
+    if (na > 0) {
+        CK(cudaMemcpy(c->h_nang.data(), c->n_ang.ptr, sizeof(int) * na, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(c->h_nbr_off.data(), c->nbr_off.ptr, sizeof(int64_t) * (na + 1), cudaMemcpyDeviceToHost));
+    }
+    c->h_lists_ok = true;
     return NEP_OK;
 }
 

@@ -384,6 +384,69 @@ def test_update_positions_matches_fresh_context():
     assert rel(g.cpu().numpy(), go) < TOL
 
 
+
+def test_update_positions_cells_kept_and_minibatches():
+    """Positions-only updates (the cells' bin grids are kept and the schedules are built on
+    the device), twice in a row, then an update with mini-batches set up (schedules built
+    on the host): E/F/W, the loss and the gradient of the full batch and of a mini-batch
+    equal those of a fresh context bit for bit."""
+    from paper_2606_19557_gb300 import NEP
+    spec = synth.SPECS["scale_t5"]
+    b = synth.batch_scale(seed=19, n_struct=16, n_big=0)
+    P = oracle.num_params(spec)
+    th = torch.tensor(synth.random_theta(P, 19), dtype=torch.float32)
+    qs = torch.tensor(f32(oracle.scale_from_range(oracle.descriptors(spec, th.double().numpy(), b))),
+                      dtype=torch.float32)
+    Er, Fr, Wr = synth.random_targets(b, 20)
+    lam = (1.0, 2.0, 0.3)
+    nep = NEP(spec)
+    nep.set_structures_batch(b)
+    nep.set_params(th, qs)
+    nep.eval()
+    rng = np.random.default_rng(21)
+
+    def fresh_for(pos, B=0):
+        f = NEP(spec)
+        f.set_structures_batch(synth.Batch(b.atom_off, pos.astype(np.float64), b.types, b.cell, b.n_types))
+        f.set_params(th, qs)
+        if B:
+            f.minibatch_setup(B)
+        return f
+
+    def same(a, f):
+        for x, y in zip(a.eval(), f.eval()):
+            assert torch.equal(x, y)
+        la, ga = a.loss_grad(Er, Fr, Wr, None, lam)
+        lf, gf = f.loss_grad(Er, Fr, Wr, None, lam)
+        assert torch.equal(la, lf) and torch.equal(ga, gf)
+
+    for _ in range(2):
+        pos = (np.asarray(b.pos) + rng.normal(scale=0.05, size=b.pos.shape)).astype(np.float32)
+        nep.update_positions(pos)
+        f = fresh_for(pos)
+        same(nep, f)
+        f.close()
+    B = 5
+    n = nep.minibatch_setup(B)
+    pos = (np.asarray(b.pos) + rng.normal(scale=0.05, size=b.pos.shape)).astype(np.float32)
+    nep.update_positions(pos)
+    f = fresh_for(pos)
+    same(nep, f)
+    f.close()
+    # the mini-batch launch shapes are chosen by timing: groups are checked against the oracle
+    b2 = synth.Batch(b.atom_off, pos.astype(np.float64), b.types, b.cell, b.n_types)
+    nep.set_targets(Er, Fr, Wr)
+    theta = th.double().numpy()
+    for m in range(n):
+        s0, s1 = m * B, min(b.n_struct, (m + 1) * B)
+        a0, a1 = b.atom_off[s0], b.atom_off[s1]
+        la, ga = nep.minibatch_loss_grad(m, lam)
+        lo, go = oracle.loss_grad(spec, theta, qs.double().numpy(), b2.subset(np.arange(s0, s1)), Er[s0:s1],
+                                  Fr[a0:a1], Wr[s0:s1], None, lam)[:2]
+        np.testing.assert_allclose(la.cpu().numpy(), lo, rtol=TOL)
+        assert rel(ga.cpu().numpy(), go) < TOL
+    nep.close()
+
 @pytest.mark.parametrize("name", ["nep44_t16", "nep88_t16"])
 def test_table2_sixteen_species_models(name):
     """The paper's 16-element models (Table 2 sizes; 80 neurons, 4- and 5-body terms) on a
