@@ -396,7 +396,7 @@ __device__ __forceinline__ uint64_t pair_key(bool ang, int tj, int j, int Sa, in
 // Pair counts per atom (one warp per atom), and the sort keys of the first `cap` pairs
 // of each atom in scratch[i * cap ...] (unordered): when no atom has more, the keys need
 // no second scan.  *overflow is set when some atom has more than cap pairs.
-__global__ void k_count_w(int64_t na, const float *pos, const float4 *pos4, const int *type, const int *struct_of,
+__global__ void __launch_bounds__(256, 4) k_count_w(int64_t na, const float *pos, const float4 *pos4, const int *type, const int *struct_of,
                           const int64_t *atom_off, const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin,
                           const int4 *atom_wrap, const int64_t *bin_start, const float4 *bin_pos,
                           const int4 *bin_wrap, float rc2R,
@@ -449,37 +449,85 @@ __global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const
     if (lane == 0 && slot[wib] != n) atomic_err(err, 5);
 }
 
-// One warp per atom: rank sort of its keys, then decode into the pair records.
+// Writes key k at its sorted position beg + rank with its decoded pair record.
+__device__ __forceinline__ void emit_pair(uint64_t k, int64_t slot, int64_t i, const float *pos, const SGeom &g,
+                                          uint64_t *keys_out, float4 *pair, int32_t *shift) {
+    keys_out[slot] = k;
+    const int j = (int)((k >> 24) & ((1ull << 35) - 1));
+    const int tj = (int)((k >> 59) & 15ull);
+    const uint32_t sp = (uint32_t)(k & 0xffffffull);
+    const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
+    float d32[3];
+    pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
+    pair[slot] = make_float4(d32[0], d32[1], d32[2], __int_as_float((j << 4) | tj));
+    shift[slot] = (int32_t)sp;
+}
+
+// Rank sort of n <= 32 R staged keys: lane l owns keys l, l + 32, ...; every staged key
+// is read once per lane, two at a time (a 16-byte broadcast), against the owned keys in
+// registers.  sk holds n keys padded to an even count with a key above all others.
+template <int R>
+__device__ __forceinline__ void rank_staged(const uint64_t *sk, int n, int lane, int64_t beg, int64_t i,
+                                            const float *pos, const SGeom &g, uint64_t *keys_out, float4 *pair,
+                                            int32_t *shift) {
+    uint64_t own[R];
+    int rank[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = lane + 32 * r;
+        own[r] = e < n ? sk[e] : 0ull;
+        rank[r] = 0;
+    }
+    const ulonglong2 *sk2 = reinterpret_cast<const ulonglong2 *>(sk);
+    for (int e2 = 0; e2 < (n + 1) >> 1; ++e2) {
+        const ulonglong2 kk = sk2[e2];
+#pragma unroll
+        for (int r = 0; r < R; ++r) rank[r] += (kk.x < own[r] ? 1 : 0) + (kk.y < own[r] ? 1 : 0);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < n) emit_pair(own[r], beg + rank[r], i, pos, g, keys_out, pair, shift);
+}
+
+// One warp per atom: the atom's keys in ascending order (angular flag, species of j, j, S)
+// with their pair records (displacement from the FP64 pair_d, j and its species).
 __global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const uint64_t *scratch, int cap,
                               const int64_t *nbr_off, const float *pos,
                               const int *struct_of, const SGeom *geom, uint64_t *keys_out, float4 *pair,
                               int32_t *shift) {
     constexpr int STAGE = 256;  // keys per warp staged in shared memory
-    __shared__ uint64_t sk[8][STAGE];
+    __shared__ __align__(16) uint64_t sk[8][STAGE];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (i >= na) return;
     const int64_t beg = nbr_off[i], n = nbr_off[i + 1] - beg;
     const SGeom &g = geom[struct_of[i]];
     const uint64_t *src = scratch ? scratch + i * (int64_t)cap : keys_in + beg;
-    if (n <= STAGE) {  // the rank sort reads every key n times: from shared memory when it fits
-        for (int64_t e = lane; e < n; e += 32) sk[wib][e] = src[e];
+    if (n <= STAGE) {
+        uint64_t *s = sk[wib];
+        for (int64_t e = lane; e < n; e += 32) s[e] = src[e];
+        if (lane == 0 && (n & 1)) s[n] = ~0ull;  // n odd: n < STAGE, pad above every key
         __syncwarp();
-        src = sk[wib];
+        const int nn = (int)n;
+        switch ((nn + 31) >> 5) {
+            case 0: break;
+            case 1: rank_staged<1>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 2: rank_staged<2>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 3: rank_staged<3>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 4: rank_staged<4>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 5: rank_staged<5>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 6: rank_staged<6>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 7: rank_staged<7>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            default: rank_staged<8>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+        }
+        return;
     }
+    // longer lists: rank against the keys in global memory
     for (int64_t e = lane; e < n; e += 32) {
         const uint64_t k = src[e];
         int64_t rank = 0;
         for (int64_t e2 = 0; e2 < n; ++e2) rank += (src[e2] < k) ? 1 : 0;
-        keys_out[beg + rank] = k;
-        const int j = (int)((k >> 24) & ((1ull << 35) - 1));
-        const int tj = (int)((k >> 59) & 15ull);
-        const uint32_t sp = (uint32_t)(k & 0xffffffull);
-        const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
-        float d32[3];
-        pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
-        pair[beg + rank] = make_float4(d32[0], d32[1], d32[2], __int_as_float((j << 4) | tj));
-        shift[beg + rank] = (int32_t)sp;
+        emit_pair(k, beg + rank, i, pos, g, keys_out, pair, shift);
     }
 }
 

@@ -147,6 +147,41 @@ def test_neighbor_edge_geometries():
 
 # ----------------------------------------------------------------------------- forward
 
+
+def test_neighbor_dense_cells():
+    """Compressed FCC cells (a = 3.5 ... 2.2 A; about 85 to 340 radial neighbours per atom):
+    lists longer than the per-atom key scratch (second scan), the staged sort at up to 8
+    keys per lane and the unstaged sort beyond 256 keys, bit-exact against brute force;
+    E/F/W against the oracle."""
+    from paper_2606_19557_gb300 import NEP
+    rng = np.random.default_rng(5)
+    basis = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]], float)
+    grid = np.array([[x, y, z] for x in range(3) for y in range(3) for z in range(3)], float)
+    frac = (grid[:, None, :] + basis[None, :, :]).reshape(-1, 3) / 3.0
+    structs = []
+    for a in (3.5, 3.1, 2.8, 2.5, 2.2):
+        cell = np.eye(3) * 3 * a
+        structs.append((frac @ cell + rng.normal(scale=0.05, size=frac.shape), cell))
+    off = np.cumsum([0] + [p.shape[0] for p, _ in structs])
+    batch = synth.Batch(off.astype(np.int64), np.concatenate([p for p, _ in structs]).astype(np.float32),
+                        rng.integers(0, 2, size=off[-1]).astype(np.int32),
+                        np.stack([c.reshape(9) for _, c in structs]).astype(np.float32), 2)
+    spec = synth.SPECS["alloy_t4"]
+    spec = synth.ModelSpec(2, spec.rc_R, spec.rc_A, 4, 4, 8, 8, 4, 1, 0, 16)
+    nep = NEP(spec)
+    nep.set_structures_batch(batch)
+    _check_neighbors(nep, batch, spec.rc_R, spec.rc_A)
+    counts = np.diff(nep.neighbors()[0].cpu().numpy())
+    assert counts.min() < 128 and counts.max() > 256
+    P = oracle.num_params(spec)
+    theta = synth.random_theta(P, 6)
+    qs = f32(oracle.scale_from_range(oracle.descriptors(spec, theta, batch)))
+    nep.set_params(torch.tensor(theta, dtype=torch.float32), torch.tensor(qs, dtype=torch.float32))
+    E, F, W = [x.cpu().numpy() for x in nep.eval()]
+    Eo, Fo, Wo = oracle.evaluate(spec, theta, qs, batch)
+    assert rel(E, Eo) < TOL and rel(F, Fo) < TOL and rel(W, Wo) < TOL
+    nep.close()
+
 @pytest.mark.parametrize("name", NAMES)
 def test_descriptors(name):
     c = get_case(name)
