@@ -449,25 +449,54 @@ __global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const
     if (lane == 0 && slot[wib] != n) atomic_err(err, 5);
 }
 
-// Writes key k at its sorted position beg + rank with its decoded pair record.
-__device__ __forceinline__ void emit_pair(uint64_t k, int64_t slot, int64_t i, const float *pos, const SGeom &g,
-                                          uint64_t *keys_out, float4 *pair, int32_t *shift) {
+constexpr uint32_t SHIFT0 = 0x808080u;  // packed S = (0, 0, 0)
+
+// Stores key k at its sorted position with its pair record (displacement, j and its species).
+__device__ __forceinline__ void store_pair(uint64_t k, int64_t slot, const float *d32, uint64_t *keys_out,
+                                           float4 *pair, int32_t *shift) {
     keys_out[slot] = k;
     const int j = (int)((k >> 24) & ((1ull << 35) - 1));
     const int tj = (int)((k >> 59) & 15ull);
-    const uint32_t sp = (uint32_t)(k & 0xffffffull);
-    const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
-    float d32[3];
-    pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
     pair[slot] = make_float4(d32[0], d32[1], d32[2], __int_as_float((j << 4) | tj));
-    shift[slot] = (int32_t)sp;
+    shift[slot] = (int32_t)(k & 0xffffffull);
+}
+
+// pair_d's displacement for a pair with S = (0, 0, 0), in FP32 and with the same bits.
+// p_j - p_i of two floats is exact in FP64 unless one operand is below 2^-29 of the other,
+// and then both fl32(p_j - p_i) and fl32(fl64(p_j - p_i)) are the larger operand.  The
+// image term 0 h_a + 0 h_b + 0 h_c is a signed zero (negative only when all three h
+// components are), and adding it follows the same sign rules in either precision.
+__device__ __forceinline__ void pair_d0(const float *pi, const float *pj, const double *h, float *d32) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const bool neg = (__double_as_longlong(h[x]) & __double_as_longlong(h[3 + x]) &
+                          __double_as_longlong(h[6 + x])) < 0;
+        d32[x] = __fadd_rn(__fsub_rn(pj[x], pi[x]), neg ? -0.0f : 0.0f);
+    }
+}
+
+// Pair record of key k from the predicate's displacement.
+__device__ __forceinline__ void emit_pair(uint64_t k, int64_t slot, int64_t i, const float *pos, const SGeom &g,
+                                          uint64_t *keys_out, float4 *pair, int32_t *shift) {
+    const int j = (int)((k >> 24) & ((1ull << 35) - 1));
+    const uint32_t sp = (uint32_t)(k & 0xffffffull);
+    float d32[3];
+    if (sp == SHIFT0) {
+        pair_d0(pos + 3 * i, pos + 3 * j, g.h, d32);
+    } else {
+        const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
+        pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
+    }
+    store_pair(k, slot, d32, keys_out, pair, shift);
 }
 
 // Rank sort of n <= 32 R staged keys: lane l owns keys l, l + 32, ...; every staged key
 // is read once per lane, two at a time (a 16-byte broadcast), against the owned keys in
 // registers.  sk holds n keys padded to an even count with a key above all others.
+// Pairs with S = 0 are then written at once (FP32); the others are queued in sk / sq and
+// written by consecutive lanes, so that the FP64 displacements run on full warps.
 template <int R>
-__device__ __forceinline__ void rank_staged(const uint64_t *sk, int n, int lane, int64_t beg, int64_t i,
+__device__ __forceinline__ void rank_staged(uint64_t *sk, int *sq, int n, int lane, int64_t beg, int64_t i,
                                             const float *pos, const SGeom &g, uint64_t *keys_out, float4 *pair,
                                             int32_t *shift) {
     uint64_t own[R];
@@ -484,19 +513,38 @@ __device__ __forceinline__ void rank_staged(const uint64_t *sk, int n, int lane,
 #pragma unroll
         for (int r = 0; r < R; ++r) rank[r] += (kk.x < own[r] ? 1 : 0) + (kk.y < own[r] ? 1 : 0);
     }
+    __syncwarp();  // every lane has read the staged keys: sk / sq now take the queue
+    int nq = 0;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-        if (lane + 32 * r < n) emit_pair(own[r], beg + rank[r], i, pos, g, keys_out, pair, shift);
+    for (int r = 0; r < R; ++r) {
+        const bool valid = lane + 32 * r < n;
+        const bool img = valid && (uint32_t)(own[r] & 0xffffffull) != SHIFT0;
+        const unsigned m = __ballot_sync(FULL, img);
+        if (img) {
+            const int q = nq + __popc(m & ((1u << lane) - 1u));
+            sk[q] = own[r];
+            sq[q] = rank[r];
+        } else if (valid) {
+            const int j = (int)((own[r] >> 24) & ((1ull << 35) - 1));
+            float d32[3];
+            pair_d0(pos + 3 * i, pos + 3 * j, g.h, d32);
+            store_pair(own[r], beg + rank[r], d32, keys_out, pair, shift);
+        }
+        nq += __popc(m);
+    }
+    __syncwarp();
+    for (int q = lane; q < nq; q += 32) emit_pair(sk[q], beg + sq[q], i, pos, g, keys_out, pair, shift);
 }
 
 // One warp per atom: the atom's keys in ascending order (angular flag, species of j, j, S)
-// with their pair records (displacement from the FP64 pair_d, j and its species).
+// with their pair records (displacement = the predicate's pair_d, j and its species).
 __global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const uint64_t *scratch, int cap,
                               const int64_t *nbr_off, const float *pos,
                               const int *struct_of, const SGeom *geom, uint64_t *keys_out, float4 *pair,
                               int32_t *shift) {
     constexpr int STAGE = 256;  // keys per warp staged in shared memory
     __shared__ __align__(16) uint64_t sk[8][STAGE];
+    __shared__ int sq[8][STAGE];
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (i >= na) return;
@@ -509,16 +557,17 @@ __global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const uint64_
         if (lane == 0 && (n & 1)) s[n] = ~0ull;  // n odd: n < STAGE, pad above every key
         __syncwarp();
         const int nn = (int)n;
+        int *q = sq[wib];
         switch ((nn + 31) >> 5) {
             case 0: break;
-            case 1: rank_staged<1>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
-            case 2: rank_staged<2>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
-            case 3: rank_staged<3>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
-            case 4: rank_staged<4>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
-            case 5: rank_staged<5>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
-            case 6: rank_staged<6>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
-            case 7: rank_staged<7>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
-            default: rank_staged<8>(s, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 1: rank_staged<1>(s, q, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 2: rank_staged<2>(s, q, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 3: rank_staged<3>(s, q, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 4: rank_staged<4>(s, q, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 5: rank_staged<5>(s, q, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 6: rank_staged<6>(s, q, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            case 7: rank_staged<7>(s, q, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
+            default: rank_staged<8>(s, q, nn, lane, beg, i, pos, g, keys_out, pair, shift); break;
         }
         return;
     }
