@@ -114,10 +114,16 @@ int nep_set_structures(nep_ctx *ctx, int64_t n_struct, const int64_t *atom_off_d
 
 /* New positions (and optionally cells) for the cached batch: same structures, atom
  * counts and species.  pos_dev [N_a*3] f32 (device); cell_dev [n_struct*9] f32 (device)
- * or NULL to keep the cells.  Rebuilds the neighbour lists on the device (step a1, as an
- * MD-style evaluation needs every step) and keeps the kernel schedules; synchronizes.
- * Errors: NEP_ESTATE (no batch), NEP_EINVAL (bad geometry: the batch is then unusable
- * until the next successful call), NEP_ENOMEM, NEP_ECUDA. */
+ * or NULL to keep the cells (their bin grids are then reused).  Rebuilds the neighbour
+ * lists on the device (step a1, as an MD-style evaluation needs every step) and
+ * re-balances the per-atom kernel schedules for the new neighbour counts with the same
+ * launch shapes, so every later result equals that of a fresh context on the new
+ * geometry, bit for bit.  Without mini-batches the schedules are built on the device;
+ * with them (nep_minibatch_setup) the group schedules are rebuilt on the host.
+ * Synchronizes with the list build; the schedule kernels are queued on the context's
+ * stream after it.  Errors: NEP_ESTATE (no batch), NEP_EINVAL (bad geometry: the batch
+ * is then unusable, and later calls return NEP_ESTATE, until nep_set_structures),
+ * NEP_ENOMEM, NEP_ECUDA. */
 int nep_update_positions(nep_ctx *ctx, const float *pos_dev, const float *cell_dev);
 
 /* Radial and angular neighbour-pair counts of the cached batch. */
