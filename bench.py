@@ -118,7 +118,7 @@ def run_reference(args):
     qs = oracle.scale_from_range(oracle.descriptors(spec, theta, sample))
     Er, Fr, Wr = synth.random_targets(sample, 3)
     times = []
-    for _ in range(args.warmup if args.warmup < 2 else 1):
+    for _ in range(args.warmup):
         oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
     for _ in range(args.steps):
         t0 = time.perf_counter()
