@@ -11,7 +11,7 @@ Follows Sec. "Training" of the paper:
     corrects afterwards, which differs), and the update
     theta_t = theta_{t-1} - eta_t m^_t / (sqrt(v^max_t) + eps);
   * the epoch-level plateau schedule eta_{e+1} = max(gamma eta_e, eta_min), applied
-    when the epoch-averaged loss has failed to improve for p consecutive epochs;
+    once the mean loss of an epoch has shown no improvement over p epochs in a row;
   * the two-stage protocol (a stage fixes lambda_E, lambda_F, lambda_V and restarts
     the learning rate; the plateau schedule runs within each stage).
 
@@ -19,7 +19,7 @@ Readings where the paper is silent:
   * parameters are stored in FP32 (the precision of the whole pass); the optimiser's
     moments and arithmetic are FP64, and the new parameters are rounded to FP32 after
     every update;
-  * "fails to improve": the epoch loss L_e is an improvement iff L_e < best (1 - tau),
+  * what counts as an improvement: the epoch loss L_e improves iff L_e < best (1 - tau),
     tau >= 0 a relative threshold (0 = any decrease); after p consecutive epochs without
     improvement the rate is reduced and the count restarts;
   * a new stage keeps the Adam moments and the step count, and restarts the schedule
