@@ -441,3 +441,139 @@ def test_radial_descriptor_linear_in_c():
     q2 = oracle.descriptors(s, th2, b)
     np.testing.assert_allclose(q2[:, :NR], -2.5 * q[:, :NR], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(q2[:, NR:], q[:, NR:], rtol=0, atol=0)
+
+
+# ------------------------------------------------------------------ hand-worked fixtures
+
+def _fixture(name):
+    rows = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            rows.setdefault(k, []).append(v)
+    return rows
+
+
+def _frac(x):
+    from fractions import Fraction
+    return float(Fraction(x))
+
+
+def loss_fixture():
+    """Inputs and hand-worked Eq. "loss" values of tests/golden/loss_terms_b1_only.txt: three
+    structures (a dimer, a triangle, one atom) in 12 A cells and a model whose only nonzero
+    parameter is b1."""
+    f = _fixture("loss_terms_b1_only.txt")
+    nat = [int(x) for x in f["natoms"][0]]
+    geo = {1: [[6.0, 6.0, 6.0]], 2: [[5.0, 6.0, 6.0], [7.1, 6.0, 6.0]],
+           3: [[5.0, 5.0, 6.0], [7.0, 5.2, 6.0], [6.1, 6.9, 6.3]]}
+    pos = np.concatenate([np.array(geo[n], np.float64) for n in nat])
+    off = np.concatenate([[0], np.cumsum(nat)]).astype(np.int64)
+    cell = np.tile((np.eye(3) * 12.0).reshape(9), (len(nat), 1))
+    batch = synth.Batch(off, pos, np.zeros(pos.shape[0], np.int32), cell, 1)
+    s = synth.SPECS["fcc_bcc_t1"]
+    P = oracle.num_params(s)
+    ND = oracle.num_descriptors(s)
+    i_b1 = s.n_types * (ND + 2) * s.n_neu
+    theta = np.zeros(P)
+    theta[i_b1] = float(f["b1"][0][0])
+    return {"spec": s, "batch": batch, "theta": theta, "i_b1": i_b1, "qs": np.ones(ND),
+            "E_ref": np.array([float(x) for x in f["E_ref"][0]]),
+            "F_ref": np.array([[float(x) for x in r] for r in f["F_ref"]]),
+            "W_ref": np.array([[float(x) for x in r] for r in f["W_ref"]]),
+            "has_W": np.array([int(x) for x in f["has_W"][0]], np.uint8),
+            "lam": tuple(float(x) for x in f["lam"][0]),
+            "loss3": np.array([_frac(x) for x in f["loss3"][0]]), "dL_db1": _frac(f["dL_db1"][0][0])}
+
+
+def test_loss_terms_hand_worked():
+    """Eq. "loss" normalisers (per-atom energy and virial residuals, 1/(3 N_a), N_s^V of the
+    structures with virials) and the sign of b1, against the hand-worked fixture."""
+    fx = loss_fixture()
+    loss3, g, E, F, W = oracle.loss_grad(fx["spec"], fx["theta"], fx["qs"], fx["batch"], fx["E_ref"], fx["F_ref"],
+                                         fx["W_ref"], fx["has_W"], fx["lam"])
+    np.testing.assert_allclose(E, -0.5 * fx["batch"].counts(), rtol=0, atol=1e-15)
+    assert np.all(F == 0.0) and np.all(W == 0.0)
+    np.testing.assert_allclose(loss3, fx["loss3"], rtol=1e-14)
+    assert abs(g[fx["i_b1"]] - fx["dL_db1"]) < 1e-14
+    rest = np.delete(g, fx["i_b1"])
+    assert np.all(rest == 0.0)
+
+
+def dimer_fixture():
+    f = _fixture("dimer_one_neuron.txt")
+    s = spec(rc_R=float(f["rc_R"][0][0]), rc_A=float(f["rc_A"][0][0]), n_max_R=0, n_max_A=0, basis_R=0, basis_A=0,
+             l_max=0, n_neu=1)
+    pos = np.array([[float(x) for x in f["pos1"][0]], [float(x) for x in f["pos2"][0]]])
+    return {"spec": s, "batch": one_batch(pos, np.eye(3) * 12.0),
+            "theta": np.array([float(x) for x in f["theta"][0]]),
+            "qs": np.array([float(x) for x in f["q_scale"][0]])}
+
+
+def dimer_closed_form():
+    """E_s, F_2 (x component) and W_xx of the one-neuron dimer (closed forms of the fixture)."""
+    t = math.tanh(0.25)
+    sech2 = 1.0 - t * t
+    return 4.0 * t - 0.2, 0.5 * math.pi * sech2, math.pi * sech2
+
+
+def test_network_signs_one_neuron_dimer():
+    """Signs of Eq. "ann" (z = w0 q~ - b0, E_i = w1 tanh z - b1), F = -dE/dr and the virial
+    convention, against closed forms of a one-neuron model on a dimer."""
+    fx = dimer_fixture()
+    assert oracle.num_params(fx["spec"]) == 6
+    E, F, W = oracle.evaluate(fx["spec"], fx["theta"], fx["qs"], fx["batch"])
+    Es, F2, Wxx = dimer_closed_form()
+    assert abs(E[0] - Es) < 1e-14
+    np.testing.assert_allclose(F, [[-F2, 0, 0], [F2, 0, 0]], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(W[0], [Wxx, 0, 0, 0, 0, 0, 0, 0, 0], rtol=0, atol=1e-14)
+
+
+def _wide_brute_force(pos, cell, rc):
+    """Every (i, j, S) with S in [-K, K]^3 for a K well beyond the needed range, kept by the
+    float predicate of the neighbour build: d = r_j + S h - r_i in FP64 rounded to float,
+    (dx dx + dy dy) + dz dz < rc rc in float without fused operations."""
+    inv = np.linalg.inv(cell)
+    w = 1.0 / np.linalg.norm(inv, axis=0)
+    K = int(math.ceil(rc / w.min())) + 3
+    rng = np.arange(-K, K + 1)
+    S = np.stack(np.meshgrid(rng, rng, rng, indexing="ij"), -1).reshape(-1, 3)
+    shift = S.astype(np.float64) @ cell
+    rc32 = np.float32(rc)
+    out = set()
+    for i in range(pos.shape[0]):
+        for j in range(pos.shape[0]):
+            d = (pos[j] - pos[i])[None, :] + shift
+            d32 = d.astype(np.float32)
+            r2 = (d32[:, 0] * d32[:, 0] + d32[:, 1] * d32[:, 1]) + d32[:, 2] * d32[:, 2]
+            keep = r2 < rc32 * rc32
+            for s in S[keep]:
+                if i != j or s.any():
+                    out.add((i, j, tuple(int(x) for x in s)))
+    return out
+
+
+def test_image_range_covers_float_predicate():
+    """The brute-force enumeration takes |S_a| <= ceil(rc/w_a + span_a).  A pair outside that
+    range has |d| >= w_a (ceil(rc/w_a + span_a) + 1 - span_a) >= rc + w_a, far beyond the
+    float predicate's slack (kept pairs have |d| < rc (1 + 3 2^-24)).  Checked against an
+    enumeration three shells wider on narrow triclinic cells whose atoms span the cell,
+    including pairs placed within a few ulp of the cutoff."""
+    rng = np.random.default_rng(7)
+    for case in range(6):
+        w = rng.uniform(1.3, 3.0)
+        cell = np.diag([w, rng.uniform(1.3, 4.0), rng.uniform(2.0, 5.0)])
+        cell = cell @ (np.eye(3) + 0.15 * rng.uniform(-1, 1, (3, 3)))
+        n = 3
+        frac = rng.uniform(0.0, 1.0, (n, 3))
+        frac[0, 0], frac[1, 0] = 0.0, 0.999
+        pos = frac @ cell
+        rc = 4.0
+        if case % 2:  # put one image pair at the cutoff: the displacement scaled to |d| = rc
+            d = pos[1] + cell[0] * 2 - pos[0]
+            pos[1] = pos[0] + d * (rc / np.linalg.norm(d)) - cell[0] * 2
+        pos = pos.astype(np.float32).astype(np.float64)
+        b = one_batch(pos, cell)
+        i, j, S, _ = oracle.neighbors(b, rc, 3.0)
+        got = set(zip(i.tolist(), j.tolist(), map(tuple, S.tolist())))
+        assert got == _wide_brute_force(pos, cell, rc), case
