@@ -1,15 +1,18 @@
 """Throughput of the batched NEP loss + parameter-gradient pass (atoms/s).
 
-Workload (default): 1000 seeded synthetic FCC/BCC structures of 64-256 atoms (strain
-+-3 %, displacements 0.05-0.3 A), 1 species, rc_R = 6 A, rc_A = 4 A, n_max 4/4, basis
-8/8, l_max 4 + 4-body, 30 neurons, full batch, FP32 with FP64 sums.  One step = one
-nep_loss_grad call (energies, forces, virials, loss, analytic gradient of every
-parameter) with the neighbour lists cached on the GPU, as in the paper.
+Headline workload (default, the largest configuration): 20,000 seeded synthetic
+structures of 2-2000 atoms (log-uniform sizes; dimers, FCC/BCC solids, 20 %
+liquid-like, 10 % slabs) plus ten 10,000-atom FCC cells, 5 species, rc_R = 6 A,
+rc_A = 4 A, n_max 6/6, basis 10/10, l_max 4 with 4- and 5-body terms, 50 neurons,
+full batch, FP32 with FP64 sums.  One step = one nep_loss_grad call (energies,
+forces, virials, loss, analytic gradient of every parameter) with the neighbour
+lists cached on the GPU, as in the paper.  The 1000-structure FCC/BCC batch and the
+5000-structure 4-species alloy batch are measured beside it (`extra_configs`).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config NAME]
 
-Under torchrun (N > 1) every rank runs its own batch (seed + rank): weak scaling, no
-collective in the timed region besides the barrier and the max-time reduction.
+Under torchrun (N > 1) every rank runs its own batch (seed + 1000 rank): weak scaling,
+no collective in the timed region besides the barrier and the max-time reduction.
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -28,29 +31,67 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "atoms/s per loss+param-grad pass (E,F,W) vs plain FP32 form; err vs FP64 oracle"
-WORKLOAD = "fcc_bcc_t1: 1000 structures x U{64..256} atoms, FCC/BCC, strain 3%, sigma 0.05-0.3 A; " \
-           "1 species, rc 6/4 A, n_max 4/4, basis 8/8, l_max 4 + 4-body, 30 neurons"
 LAM = (1.0, 1.0, 0.1)
+GEN_WORKERS = min(16, os.cpu_count() or 1)
+
+# Workloads: model (synth.SPECS key), batch generator, and the oracle sample (structure
+# indices) on which the CPU baseline, the reference arm and the error figures run.
+WORKLOADS = {
+    "scale_t5": {
+        "desc": "scale_t5: 20,000 structures x 2-2000 atoms (log-uniform; dimers, FCC/BCC, 20% liquid-like "
+                "sigma 0.5 A, 10% slabs) + ten 10,000-atom FCC cells; 5 species, rc 6/4 A, n_max 6/6, "
+                "basis 10/10, l_max 4 + 4-body + 5-body, 50 neurons",
+        "sample": list(range(0, 20000, 1250)),
+        "sample_desc": "structures 0, 1250, ..., 18750 of the batch (every 1250th: 16 structures)",
+    },
+    "alloy_t4": {
+        "desc": "alloy_t4: 5000 structures x U{16..512} atoms, 4-species random alloy, 20% liquid-like "
+                "sigma 0.5 A, 10% slabs (+10 A vacuum), rc 6/4 A, n_max 4/4, basis 8/8, l_max 4 + 4-body, "
+                "30 neurons",
+        "sample": list(range(0, 5000, 125)),
+        "sample_desc": "every 125th structure (40 structures)",
+    },
+    "fcc_bcc_t1": {
+        "desc": "fcc_bcc_t1: 1000 structures x U{64..256} atoms, FCC/BCC, strain 3%, sigma 0.05-0.3 A; "
+                "1 species, rc 6/4 A, n_max 4/4, basis 8/8, l_max 4 + 4-body, 30 neurons",
+        "sample": list(range(150)),
+        "sample_desc": "first 150 structures",
+    },
+}
+
+
+def build_workload(name: str, rank: int, only=None):
+    from paper_2606_19557_gb300 import synth
+    spec = synth.SPECS[name]
+    if name == "scale_t5":
+        return spec, synth.batch_scale(seed=5 + 1000 * rank, only=only, workers=0 if only else GEN_WORKERS)
+    if name == "alloy_t4":
+        b = synth.batch_alloy(seed=3 + 1000 * rank, n_struct=5000)
+    else:
+        b = synth.batch_fcc_bcc(seed=2 + 1000 * rank, n_struct=1000)
+    return spec, (b if only is None else b.subset(only))
+
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per atom of the per-atom
-# kernels, from one ncu capture of the first 200 structures of this workload at the bench's
-# launch shape (profiles/forward_adjoint_gather_ann_fcc_bcc_200.md), scaled to a launch by
-# its atoms.  Valid only for the kernel sources with this SHA-256; otherwise null.
+# kernels, from one ncu capture of a small cut of each workload at the bench's launch
+# shape, scaled to a launch by its atoms.  Valid only for the kernel sources with the
+# recorded SHA-256; otherwise the bench reports null.
 KERNEL_SOURCES = ("paper_2606_19557_gb300/csrc/nep_model.cuh", "paper_2606_19557_gb300/csrc/nep_internal.cuh")
-TRAFFIC = {"sha256": "07e1680e57821aee0670bc7346dc44bab6ab630955a732aebf27ab8e4ed78638",
-           "bytes_per_atom": {"forward": (38.189568e6 + 10.1248e6) / 32546,
-                              "adjoint": (58.17472e6 + 1.142272e6) / 32546}}
+TRAFFIC = {}
 
 
-def kernel_traffic(kernel: str, n_atoms: int):
+def kernel_traffic(workload: str, kernel: str, n_atoms: int):
     import hashlib
+    t = TRAFFIC.get(workload)
+    if t is None:
+        return None
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != TRAFFIC["sha256"] or kernel not in TRAFFIC["bytes_per_atom"]:
+    if h.hexdigest() != t["sha256"] or kernel not in t["bytes_per_atom"]:
         return None
-    return TRAFFIC["bytes_per_atom"][kernel] * n_atoms
+    return t["bytes_per_atom"][kernel] * n_atoms
 
 
 def _dist():
@@ -98,78 +139,6 @@ def _clock_summary(proc, gpu_index: int):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(rank: int, n_struct: int):
-    from paper_2606_19557_gb300 import synth
-    batch = synth.batch_fcc_bcc(seed=2 + 1000 * rank, n_struct=n_struct)
-    return synth.SPECS["fcc_bcc_t1"], batch
-
-
-def run_reference(args):
-    """FP64 CPU oracle on a bounded sample of the workload (the reference arm)."""
-    ws, rank = _dist()
-    if rank != 0:
-        return
-    import oracle
-    from paper_2606_19557_gb300 import synth
-    spec, batch = build_workload(0, args.n_struct)
-    sample = batch.subset(range(args.cpu_sample))
-    P = oracle.num_params(spec)
-    theta = synth.random_theta(P, 1)
-    qs = oracle.scale_from_range(oracle.descriptors(spec, theta, sample))
-    Er, Fr, Wr = synth.random_targets(sample, 3)
-    times = []
-    for _ in range(args.warmup):
-        oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
-        times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    value = sample.n_atoms * len(times) / tot
-    cb = {"value": value, "unit": "atoms/s", "cores": oracle.threads(), "kind": "oracle",
-          "sample": f"first {args.cpu_sample} structures ({sample.n_atoms} atoms) of the workload per step"}
-    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "atoms/s", "n_gpus": ws,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
-                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": WORKLOAD, "sample_structures": args.cpu_sample},
-                      "cpu_baseline": cb,
-                      "e2e": {"value": value, "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
-
-
-def cpu_baseline(spec, batch, n_sample: int):
-    """Times the oracle on a sample of the workload; also returns its inputs and results,
-    against which the GPU path's errors are reported."""
-    import oracle
-    from paper_2606_19557_gb300 import synth
-    sample = batch.subset(range(min(n_sample, batch.n_struct)))
-    P = oracle.num_params(spec)
-    theta = synth.random_theta(P, 1)
-    qs = oracle.scale_from_range(oracle.descriptors(spec, theta, sample)).astype(np.float32).astype(np.float64)
-    Er, Fr, Wr = synth.random_targets(sample, 3)
-    t0 = time.perf_counter()
-    loss3, grad, E, F, W = oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
-    dt = time.perf_counter() - t0
-    cores = oracle.threads()
-    cb = {"value": sample.n_atoms / dt, "unit": "atoms/s", "cores": cores, "kind": "oracle",
-          "sample": f"first {sample.n_struct} structures ({sample.n_atoms} atoms), one loss+grad pass, {dt:.1f} s",
-          "cpu_model": _cpu_model()}
-    # the same oracle on one core, on a smaller sample
-    small = batch.subset(range(min(max(1, n_sample // 8), batch.n_struct)))
-    Es, Fs, Ws = synth.random_targets(small, 3)
-    oracle.set_threads(1)
-    try:
-        t0 = time.perf_counter()
-        oracle.loss_grad(spec, theta, qs, small, Es, Fs, Ws, None, LAM)
-        d1 = time.perf_counter() - t0
-    finally:
-        oracle.set_threads(0)
-    cb["single_core"] = {"value": small.n_atoms / d1, "unit": "atoms/s",
-                         "sample": f"first {small.n_struct} structures ({small.n_atoms} atoms), {d1:.1f} s"}
-    ref = {"sample": sample, "theta": theta, "qs": qs, "targets": (Er, Fr, Wr),
-           "out": {"loss3": loss3, "grad": grad, "E": E, "F": F, "W": W}}
-    return cb, ref
-
-
 def _cpu_model() -> str:
     """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
     try:
@@ -192,12 +161,103 @@ def _cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
+def _oracle_inputs(spec, sample):
+    """Parameters, normalisation factors (from the oracle's descriptors of the sample) and
+    seeded targets for a loss pass of the oracle on `sample`."""
+    import oracle
+    from paper_2606_19557_gb300 import synth
+    theta = synth.random_theta(oracle.num_params(spec), 1)
+    qs = oracle.scale_from_range(oracle.descriptors(spec, theta, sample)).astype(np.float32).astype(np.float64)
+    return theta, qs, synth.random_targets(sample, 3)
+
+
+def run_reference(args):
+    """FP64 CPU oracle on a bounded sample of the workload (the reference arm)."""
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import oracle
+    w = sample_of(args.config, args.sample_structures)
+    spec, sample = build_workload(args.config, 0, only=w["sample"])
+    theta, qs, (Er, Fr, Wr) = _oracle_inputs(spec, sample)
+    for _ in range(args.warmup):
+        oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = sample.n_atoms * len(times) / tot
+    cb = {"value": value, "unit": "atoms/s", "cores": oracle.threads(), "kind": "oracle",
+          "sample": f"{w['sample_desc']}, {sample.n_atoms} atoms, one loss+grad pass per step",
+          "cpu_model": _cpu_model()}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "atoms/s", "n_gpus": ws,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": config_block(args.config), "cpu_baseline": cb,
+                      "e2e": {"value": value, "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def sample_of(name: str, n: int = 0) -> dict:
+    """The workload's oracle sample, cut to its first n structures when n > 0."""
+    w = WORKLOADS[name]
+    if n <= 0 or n >= len(w["sample"]):
+        return w
+    return {"sample": w["sample"][:n], "sample_desc": f"the first {n} structures of: {w['sample_desc']}"}
+
+
+def config_block(name: str) -> dict:
+    return {"workload": WORKLOADS[name]["desc"], "l2": "flushed (256 MB write) between steps; inputs exceed L2"}
+
+
+def cpu_baseline(name: str, n_sample: int = 0):
+    """Times the oracle (all host cores, then one core) on the workload's sample; also
+    returns its inputs and results, against which the GPU path's errors are reported."""
+    import oracle
+    w = sample_of(name, n_sample)
+    spec, sample = build_workload(name, 0, only=w["sample"])
+    theta, qs, (Er, Fr, Wr) = _oracle_inputs(spec, sample)
+    t0 = time.perf_counter()
+    loss3, grad, E, F, W = oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
+    dt = time.perf_counter() - t0
+    cb = {"value": sample.n_atoms / dt, "unit": "atoms/s", "cores": oracle.threads(), "kind": "oracle",
+          "sample": f"{w['sample_desc']}, {sample.n_atoms} atoms, one loss+grad pass, {dt:.1f} s",
+          "cpu_model": _cpu_model()}
+    small = sample.subset(range(min(4, sample.n_struct)))
+    Es, Fs, Ws = Er[:small.n_struct], Fr[:small.n_atoms], Wr[:small.n_struct]
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.loss_grad(spec, theta, qs, small, Es, Fs, Ws, None, LAM)
+        d1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(0)
+    cb["single_core"] = {"value": small.n_atoms / d1, "unit": "atoms/s",
+                         "sample": f"first {small.n_struct} structures of the sample ({small.n_atoms} atoms), {d1:.1f} s"}
+    ref = {"sample": sample, "sample_desc": w["sample_desc"], "theta": theta, "qs": qs, "targets": (Er, Fr, Wr),
+           "out": {"loss3": loss3, "grad": grad, "E": E, "F": F, "W": W}}
+    return cb, ref
+
+
+def oracle_reference(name: str, n_sample: int = 0):
+    """The oracle's inputs and results on the workload's sample (no timing)."""
+    import oracle
+    w = sample_of(name, n_sample)
+    spec, sample = build_workload(name, 0, only=w["sample"])
+    theta, qs, (Er, Fr, Wr) = _oracle_inputs(spec, sample)
+    loss3, grad, E, F, W = oracle.loss_grad(spec, theta, qs, sample, Er, Fr, Wr, None, LAM)
+    return {"sample": sample, "sample_desc": w["sample_desc"], "theta": theta, "qs": qs, "targets": (Er, Fr, Wr),
+            "out": {"loss3": loss3, "grad": grad, "E": E, "F": F, "W": W}}
+
+
 def errors_vs_oracle(spec, ref, device: int):
-    """The GPU path on the oracle's sample and inputs; norm-wise relative errors per
-    quantity plus the largest per-atom energy and force errors."""
+    """The GPU path on the oracle's sample and inputs: norm-wise relative errors per
+    quantity, the largest per-atom energy and force errors, and the worst relative error
+    over the gradient's parameter blocks."""
     import torch
 
-    from paper_2606_19557_gb300 import NEP
+    from paper_2606_19557_gb300 import NEP, param_blocks
     s = ref["sample"]
     nep = NEP(spec, device=device)
     nep.set_structures_batch(s)
@@ -205,17 +265,146 @@ def errors_vs_oracle(spec, ref, device: int):
     Er, Fr, Wr = ref["targets"]
     l3, g = [x.cpu().numpy().astype(np.float64) for x in nep.loss_grad(Er, Fr, Wr, None, LAM)]
     E, F, W = [x.cpu().numpy().astype(np.float64) for x in nep.eval()]
+    nep.close()
     o = ref["out"]
 
     def rel(a, b):
         return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(np.asarray(b).ravel()), 1e-300))
 
+    blocks = {k: rel(g[sl], o["grad"][sl]) for k, sl in param_blocks(spec).items()
+              if np.linalg.norm(o["grad"][sl]) > 0}
+    worst = max(blocks, key=blocks.get)
     nat = s.counts().astype(np.float64)
     return {"E_rel": rel(E, o["E"]), "F_rel": rel(F, o["F"]), "W_rel": rel(W, o["W"]),
             "loss_rel": rel(l3, o["loss3"]), "grad_rel": rel(g, o["grad"]),
+            "grad_block_rel_max": blocks[worst], "grad_block_worst": worst,
             "E_meV_per_atom_max": float(np.max(np.abs(E - o["E"]) / nat) * 1e3),
             "F_meV_per_A_max": float(np.max(np.abs(F - o["F"])) * 1e3),
-            "sample": f"first {s.n_struct} structures ({s.n_atoms} atoms), oracle-computed inputs"}
+            "sample": f"{ref['sample_desc']} ({s.n_atoms} atoms), oracle-computed inputs"}
+
+
+def fp32_peak(device: int):
+    """Measured FP32 FMA throughput of this GPU (the library's probe kernel, 8 blocks of
+    256 threads per SM, 8 independent FMA chains per thread), timed with CUDA events on the
+    probe's stream: one launch (burst) and ~1.5 s of back-to-back launches (sustained),
+    with the SM clock sampled during the sustained loop."""
+    import torch
+
+    from paper_2606_19557_gb300 import fp32_fma_probe
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    st = torch.cuda.Stream()
+    sink = torch.zeros(1, device="cuda")
+    blocks, iters = 8 * n_sm, 1 << 17
+    for _ in range(3):
+        fp32_fma_probe(st, blocks, iters, sink)
+    st.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(st)
+    fl = fp32_fma_probe(st, blocks, iters, sink)
+    e.record(st)
+    e.synchronize()
+    burst = fl / (s.elapsed_time(e) * 1e-3) / 1e12
+    n = max(1, int(1.5 / (fl / (burst * 1e12))))
+    clk = _clock_sampler()
+    time.sleep(0.3 if clk else 0.0)
+    s.record(st)
+    for _ in range(n):
+        fp32_fma_probe(st, blocks, iters, sink)
+    e.record(st)
+    e.synchronize()
+    sustained = n * fl / (s.elapsed_time(e) * 1e-3) / 1e12
+    clocks = _clock_summary(clk, device) if clk else None
+    return {"burst_tflops": burst, "sustained_tflops": sustained, "n_sm": n_sm, "launches": n,
+            "sm_mhz_median": clocks["sm_mhz"] if clocks else None}
+
+
+def setup_model(spec, batch, device: int, args):
+    """Context with the batch cached, parameters set (normalisation from the GPU's own
+    descriptor range), teacher targets from the GPU's eval, and the launch shape."""
+    import torch
+
+    from paper_2606_19557_gb300 import NEP, synth
+    nep = NEP(spec, device=device)
+    t0 = time.perf_counter()
+    nep.set_structures_batch(batch)
+    torch.cuda.synchronize()
+    t_nbr = time.perf_counter() - t0
+    P = nep.P
+    theta = torch.tensor(synth.random_theta(P, 1), dtype=torch.float32, device="cuda")
+    teacher = torch.tensor(synth.random_theta(P, 2), dtype=torch.float32, device="cuda")
+    nep.set_params(theta, torch.ones(nep.n_des, device="cuda"))
+    lo, hi = nep.descriptor_range()
+    span = (hi - lo).double()
+    qs = torch.where(span > 0, 1.0 / torch.where(span > 0, span, torch.ones_like(span)), torch.ones_like(span)).float()
+    nep.set_params(teacher, qs)
+    E_ref, F_ref, W_ref = [x.clone() for x in nep.eval()]
+    nep.set_params(theta, qs)
+    if args.launch:
+        fv, av, fw, fb, aw, ab = [int(x) for x in args.launch.split(",")]
+        nep.set_variant(fv, av)
+        nep.set_launch(fw, fb, aw, ab)
+        shape = nep.launch_shape()
+    else:
+        shape = nep.autotune() if args.autotune else nep.launch_shape()
+    return nep, theta, (E_ref, F_ref, W_ref), shape, t_nbr
+
+
+def time_steps(nep, refs, steps: int, flush, out=None):
+    """Device time (ms) of each of `steps` nep_loss_grad calls, L2 flushed before each."""
+    import torch
+    E_ref, F_ref, W_ref = refs
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        nep.loss_grad(E_ref, F_ref, W_ref, None, LAM, out=out)
+        e.record()
+        e.synchronize()
+        ms.append(s.elapsed_time(e))
+    return ms
+
+
+def kernel_profile(nep, refs, steps: int, flush):
+    """Per-kernel device times (ms, mean over `steps` calls) from a separate pass with the
+    graph's timing events on; the headline steps run without them."""
+    E_ref, F_ref, W_ref = refs
+    nep.set_timing(True)
+    kt = {}
+    try:
+        nep.loss_grad(E_ref, F_ref, W_ref, None, LAM)
+        for _ in range(steps):
+            flush.zero_()
+            nep.loss_grad(E_ref, F_ref, W_ref, None, LAM)
+            for k, v in nep.kernel_times().items():
+                kt.setdefault(k, []).append(v)
+    finally:
+        nep.set_timing(False)
+    return {k: sum(v) / len(v) for k, v in kt.items()}
+
+
+def extra_config(name: str, device: int, args, flush):
+    """Atoms/s, per-kernel times and errors vs the oracle of another configuration."""
+    from paper_2606_19557_gb300 import flops
+    spec, batch = build_workload(name, 0)
+    ref = oracle_reference(name, args.sample_structures) if args.cpu_sample else None
+    nep, _, refs, shape, t_nbr = setup_model(spec, batch, device, args)
+    for _ in range(3):
+        time_steps(nep, refs, 1, flush)
+    ms = time_steps(nep, refs, args.extra_steps, flush)
+    kt = kernel_profile(nep, refs, 3, flush)
+    n_rad, n_ang = nep.num_pairs()
+    fl = flops.per_kernel(spec, batch.n_atoms, n_rad, n_ang)
+    res = {"workload": WORKLOADS[name]["desc"], "atoms": batch.n_atoms, "radial_pairs": n_rad,
+           "angular_pairs": n_ang, "steps": len(ms), "ms_per_step": sum(ms) / len(ms),
+           "atoms_per_s": batch.n_atoms * len(ms) / (sum(ms) / 1e3), "launch_shape": list(shape),
+           "kernel_variant": list(nep.variant()), "kernel_ms": kt,
+           "kernel_tflops": {k: fl[k] / (kt[k] * 1e-3) / 1e12 for k in ("forward", "adjoint") if k in kt},
+           "neighbor_build_ms": 1e3 * t_nbr}
+    nep.close()
+    if ref is not None:
+        res["err_vs_oracle"] = errors_vs_oracle(spec, ref, device)
+    return res
 
 
 def md_eval(steps: int, device: int):
@@ -253,6 +442,7 @@ def md_eval(steps: int, device: int):
         wall.append(time.perf_counter() - t0)
         ev_ms.append(s.elapsed_time(e))
     n_rad, n_ang = nep.num_pairs()
+    nep.close()
     step_s = sum(wall) / steps
     return {"workload": "10 FCC cells x 10,000 atoms, 5 species, rc 6/4 A, n_max 6/6, basis 10/10, "
                         "l_max 4 + 4-body + 5-body, 50 neurons; positions jittered 0.02 A per step",
@@ -262,80 +452,75 @@ def md_eval(steps: int, device: int):
             "neighbor_rebuild_ms": 1e3 * step_s - sum(ev_ms) / steps}
 
 
+def minibatch_epochs(device: int, args, flush):
+    """Mini-batch training epochs on the 1000-structure FCC/BCC batch (16 structures per
+    step, as in the paper's training runs): loss + gradient + AMSGrad per step, epoch
+    driven by the library."""
+    import torch
+    spec, batch = build_workload("fcc_bcc_t1", 0)
+    nep, _, refs, _, _ = setup_model(spec, batch, device, args)
+    nep.set_targets(*refs)
+    nmb = nep.minibatch_setup(args.mb_size)
+    nep.optim_init(lr=1e-3)
+    order = np.arange(nmb)
+    nep.minibatch_epoch(order, LAM)  # warm-up epoch
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rng = np.random.default_rng(0)
+    orders = [rng.permutation(nmb) for _ in range(args.mb_epochs)]
+    s.record(nep.stream)
+    for o in orders:
+        nep.minibatch_epoch(o, LAM)
+    e.record(nep.stream)
+    e.synchronize()
+    ep_ms = s.elapsed_time(e) / args.mb_epochs
+    nep.close()
+    return {"workload": WORKLOADS["fcc_bcc_t1"]["desc"], "batch_structures": args.mb_size, "steps_per_epoch": nmb,
+            "epoch_ms": ep_ms, "atoms_per_s": batch.n_atoms / (ep_ms / 1e3), "epochs_timed": args.mb_epochs,
+            "kernels_per_step": 12}
+
+
 def run_ours(args):
     import torch
 
-    from paper_2606_19557_gb300 import NEP, SCHED_PERSISTENT, SCHED_PLAIN, flops, synth
+    from paper_2606_19557_gb300 import SCHED_PERSISTENT, SCHED_PLAIN, flops
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
     dist = None
+    name = args.config
+    # host work first: the batch, and the oracle leg (before any GPU work of this process)
+    spec, batch = build_workload(name, rank)
+    cb, ref = cpu_baseline(name, args.sample_structures) if (rank == 0 and ws == 1 and args.cpu_sample) \
+        else (None, None)
+    torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    spec, batch = build_workload(rank, args.n_struct)
-    # the CPU baseline runs before any GPU work of this process
-    cb, ref = cpu_baseline(spec, batch, args.cpu_sample) if (rank == 0 and ws == 1 and args.cpu_sample > 0) \
-        else (None, None)
 
-    nep = NEP(spec, device=local)
+    peak = fp32_peak(local)
+    nep, theta, refs, shape, t_nbr = setup_model(spec, batch, local, args)
+    n_rad, n_ang = nep.num_pairs()
+    P = nep.P
+    # neighbour build alone, a second time (the first one above includes allocations)
     t0 = time.perf_counter()
     nep.set_structures_batch(batch)
     torch.cuda.synchronize()
-    t_nbr = time.perf_counter() - t0
-    # neighbour build alone, a second time, on the device clock
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    nep.set_structures_batch(batch)
     t_nbr2 = time.perf_counter() - t0
-    n_rad, n_ang = nep.num_pairs()
-
-    P = nep.P
-    theta = torch.tensor(synth.random_theta(P, 1), dtype=torch.float32, device="cuda")
-    teacher = torch.tensor(synth.random_theta(P, 2), dtype=torch.float32, device="cuda")
-    nep.set_params(theta, torch.ones(nep.n_des, device="cuda"))
-    lo, hi = nep.descriptor_range()
-    span = (hi - lo).double()
-    qs = torch.where(span > 0, 1.0 / torch.where(span > 0, span, torch.ones_like(span)), torch.ones_like(span)).float()
-    nep.set_params(teacher, qs)
-    E_ref, F_ref, W_ref = [x.clone() for x in nep.eval()]
-    nep.set_params(theta, qs)
-    if args.launch:
-        fv, av, fw, fb, aw, ab = [int(x) for x in args.launch.split(",")]
-        nep.set_variant(fv, av)
-        nep.set_launch(fw, fb, aw, ab)
-        shape = nep.launch_shape()
-    else:
-        shape = nep.autotune() if args.autotune else nep.launch_shape()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        nep.loss_grad(E_ref, F_ref, W_ref, None, LAM)
-    nep.set_timing(True)
-    nep.loss_grad(E_ref, F_ref, W_ref, None, LAM)
+    out = (torch.empty(3, dtype=torch.float64, device="cuda"), torch.empty(P, dtype=torch.float32, device="cuda"))
+    time_steps(nep, refs, args.warmup, flush, out)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = _clock_sampler() if rank == 0 else None
     time.sleep(0.3 if clk else 0.0)
-    step_ms, kt = [], {}
-    out = (torch.empty(3, dtype=torch.float64, device="cuda"), torch.empty(P, dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps (outside the events)
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record()
-        nep.loss_grad(E_ref, F_ref, W_ref, None, LAM, out=out)
-        e.record()
-        e.synchronize()
-        step_ms.append(s.elapsed_time(e))
-        for k, v in nep.kernel_times().items():
-            kt.setdefault(k, []).append(v)
+    step_ms = time_steps(nep, refs, args.steps, flush, out)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks = _clock_summary(clk, local) if clk else None
-    nep.set_timing(False)
     tot_ms = sum(step_ms)
     if dist:
         tt = torch.tensor([tot_ms], device="cuda")
@@ -348,8 +533,11 @@ def run_ours(args):
         atoms_all = float(batch.n_atoms)
     value = atoms_all * args.steps / (tot_ms / 1e3)
 
+    # per-kernel times: a separate pass with the graph's timing events on
+    kavg = kernel_profile(nep, refs, 3, flush)
+
     # end to end through the host-buffer entry point: theta H2D, loss3 + grad D2H
-    nep.set_targets(E_ref, F_ref, W_ref)
+    nep.set_targets(*refs)
     th_host = theta.cpu().pin_memory()
     l3h = torch.empty(3, dtype=torch.float64, pin_memory=True)
     gh = torch.empty(P, dtype=torch.float32, pin_memory=True)
@@ -374,85 +562,67 @@ def run_ours(args):
     if args.plain_steps > 0:
         try:
             nep.set_schedule(SCHED_PLAIN)
-            nep.loss_grad(E_ref, F_ref, W_ref, None, LAM)
-            torch.cuda.synchronize()
-            pm = []
-            for _ in range(args.plain_steps):
-                flush.zero_()
-                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s.record()
-                nep.loss_grad(E_ref, F_ref, W_ref, None, LAM)
-                e.record()
-                e.synchronize()
-                pm.append(s.elapsed_time(e))
+            time_steps(nep, refs, 1, flush)
+            pm = time_steps(nep, refs, args.plain_steps, flush)
             pv = batch.n_atoms * len(pm) / (sum(pm) / 1e3)
-            plain = {"value": pv, "unit": "atoms/s", "ms_per_step": sum(pm) / len(pm),
+            plain = {"value": pv, "unit": "atoms/s", "ms_per_step": sum(pm) / len(pm), "steps": len(pm),
                      "speedup": (batch.n_atoms * args.steps / (sum(step_ms) / 1e3)) / pv}
         except Exception as ex:  # reported, not hidden
             plain = {"unavailable": str(ex).splitlines()[0]}
         finally:
             nep.set_schedule(SCHED_PERSISTENT)
+    variant = list(nep.variant())
+    nep.close()
+    del flush
 
-    # mini-batch training epochs (batch of 16 structures per step, as in the paper's
-    # training runs): loss + gradient + AMSGrad per step, library-driven epoch
-    mbe = None
-    if args.mb_epochs > 0:
-        try:
-            nmb = nep.minibatch_setup(args.mb_size)
-            nep.optim_init(lr=1e-3)
-            order = np.arange(nmb)
-            nep.minibatch_epoch(order, LAM)  # warm-up epoch
-            torch.cuda.synchronize()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            rng = np.random.default_rng(0)
-            orders = [rng.permutation(nmb) for _ in range(args.mb_epochs)]
-            s.record(nep.stream)
-            for o in orders:
-                nep.minibatch_epoch(o, LAM)
-            e.record(nep.stream)
-            e.synchronize()
-            ep_ms = s.elapsed_time(e) / args.mb_epochs
-            mbe = {"batch_structures": args.mb_size, "steps_per_epoch": nmb, "epoch_ms": ep_ms,
-                   "atoms_per_s": batch.n_atoms / (ep_ms / 1e3), "epochs_timed": args.mb_epochs,
-                   "kernels_per_step": 12}
-        except Exception as ex:  # reported, not hidden
-            mbe = {"unavailable": str(ex).splitlines()[0]}
-
-    # MD-style evaluation of large cells (E, F, W only), neighbour lists rebuilt every step
-    md = None
-    if args.md_steps > 0 and rank == 0:
-        try:
-            md = md_eval(args.md_steps, local)
-        except Exception as ex:  # reported, not hidden
-            md = {"unavailable": str(ex).splitlines()[0]}
-
-    err = None
-    if ref is not None:
-        try:
-            err = errors_vs_oracle(spec, ref, local)
-        except Exception as ex:  # reported, not hidden
-            err = {"unavailable": str(ex).splitlines()[0]}
-
-    kavg = {k: sum(v) / len(v) for k, v in kt.items()}
     fl = flops.per_kernel(spec, batch.n_atoms, n_rad, n_ang)
     dom = max(("forward", "adjoint"), key=lambda k: kavg.get(k, 0.0))
-    peak = flops.fp32_peak_tflops()
     achieved = fl[dom] / (kavg[dom] * 1e-3) / 1e12
+    pk = peak["sustained_tflops"]
+
+    extras, mbe, md, err = {}, None, None, None
+    if rank == 0 and ws == 1:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for other in [x for x in args.extra.split(",") if x and x != name]:
+            try:
+                extras[other] = extra_config(other, local, args, flush)
+            except Exception as ex:  # reported, not hidden
+                extras[other] = {"unavailable": str(ex).splitlines()[0]}
+        if args.mb_epochs > 0:
+            try:
+                mbe = minibatch_epochs(local, args, flush)
+            except Exception as ex:  # reported, not hidden
+                mbe = {"unavailable": str(ex).splitlines()[0]}
+        if args.md_steps > 0:
+            try:
+                md = md_eval(args.md_steps, local)
+            except Exception as ex:  # reported, not hidden
+                md = {"unavailable": str(ex).splitlines()[0]}
+        if ref is not None:
+            try:
+                err = errors_vs_oracle(spec, ref, local)
+            except Exception as ex:  # reported, not hidden
+                err = {"unavailable": str(ex).splitlines()[0]}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+    cfg = config_block(name)
+    cfg.update({"structures_per_gpu": batch.n_struct, "atoms_per_gpu": batch.n_atoms, "radial_pairs": n_rad,
+                "angular_pairs": n_ang, "launch_shape": list(shape), "kernel_variant": variant,
+                "neighbor_build_ms": 1e3 * t_nbr2})
     res = {
         "metric": METRIC, "value": value, "unit": "atoms/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "structures_per_gpu": batch.n_struct, "atoms_per_gpu": batch.n_atoms,
-                   "radial_pairs": n_rad, "angular_pairs": n_ang, "l2": "flushed (256 MB write) between steps",
-                   "launch_shape": list(shape), "kernel_variant": list(nep.variant()),
-                   "neighbor_build_ms": 1e3 * t_nbr2},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": kernel_traffic(dom, batch.n_atoms), "traffic_unit": "bytes",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                     "frac": achieved / pk, "traffic": kernel_traffic(name, dom, batch.n_atoms),
+                     "traffic_unit": "bytes",
+                     "peak_source": f"measured: FP32 FMA probe kernel, {peak['n_sm']} SMs, sustained over "
+                                    f"{peak['launches']} launches, SM clock median {peak['sm_mhz_median']} MHz "
+                                    f"(burst {peak['burst_tflops']:.1f} TFLOP/s)",
+                     "achieved_source": "flops.py algorithmic count / kernel time (CUDA events in a separate "
+                                        "instrumented pass of 3 steps)"},
         "kernel_ms": kavg,
         "e2e": {"value": e2e_value, "unit": "atoms/s", "h2d_bytes_per_step": 4 * P, "d2h_bytes_per_step": 24 + 4 * P},
         "gpu_launches": 10 * args.steps,  # kernels of one loss + gradient graph
@@ -460,8 +630,10 @@ def run_ours(args):
         "cpu_baseline": cb,
         "err_vs_oracle": err,
         "plain_form": plain,
+        "extra_configs": extras,
         "minibatch_epoch": mbe,
         "md_eval": md,
+        "fp32_peak": peak,
         "wall_s": wall,
     }
     print(json.dumps(res))
@@ -475,9 +647,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-struct", dest="n_struct", type=int, default=1000)
-    ap.add_argument("--cpu-sample", dest="cpu_sample", type=int, default=150)
-    ap.add_argument("--plain-steps", dest="plain_steps", type=int, default=2)
+    ap.add_argument("--config", default="scale_t5", choices=sorted(WORKLOADS))
+    ap.add_argument("--extra", default="fcc_bcc_t1,alloy_t4", help="other workloads measured beside the headline")
+    ap.add_argument("--extra-steps", dest="extra_steps", type=int, default=10)
+    ap.add_argument("--no-oracle", dest="cpu_sample", action="store_false")
+    ap.add_argument("--sample-structures", dest="sample_structures", type=int, default=0,
+                    help="cut the oracle sample to its first N structures (0: the whole sample)")
+    ap.add_argument("--plain-steps", dest="plain_steps", type=int, default=5)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--mb-epochs", dest="mb_epochs", type=int, default=2)
     ap.add_argument("--mb-size", dest="mb_size", type=int, default=16)

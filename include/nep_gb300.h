@@ -313,6 +313,17 @@ int nep_set_timing(nep_ctx *ctx, int on);
 int nep_kernel_times(nep_ctx *ctx, float *ms, int *n_io);
 const char *nep_kernel_name(int k);
 
+/* FP32 fused multiply-add throughput probe (measurement helper, no counterpart in the
+ * paper): queues on cuda_stream (a cudaStream_t; NULL = legacy default stream) one
+ * kernel of `blocks` blocks x 256 threads, each thread running 8 independent chains of
+ * `iters` dependent FMAs.  *flops receives the kernel's floating-point operations
+ * (2 per FMA); divided by the kernel's duration (CUDA events on the same stream) it is
+ * the measured FP32 peak that the per-atom kernels' roofline fractions use.  Use a grid
+ * of several blocks per SM (e.g. 8 x the SM count).  sink_dev: device float (never
+ * written in practice; it keeps the arithmetic live).  Errors: NEP_EINVAL (blocks < 1,
+ * iters not a positive multiple of 16, NULL pointers), NEP_ECUDA (launch failed). */
+int nep_fp32_fma_probe(void *cuda_stream, int blocks, int64_t iters, float *sink_dev, double *flops);
+
 /* Last error message of this context (or of the latest failed nep_create when ctx is NULL). */
 const char *nep_last_error(const nep_ctx *ctx);
 

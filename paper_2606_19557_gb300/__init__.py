@@ -115,6 +115,7 @@ def load_library():
             "nep_kernel_times": (I, [P, P, ctypes.POINTER(I)]),
             "nep_kernel_name": (ctypes.c_char_p, [I]),
             "nep_last_error": (ctypes.c_char_p, [P]),
+            "nep_fp32_fma_probe": (I, [P, I, I64, P, ctypes.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -433,6 +434,40 @@ class NEP:
         n = ctypes.c_int(KERNEL_COUNT)
         self._check(self.lib.nep_kernel_times(self.h, arr, ctypes.byref(n)))
         return {self.lib.nep_kernel_name(k).decode(): float(arr[k]) for k in range(n.value)}
+
+
+def param_blocks(spec) -> dict:
+    """Slices of theta (layout of include/nep_gb300.h) by parameter block: w0, b0 and w1 of
+    each species, the shared b1, and c_R and c_A of each ordered species pair."""
+    T, NN = int(spec.n_types), int(spec.n_neu)
+    NR, KR = spec.n_max_R + 1, spec.basis_R + 1
+    NA, KA = spec.n_max_A + 1, spec.basis_A + 1
+    ND = NR + NA * (spec.l_max + spec.has_4b + spec.has_5b)
+    out, o = {}, 0
+    for name, size in (("w0", NN * ND), ("b0", NN), ("w1", NN)):
+        for t in range(T):
+            out[f"{name}[{t}]"] = slice(o, o + size)
+            o += size
+    out["b1"] = slice(o, o + 1)
+    o += 1
+    for name, size in (("cR", NR * KR), ("cA", NA * KA)):
+        for a in range(T):
+            for b in range(T):
+                out[f"{name}[{a},{b}]"] = slice(o, o + size)
+                o += size
+    return out
+
+
+def fp32_fma_probe(stream, blocks: int, iters: int, sink) -> float:
+    """Queues the library's FP32 FMA throughput kernel on `stream` (a torch.cuda.Stream)
+    and returns its floating-point operation count (nep_fp32_fma_probe)."""
+    lib = load_library()
+    fl = ctypes.c_double(0.0)
+    rc = lib.nep_fp32_fma_probe(ctypes.c_void_p(stream.cuda_stream), int(blocks), int(iters),
+                                ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fl))
+    if rc != NEP_OK:
+        raise NepError(rc, "nep_fp32_fma_probe failed")
+    return fl.value
 
 
 class NEPFunction:

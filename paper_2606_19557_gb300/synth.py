@@ -284,22 +284,45 @@ def batch_alloy(seed: int = 3, n_struct: int = 5000, n_types: int = 4, n_lo: int
     return _assemble(structs, n_types)
 
 
+def _scale_structure(seed: int, s: int, n_struct: int, n_types: int, big_atoms: int):
+    """Structure s of the scale batch, from its own random stream (seed, s): structures
+    s < n_struct have log-uniform sizes in [2, 2000], the rest are large FCC cells."""
+    rng = np.random.default_rng([seed, s])
+    if s >= n_struct:
+        return make_structure(rng, big_atoms, "fcc", 0.03, rng.uniform(0.05, 0.3), n_types)
+    n = int(round(math.exp(rng.uniform(math.log(2), math.log(2000)))))
+    if n <= 2:
+        return make_structure(rng, 2, "dimer", 0.0, 0.0, n_types)
+    kind = "fcc" if rng.random() < 0.5 else "bcc"
+    u = rng.random()
+    sigma = 0.5 if u < 0.2 else rng.uniform(0.05, 0.3)
+    return make_structure(rng, n, kind, 0.03, sigma, n_types, slab=(0.2 <= u < 0.3))
+
+
+def _scale_chunk(args):
+    seed, idx, n_struct, n_types, big_atoms = args
+    return [_scale_structure(seed, int(s), n_struct, n_types, big_atoms) for s in idx]
+
+
 def batch_scale(seed: int = 5, n_struct: int = 20000, n_types: int = 5, n_big: int = 10,
-                big_atoms: int = 10000) -> Batch:
-    """Sizes log-uniform in [2, 2000] (2 atoms: a dimer in a 12 A cubic cell) plus large FCC cells."""
-    rng = np.random.default_rng(seed)
-    structs = []
-    for _ in range(n_struct):
-        n = int(round(math.exp(rng.uniform(math.log(2), math.log(2000)))))
-        if n <= 2:
-            structs.append(make_structure(rng, 2, "dimer", 0.0, 0.0, n_types))
-            continue
-        kind = "fcc" if rng.random() < 0.5 else "bcc"
-        u = rng.random()
-        sigma = 0.5 if u < 0.2 else rng.uniform(0.05, 0.3)
-        structs.append(make_structure(rng, n, kind, 0.03, sigma, n_types, slab=(0.2 <= u < 0.3)))
-    for _ in range(n_big):
-        structs.append(make_structure(rng, big_atoms, "fcc", 0.03, rng.uniform(0.05, 0.3), n_types))
+                big_atoms: int = 10000, only=None, workers: int = 0) -> Batch:
+    """Sizes log-uniform in [2, 2000] (2 atoms: a dimer in a 12 A cubic cell) plus n_big
+    large FCC cells (indices n_struct .. n_struct + n_big - 1).
+
+    Every structure draws from its own stream (seed, index), so `only` (a list of
+    indices) builds exactly those structures of the full batch, in that order, without
+    the others.  workers > 1 spreads the structures over that many spawned processes."""
+    idx = np.arange(n_struct + n_big) if only is None else np.asarray(only, np.int64)
+    if workers > 1 and idx.size > 256:
+        import concurrent.futures
+        import multiprocessing
+        parts = np.array_split(idx, 4 * workers)
+        ctx = multiprocessing.get_context("spawn")
+        with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+            chunks = ex.map(_scale_chunk, [(seed, p, n_struct, n_types, big_atoms) for p in parts])
+            structs = [st for ch in chunks for st in ch]
+    else:
+        structs = _scale_chunk((seed, idx, n_struct, n_types, big_atoms))
     return _assemble(structs, n_types)
 
 

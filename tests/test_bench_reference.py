@@ -13,7 +13,7 @@ def _run(extra_env=None):
     env = dict(os.environ)
     env.update(extra_env or {})
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
-                        "--cpu-sample", "2"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+                        "--sample-structures", "2"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     return [ln for ln in r.stdout.splitlines() if ln.strip()]
 
@@ -26,9 +26,9 @@ def test_reference_line():
     assert d["unit"] == "atoms/s" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
     assert d["ms_per_step"] > 0 and d["dtype"] == "f64" and d["data"] == "synthetic"
-    assert d["config"]["workload"].startswith("fcc_bcc_t1") and d["config"]["sample_structures"] == 2
+    assert d["config"]["workload"].startswith("scale_t5")
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "2 structures" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "first 2 structures" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _gradcheck import assert_grad_close
 from paper_2606_19557_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -142,7 +143,7 @@ def test_neighbor_edge_geometries():
     l3, g = nep.loss_grad(Er, Fr, Wr, None, (1.0, 2.0, 0.3))
     l3o, go = oracle.loss_grad(spec, theta, qs, batch, Er, Fr, Wr, None, (1.0, 2.0, 0.3))[:2]
     np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
-    assert rel(g.cpu().numpy(), go) < TOL
+    assert_grad_close(g.cpu().numpy(), go, spec, TOL)
 
 
 # ----------------------------------------------------------------------------- forward
@@ -215,7 +216,7 @@ def test_loss_and_gradient(name):
     l3, g = l3.cpu().numpy(), g.cpu().numpy()
     l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, c.batch, c.E_ref, c.F_ref, c.W_ref, hw, lam)[:2]
     np.testing.assert_allclose(l3, l3o, rtol=TOL)
-    assert rel(g, go) < TOL
+    assert_grad_close(g, go, c.spec, TOL)
 
 
 @pytest.mark.parametrize("name", ["fcc_bcc_t1", "alloy_t4", "scale_t5"])
@@ -228,7 +229,7 @@ def test_backward_vjp(name):
     c.nep.eval()
     g = c.nep.backward(dE, dF, dW).cpu().numpy()
     go = oracle.backward(c.spec, c.theta, c.qs, c.batch, dE, dF, dW)
-    assert rel(g, go) < TOL
+    assert_grad_close(g, go, c.spec, TOL)
 
 
 def test_autograd_function_matches_oracle():
@@ -244,7 +245,7 @@ def test_autograd_function_matches_oracle():
         + 0.1 * (((W - Wr) / cnt[:, None]) ** 2).sum() / (9 * W.shape[0])
     L.backward()
     go = oracle.loss_grad(c.spec, c.theta, c.qs, c.batch, c.E_ref, c.F_ref, c.W_ref, None, (1.0, 1.0, 0.1))[1]
-    assert rel(th.grad.cpu().numpy(), go) < TOL
+    assert_grad_close(th.grad.cpu().numpy(), go, c.spec, TOL)
 
 
 # ----------------------------------------------------------------------------- properties
@@ -343,7 +344,7 @@ def test_plain_form_matches_oracle(name):
         c.nep.set_schedule(SCHED_PERSISTENT)
     l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, c.batch, c.E_ref, c.F_ref, c.W_ref)[:2]
     np.testing.assert_allclose(l3, l3o, rtol=TOL)
-    assert rel(g, go) < TOL
+    assert_grad_close(g, go, c.spec, TOL)
 
 
 def test_shards_sum_to_full_batch():
@@ -375,7 +376,7 @@ def test_shards_sum_to_full_batch():
         l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, sub, c.E_ref[idx], c.F_ref[a_idx], c.W_ref[idx],
                                    hw[idx], lam)[:2]
         np.testing.assert_allclose(l3s.cpu().numpy(), l3o, rtol=TOL)
-        assert rel(gs.cpu().numpy(), go) < TOL
+        assert_grad_close(gs.cpu().numpy(), go, c.spec, TOL)
         nep.close()
     l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, b, c.E_ref, c.F_ref, c.W_ref, hw, lam)[:2]
     np.testing.assert_allclose(L, l3o, rtol=TOL)
@@ -416,7 +417,7 @@ def test_update_positions_matches_fresh_context():
     l3, g = nep.loss_grad(Er, Fr, Wr)
     l3o, go = oracle.loss_grad(spec, theta, qs, b2, Er, Fr, Wr)[:2]
     np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
-    assert rel(g.cpu().numpy(), go) < TOL
+    assert_grad_close(g.cpu().numpy(), go, spec, TOL)
 
 
 
@@ -479,7 +480,7 @@ def test_update_positions_cells_kept_and_minibatches():
         lo, go = oracle.loss_grad(spec, theta, qs.double().numpy(), b2.subset(np.arange(s0, s1)), Er[s0:s1],
                                   Fr[a0:a1], Wr[s0:s1], None, lam)[:2]
         np.testing.assert_allclose(la.cpu().numpy(), lo, rtol=TOL)
-        assert rel(ga.cpu().numpy(), go) < TOL
+        assert_grad_close(ga.cpu().numpy(), go, spec, TOL)
     nep.close()
 
 @pytest.mark.parametrize("name", ["nep44_t16", "nep88_t16"])
@@ -503,10 +504,10 @@ def test_table2_sixteen_species_models(name):
     l3, g = nep.loss_grad(Er, Fr, Wr, None, lam)
     l3o, go = oracle.loss_grad(spec, theta, qs, b, Er, Fr, Wr, None, lam)[:2]
     np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
-    assert rel(g.cpu().numpy(), go) < TOL
+    assert_grad_close(g.cpu().numpy(), go, spec, TOL)
     nep.autotune()  # every variant that fits the 16-species shared-memory tail
     g2 = nep.loss_grad(Er, Fr, Wr, None, lam)[1].cpu().numpy()
-    assert rel(g2, go) < TOL
+    assert_grad_close(g2, go, spec, TOL)
 
 
 
@@ -543,5 +544,5 @@ def test_model_variants(name):
     l3, g = nep.loss_grad(Er, Fr, Wr, None, (1.0, 1.0, 0.1))
     l3o, go = oracle.loss_grad(spec, theta, qs, b, Er, Fr, Wr, None, (1.0, 1.0, 0.1))[:2]
     np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
-    assert rel(g.cpu().numpy(), go) < TOL
+    assert_grad_close(g.cpu().numpy(), go, spec, TOL)
     nep.close()
