@@ -186,7 +186,23 @@ int nep_loss_grad(nep_ctx *ctx, const double *E_ref_dev, const float *F_ref_dev,
  * Errors: NEP_EINVAL (negative or non-finite). */
 int nep_set_loss_normalizers(nep_ctx *ctx, double N_s, double N_a, double N_s_V);
 
-/* Vector-Jacobian product for autograd: grad_dev [P] = d/dtheta of
+/* Ziegler-Biersack-Littmark short-range repulsion added to the energies, forces and
+ * virials (Sec. "Training": TorchNEP supports ZBL as NEP does, citing the ZBL
+ * treatise; the paper prints no formula).  Pair term, from the treatise's universal
+ * screening function:
+ *   V(r) = (e^2/(4 pi eps0)) Z_i Z_j phi(r/a) / r,  a = 0.8854 a_0 / (Z_i^0.23 + Z_j^0.23),
+ *   phi(x) = 0.1818 e^{-3.2x} + 0.5099 e^{-0.9423x} + 0.2802 e^{-0.4029x} + 0.02817 e^{-0.2016x},
+ * times the switch f_s = 1 for r < r1, (1 + cos(pi (r - r1)/(r2 - r1)))/2 for r1 <= r < r2,
+ * 0 beyond; each ordered neighbour pair (i, j) adds f_s V / 2 to E_i.  The term has no
+ * trainable parameter: it shifts E, F, W and the loss residuals, not the form of the
+ * gradient.  Z_host [n_types] (host, atomic numbers in (0, 200)), 0 <= r1 < r2 <= rc_R;
+ * r2 = 0 switches the term off (the default).  Takes effect from the next call.
+ * Errors: NEP_EINVAL (values out of range), NEP_ENOMEM, NEP_ECUDA. */
+int nep_set_zbl(nep_ctx *ctx, float r1, float r2, const float *Z_host);
+
+/* Vector-Jacobian product for autograd (the analytic route of Sec. "Training
+ * efficiency": the parameter gradient through the descriptor-coordinate Jacobian,
+ * without a second-order autograd pass): grad_dev [P] = d/dtheta of
  *   sum_s dE_s E_s + sum_i dF_i . F_i + sum_s dW_s : W_s
  * with cotangents dE_dev [n_struct] f64, dF_dev [N_a*3] f32, dW_dev [n_struct*9] f64.
  * Uses the per-atom state of the latest nep_eval, which must have run with the

@@ -34,7 +34,8 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("n_types", ctypes.c_int), ("rc_R", ctypes.c_double), ("rc_A", ctypes.c_double),
                 ("n_max_R", ctypes.c_int), ("n_max_A", ctypes.c_int), ("basis_R", ctypes.c_int),
                 ("basis_A", ctypes.c_int), ("l_max", ctypes.c_int), ("has_4b", ctypes.c_int),
-                ("has_5b", ctypes.c_int), ("n_neu", ctypes.c_int)]
+                ("has_5b", ctypes.c_int), ("n_neu", ctypes.c_int), ("zbl", ctypes.c_int),
+                ("zbl_r1", ctypes.c_double), ("zbl_r2", ctypes.c_double), ("zbl_Z", ctypes.c_double * 16)]
 
 
 def build(force: bool = False) -> str:
@@ -83,9 +84,13 @@ def _load():
 
 
 def _cfg(spec) -> _Cfg:
+    """The spec's model keys; an optional attribute zbl = (r1, r2, Z per species) adds the
+    ZBL short-range term."""
+    z = getattr(spec, "zbl", None)
+    Z = (ctypes.c_double * 16)(*([float(x) for x in z[2]] if z else []))
     return _Cfg(int(spec.n_types), float(spec.rc_R), float(spec.rc_A), int(spec.n_max_R), int(spec.n_max_A),
                 int(spec.basis_R), int(spec.basis_A), int(spec.l_max), int(spec.has_4b), int(spec.has_5b),
-                int(spec.n_neu))
+                int(spec.n_neu), 1 if z else 0, float(z[0]) if z else 0.0, float(z[1]) if z else 0.0, Z)
 
 
 def _p(a: np.ndarray):

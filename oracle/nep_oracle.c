@@ -63,6 +63,11 @@ typedef struct {
     int n_max_R, n_max_A, basis_R, basis_A;
     int l_max, has_4b, has_5b;
     int n_neu;
+    /* optional ZBL short-range term (zbl != 0): switch from zbl_r1 to zbl_r2, atomic
+     * numbers of the species */
+    int zbl;
+    double zbl_r1, zbl_r2;
+    double zbl_Z[16];
 } orc_cfg;
 
 /* ------------------------------------------------------------------ sizes */
@@ -99,6 +104,10 @@ int orc_num_descriptors(const orc_cfg *c) { return get_sizes(c).ND; }
 
 static int cfg_ok(const orc_cfg *c) {
     if (c->n_types < 1 || c->n_max_R < 0 || c->n_max_A < 0 || c->basis_R < 0 || c->basis_A < 0) return 0;
+    if (c->zbl) {
+        if (c->n_types > 16 || !(c->zbl_r1 >= 0) || !(c->zbl_r2 > c->zbl_r1) || c->zbl_r2 > c->rc_R) return 0;
+        for (int t = 0; t < c->n_types; t++) if (!(c->zbl_Z[t] > 0)) return 0;
+    }
     if (c->l_max < 0 || c->l_max > 4 || c->n_neu < 1) return 0;
     if (c->has_4b && c->l_max < 2) return 0;
     if (c->has_5b && c->l_max < 1) return 0;
@@ -647,6 +656,43 @@ static void atom_adjoint(const orc_cfg *cfg, const sizes *z, const double *th, c
     free(R); free(dR); free(Am); free(dAm); free(Mm); free(dMm); free(dA); free(dM);
 }
 
+/* ---------------------------------------------------------- ZBL short-range term
+ * Sec. "Training" lets TorchNEP add, as NEP does, the Ziegler-Biersack-Littmark
+ * screened Coulomb repulsion (the paper cites the ZBL treatise and prints no formula).
+ * Taken from that treatise: the universal screening function
+ *   phi(x) = 0.1818 e^{-3.2 x} + 0.5099 e^{-0.9423 x} + 0.2802 e^{-0.4029 x} + 0.02817 e^{-0.2016 x},
+ *   x = r / a,  a = 0.8854 a_0 / (Z_i^0.23 + Z_j^0.23)  (a_0 the Bohr radius),
+ *   V(r) = (e^2 / (4 pi eps_0)) Z_i Z_j phi(r / a) / r.
+ * Reading of NEP's switch (not in the paper): V is multiplied by
+ *   f_s = 1 (r < r1),  (1 + cos(pi (r - r1)/(r2 - r1)))/2 (r1 <= r < r2),  0 (r >= r2),
+ * and every ordered neighbour pair (i, j) adds f_s V / 2 to E_i, so a pair of atoms
+ * contributes f_s V in all.  Returns e = f_s V and de = d(f_s V)/dr. */
+static void zbl_pair(const orc_cfg *cfg, int ti, int tj, double r, double *e, double *de) {
+    const double ke = 14.399645;     /* e^2 / (4 pi eps_0) in eV A */
+    const double a0 = 0.52917721;    /* Bohr radius in A */
+    const double zi = cfg->zbl_Z[ti], zj = cfg->zbl_Z[tj];
+    const double a = 0.8854 * a0 / (pow(zi, 0.23) + pow(zj, 0.23));
+    const double c[4] = {0.1818, 0.5099, 0.2802, 0.02817}, d[4] = {3.2, 0.9423, 0.4029, 0.2016};
+    double phi = 0.0, dphi = 0.0; /* phi(r/a) and its r-derivative */
+    for (int k = 0; k < 4; k++) {
+        double t = c[k] * exp(-d[k] * r / a);
+        phi += t;
+        dphi -= d[k] / a * t;
+    }
+    double v = ke * zi * zj * phi / r;
+    double dv = ke * zi * zj * (dphi / r - phi / (r * r));
+    double f = 0.0, fp = 0.0;
+    if (r < cfg->zbl_r1) {
+        f = 1.0;
+    } else if (r < cfg->zbl_r2) {
+        double w = cfg->zbl_r2 - cfg->zbl_r1, t = M_PI * (r - cfg->zbl_r1) / w;
+        f = 0.5 * (1.0 + cos(t));
+        fp = -0.5 * sin(t) * M_PI / w;
+    }
+    *e = f * v;
+    *de = f * dv + fp * v;
+}
+
 /* ---------------------------------------------------------- structure pass
  * mode 0: E, F, W (and optionally q).  mode 1: also the adjoint with the loss
  * cotangents (eb_s, fb, Wb_s) given by the caller.  Returns 0 or -1 on a bad cell. */
@@ -678,6 +724,16 @@ static int structure_pass(const orc_cfg *cfg, const sizes *z, const double *th, 
             double G[3];
             pair_gradient(z, qs, &w, np, p, G);
             int j = pi[p].j;
+            if (cfg->zbl) {
+                const double *d = pi[p].d;
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                if (r < cfg->zbl_r2) {
+                    double e, de;
+                    zbl_pair(cfg, type_s[i], type_s[j], r, &e, &de);
+                    Es += 0.5 * e;
+                    for (int a = 0; a < 3; a++) G[a] += 0.5 * de * d[a] / r;
+                }
+            }
             for (int a = 0; a < 3; a++) {
                 F[3 * i + a] += G[a];
                 F[3 * j + a] -= G[a];

@@ -91,6 +91,7 @@ def load_library():
             "nep_descriptor_range": (I, [P, P, P]),
             "nep_loss_grad": (I, [P, P, P, P, P, D, D, D, P, P]),
             "nep_backward": (I, [P, P, P, P, P]),
+            "nep_set_zbl": (I, [P, ctypes.c_float, ctypes.c_float, P]),
             "nep_set_loss_normalizers": (I, [P, D, D, D]),
             "nep_set_targets": (I, [P, P, P, P, P]),
             "nep_loss_grad_host": (I, [P, P, D, D, D, P, P]),
@@ -160,6 +161,9 @@ class NEP:
         self.n_struct = 0
         self.n_atoms = 0
         self._keep = []
+        zbl = getattr(spec, "zbl", None)
+        if zbl:
+            self.set_zbl(*zbl)
 
     # ------------------------------------------------------------------ plumbing
     def _check(self, rc: int):
@@ -287,6 +291,15 @@ class NEP:
                    float(lam[2]), _ptr(loss3), _ptr(grad))
         self._refs = (Er, Fr, Wr, hw)
         return loss3, grad
+
+    def set_zbl(self, r1: float, r2: float, Z=None):
+        """ZBL short-range term with switch radii r1 < r2 and atomic numbers Z [n_types]
+        (nep_set_zbl); r2 = 0 switches it off."""
+        if r2 == 0:
+            self._check(self.lib.nep_set_zbl(self.h, 0.0, 0.0, None))
+            return
+        z = (ctypes.c_float * len(Z))(*[float(x) for x in Z])
+        self._check(self.lib.nep_set_zbl(self.h, float(r1), float(r2), ctypes.cast(z, ctypes.c_void_p)))
 
     def set_loss_normalizers(self, N_s: float = 0.0, N_a: float = 0.0, N_s_V: float = 0.0):
         """Global N_s, N_a, N_s^V for a shard of a larger batch (0 = this batch's own)."""

@@ -685,6 +685,37 @@ int nep_set_loss_normalizers(nep_ctx *c, double Ns, double Na, double NsV) {
     return NEP_OK;
 }
 
+int nep_set_zbl(nep_ctx *c, float r1, float r2, const float *Z) {
+    if (!c) return NEP_EINVAL;
+    if (r2 == 0.0f) {
+        c->zbl_r1 = c->zbl_r2 = 0.0f;
+        drop_graphs(c);
+        c->state_valid = false;
+        return NEP_OK;
+    }
+    if (!Z) return c->fail(NEP_EINVAL, "ZBL: atomic numbers missing");
+    if (!(r1 >= 0.0f) || !(r2 > r1) || !(r2 <= c->cfg.rc_R))
+        return c->fail(NEP_EINVAL, "ZBL: the switch radii must satisfy 0 <= r1 < r2 <= rc_R");
+    for (int t = 0; t < c->T; ++t)
+        if (!(Z[t] > 0.0f) || !(Z[t] < 200.0f)) return c->fail(NEP_EINVAL, "ZBL: atomic numbers must be in (0, 200)");
+    const double ke = 14.399645, a0 = 0.52917721;  // e^2/(4 pi eps0) in eV A, Bohr radius in A
+    std::vector<float> tab((size_t)c->T * c->T * 2);
+    for (int i = 0; i < c->T; ++i)
+        for (int j = 0; j < c->T; ++j) {
+            const double zi = Z[i], zj = Z[j];
+            tab[2 * (i * c->T + j)] = (float)(ke * zi * zj);
+            tab[2 * (i * c->T + j) + 1] = (float)((std::pow(zi, 0.23) + std::pow(zj, 0.23)) / (0.8854 * a0));
+        }
+    CK(cudaSetDevice(c->dev));
+    if (c->zbl_tab.ensure<float>((int64_t)tab.size())) return c->fail(NEP_ENOMEM, "ZBL table");
+    CK(cudaMemcpy(c->zbl_tab.ptr, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
+    c->zbl_r1 = r1;
+    c->zbl_r2 = r2;
+    drop_graphs(c);
+    c->state_valid = false;
+    return NEP_OK;
+}
+
 int nep_backward(nep_ctx *c, const double *dE, const float *dF, const double *dW, float *grad) {
     if (!c) return NEP_EINVAL;
     int rc = ready(c);

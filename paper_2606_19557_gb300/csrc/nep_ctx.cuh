@@ -133,6 +133,10 @@ struct Ctx {
     bool have_targets = false, tgt_has_hw = false;
     DevBuf hostbuf_theta;             // device copy target of nep_loss_grad_host
 
+    // ZBL short-range term (nep_set_zbl): per species pair e^2/(4 pi eps0) Z_i Z_j and 1/a_ij
+    DevBuf zbl_tab;
+    float zbl_r1 = 0.0f, zbl_r2 = 0.0f;  // zbl_r2 = 0: off
+
     // loss normalisers (0 = this batch's own N_s, N_a, N_s^V); set for one shard of a batch
     double ov_Ns = 0.0, ov_Na = 0.0, ov_NsV = 0.0;
     int64_t struct_parts = 0;  // loss partials written by the latest k_struct launch (one per structure)

@@ -29,9 +29,12 @@ struct Shape {
     static constexpr int NC = NCR + NCA;
 };
 
-// Offsets (in floats) of the padded parameter buffer.
+__host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
+
+// Offsets (in floats) of the padded parameter buffer.  cRp / cAp repeat the coefficients
+// with each (n) row padded to a multiple of 4 floats and 16-byte aligned, for float4 loads.
 struct ParOff {
-    int64_t w0, w0t, b0, w1, b1, cR, cA, scale, total;
+    int64_t w0, w0t, b0, w1, b1, cR, cA, scale, cRp, cAp, total;
 };
 
 __host__ __device__ inline ParOff par_offsets(int T, int NN, int NR, int KR, int NA, int KA) {
@@ -45,7 +48,9 @@ __host__ __device__ inline ParOff par_offsets(int T, int NN, int NR, int KR, int
     o.cR = o.b1 + 4;                           // [T][T][NR][KR]
     o.cA = o.cR + (int64_t)T * T * NR * KR;    // [T][T][NA][KA]
     o.scale = o.cA + (int64_t)T * T * NA * KA; // [ND]
-    o.total = o.scale + ND;
+    o.cRp = (o.scale + ND + 3) & ~(int64_t)3;  // [T][T][NR][round4(KR)]
+    o.cAp = o.cRp + (int64_t)T * T * NR * round4(KR);  // [T][T][NA][round4(KA)]
+    o.total = o.cAp + (int64_t)T * T * NA * round4(KA);
     return o;
 }
 
@@ -64,6 +69,8 @@ struct AtomArgs {
     const float *par;       // padded parameters (ParOff layout)
     int T, NN;
     float inv_rcR, inv_rcA, rc2A;
+    const float *zbl;       // [T][T][2]: e^2/(4 pi eps0) Z_i Z_j and 1/a_ij of the ZBL term
+    float zbl_r1, zbl_r2;   // ZBL switch radii (zbl_r2 = 0: no ZBL term)
     // forward outputs
     float *E_atom;          // [Na]
     float *F_own;           // [Na*3]   sum over own pairs of G
@@ -476,6 +483,33 @@ __device__ __forceinline__ void l2_project(const float *X, float *p) {
 
 __device__ __forceinline__ float sym_trace_prod(const float *A, const float *B) {  // tr(A B)
     return A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + 2.0f * (A[3] * B[3] + A[4] * B[4] + A[5] * B[5]);
+}
+
+// Ziegler-Biersack-Littmark screened Coulomb term of one pair (Sec. "Training": ZBL
+// support as in NEP; the universal screening function of the ZBL treatise):
+//   V = kzz phi(r/a) / r,  phi(x) = 0.1818 e^{-3.2x} + 0.5099 e^{-0.9423x} + 0.2802 e^{-0.4029x}
+//       + 0.02817 e^{-0.2016x},  kzz = e^2/(4 pi eps0) Z_i Z_j,  a = 0.8854 a_0/(Z_i^0.23 + Z_j^0.23),
+// times the switch f_s = 1 below r1, (1 + cos(pi (r - r1)/(r2 - r1)))/2 up to r2.  Called for
+// r < r2 only; e = f_s V, de = d(f_s V)/dr.
+__device__ __forceinline__ void zbl_term(float r, float kzz, float inv_a, float r1, float r2, float &e, float &de) {
+    const float x = r * inv_a;
+    const float t0 = 0.1818f * expf(-3.2f * x), t1 = 0.5099f * expf(-0.9423f * x);
+    const float t2 = 0.2802f * expf(-0.4029f * x), t3 = 0.02817f * expf(-0.2016f * x);
+    const float phi = (t0 + t1) + (t2 + t3);
+    const float dphi = -inv_a * ((3.2f * t0 + 0.9423f * t1) + (0.4029f * t2 + 0.2016f * t3));
+    const float rinv = 1.0f / r;
+    const float v = kzz * phi * rinv;
+    const float dv = kzz * (dphi - phi * rinv) * rinv;
+    float f = 1.0f, fp = 0.0f;
+    if (r >= r1) {
+        const float w = r2 - r1;
+        float sn, cs;
+        sincosf(PI_F * (r - r1) / w, &sn, &cs);
+        f = 0.5f * (1.0f + cs);
+        fp = -0.5f * sn * PI_F / w;
+    }
+    e = f * v;
+    de = f * dv + fp * v;
 }
 
 // 1/|d| for a pair displacement (hardware reciprocal square root, <= 2 ulp).

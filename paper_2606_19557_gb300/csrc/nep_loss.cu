@@ -62,9 +62,24 @@ __global__ void k_expand(ExpandArgs x) {
         const int n = (int)((r / x.KAP) % x.NAP);
         const int64_t ab = r / ((int64_t)x.KAP * x.NAP);
         if (n < x.nA && k < x.kA) v = x.theta[ccA + (ab * x.nA + n) * x.kA + k];
-    } else {
-        const int vc = x.inv[e - po.scale];
+    } else if (e < po.cRp) {
+        const int64_t r = e - po.scale;
+        const int vc = r < NDP ? x.inv[r] : -1;
         if (vc >= 0) v = x.qscale[vc];
+    } else if (e < po.cAp) {
+        const int K4 = round4(x.KRP);
+        const int64_t r = e - po.cRp;
+        const int k = (int)(r % K4);
+        const int n = (int)((r / K4) % x.NRP);
+        const int64_t ab = r / ((int64_t)K4 * x.NRP);
+        if (n < x.nR && k < x.kR) v = x.theta[ccR + (ab * x.nR + n) * x.kR + k];
+    } else {
+        const int K4 = round4(x.KAP);
+        const int64_t r = e - po.cAp;
+        const int k = (int)(r % K4);
+        const int n = (int)((r / K4) % x.NAP);
+        const int64_t ab = r / ((int64_t)K4 * x.NAP);
+        if (n < x.nA && k < x.kA) v = x.theta[ccA + (ab * x.nA + n) * x.kA + k];
     }
     x.par[e] = v;
 }
@@ -557,6 +572,9 @@ static AtomArgs atom_args(Ctx *c) {
     a.inv_rcR = 1.0f / c->cfg.rc_R;
     a.inv_rcA = 1.0f / c->cfg.rc_A;
     a.rc2A = c->cfg.rc_A * c->cfg.rc_A;
+    a.zbl = c->zbl_r2 > 0.0f ? c->zbl_tab.as<float>() : nullptr;
+    a.zbl_r1 = c->zbl_r1;
+    a.zbl_r2 = c->zbl_r2;
     a.E_atom = c->E_atom.as<float>();
     a.F_own = c->F_own.as<float>();
     a.W_atom = c->W_atom.as<float>();

@@ -18,71 +18,90 @@
 //   reverse through the network (tanh', tanh'') -> per-atom vectors for the network
 //   gradient, abar = dJ/dq; then dJ/dc (radial part factorised over species sums,
 //   angular part per pair).
-// FP32 arithmetic with FP32 accumulation inside an atom; no floating-point atomics:
-// species runs of different groups are flushed into the warp's accumulators one group
-// after the other, so results are bit-reproducible for a fixed launch shape.
+//
+// Work layout.  Per-pair quantities are computed one pair per lane; reductions over
+// the pairs of an atom go through rows staged in shared memory and read by lanes that
+// own outputs, in a fixed order:
+//   * angular moments and their JVP: lanes own (l, m);
+//   * radial species sums S^b_k (more than one species): lanes own k and walk their
+//     atom's rows, which come sorted by neighbour species, adding each species run into
+//     the atom's S^b (one species: every lane sums its own pairs, one reduction per atom);
+//   * angular coefficient gradient: all 32 lanes own (n, k-range) tiles of the current
+//     (t_i, t_j) block and walk the rows of every atom of the batch; a species change
+//     flushes the tile into the warp's shared accumulator.
+// Per-atom matrices that every pair of an atom reads (dE/dA, dJ/dA) are stored [lm][n]
+// with n padded to a multiple of 4, and the coefficient rows c[n][k] are 16-byte-aligned
+// copies in the parameter buffer, so both are read with 128-bit loads.
+// FP32 arithmetic with FP32 accumulation inside an atom; no floating-point atomics, so
+// results are bit-reproducible for a fixed launch shape.
 #pragma once
 
 #include "nep_ctx.cuh"
 
 namespace nep {
 
-// ============================================================================= layouts
+// ============================================================================= helpers
 
-template <class S, int SW>
-struct FwdL {
-    static constexpr int G = 32 / SW;
-    static constexpr int SGS = (S::NA + 3) & ~3;  // rows of g_n padded to float4
-    static constexpr int NLMO = (L3 + SW - 1) / SW;  // (l, m) outputs owned per lane
-    struct Atom {
-        float q[S::ND];
-        float qt[S::ND];
-        float b[S::ND];
-        float A[S::NA * L3];
-        float Ah[S::NA * L3];
-        float G4[S::NA * 5];
-    };
-    Atom at[G];
-    __align__(16) float sg[G][SW][SGS];
-    float sY[G][SW][25];
-    // runtime tail (floats): u[G][NN], Sr[G][T][KR], beta[G][T][KR], cw[T][NC]
-    __host__ __device__ static size_t tail(int T, int NN) {
-        return (size_t)G * NN + 2 * (size_t)G * T * S::KR + (size_t)T * S::NC;
-    }
-    __host__ __device__ static size_t bytes(int T, int NN) {
-        return ((sizeof(FwdL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
-    }
-};
+// v[i] for a compile-time array of length K; the index is clamped so that unrolled,
+// compile-time-dead terms never name an element past the end.
+template <int K>
+__device__ __forceinline__ float at_k(const float *v, int i) { return v[i < K ? i : K - 1]; }
 
-template <class S, int SW>
-struct AdjL {
-    static constexpr int G = 32 / SW;
-    static constexpr int SGS = (S::NA + 3) & ~3;
-    static constexpr int NLMO = (L3 + SW - 1) / SW;
-    struct Atom {
-        float b[S::ND];
-        float ab[S::ND];
-        float dqt[S::ND];
-        float A[S::NA * L3];
-        float dA[S::NA * L3];  // dA, then dJ/dA in place
-        float Ah[S::NA * L3];
-        float G4[S::NA * 5];
-        float H4[S::NA * 5];
-        float ad[S::NA];  // sum_m A_n1m dA_n1m (read by every l = 1 lane before dA is overwritten)
-    };
-    Atom at[G];
-    __align__(16) float sg[G][SW][SGS];
-    __align__(16) float sgp[G][SW][SGS];
-    float sY[G][SW][25];
-    float sP[G][SW][25];
-    // runtime tail: u[G][NN], Sr[G][T][2 KR], accR[T][NCR], accA[T][NCA], cw[T][NC]
-    __host__ __device__ static size_t tail(int T, int NN) {
-        return (size_t)G * NN + 2 * (size_t)G * T * S::KR + (size_t)T * (S::NCR + S::NCA) + (size_t)T * S::NC;
+// g_n = sum_k c[n][k] f_k, n < N, from 16-byte-aligned rows of round4(K) floats.
+template <int N, int K>
+__device__ __forceinline__ void contract_c(const float *c, const float *f, float *g) {
+    constexpr int K4 = round4(K);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        const float4 *r = reinterpret_cast<const float4 *>(c + n * K4);
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < K4 / 4; ++q) {
+            const float4 v = __ldg(r + q);
+            if (4 * q + 0 < K) s += v.x * at_k<K>(f, 4 * q + 0);
+            if (4 * q + 1 < K) s += v.y * at_k<K>(f, 4 * q + 1);
+            if (4 * q + 2 < K) s += v.z * at_k<K>(f, 4 * q + 2);
+            if (4 * q + 3 < K) s += v.w * at_k<K>(f, 4 * q + 3);
+        }
+        g[n] = s;
     }
-    __host__ __device__ static size_t bytes(int T, int NN) {
-        return ((sizeof(AdjL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
+}
+
+// g_n = sum_k c[n][k] f_k and gp_n = sum_k c[n][k] fp_k from the same rows.
+template <int N, int K>
+__device__ __forceinline__ void contract_c2(const float *c, const float *f, const float *fp, float *g, float *gp) {
+    constexpr int K4 = round4(K);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        const float4 *r = reinterpret_cast<const float4 *>(c + n * K4);
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < K4 / 4; ++q) {
+            const float4 v = __ldg(r + q);
+            const float cv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (4 * q + e < K) {
+                    s0 += cv[e] * at_k<K>(f, 4 * q + e);
+                    s1 += cv[e] * at_k<K>(fp, 4 * q + e);
+                }
+            }
+        }
+        g[n] = s0;
+        gp[n] = s1;
     }
-};
+}
+
+// Stores v[0..N) as a row of round4(N) floats (zero padding) with 128-bit stores.
+template <int N>
+__device__ __forceinline__ void store_row4(float *dst, const float *v) {
+    constexpr int N4 = round4(N);
+    float4 *d = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int q = 0; q < N4 / 4; ++q)
+        d[q] = make_float4(4 * q + 0 < N ? at_k<N>(v, 4 * q + 0) : 0.0f, 4 * q + 1 < N ? at_k<N>(v, 4 * q + 1) : 0.0f,
+                           4 * q + 2 < N ? at_k<N>(v, 4 * q + 2) : 0.0f, 4 * q + 3 < N ? at_k<N>(v, 4 * q + 3) : 0.0f);
+}
 
 // Loads a padded row of N floats (N a multiple of 4, 16-byte aligned) from shared memory.
 template <int N>
@@ -149,14 +168,139 @@ __device__ __forceinline__ void flush_groups(float *v, float *dst, int K, bool h
     for (int k = 0; k < V; ++k) v[k] = 0.0f;
 }
 
+// Species sums over an atom's radial neighbours, several species: the group's lanes each
+// computed the C values of one pair and staged them in rows[SW][C + 1] (the species bits in
+// the last slot); lane sl owns columns sl, sl + SW, ... and walks the cnt rows in order,
+// adding each species run into S[b][0..C).  v / bcur carry the open run across chunks.
+template <int C, int SW>
+__device__ __forceinline__ void walk_species_rows(const float (*rows)[C + 1], int cnt, int sl, float *S, float *v,
+                                                  int &bcur) {
+    constexpr int RC = (C + SW - 1) / SW;
+    for (int pp = 0; pp < cnt; ++pp) {
+        const float *row = rows[pp];
+        const int t = __float_as_int(row[C]);
+        if (t != bcur) {
+            if (bcur >= 0) {
+#pragma unroll
+                for (int j = 0; j < RC; ++j)
+                    if (sl + j * SW < C) S[bcur * C + sl + j * SW] += v[j];
+            }
+#pragma unroll
+            for (int j = 0; j < RC; ++j) v[j] = 0.0f;
+            bcur = t;
+        }
+#pragma unroll
+        for (int j = 0; j < RC; ++j)
+            if (sl + j * SW < C) v[j] += row[sl + j * SW];
+    }
+}
+
+template <int C, int SW>
+__device__ __forceinline__ void close_species_run(int sl, float *S, const float *v, int bcur) {
+    constexpr int RC = (C + SW - 1) / SW;
+    if (bcur >= 0) {
+#pragma unroll
+        for (int j = 0; j < RC; ++j)
+            if (sl + j * SW < C) S[bcur * C + sl + j * SW] += v[j];
+    }
+}
+
+// The l = 2 moments (m = -2..2) of channel n from a [lm][n] matrix with row stride NAP.
+template <int NAP>
+__device__ __forceinline__ void l2_block(const float *M, int n, float *a) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) a[m] = M[(3 + m) * NAP + n];
+}
+
+// ============================================================================= layouts
+
+template <class S, int SW>
+struct FwdL {
+    static constexpr int G = 32 / SW;
+    static constexpr int NAP = round4(S::NA);
+    static constexpr int NLMO = (L3 + SW - 1) / SW;  // (l, m) outputs owned per lane
+    struct __align__(16) Atom {
+        float A[L3 * NAP];   // A_nlm at [lm][n]
+        float Ah[L3 * NAP];  // dE_i/dA_nlm at [lm][n]
+        float q[S::ND];
+        float qt[S::ND];
+        float b[S::ND];
+        float G4[S::NA * 5];
+    };
+    struct __align__(16) Mom {
+        float g[G][SW][NAP];  // g^A_n of each lane's pair
+        float Y[G][SW][L3];
+    };
+    struct __align__(16) Rad {
+        float f[G][SW][S::KR + 1];  // f_k, then the species bits
+    };
+    Atom at[G];
+    union {
+        Mom m;
+        Rad r;
+    } st;
+    // runtime tail (floats): u[G][NN], Sr[G][T][KR], beta[G][T][KR]
+    __host__ __device__ static size_t tail(int T, int NN) { return (size_t)G * NN + 2 * (size_t)G * T * S::KR; }
+    __host__ __device__ static size_t bytes(int T, int NN) {
+        return ((sizeof(FwdL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
+    }
+};
+
+template <class S, int SW>
+struct AdjL {
+    static constexpr int G = 32 / SW;
+    static constexpr int NAP = round4(S::NA);
+    static constexpr int NLMO = (L3 + SW - 1) / SW;
+    struct __align__(16) Atom {
+        float A[L3 * NAP];   // A_nlm at [lm][n]
+        float D[L3 * NAP];   // dA (the JVP), then dJ/dA in place
+        float Ah[L3 * NAP];  // dE_i/dA
+        float b[S::ND];
+        float ab[S::ND];
+        float dqt[S::ND];
+        float G4[S::NA * 5];
+        float H4[S::NA * 5];
+        float ad[S::NA];  // sum_m A_n1m dA_n1m (read by every l = 1 lane before dA is overwritten)
+    };
+    struct __align__(16) Jvp {
+        float g[G][SW][NAP];   // g^A_n
+        float gp[G][SW][NAP];  // (r^.lambda) dg^A_n/dr
+        float Y[G][SW][L3];
+        float P[G][SW][L3];    // grad Y_lm . p, p the part of lambda / r normal to r^
+    };
+    struct __align__(16) Cg {
+        float2 ab[G][SW][S::NA];  // (alpha_n, beta_n) of each lane's pair
+        float2 ff[G][SW][S::KA];  // (f_k, f'_k)
+        int t[G][SW];             // species of the neighbour
+    };
+    struct __align__(16) Rad {
+        float f[G][SW][2 * S::KR + 1];  // f_k, (r^.lambda) f'_k, then the species bits
+    };
+    Atom at[G];
+    union {
+        Jvp j;
+        Cg c;
+        Rad r;
+    } st;
+    // runtime tail: u[G][NN], Sr[G][T][2 KR], accR[T][NCR], accA[T][NCA]
+    __host__ __device__ static size_t tail(int T, int NN) {
+        return (size_t)G * NN + 2 * (size_t)G * T * S::KR + (size_t)T * (S::NCR + S::NCA);
+    }
+    __host__ __device__ static size_t bytes(int T, int NN) {
+        return ((sizeof(AdjL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
+    }
+};
+
 // ============================================================================= forward
 
 template <class S, int SW, int VAR>
 __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forward(AtomArgs a) {
     using L = FwdL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
-    constexpr int G = L::G, SGS = L::SGS, NLMO = L::NLMO;
+    constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
+    constexpr int KR4 = round4(KR), KA4 = round4(KA);
     constexpr int VR = pow2ceil(KR);
+    constexpr int RC = (KR + SW - 1) / SW;
     extern __shared__ __align__(16) float smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int grp = lane / SW, sl = lane % SW;
@@ -164,9 +308,8 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
     float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
     L &sm = *reinterpret_cast<L *>(base_ptr);
     float *tail = base_ptr + sizeof(L) / sizeof(float);
-    float *Sr = tail + G * NN + grp * T * KR;                // [T][KR] of this group
-    float *beta = tail + G * NN + G * T * KR + grp * T * KR; // [T][KR] of this group
-    float *cw = tail + G * NN + 2 * G * T * KR;              // [T][NCR] | [T][NCA], current species
+    float *Sr = tail + G * NN + grp * T * KR;                 // [T][KR] of this group
+    float *beta = tail + G * NN + G * T * KR + grp * T * KR;  // [T][KR] of this group
 
     const int w = blockIdx.x * (blockDim.x >> 5) + wib;
     const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
@@ -177,7 +320,6 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
     const float *w1 = a.par + po.w1;
     const float b1 = a.par[po.b1];
     const float *scale = a.par + po.scale;
-    int cur_t = -1;
 
     for (int bp = wbeg; bp < wend;) {
         int ti, nb, i;
@@ -186,15 +328,8 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
         const int bp0 = bp;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
-        if (ti != cur_t) {  // species-sorted work: rare
-            __syncwarp();
-            for (int e = lane; e < T * S::NCR; e += 32) cw[e] = a.par[po.cR + (size_t)ti * T * S::NCR + e];
-            for (int e = lane; e < T * S::NCA; e += 32) cw[T * S::NCR + e] = a.par[po.cA + (size_t)ti * T * S::NCA + e];
-            cur_t = ti;
-            __syncwarp();
-        }
-        const float *cRi = cw;
-        const float *cAi = cw + T * S::NCR;
+        const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;  // [b][n][KR4]
+        const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;  // [b][n][KA4]
         const int64_t beg = a.nbr_off[i];
         const int nRad = act ? (int)(a.nbr_off[i + 1] - beg) : 0;
         const int nAng = act ? a.n_ang[i] : 0;
@@ -224,31 +359,25 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                 const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                 const float rinv = inv_norm(r2);
                 const float r = r2 * rinv;
-                float f[KA];
+                float f[KA], g[NA];
                 basis_val<KA>(r, a.inv_rcA, f);
-                const float *c = cAi + tj * S::NCA;
-#pragma unroll
-                for (int n = 0; n < NA; ++n) {
-                    float g = 0.0f;
-#pragma unroll
-                    for (int kk = 0; kk < KA; ++kk) g += c[n * KA + kk] * f[kk];
-                    sm.sg[grp][sl][n] = g;
-                }
+                contract_c<NA, KA>(cAi + tj * NA * KA4, f, g);
+                store_row4<NA>(sm.st.m.g[grp][sl], g);
                 float Y[L3];
                 ylm_val(pd.x * rinv, pd.y * rinv, pd.z * rinv, Y);
 #pragma unroll
-                for (int lm = 0; lm < L3; ++lm) sm.sY[grp][sl][lm] = Y[lm];
+                for (int lm = 0; lm < L3; ++lm) sm.st.m.Y[grp][sl][lm] = Y[lm];
             }
             __syncwarp();
             const int cnt = min(SW, nAng - c0);
             for (int pp = 0; pp < cnt; ++pp) {
-                float gv[SGS];
-                load_row<SGS>(sm.sg[grp][pp], gv);
+                float gv[NAP];
+                load_row<NAP>(sm.st.m.g[grp][pp], gv);
 #pragma unroll
                 for (int j = 0; j < NLMO; ++j) {
                     const int lm = sl + j * SW;
                     if (lm < L3) {
-                        const float y = sm.sY[grp][pp][lm];
+                        const float y = sm.st.m.Y[grp][pp][lm];
 #pragma unroll
                         for (int n = 0; n < NA; ++n) accA[j][n] += gv[n] * y;
                     }
@@ -259,62 +388,49 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
 #pragma unroll
         for (int j = 0; j < NLMO; ++j) {
             const int lm = sl + j * SW;
-            if (lm < L3) {
-#pragma unroll
-                for (int n = 0; n < NA; ++n) at.A[n * L3 + lm] = accA[j][n];
-            }
+            if (lm < L3) store_row4<NA>(at.A + lm * NAP, accA[j]);
         }
 
         // ---------------------------------------------------------------- radial species sums S^b_k
         for (int e = sl; e < T * KR; e += SW) Sr[e] = 0.0f;
         __syncwarp();
-        {
+        if (T == 1) {  // one species: every lane sums its own pairs, one reduction per atom
             float v[VR];
 #pragma unroll
             for (int k = 0; k < VR; ++k) v[k] = 0.0f;
+            float4 nxr = pair_or_zero(prs, sl, nRad);
+            for (int c0 = 0; c0 < maxR; c0 += SW) {
+                const int k = c0 + sl;
+                const float4 pd = nxr;
+                nxr = pair_or_zero(prs, k + SW, nRad);
+                if (k < nRad) {
+                    const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
+                    float f[KR];
+                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) v[kk] += f[kk];
+                }
+            }
+            if (__any_sync(FULL, nRad > 0)) flush_groups<VR, SW>(v, Sr, KR, nRad > 0, lane, false);
+        } else {
+            float v[RC];
             int bcur = -1;
             float4 nxr = pair_or_zero(prs, sl, nRad);
             for (int c0 = 0; c0 < maxR; c0 += SW) {
                 const int k = c0 + sl;
-                const bool valid = k < nRad;
                 const float4 pd = nxr;
                 nxr = pair_or_zero(prs, k + SW, nRad);
-                int tj = -1;
-                float f[KR];
-#pragma unroll
-                for (int kk = 0; kk < KR; ++kk) f[kk] = 0.0f;
-                if (valid) {
-                    tj = pair_t(pd);
+                if (k < nRad) {
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
+                    float *row = sm.st.r.f[grp][sl];
+                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, row);
+                    row[KR] = __int_as_float(pair_t(pd));
                 }
-                if (T == 1) {  // one species: no runs to track
-                    if (valid) {
-#pragma unroll
-                        for (int kk = 0; kk < KR; ++kk) v[kk] += f[kk];
-                    }
-                    continue;
-                }
-                unsigned rem = group_bits<SW>(__ballot_sync(FULL, valid), lane);
-                while (__any_sync(FULL, rem != 0)) {
-                    const bool has = rem != 0;
-                    const int leader = has ? __ffs(rem) - 1 : 0;
-                    int bsp = __shfl_sync(FULL, tj, (lane & ~(SW - 1)) + leader);
-                    if (!has) bsp = bcur;
-                    const bool inb = valid && has && tj == bsp;
-                    rem &= ~group_bits<SW>(__ballot_sync(FULL, inb), lane);
-                    const bool change = bsp != bcur;
-                    if (__any_sync(FULL, change && bcur >= 0))
-                        flush_groups<VR, SW>(v, Sr + (bcur >= 0 ? bcur : 0) * KR, KR, bcur >= 0, lane, false);
-                    bcur = bsp;
-                    if (inb) {
-#pragma unroll
-                        for (int kk = 0; kk < KR; ++kk) v[kk] += f[kk];
-                    }
-                }
+                __syncwarp();
+                walk_species_rows<KR, SW>(sm.st.r.f[grp], min(SW, nRad - c0), sl, Sr, v, bcur);
+                __syncwarp();
             }
-            if (T == 1 && nRad > 0) bcur = 0;
-            if (__any_sync(FULL, bcur >= 0)) flush_groups<VR, SW>(v, Sr + (bcur >= 0 ? bcur : 0) * KR, KR, bcur >= 0, lane, false);
+            close_species_run<KR, SW>(sl, Sr, v, bcur);
         }
         __syncwarp();
 
@@ -322,28 +438,32 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
         for (int n = sl; n < NR; n += SW) {
             float q = 0.0f;
             for (int bb = 0; bb < T; ++bb) {
+                const float *cr = cRi + (bb * NR + n) * KR4;
 #pragma unroll
-                for (int kk = 0; kk < KR; ++kk) q += cRi[bb * S::NCR + n * KR + kk] * Sr[bb * KR + kk];
+                for (int kk = 0; kk < KR; ++kk) q += __ldg(cr + kk) * Sr[bb * KR + kk];
             }
             at.q[n] = q;
         }
         for (int e = sl; e < 4 * NA; e += SW) {
             const int n = e % NA, l = e / NA + 1;
-            const float *Ar = at.A + n * L3 + l * l - 1;
             float s2 = 0.0f;
-            for (int m = 0; m < 2 * l + 1; ++m) s2 += Ar[m] * Ar[m];
+            for (int m = 0; m < 2 * l + 1; ++m) {
+                const float v = at.A[(l * l - 1 + m) * NAP + n];
+                s2 += v * v;
+            }
             at.q[NR + (l - 1) * NA + n] = s2;
         }
         for (int n = sl; n < NA; n += SW) {
-            const float *An = at.A + n * L3;
-            float Mt[6], M2[6], pr[5];
-            l2_matrix(An + 3, Mt);
+            float a2[5], Mt[6], M2[6], pr[5];
+            l2_block<NAP>(at.A, n, a2);
+            l2_matrix(a2, Mt);
             sym_prod(Mt, Mt, M2);
             at.q[NR + 4 * NA + n] = KAPPA_REAL * sym_trace_prod(M2, Mt);
             l2_project(M2, pr);
 #pragma unroll
             for (int m = 0; m < 5; ++m) at.G4[n * 5 + m] = 3.0f * KAPPA_REAL * pr[m];
-            const float q1 = An[0] * An[0] + An[1] * An[1] + An[2] * An[2];
+            const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
+            const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
             at.q[NR + 5 * NA + n] = q1 * q1;
         }
         __syncwarp();
@@ -408,26 +528,30 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
             const int lm = sl + j * SW;
             if (lm < L3) {
                 const int l = l_of_lm(lm);
+                float ah[NA];
 #pragma unroll
                 for (int n = 0; n < NA; ++n) {
-                    const float av = at.A[n * L3 + lm];
-                    float ah = 2.0f * at.b[NR + (l - 1) * NA + n] * av;
-                    if (l == 2) ah += at.b[NR + 4 * NA + n] * at.G4[n * 5 + (lm - 3)];
-                    if (l == 1) ah += at.b[NR + 5 * NA + n] * 4.0f * at.q[NR + n] * av;
-                    at.Ah[n * L3 + lm] = ah;
+                    const float av = at.A[lm * NAP + n];
+                    float x = 2.0f * at.b[NR + (l - 1) * NA + n] * av;
+                    if (l == 2) x += at.b[NR + 4 * NA + n] * at.G4[n * 5 + (lm - 3)];
+                    if (l == 1) x += at.b[NR + 5 * NA + n] * 4.0f * at.q[NR + n] * av;
+                    ah[n] = x;
                 }
+                store_row4<NA>(at.Ah + lm * NAP, ah);
             }
         }
         for (int e = sl; e < T * KR; e += SW) {
             const int bb = e / KR, kk = e - bb * KR;
             float s2 = 0.0f;
 #pragma unroll
-            for (int n = 0; n < NR; ++n) s2 += at.b[n] * cRi[bb * S::NCR + n * KR + kk];
+            for (int n = 0; n < NR; ++n) s2 += at.b[n] * __ldg(cRi + (bb * NR + n) * KR4 + kk);
             beta[e] = s2;
         }
         __syncwarp();
 
         // ---------------------------------------------------------------- pair gradients
+        const float *zbl_ti = a.zbl ? a.zbl + (size_t)ti * T * 2 : nullptr;
+        float Ez = 0.0f;  // ZBL energy of this lane's pairs (half of each pair term)
         float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
         float W9[9];
 #pragma unroll
@@ -443,29 +567,24 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
             const float rinv = inv_norm(r2);
             const float r = r2 * rinv;
             const float ux = pd.x * rinv, uy = pd.y * rinv, uz = pd.z * rinv;
-            float f[KA], fp[KA];
+            float f[KA], fp[KA], g[NA], gp[NA];
             basis_val_der<KA>(r, a.inv_rcA, f, fp);
-            const float *c = cAi + tj * S::NCA;
-            float g[NA], gp[NA];
-#pragma unroll
-            for (int n = 0; n < NA; ++n) {
-                float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-                for (int kk = 0; kk < KA; ++kk) {
-                    s0 += c[n * KA + kk] * f[kk];
-                    s1 += c[n * KA + kk] * fp[kk];
-                }
-                g[n] = s0;
-                gp[n] = s1;
-            }
+            contract_c2<NA, KA>(cAi + tj * NA * KA4, f, fp, g, gp);
             float srad = 0.0f, Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
             ylm_each(ux, uy, uz, [&](int lm, float Y, float gx, float gy, float gz) {
+                const float4 *h4 = reinterpret_cast<const float4 *>(at.Ah + lm * NAP);
                 float a1 = 0.0f, a2 = 0.0f;
 #pragma unroll
-                for (int n = 0; n < NA; ++n) {
-                    const float ah = at.Ah[n * L3 + lm];
-                    a1 += ah * g[n];
-                    a2 += ah * gp[n];
+                for (int q = 0; q < NAP / 4; ++q) {
+                    const float4 h = h4[q];
+                    const float hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (4 * q + e < NA) {
+                            a1 += hv[e] * at_k<NA>(g, 4 * q + e);
+                            a2 += hv[e] * at_k<NA>(gp, 4 * q + e);
+                        }
+                    }
                 }
                 srad += a2 * Y;
                 Vx += a1 * gx;
@@ -478,6 +597,12 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                 const float *be = beta + tj * KR;
 #pragma unroll
                 for (int kk = 0; kk < KR; ++kk) srad += be[kk] * fpr[kk];
+            }
+            if (r < a.zbl_r2) {
+                float ez, dez;
+                zbl_term(r, zbl_ti[2 * tj], zbl_ti[2 * tj + 1], a.zbl_r1, a.zbl_r2, ez, dez);
+                Ez += 0.5f * ez;
+                srad += 0.5f * dez;
             }
             const float uv = ux * Vx + uy * Vy + uz * Vz;
             const float Gx = srad * ux + (Vx - ux * uv) * rinv;
@@ -506,6 +631,12 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
             float s2 = 0.0f;
 #pragma unroll
             for (int kk = 0; kk < KR; ++kk) s2 += be[kk] * fp[kk];
+            if (r2 * rinv < a.zbl_r2) {
+                float ez, dez;
+                zbl_term(r2 * rinv, zbl_ti[2 * tj], zbl_ti[2 * tj + 1], a.zbl_r1, a.zbl_r2, ez, dez);
+                Ez += 0.5f * ez;
+                s2 += 0.5f * dez;
+            }
             s2 *= rinv;
             const float Gx = s2 * pd.x, Gy = s2 * pd.y, Gz = s2 * pd.z;
             a.G[p] = make_float4(Gx, Gy, Gz, 0.0f);
@@ -518,7 +649,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
         }
         {
             float v[16] = {Fx, Fy, Fz, W9[0], W9[1], W9[2], W9[3], W9[4], W9[5], W9[6], W9[7], W9[8],
-                           0.0f, 0.0f, 0.0f, 0.0f};
+                           Ez, 0.0f, 0.0f, 0.0f};
             group_reduce_scatter<16, SW>(v, lane);
             const int base = grs_base<16, SW>(lane);
             if (act && (lane & GRS<16, SW>::DUP_MASK) == 0) {
@@ -527,13 +658,16 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                     const int idx = base + o;
                     if (idx < 3) a.F_own[(size_t)i * 3 + idx] = v[o];
                     else if (idx < 12) a.W_atom[(size_t)i * 9 + idx - 3] = v[o];
+                    else if (idx == 12) a.E_atom[i] = Ei + v[o];
                 }
             }
         }
         if (act) {
-            if (sl == 0) a.E_atom[i] = Ei;
             for (int e = sl; e < ND; e += SW) a.st_qt[(size_t)wi * ND + e] = at.qt[e];
-            for (int e = sl; e < NA * L3; e += SW) a.st_A[(size_t)wi * NA * L3 + e] = at.A[e];
+            for (int e = sl; e < L3 * NA; e += SW) {  // [lm][n], n packed
+                const int lm = e / NA, n = e - lm * NA;
+                a.st_A[(size_t)wi * NA * L3 + e] = at.A[lm * NAP + n];
+            }
             if (a.q_raw)
                 for (int e = sl; e < ND; e += SW) a.q_raw[(size_t)i * ND + e] = at.q[e];
         }
@@ -548,9 +682,13 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
     using L = AdjL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int NCR = S::NCR, NCA = S::NCA, NC = S::NC;
-    constexpr int G = L::G, NLMO = L::NLMO;
+    constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
+    constexpr int KR4 = round4(KR), KA4 = round4(KA);
     constexpr int VR2 = pow2ceil(2 * KR);
-    constexpr int VA = pow2ceil(NCA);
+    constexpr int RC2 = (2 * KR + SW - 1) / SW;
+    // angular coefficient-gradient tiles: lane -> (n, k-range of width TW), 32 lanes
+    constexpr int NKT = 32 / NA;
+    constexpr int TW = (KA + NKT - 1) / NKT;
     extern __shared__ __align__(16) float smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int grp = lane / SW, sl = lane % SW;
@@ -558,10 +696,11 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
     float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
     L &sm = *reinterpret_cast<L *>(base_ptr);
     float *tail = base_ptr + sizeof(L) / sizeof(float);
-    float *Sr = tail + G * NN + grp * T * 2 * KR;         // [T][2 KR] S^b_k | S'^b_k of this group
-    float *accR = tail + G * NN + G * T * 2 * KR;         // [T][NCR] (warp)
-    float *accA = accR + T * NCR;                         // [T][NCA] (warp)
-    float *cw = accA + T * NCA;                           // [T][NCR] | [T][NCA], current species
+    float *Sr = tail + G * NN + grp * T * 2 * KR;  // [T][2 KR] S^b_k | S'^b_k of this group
+    float *accR = tail + G * NN + G * T * 2 * KR;  // [T][NCR] (warp)
+    float *accA = accR + T * NCR;                  // [T][NCA] (warp)
+    const int tn = lane % NA, tk0 = (lane / NA) * TW;
+    const bool tile_own = lane / NA < NKT && tk0 < KA;
 
     const int w = blockIdx.x * (blockDim.x >> 5) + wib;
     const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
@@ -572,6 +711,20 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
     const float *scale = a.par + po.scale;
 
     int cur_t = -1;
+    // open (t_i, t_j) tile of the angular coefficient gradient, carried across batches
+    float X[TW];
+#pragma unroll
+    for (int jj = 0; jj < TW; ++jj) X[jj] = 0.0f;
+    int xb = -1;
+    auto close_tile = [&]() {
+        if (xb >= 0 && tile_own) {
+#pragma unroll
+            for (int jj = 0; jj < TW; ++jj)
+                if (tk0 + jj < KA) accA[xb * NCA + tn * KA + tk0 + jj] += X[jj];
+        }
+#pragma unroll
+        for (int jj = 0; jj < TW; ++jj) X[jj] = 0.0f;
+    };
     auto flush_slot = [&](int t) {
         float *dst = a.cpart + (size_t)(w + t) * T * NC;
         for (int bb = 0; bb < T; ++bb) {
@@ -589,16 +742,17 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         bp += nb;
         if (ti != cur_t) {
             __syncwarp();
+            close_tile();
+            xb = -1;
+            __syncwarp();
             if (cur_t >= 0) flush_slot(cur_t);
             for (int e = lane; e < T * NCR; e += 32) accR[e] = 0.0f;
             for (int e = lane; e < T * NCA; e += 32) accA[e] = 0.0f;
-            for (int e = lane; e < T * NCR; e += 32) cw[e] = a.par[po.cR + (size_t)ti * T * NCR + e];
-            for (int e = lane; e < T * NCA; e += 32) cw[T * NCR + e] = a.par[po.cA + (size_t)ti * T * NCA + e];
             cur_t = ti;
             __syncwarp();
         }
-        const float *cRi = cw;
-        const float *cAi = cw + T * NCR;
+        const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;
+        const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;
         const int s = a.struct_of[i];
         const int64_t beg = a.nbr_off[i];
         const int nRad = act ? (int)(a.nbr_off[i + 1] - beg) : 0;
@@ -613,8 +767,10 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         }
 
         // ---------------------------------------------------------------- state of the forward pass
-#pragma unroll
-        for (int e = sl; e < NA * L3; e += SW) at.A[e] = a.st_A[(size_t)wi * NA * L3 + e];
+        for (int e = sl; e < L3 * NA; e += SW) {  // stored [lm][n], n packed
+            const int lm = e / NA, n = e - lm * NA;
+            at.A[lm * NAP + n] = a.st_A[(size_t)wi * NA * L3 + e];
+        }
         for (int mu = lane; mu < NN; mu += 32) {
             const float wo = w1[ti * NN + mu];
 #pragma unroll
@@ -640,9 +796,9 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
             for (int g = 0; g < G; ++g) sm.at[g].b[v] = e[g] * sc;
         }
         for (int n = sl; n < NA; n += SW) {
-            const float *An = at.A + n * L3;
-            float Mt[6], M2[6], pr[5];
-            l2_matrix(An + 3, Mt);
+            float a2[5], Mt[6], M2[6], pr[5];
+            l2_block<NAP>(at.A, n, a2);
+            l2_matrix(a2, Mt);
             sym_prod(Mt, Mt, M2);
             l2_project(M2, pr);
 #pragma unroll
@@ -654,18 +810,19 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
             const int lm = sl + j * SW;
             if (lm < L3) {
                 const int l = l_of_lm(lm);
+                float ah[NA];
 #pragma unroll
                 for (int n = 0; n < NA; ++n) {
-                    const float *An = at.A + n * L3;
-                    const float av = An[lm];
-                    float ah = 2.0f * at.b[NR + (l - 1) * NA + n] * av;
-                    if (l == 2) ah += at.b[NR + 4 * NA + n] * at.G4[n * 5 + (lm - 3)];
+                    const float av = at.A[lm * NAP + n];
+                    float x = 2.0f * at.b[NR + (l - 1) * NA + n] * av;
+                    if (l == 2) x += at.b[NR + 4 * NA + n] * at.G4[n * 5 + (lm - 3)];
                     if (l == 1) {
-                        const float q1 = An[0] * An[0] + An[1] * An[1] + An[2] * An[2];
-                        ah += at.b[NR + 5 * NA + n] * 4.0f * q1 * av;
+                        const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
+                        x += at.b[NR + 5 * NA + n] * 4.0f * (x0 * x0 + x1 * x1 + x2 * x2) * av;
                     }
-                    at.Ah[n * L3 + lm] = ah;
+                    ah[n] = x;
                 }
+                store_row4<NA>(at.Ah + lm * NAP, ah);
             }
         }
         const float4 *prs = a.pair + beg;
@@ -701,36 +858,30 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     const float ux = pd.x * rinv, uy = pd.y * rinv, uz = pd.z * rinv;
                     const float rl = ux * lx + uy * ly + uz * lz;
                     const float px = (lx - rl * ux) * rinv, py = (ly - rl * uy) * rinv, pz = (lz - rl * uz) * rinv;
-                    float f[KA], fp[KA];
+                    float f[KA], fp[KA], g[NA], gp[NA];
                     basis_val_der<KA>(r, a.inv_rcA, f, fp);
-                    const float *c = cAi + tj * NCA;
+                    contract_c2<NA, KA>(cAi + tj * NA * KA4, f, fp, g, gp);
 #pragma unroll
-                    for (int n = 0; n < NA; ++n) {
-                        float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-                        for (int kk = 0; kk < KA; ++kk) {
-                            s0 += c[n * KA + kk] * f[kk];
-                            s1 += c[n * KA + kk] * fp[kk];
-                        }
-                        sm.sg[grp][sl][n] = s0;
-                        sm.sgp[grp][sl][n] = s1 * rl;
-                    }
+                    for (int n = 0; n < NA; ++n) gp[n] *= rl;
+                    store_row4<NA>(sm.st.j.g[grp][sl], g);
+                    store_row4<NA>(sm.st.j.gp[grp][sl], gp);
+                    float *Yr = sm.st.j.Y[grp][sl], *Pr = sm.st.j.P[grp][sl];
                     ylm_each(ux, uy, uz, [&](int lm, float Y, float gx, float gy, float gz) {
-                        sm.sY[grp][sl][lm] = Y;
-                        sm.sP[grp][sl][lm] = gx * px + gy * py + gz * pz;
+                        Yr[lm] = Y;
+                        Pr[lm] = gx * px + gy * py + gz * pz;
                     });
                 }
                 __syncwarp();
                 const int cnt = min(SW, nAng - c0);
                 for (int pp = 0; pp < cnt; ++pp) {
-                    float gv[L::SGS], gpv[L::SGS];
-                    load_row<L::SGS>(sm.sg[grp][pp], gv);
-                    load_row<L::SGS>(sm.sgp[grp][pp], gpv);
+                    float gv[NAP], gpv[NAP];
+                    load_row<NAP>(sm.st.j.g[grp][pp], gv);
+                    load_row<NAP>(sm.st.j.gp[grp][pp], gpv);
 #pragma unroll
                     for (int jj = 0; jj < NLMO; ++jj) {
                         const int lm = sl + jj * SW;
                         if (lm < L3) {
-                            const float y = sm.sY[grp][pp][lm], ps = sm.sP[grp][pp][lm];
+                            const float y = sm.st.j.Y[grp][pp][lm], ps = sm.st.j.P[grp][pp][lm];
 #pragma unroll
                             for (int n = 0; n < NA; ++n) accd[jj][n] += gpv[n] * y + gv[n] * ps;
                         }
@@ -741,78 +892,70 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
             for (int jj = 0; jj < NLMO; ++jj) {
                 const int lm = sl + jj * SW;
-                if (lm < L3) {
-#pragma unroll
-                    for (int n = 0; n < NA; ++n) at.dA[n * L3 + lm] = accd[jj][n];
-                }
+                if (lm < L3) store_row4<NA>(at.D + lm * NAP, accd[jj]);
             }
         }
 
         // ---------------------------------------------------------------- radial JVP species sums
         for (int e = sl; e < T * 2 * KR; e += SW) Sr[e] = 0.0f;
         __syncwarp();
-        {
+        if (T == 1) {  // one species: every lane sums its own pairs, one reduction per atom
             float v[VR2];
 #pragma unroll
             for (int k = 0; k < VR2; ++k) v[k] = 0.0f;
-            int bcur = -1;
             float4 nxt = pair_or_zero(prs, sl, nRad);
             for (int c0 = 0; c0 < maxR; c0 += SW) {
                 const int k = c0 + sl;
-                const bool valid = k < nRad;
                 const float4 pd = nxt;
                 nxt = pair_or_zero(prs, k + SW, nRad);
-                int tj = -1;
-                float f[KR], fp[KR];
-#pragma unroll
-                for (int kk = 0; kk < KR; ++kk) f[kk] = fp[kk] = 0.0f;
-                float rl = 0.0f;
-                if (valid) {
+                if (k < nRad) {
                     const int j = pair_j(pd);
-                    tj = pair_t(pd);
                     const float4 fbj = a.fbar[j];
                     const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
                     const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
                     const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     const float rinv = inv_norm(r2);
-                    rl = (pd.x * lx + pd.y * ly + pd.z * lz) * rinv;
+                    const float rl = (pd.x * lx + pd.y * ly + pd.z * lz) * rinv;
+                    float f[KR], fp[KR];
                     basis_val_der<KR>(r2 * rinv, a.inv_rcR, f, fp);
-                }
-                if (T == 1) {  // one species: no runs to track
-                    if (valid) {
 #pragma unroll
-                        for (int kk = 0; kk < KR; ++kk) {
-                            v[kk] += f[kk];
-                            v[KR + kk] += rl * fp[kk];
-                        }
-                    }
-                    continue;
-                }
-                unsigned rem = group_bits<SW>(__ballot_sync(FULL, valid), lane);
-                while (__any_sync(FULL, rem != 0)) {
-                    const bool has = rem != 0;
-                    const int leader = has ? __ffs(rem) - 1 : 0;
-                    int bsp = __shfl_sync(FULL, tj, (lane & ~(SW - 1)) + leader);
-                    if (!has) bsp = bcur;
-                    const bool inb = valid && has && tj == bsp;
-                    rem &= ~group_bits<SW>(__ballot_sync(FULL, inb), lane);
-                    const bool change = bsp != bcur;
-                    if (__any_sync(FULL, change && bcur >= 0))
-                        flush_groups<VR2, SW>(v, Sr + (bcur >= 0 ? bcur : 0) * 2 * KR, 2 * KR, bcur >= 0, lane, false);
-                    bcur = bsp;
-                    if (inb) {
-#pragma unroll
-                        for (int kk = 0; kk < KR; ++kk) {
-                            v[kk] += f[kk];
-                            v[KR + kk] += rl * fp[kk];
-                        }
+                    for (int kk = 0; kk < KR; ++kk) {
+                        v[kk] += f[kk];
+                        v[KR + kk] += rl * fp[kk];
                     }
                 }
             }
-            if (T == 1 && nRad > 0) bcur = 0;
-            if (__any_sync(FULL, bcur >= 0))
-                flush_groups<VR2, SW>(v, Sr + (bcur >= 0 ? bcur : 0) * 2 * KR, 2 * KR, bcur >= 0, lane, false);
+            if (__any_sync(FULL, nRad > 0)) flush_groups<VR2, SW>(v, Sr, 2 * KR, nRad > 0, lane, false);
+        } else {
+            float v[RC2];
+            int bcur = -1;
+            float4 nxt = pair_or_zero(prs, sl, nRad);
+            for (int c0 = 0; c0 < maxR; c0 += SW) {
+                const int k = c0 + sl;
+                const float4 pd = nxt;
+                nxt = pair_or_zero(prs, k + SW, nRad);
+                if (k < nRad) {
+                    const int j = pair_j(pd);
+                    const float4 fbj = a.fbar[j];
+                    const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
+                    const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
+                    const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+                    const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
+                    const float rinv = inv_norm(r2);
+                    const float rl = (pd.x * lx + pd.y * ly + pd.z * lz) * rinv;
+                    float *row = sm.st.r.f[grp][sl];
+                    float fp[KR];
+                    basis_val_der<KR>(r2 * rinv, a.inv_rcR, row, fp);
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) row[KR + kk] = rl * fp[kk];
+                    row[2 * KR] = __int_as_float(pair_t(pd));
+                }
+                __syncwarp();
+                walk_species_rows<2 * KR, SW>(sm.st.r.f[grp], min(SW, nRad - c0), sl, Sr, v, bcur);
+                __syncwarp();
+            }
+            close_species_run<2 * KR, SW>(sl, Sr, v, bcur);
         }
         __syncwarp();
 
@@ -820,36 +963,40 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         for (int n = sl; n < NR; n += SW) {
             float d = 0.0f;
             for (int bb = 0; bb < T; ++bb) {
+                const float *cr = cRi + (bb * NR + n) * KR4;
 #pragma unroll
-                for (int kk = 0; kk < KR; ++kk) d += cRi[bb * NCR + n * KR + kk] * Sr[bb * 2 * KR + KR + kk];
+                for (int kk = 0; kk < KR; ++kk) d += __ldg(cr + kk) * Sr[bb * 2 * KR + KR + kk];
             }
             at.dqt[n] = d * scale[n];
         }
         for (int e = sl; e < 4 * NA; e += SW) {
             const int n = e % NA, l = e / NA + 1;
-            const float *Ar = at.A + n * L3 + l * l - 1;
-            const float *dAr = at.dA + n * L3 + l * l - 1;
             float s2 = 0.0f;
-            for (int m = 0; m < 2 * l + 1; ++m) s2 += Ar[m] * dAr[m];
+            for (int m = 0; m < 2 * l + 1; ++m) {
+                const int lm = l * l - 1 + m;
+                s2 += at.A[lm * NAP + n] * at.D[lm * NAP + n];
+            }
             const int v = NR + (l - 1) * NA + n;
             at.dqt[v] = 2.0f * s2 * scale[v];
         }
         for (int n = sl; n < NA; n += SW) {
-            const float *An = at.A + n * L3;
-            const float *dAn = at.dA + n * L3;
+            float a2[5], d2[5];
+            l2_block<NAP>(at.A, n, a2);
+            l2_block<NAP>(at.D, n, d2);
             float d4 = 0.0f;
 #pragma unroll
-            for (int m = 0; m < 5; ++m) d4 += at.G4[n * 5 + m] * dAn[3 + m];
+            for (int m = 0; m < 5; ++m) d4 += at.G4[n * 5 + m] * d2[m];
             at.dqt[NR + 4 * NA + n] = d4 * scale[NR + 4 * NA + n];
             float Mt[6], dMt[6], Pm[6], pr[5];
-            l2_matrix(An + 3, Mt);
-            l2_matrix(dAn + 3, dMt);
+            l2_matrix(a2, Mt);
+            l2_matrix(d2, dMt);
             sym_prod(Mt, dMt, Pm);
             l2_project(Pm, pr);
 #pragma unroll
             for (int m = 0; m < 5; ++m) at.H4[n * 5 + m] = 6.0f * KAPPA_REAL * pr[m];
-            const float q1 = An[0] * An[0] + An[1] * An[1] + An[2] * An[2];
-            const float ad = An[0] * dAn[0] + An[1] * dAn[1] + An[2] * dAn[2];
+            const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
+            const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
+            const float ad = x0 * at.D[n] + x1 * at.D[NAP + n] + x2 * at.D[2 * NAP + n];
             at.ad[n] = ad;
             at.dqt[NR + 5 * NA + n] = 4.0f * q1 * ad * scale[NR + 5 * NA + n];
         }
@@ -914,21 +1061,23 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
             const int lm = sl + jj * SW;
             if (lm < L3) {
                 const int l = l_of_lm(lm);
+                float xr[NA];
 #pragma unroll
                 for (int n = 0; n < NA; ++n) {
-                    const float *An = at.A + n * L3;
-                    const float *dAn = at.dA + n * L3;
+                    const float av = at.A[lm * NAP + n], dv = at.D[lm * NAP + n];
                     const int v3 = NR + (l - 1) * NA + n;
-                    float x = 2.0f * at.ab[v3] * An[lm] + 2.0f * at.b[v3] * dAn[lm];
+                    float x = 2.0f * at.ab[v3] * av + 2.0f * at.b[v3] * dv;
                     if (l == 2)
                         x += at.ab[NR + 4 * NA + n] * at.G4[n * 5 + lm - 3] + at.b[NR + 4 * NA + n] * at.H4[n * 5 + lm - 3];
                     if (l == 1) {
-                        const float q1 = An[0] * An[0] + An[1] * An[1] + An[2] * An[2];
+                        const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
+                        const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
                         const int v5 = NR + 5 * NA + n;
-                        x += at.ab[v5] * 4.0f * q1 * An[lm] + at.b[v5] * (8.0f * at.ad[n] * An[lm] + 4.0f * q1 * dAn[lm]);
+                        x += at.ab[v5] * 4.0f * q1 * av + at.b[v5] * (8.0f * at.ad[n] * av + 4.0f * q1 * dv);
                     }
-                    at.dA[n * L3 + lm] = x;  // only this lane reads or writes element (n, lm) here
+                    xr[n] = x;
                 }
+                store_row4<NA>(at.D + lm * NAP, xr);  // only this lane reads or writes row lm here
             }
         }
         __syncwarp();
@@ -946,27 +1095,17 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         }
 
         // ---------------------------------------------------------------- angular coefficient gradient
+        // per pair p (species b): X^b_nk += alpha_n f_k + beta_n f'_k with
+        //   alpha_n = sum_lm dJ/dA_nlm Y_lm + dE/dA_nlm (grad Y_lm . p),
+        //   beta_n  = (r^.lambda) sum_lm dE/dA_nlm Y_lm
         {
-            const float *Ab = at.dA;
-            float X[VA];
-#pragma unroll
-            for (int e = 0; e < VA; ++e) X[e] = 0.0f;
-            int bcur = -1;
             float4 nxt = pair_or_zero(prs, sl, nAng);
             for (int c0 = 0; c0 < maxA; c0 += SW) {
                 const int k = c0 + sl;
-                const bool valid = k < nAng;
                 const float4 pd = nxt;
                 nxt = pair_or_zero(prs, k + SW, nAng);
-                int tj = -1;
-                float f[KA], fp[KA], al[NA], be[NA];
-#pragma unroll
-                for (int kk = 0; kk < KA; ++kk) f[kk] = fp[kk] = 0.0f;
-#pragma unroll
-                for (int n = 0; n < NA; ++n) al[n] = be[n] = 0.0f;
-                if (valid) {
-                    const int j = pair_j(pd);
-                    tj = pair_t(pd);
+                if (k < nAng) {
+                    const int j = pair_j(pd), tj = pair_t(pd);
                     const float4 fbj = a.fbar[j];
                     const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
                     const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
@@ -977,54 +1116,65 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     const float ux = pd.x * rinv, uy = pd.y * rinv, uz = pd.z * rinv;
                     const float rl = ux * lx + uy * ly + uz * lz;
                     const float px = (lx - rl * ux) * rinv, py = (ly - rl * uy) * rinv, pz = (lz - rl * uz) * rinv;
-                    basis_val_der<KA>(r, a.inv_rcA, f, fp);
+                    float al[NA], be[NA];
+#pragma unroll
+                    for (int n = 0; n < NA; ++n) al[n] = be[n] = 0.0f;
                     ylm_each(ux, uy, uz, [&](int lm, float Y, float gx, float gy, float gz) {
                         const float ps = gx * px + gy * py + gz * pz;
+                        const float4 *d4 = reinterpret_cast<const float4 *>(at.D + lm * NAP);
+                        const float4 *h4 = reinterpret_cast<const float4 *>(at.Ah + lm * NAP);
 #pragma unroll
-                        for (int n = 0; n < NA; ++n) {
-                            const float ah = at.Ah[n * L3 + lm];
-                            al[n] += Ab[n * L3 + lm] * Y + ah * ps;
-                            be[n] += ah * Y;
+                        for (int q = 0; q < NAP / 4; ++q) {
+                            const float4 dq = d4[q], hq = h4[q];
+                            const float dv[4] = {dq.x, dq.y, dq.z, dq.w}, hv[4] = {hq.x, hq.y, hq.z, hq.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int n = 4 * q + e;
+                                if (n < NA) {
+                                    al[n < NA ? n : 0] += dv[e] * Y + hv[e] * ps;
+                                    be[n < NA ? n : 0] += hv[e] * Y;
+                                }
+                            }
                         }
                     });
+                    float f[KA], fp[KA];
+                    basis_val_der<KA>(r, a.inv_rcA, f, fp);
 #pragma unroll
-                    for (int n = 0; n < NA; ++n) be[n] *= rl;
+                    for (int n = 0; n < NA; ++n) sm.st.c.ab[grp][sl][n] = make_float2(al[n], be[n] * rl);
+#pragma unroll
+                    for (int kk = 0; kk < KA; ++kk) sm.st.c.ff[grp][sl][kk] = make_float2(f[kk], fp[kk]);
+                    sm.st.c.t[grp][sl] = tj;
                 }
-                if (T == 1) {  // one species: no runs to track
-                    if (valid) {
+                __syncwarp();
+                // every lane walks the rows of every atom of the batch (uniform control flow)
+#pragma unroll 1
+                for (int g2 = 0; g2 < G; ++g2) {
+                    const int cnt = min(SW, __shfl_sync(FULL, nAng, g2 * SW) - c0);
+                    for (int pp = 0; pp < cnt; ++pp) {
+                        const int t = sm.st.c.t[g2][pp];
+                        if (t != xb) {
+                            close_tile();
+                            xb = t;
+                        }
+                        if (tile_own) {
+                            const float2 abv = sm.st.c.ab[g2][pp][tn];
 #pragma unroll
-                        for (int n = 0; n < NA; ++n)
-#pragma unroll
-                            for (int kk = 0; kk < KA; ++kk) X[n * KA + kk] += al[n] * f[kk] + be[n] * fp[kk];
+                            for (int jj = 0; jj < TW; ++jj) {
+                                if (tk0 + jj < KA) {
+                                    const float2 ffv = sm.st.c.ff[g2][pp][tk0 + jj];
+                                    X[jj] += abv.x * ffv.x + abv.y * ffv.y;
+                                }
+                            }
+                        }
                     }
-                    continue;
                 }
-                unsigned rem = group_bits<SW>(__ballot_sync(FULL, valid), lane);
-                while (__any_sync(FULL, rem != 0)) {
-                    const bool has = rem != 0;
-                    const int leader = has ? __ffs(rem) - 1 : 0;
-                    int bsp = __shfl_sync(FULL, tj, (lane & ~(SW - 1)) + leader);
-                    if (!has) bsp = bcur;
-                    const bool inb = valid && has && tj == bsp;
-                    rem &= ~group_bits<SW>(__ballot_sync(FULL, inb), lane);
-                    const bool change = bsp != bcur;
-                    if (__any_sync(FULL, change && bcur >= 0))
-                        flush_groups<VA, SW>(X, accA + (bcur >= 0 ? bcur : 0) * NCA, NCA, bcur >= 0, lane, true);
-                    bcur = bsp;
-                    if (inb) {
-#pragma unroll
-                        for (int n = 0; n < NA; ++n)
-#pragma unroll
-                            for (int kk = 0; kk < KA; ++kk) X[n * KA + kk] += al[n] * f[kk] + be[n] * fp[kk];
-                    }
-                }
+                __syncwarp();
             }
-            if (T == 1 && nAng > 0) bcur = 0;
-            if (__any_sync(FULL, bcur >= 0))
-                flush_groups<VA, SW>(X, accA + (bcur >= 0 ? bcur : 0) * NCA, NCA, bcur >= 0, lane, true);
         }
         __syncwarp();
     }
+    __syncwarp();
+    close_tile();
     __syncwarp();
     if (cur_t >= 0) flush_slot(cur_t);
 }

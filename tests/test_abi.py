@@ -49,3 +49,19 @@ def test_null_handles_rejected(lib):
     assert lib.nep_eval(None, None, None, None) == pkg.NEP_EINVAL
     assert lib.nep_loss_grad(None, None, None, None, None, 1.0, 1.0, 1.0, None, None) == pkg.NEP_EINVAL
     lib.nep_destroy(None)
+
+
+def test_param_blocks_partition_theta():
+    """The parameter blocks the gradient checks use cover theta [0, P) exactly, in the
+    header's order, and put b1 where the oracle's hand-worked loss fixture has its only
+    nonzero derivative."""
+    import oracle
+    from paper_2606_19557_gb300 import synth
+    for name, spec in synth.SPECS.items():
+        blocks = list(pkg.param_blocks(spec).values())
+        assert blocks[0].start == 0 and blocks[-1].stop == oracle.num_params(spec), name
+        assert all(a.stop == b.start and a.stop > a.start for a, b in zip(blocks, blocks[1:])), name
+    spec = synth.SPECS["fcc_bcc_t1"]
+    b1 = pkg.param_blocks(spec)["b1"]
+    nd = oracle.num_descriptors(spec)
+    assert b1.start == spec.n_types * (nd + 2) * spec.n_neu and b1.stop == b1.start + 1

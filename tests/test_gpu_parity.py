@@ -546,3 +546,50 @@ def test_model_variants(name):
     np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
     assert_grad_close(g.cpu().numpy(), go, spec, TOL)
     nep.close()
+
+
+class _SpecZBL:
+    """A model spec with the ZBL short-range term (switch radii, atomic numbers)."""
+
+    def __init__(self, base, zbl):
+        for k in ("n_types", "rc_R", "rc_A", "n_max_R", "n_max_A", "basis_R", "basis_A", "l_max", "has_4b",
+                  "has_5b", "n_neu"):
+            setattr(self, k, getattr(base, k))
+        self.zbl = zbl
+
+
+@pytest.mark.parametrize("name,zbl", [("alloy_t4", (1.5, 2.4, [29.0, 28.0, 26.0, 13.0])),
+                                      ("scale_t5", (0.0, 2.2, [6.0, 14.0, 8.0, 1.0, 79.0]))])
+def test_zbl_matches_oracle(name, zbl):
+    """E, F, W, loss and gradient with the ZBL term on (Sec. "Training"), on liquid-like
+    structures whose closest pairs fall inside the switch and below r1."""
+    from paper_2606_19557_gb300 import NEP
+    spec = _SpecZBL(synth.SPECS[name], zbl)
+    b = synth.batch_alloy(seed=91, n_struct=8, n_types=spec.n_types, n_lo=12, n_hi=60)
+    P = oracle.num_params(spec)
+    theta = synth.random_theta(P, 91)
+    qs = f32(oracle.scale_from_range(oracle.descriptors(spec, theta, b)))
+    i, j, S, ang = oracle.neighbors(b, spec.rc_R, spec.rc_A)
+    d = b.pos[j] - b.pos[i] + np.einsum("pk,pkx->px", S.astype(np.float64),
+                                        b.cell.reshape(-1, 3, 3)[np.searchsorted(b.atom_off, i, side="right") - 1])
+    r = np.linalg.norm(d, axis=1)
+    assert np.sum(r < zbl[1]) > 20  # the term is exercised
+    nep = NEP(spec)
+    nep.set_structures_batch(b)
+    nep.set_params(torch.tensor(theta, dtype=torch.float32), torch.tensor(qs, dtype=torch.float32))
+    E, F, W = [x.cpu().numpy() for x in nep.eval()]
+    Eo, Fo, Wo = oracle.evaluate(spec, theta, qs, b)
+    assert rel(E, Eo) < TOL and rel(F, Fo) < TOL and rel(W, Wo) < TOL
+    E0 = oracle.evaluate(_SpecZBL(synth.SPECS[name], None), theta, qs, b)[0]
+    assert rel(E0, Eo) > 1e-3  # the ZBL term changes the energies well beyond the tolerance
+    Er, Fr, Wr = synth.random_targets(b, 92)
+    lam = (1.0, 1.0, 0.1)
+    l3, g = nep.loss_grad(Er, Fr, Wr, None, lam)
+    l3o, go = oracle.loss_grad(spec, theta, qs, b, Er, Fr, Wr, None, lam)[:2]
+    np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
+    assert_grad_close(g.cpu().numpy(), go, spec, TOL)
+    # switched off again: the plain model
+    nep.set_zbl(0.0, 0.0)
+    E2 = nep.eval()[0].cpu().numpy()
+    assert rel(E2, E0) < TOL
+    nep.close()

@@ -577,3 +577,118 @@ def test_image_range_covers_float_predicate():
         i, j, S, _ = oracle.neighbors(b, rc, 3.0)
         got = set(zip(i.tolist(), j.tolist(), map(tuple, S.tolist())))
         assert got == _wide_brute_force(pos, cell, rc), case
+
+
+# ------------------------------------------------------------------ ZBL short-range term
+
+E2_4PI_EPS0 = 14.399645  # e^2 / (4 pi eps_0) in eV A (CODATA)
+
+
+def zbl_spec(Z, r1=1.0, r2=2.0, n_types=2):
+    s = spec(n_types=n_types, rc_R=5.0, rc_A=4.0, n_max_R=3, n_max_A=3, basis_R=5, basis_A=5, l_max=4, has_4b=1,
+             has_5b=1, n_neu=6)
+    s.zbl = (r1, r2, list(Z))
+    return s
+
+
+def _dimer_energy(s, r, types, theta=None):
+    pos = np.array([[6.0, 6.0, 6.0], [6.0 + r, 6.0, 6.0]])
+    b = one_batch(pos, np.eye(3) * 12.0, types)
+    th = np.zeros(oracle.num_params(s)) if theta is None else theta
+    return oracle.evaluate(s, th, np.ones(oracle.num_descriptors(s)), b)
+
+
+def test_zbl_coulomb_limit():
+    """At short range the screened repulsion of a pair tends to the bare Coulomb energy
+    Z_i Z_j e^2 / (4 pi eps_0 r): the universal screening function is 1 at the origin (its
+    four published coefficients add up to 1.00007).  Only the ZBL term is nonzero here
+    (all network parameters zero)."""
+    Z = (14.0, 6.0)
+    s = zbl_spec(Z)
+    g = []
+    for r in (1e-4, 2e-4):
+        E = _dimer_energy(s, r, [0, 1])[0][0]
+        g.append(E * r / (E2_4PI_EPS0 * Z[0] * Z[1]))
+    g0 = 2 * g[0] - g[1]  # linear extrapolation to r = 0
+    assert abs(g0 - 1.0) < 1e-4
+    assert g[0] < g0  # screening lowers the energy below the bare Coulomb value
+
+
+def test_zbl_universal_scaling_and_switch():
+    """The screened energy depends on the pair only through Z_i Z_j / r and the universal
+    length r (Z_i^0.23 + Z_j^0.23): two species pairs at the same reduced distance give the
+    same phi.  Inside r1 the switch is 1; at and beyond r2 the term is exactly zero, and it
+    goes to zero smoothly (energy and force continuous)."""
+    Za, Zb = (29.0, 29.0), (8.0, 1.0)
+    sa, sb = zbl_spec(Za, r1=3.0, r2=4.0), zbl_spec(Zb, r1=3.0, r2=4.0)
+    ua = Za[0] ** 0.23 + Za[1] ** 0.23
+    ub = Zb[0] ** 0.23 + Zb[1] ** 0.23
+    for x in (0.3, 1.0, 2.5):  # r (Z_i^0.23 + Z_j^0.23) in A
+        ra, rb = x / ua, x / ub
+        pa = _dimer_energy(sa, ra, [0, 1])[0][0] * ra / (Za[0] * Za[1])
+        pb = _dimer_energy(sb, rb, [0, 1])[0][0] * rb / (Zb[0] * Zb[1])
+        assert abs(pa - pb) < 1e-12 * abs(pa)
+    s = zbl_spec((26.0, 26.0), r1=1.2, r2=1.8)
+    assert _dimer_energy(s, 1.8, [0, 0])[0][0] == 0.0
+    assert _dimer_energy(s, 2.5, [0, 0])[0][0] == 0.0
+    e_in = [_dimer_energy(s, r, [0, 0])[0][0] for r in (1.79999, 1.8 - 2e-5)]
+    assert 0.0 < e_in[0] < e_in[1] < 1e-6  # vanishes quadratically at r2
+    # at r < r1 the switch is 1: the energy equals the unswitched one of a wider switch
+    wide = zbl_spec((26.0, 26.0), r1=1.5, r2=1.9)
+    assert _dimer_energy(s, 1.1, [0, 0])[0][0] == _dimer_energy(wide, 1.1, [0, 0])[0][0]
+
+
+def test_zbl_forces_and_virial_finite_difference():
+    """F = -dE/dr and W = -dE/d(eps) with the ZBL term on, on a compressed two-species cell
+    where many pairs fall inside the switch region and inside r1."""
+    s = zbl_spec((14.0, 6.0), r1=1.2, r2=2.2)
+    rng = np.random.default_rng(3)
+    cell = np.eye(3) * 4.2 + 0.1 * rng.uniform(-1, 1, (3, 3))
+    pos = rng.uniform(0, 1, (9, 3)) @ cell
+    b = fd_batch(one_batch(pos, cell, rng.integers(0, 2, 9)))
+    theta = synth.random_theta(oracle.num_params(s), 4)
+    qs = oracle.scale_from_range(oracle.descriptors(s, theta, b))
+    E, F, W = oracle.evaluate(s, theta, qs, b)
+    E0 = oracle.evaluate(zbl_spec_off(s), theta, qs, b)[0]
+    assert abs(E[0] - E0[0]) > 1.0  # the ZBL term is a large part of this cell's energy
+    h = 1e-6
+    for i in range(b.n_atoms):
+        for a in range(3):
+            bp, bm = fd_batch(b), fd_batch(b)
+            bp.pos[i, a] += h
+            bm.pos[i, a] -= h
+            fd = -(oracle.evaluate(s, theta, qs, bp)[0][0] - oracle.evaluate(s, theta, qs, bm)[0][0]) / (2 * h)
+            assert abs(fd - F[i, a]) < 1e-6 * max(1.0, np.abs(F).max())
+    for ab in range(9):
+        eps = np.zeros(9)
+        eps[ab] = h
+        out = []
+        for sgn in (1, -1):
+            Fm = np.eye(3) + sgn * eps.reshape(3, 3)
+            bb = fd_batch(b)
+            bb.pos = bb.pos @ Fm.T
+            bb.cell[0] = (bb.cell[0].reshape(3, 3) @ Fm.T).reshape(9)
+            out.append(oracle.evaluate(s, theta, qs, bb)[0][0])
+        assert abs(-(out[0] - out[1]) / (2 * h) - W[0, ab]) < 1e-6 * max(1.0, np.abs(W).max())
+    assert np.allclose(F.sum(axis=0), 0.0, atol=1e-9)
+
+
+def zbl_spec_off(s):
+    t = Spec(**{k: v for k, v in s.__dict__.items() if k != "zbl"})
+    return t
+
+
+def test_zbl_leaves_the_parameter_gradient_to_the_network():
+    """The ZBL term has no trainable parameter: the parameter gradient of a fixed-cotangent
+    objective sum dE E + sum dF.F + sum dW:W does not change when it is switched on."""
+    s = zbl_spec((14.0, 6.0), r1=1.2, r2=2.2)
+    rng = np.random.default_rng(5)
+    cell = np.eye(3) * 4.4
+    pos = rng.uniform(0, 1, (8, 3)) @ cell
+    b = one_batch(pos, cell, rng.integers(0, 2, 8))
+    theta = synth.random_theta(oracle.num_params(s), 6)
+    qs = oracle.scale_from_range(oracle.descriptors(s, theta, b))
+    dE, dF, dW = rng.normal(size=1), rng.normal(size=(8, 3)), rng.normal(size=(1, 9))
+    g_on = oracle.backward(s, theta, qs, b, dE, dF, dW)
+    g_off = oracle.backward(zbl_spec_off(s), theta, qs, b, dE, dF, dW)
+    assert np.array_equal(g_on, g_off)
