@@ -146,6 +146,8 @@ constexpr int SMAX = 127;      // |S_a| limit of the packed shift
 struct SGeom {
     double h[9];
     double inv[9];
+    float invf[9];  // inv rounded to float
+    float nb[3];    // |b_a|, the norms of the columns of inv (reciprocal vectors), in float
     int n[3];
     int m[3];
 };
@@ -175,6 +177,9 @@ __global__ void k_struct_geom(int64_t ns, const float *cell, double rc, SGeom *g
         g.inv[3 * x + 1] = c1[x] / vol;
         g.inv[3 * x + 2] = c2[x] / vol;
     }
+    for (int k = 0; k < 9; ++k) g.invf[k] = (float)g.inv[k];
+    for (int a = 0; a < 3; ++a)
+        g.nb[a] = (float)sqrt(g.inv[a] * g.inv[a] + g.inv[3 + a] * g.inv[3 + a] + g.inv[6 + a] * g.inv[6 + a]);
     const double w[3] = {fabs(vol) / sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]),
                          fabs(vol) / sqrt(c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2]),
                          fabs(vol) / sqrt(c2[0] * c2[0] + c2[1] * c2[1] + c2[2] * c2[2])};
@@ -267,6 +272,95 @@ __device__ __forceinline__ float pair_d(const float *pi, const float *pj, const 
     return __fadd_rn(__fadd_rn(__fmul_rn(d32[0], d32[0]), __fmul_rn(d32[1], d32[1])), __fmul_rn(d32[2], d32[2]));
 }
 
+// Knuth's TwoSum: s + e = a + b exactly (round to nearest, no overflow).
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// TwoProduct by a fused multiply-add (Ogita, Rump and Oishi, "Accurate sum and dot product",
+// 2005): p + e = a b exactly when a b does not underflow.
+__device__ __forceinline__ float two_prod(float a, float b, float &e) {
+    const float p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+    return p;
+}
+
+// Exponent of the lowest set-able bit (unit in the last place) of a nonzero float.
+__device__ __forceinline__ int lsb_exp(float v) {
+    const int ev = (__float_as_int(v) >> 23) & 0xff;
+    return (ev > 0 ? ev : 1) - 150;
+}
+
+// pair_d's displacement in FP32 arithmetic, for pairs with a periodic image.  Per
+// component, X = (p_j - p_i) + S_a h_a + S_b h_b + S_c h_c is carried exactly as the
+// float expansion h3 + (error terms) (TwoSum of the difference, TwoProduct of the image
+// terms, TwoSum of the running sum), and c = RN(h3 + lo) with the exact remainder r.
+// Bounds: |X - (c + r)| <= 6 2^-48 M (the float sum lo of seven error terms, each at
+// most 2^-24 of its operand, M the sum of the operand magnitudes), and the FP64 form
+// D of pair_d differs from X by at most 2^-53 (|p_j - p_i| + |S_a h_a + S_b h_b| +
+// |sum of the image terms| + |D|) <= 2^-52 M + 2^-51 |c|.  With B >= both, if r + B and
+// r - B stay inside half the float gaps above and below c, then X and D lie in the
+// rounding interval of c, so fl32(D), the predicate's float, equals c.  Near a rounding
+// boundary (an exact tie is common: X then has one bit more than a float) c is kept when
+// nothing was rounded at all: lo's own sum is exact and every FP64 partial sum of pair_d
+// is exact, because all operands are multiples of 2^q (q the lowest unit in the last
+// place among them) and every partial sum is below M < 2^(q+52); then D = X = h3 + lo and
+// c = RN(X) = fl32(D), ties to even included.  Returns false (the caller takes the FP64
+// form) when neither can be shown, and for a zero or tiny c.
+// An all-zero component is summed as the FP64 form associates it, so its zero sign
+// follows the same IEEE rules.
+__device__ __forceinline__ bool pair_d_fp32(const float *pi, const float *pj, const float *hf, int Sa, int Sb,
+                                            int Sc, float *d32) {
+    const float fa = (float)Sa, fb = (float)Sb, fc = (float)Sc;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        float e0, e1, e2, e3, t1, t2, t3, rr;
+        const float s0 = two_sum(pj[x], -pi[x], e0);
+        const float p1 = two_prod(fa, hf[x], e1);
+        const float p2 = two_prod(fb, hf[3 + x], e2);
+        const float p3 = two_prod(fc, hf[6 + x], e3);
+        const float h1 = two_sum(s0, p1, t1);
+        const float h2 = two_sum(h1, p2, t2);
+        const float h3 = two_sum(h2, p3, t3);
+        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, e3)), __fadd_rn(__fadd_rn(t1, t2), t3));
+        const float c = two_sum(h3, lo, rr);
+        const float M = fabsf(s0) + fabsf(p1) + fabsf(p2) + fabsf(p3) + fabsf(h1) + fabsf(h2) + fabsf(h3);
+        if (c == 0.0f) {
+            if (M != 0.0f || lo != 0.0f || rr != 0.0f) return false;
+            d32[x] = __fadd_rn(s0, __fadd_rn(__fadd_rn(p1, p2), p3));  // zeros, associated as in pair_d
+            continue;
+        }
+        const int ec = (__float_as_int(c) >> 23) & 0xff;
+        if (ec < 40 || ec == 255) return false;
+        // half the gaps to the floats above and below |c| = 2^e (1 + m): 2^(e-24) each, except
+        // below a power of two (m = 0), where the gap halves
+        const float hg = __int_as_float((ec - 24) << 23);
+        const float hg_small = (__float_as_int(c) & 0x7fffff) ? hg : __int_as_float((ec - 25) << 23);
+        const float up = c > 0.0f ? hg : hg_small, down = c > 0.0f ? hg_small : hg;  // towards +inf / -inf
+        const float B = 0x1p-44f * M + 0x1p-51f * fabsf(c) + 0x1p-110f;
+        if (!(rr + B < up && rr - B > -down)) {
+            float r1, r2, r3, r4, r5, r6;
+            const float a1 = two_sum(e0, e1, r1), a2 = two_sum(e2, e3, r2), a3 = two_sum(a1, a2, r3);
+            const float b1 = two_sum(t1, t2, r4), b2 = two_sum(b1, t3, r5);
+            two_sum(a3, b2, r6);  // its sum is lo
+            if (r1 != 0.0f || r2 != 0.0f || r3 != 0.0f || r4 != 0.0f || r5 != 0.0f || r6 != 0.0f) return false;
+            int q = 1000;
+            if (pj[x] != 0.0f) q = min(q, lsb_exp(pj[x]));
+            if (pi[x] != 0.0f) q = min(q, lsb_exp(pi[x]));
+            if (Sa != 0 && hf[x] != 0.0f) q = min(q, lsb_exp(hf[x]));
+            if (Sb != 0 && hf[3 + x] != 0.0f) q = min(q, lsb_exp(hf[3 + x]));
+            if (Sc != 0 && hf[6 + x] != 0.0f) q = min(q, lsb_exp(hf[6 + x]));
+            const int eM = ((__float_as_int(M) >> 23) & 0xff) - 127;  // M < 2^(eM + 1)
+            if (eM + 2 > q + 52) return false;
+        }
+        d32[x] = c;
+    }
+    return true;
+}
+
 __device__ __forceinline__ uint32_t pack_shift(int Sa, int Sb, int Sc) {
     return ((uint32_t)(Sa + 128) << 16) | ((uint32_t)(Sb + 128) << 8) | (uint32_t)(Sc + 128);
 }
@@ -336,20 +430,32 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
         if (inR) hit(j, Sa, Sb, Sc, inA);
     };
     if (g.n[0] == 1 && g.n[1] == 1 && g.n[2] == 1) {
-        double R[3];  // rcq |b_a|
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            R[a] = (double)rcq * sqrt(g.inv[a] * g.inv[a] + g.inv[3 + a] * g.inv[3 + a] + g.inv[6 + a] * g.inv[6 + a]);
-        const double pid[3] = {(double)pi[0], (double)pi[1], (double)pi[2]};
+        // Image box of each candidate j in FP32, widened by more than the FP32 rounding of
+        // f = (p_j - p_i) h^-1 (relative 2^-20 of the magnitudes involved), so it holds every
+        // image the exact box holds; the extra images are rejected by the pair predicate.
+        // Only a box that reaches past the packed shift range is recomputed in FP64.
+        const float *invf = g.invf;
         for (int64_t j = atom_off[s] + lane; j < atom_off[s + 1]; j += 32) {
             const float4 pj = pos4[j];
-            const double d0[3] = {(double)pj.x - pid[0], (double)pj.y - pid[1], (double)pj.z - pid[2]};
+            const float d0[3] = {pj.x - pi[0], pj.y - pi[1], pj.z - pi[2]};
             int lo[3], hi[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const double f = d0[0] * g.inv[a] + d0[1] * g.inv[3 + a] + d0[2] * g.inv[6 + a];
-                lo[a] = (int)ceil(-f - R[a]);
-                hi[a] = (int)floor(-f + R[a]);
+                const float R = rcq * g.nb[a];
+                const float f = d0[0] * invf[a] + d0[1] * invf[3 + a] + d0[2] * invf[6 + a];
+                const float bound = fabsf(d0[0] * invf[a]) + fabsf(d0[1] * invf[3 + a]) + fabsf(d0[2] * invf[6 + a]);
+                const float m = 0x1p-20f * (bound + R) + 1e-30f;
+                lo[a] = (int)ceilf(-f - R - m);
+                hi[a] = (int)floorf(-f + R + m);
+                if (lo[a] < -SMAX - 1 || hi[a] > SMAX + 1) {
+                    const double fd = ((double)pj.x - (double)pi[0]) * g.inv[a] +
+                                      ((double)pj.y - (double)pi[1]) * g.inv[3 + a] +
+                                      ((double)pj.z - (double)pi[2]) * g.inv[6 + a];
+                    const double Rd = (double)rcq * sqrt(g.inv[a] * g.inv[a] + g.inv[3 + a] * g.inv[3 + a] +
+                                                         g.inv[6 + a] * g.inv[6 + a]);
+                    lo[a] = (int)ceil(-fd - Rd);
+                    hi[a] = (int)floor(-fd + Rd);
+                }
                 if (lo[a] < -SMAX - 1 || hi[a] > SMAX + 1) {  // beyond the packed shift range
                     atomic_err(err, 2);
                     lo[a] = 1;
@@ -485,7 +591,9 @@ __device__ __forceinline__ void emit_pair(uint64_t k, int64_t slot, int64_t i, c
         pair_d0(pos + 3 * i, pos + 3 * j, g.h, d32);
     } else {
         const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
-        pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
+        const float hf[9] = {(float)g.h[0], (float)g.h[1], (float)g.h[2], (float)g.h[3], (float)g.h[4],
+                             (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
+        if (!pair_d_fp32(pos + 3 * i, pos + 3 * j, hf, Sa, Sb, Sc, d32)) pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
     }
     store_pair(k, slot, d32, keys_out, pair, shift);
 }
