@@ -26,8 +26,9 @@ Ctx::~Ctx() {
 
 static thread_local std::string g_create_err;
 
-static const char *kernel_names[KID_COUNT] = {"expand_params", "forward", "force_gather", "struct_sums",
-                                              "loss_final",    "adjoint", "net_grad",     "grad_reduce"};
+static const char *kernel_names[KID_COUNT] = {"expand_params", "forward",     "force_gather",  "struct_sums",
+                                              "loss_final",    "adjoint_jvp", "net_reverse",   "adjoint_cgrad",
+                                              "net_grad",      "grad_reduce"};
 
 // ----------------------------------------------------------------------------- helpers
 
@@ -204,10 +205,13 @@ static int set_smem_attr(Ctx *c) {
     CK(cudaDeviceGetAttribute(&maxo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
     if (c->ks->fwd_smem[2](c->T, c->NN) > (size_t)maxo || c->ks->adj_smem[2](c->T, c->NN) > (size_t)maxo)
         return c->fail(NEP_EINVAL, "model too large for shared memory");
+    if (c->ks->net_rev_smem(c->NN) > (size_t)maxo) return c->fail(NEP_EINVAL, "model too large for shared memory");
     for (int v = 0; v < NVAR; ++v) {
         CK(cudaFuncSetAttribute(c->ks->fwd_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
         CK(cudaFuncSetAttribute(c->ks->adj_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+        CK(cudaFuncSetAttribute(c->ks->jvp_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     }
+    CK(cudaFuncSetAttribute(c->ks->net_rev_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     return NEP_OK;
 }
 
@@ -278,12 +282,16 @@ static int body_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr
     mark(c, 4);
     if ((rc = launch_loss_final(c, loss3))) return rc;
     mark(c, 5);
-    if ((rc = launch_adjoint(c))) return rc;
+    if ((rc = launch_adjoint(c, 0))) return rc;
     mark(c, 6);
-    if ((rc = launch_ann_grad(c))) return rc;
+    if ((rc = launch_adjoint(c, 1))) return rc;
     mark(c, 7);
-    if ((rc = launch_grad_final(c, grad))) return rc;
+    if ((rc = launch_adjoint(c, 2))) return rc;
     mark(c, 8);
+    if ((rc = launch_ann_grad(c))) return rc;
+    mark(c, 9);
+    if ((rc = launch_grad_final(c, grad))) return rc;
+    mark(c, 10);
     return NEP_OK;
 }
 
@@ -511,7 +519,9 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
         c->ebar.ensure<float>(ns) || c->wbar.ensure<float>(ns * 9) || c->zt.ensure<float>(na * NN) ||
         c->ut.ensure<float>(na * NN) || c->om.ensure<float>(na * NN) || c->dqt.ensure<float>(na * NDP) ||
         c->F_int.ensure<float>(na * 3) || c->E_int.ensure<double>(ns) || c->W_int.ensure<double>(ns * 9) ||
-        c->loss_part.ensure<double>(nlp))
+        c->loss_part.ensure<double>(nlp) || c->st_D.ensure<float>(na * NAL) ||
+        c->st_S.ensure<float>(na * 2 * (int64_t)c->T * c->ks->KR) || c->st_b.ensure<float>(na * NDP) ||
+        c->st_ab.ensure<float>(na * NDP))
         return c->fail(NEP_ENOMEM, "step buffers");
     if ((rc = default_shapes(c))) return rc;
     CK(cudaDeviceSynchronize());

@@ -56,7 +56,10 @@ struct Sched {
 
 constexpr int NVAR = 4;
 
-enum KernelId { KID_EXPAND = 0, KID_FWD, KID_GATHER, KID_STRUCT, KID_LOSS, KID_ADJ, KID_ANN, KID_GRAD, KID_COUNT };
+enum KernelId {
+    KID_EXPAND = 0, KID_FWD, KID_GATHER, KID_STRUCT, KID_LOSS, KID_ADJ, KID_NETREV, KID_ADJCG, KID_ANN, KID_GRAD,
+    KID_COUNT
+};
 
 struct Ctx;
 
@@ -66,13 +69,17 @@ struct KernelSet {
     // variants v = 0..3: lanes per atom sw[v] (8 or 16), register budget v & 1
     // (0: 128 threads x 3 blocks per SM, 168 registers; 1: 256 x 2, 128 registers)
     const void *fwd_fn[NVAR];
-    const void *adj_fn[NVAR];
+    const void *adj_fn[NVAR];   // adjoint coefficient-gradient stage (the larger footprint)
+    const void *jvp_fn[NVAR];   // adjoint JVP stage
+    const void *net_rev_fn;     // network reverse pass (one block per chunk)
+    size_t (*net_rev_smem)(int NN);
     int max_wpb[NVAR];                   // largest warps per block each variant allows
     int sw[NVAR];
     size_t (*fwd_smem[NVAR])(int T, int NN);  // bytes per warp
     size_t (*adj_smem[NVAR])(int T, int NN);
     void (*launch_fwd[NVAR])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
-    void (*launch_adj[NVAR])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
+    // adjoint stages (0 JVP, 1 network reverse, 2 coefficient gradient; -1 all)
+    void (*launch_adj[NVAR])(const AtomArgs &, int blocks, int wpb, int stage, cudaStream_t);
 };
 
 const KernelSet *select_kernels(int nR, int kR, int nA, int kA);
@@ -125,6 +132,7 @@ struct Ctx {
 
     // per-step buffers
     DevBuf E_atom, F_own, W_atom, G, st_qt, st_h, st_A;
+    DevBuf st_D, st_S, st_b, st_ab;   // adjoint stage outputs (JVP of A, radial species sums, b, abar)
     DevBuf fbar, ebar, wbar, zt, ut, om, dqt, cpart, annpart;
     DevBuf F_int, E_int, W_int;       // internal outputs for nep_loss_grad
     DevBuf loss_part, gb1, n_sv, loss3_int, grad_int;
@@ -220,7 +228,8 @@ int launch_expand(Ctx *c);
 int launch_forward(Ctx *c, float *q_raw);
 // explicit schedules (mini-batch mode)
 int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb);
-int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb);
+int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
+                         const int *chunks, int n_chunks);
 int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks);
 int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi, const int *wlo, const int *whi,
                             const int *warp_begin);
@@ -235,7 +244,7 @@ int launch_loss_final(Ctx *c, double *loss3, const double *fpart = nullptr, int 
 int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
                    double lF, double lV, double *loss3, float *grad);
 int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *dW);
-int launch_adjoint(Ctx *c);
+int launch_adjoint(Ctx *c, int stage = -1);
 int launch_ann_grad(Ctx *c);
 int launch_grad_final(Ctx *c, float *grad);
 int launch_range(Ctx *c, const float *q, float *qmin, float *qmax);

@@ -88,7 +88,19 @@ struct AtomArgs {
     float *dqt;             // [Na_work][ND] normalised descriptor JVP
     float *cpart;           // [(W + T)][T][NC] per-warp c-gradient partials
     float *q_raw;           // optional [Na][ND] raw descriptors (descriptor export), may be null
+    // adjoint stages: JVP -> network reverse (chunks of <= 128 work positions of one
+    // species) -> coefficient gradient
+    const int *chunks;      // [n_chunks + 1] chunk boundaries (work positions)
+    int n_chunks;
+    int NDP;                // padded descriptor length
+    float *st_D;            // [Na_work][NA*24] JVP of the angular moments, [lm][n]
+    float *st_S;            // [Na_work][T][2 KR] radial species sums S^b_k | S'^b_k
+    float *st_b;            // [Na_work][ND] s * dE_i/dq~
+    float *st_ab;           // [Na_work][ND] abar = dJ/dq (scaled)
 };
+
+// Network reverse pass over the chunks (nep_net.cu).
+void launch_net_rev(const AtomArgs &a, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- warp helpers
 
@@ -490,11 +502,12 @@ __device__ __forceinline__ float sym_trace_prod(const float *A, const float *B) 
 //   V = kzz phi(r/a) / r,  phi(x) = 0.1818 e^{-3.2x} + 0.5099 e^{-0.9423x} + 0.2802 e^{-0.4029x}
 //       + 0.02817 e^{-0.2016x},  kzz = e^2/(4 pi eps0) Z_i Z_j,  a = 0.8854 a_0/(Z_i^0.23 + Z_j^0.23),
 // times the switch f_s = 1 below r1, (1 + cos(pi (r - r1)/(r2 - r1)))/2 up to r2.  Called for
-// r < r2 only; e = f_s V, de = d(f_s V)/dr.
+// r < r2 only; e = f_s V, de = d(f_s V)/dr.  Hardware exponential and sine/cosine: a few
+// ulp, far inside the FP32 path's tolerance.
 __device__ __forceinline__ void zbl_term(float r, float kzz, float inv_a, float r1, float r2, float &e, float &de) {
     const float x = r * inv_a;
-    const float t0 = 0.1818f * expf(-3.2f * x), t1 = 0.5099f * expf(-0.9423f * x);
-    const float t2 = 0.2802f * expf(-0.4029f * x), t3 = 0.02817f * expf(-0.2016f * x);
+    const float t0 = 0.1818f * __expf(-3.2f * x), t1 = 0.5099f * __expf(-0.9423f * x);
+    const float t2 = 0.2802f * __expf(-0.4029f * x), t3 = 0.02817f * __expf(-0.2016f * x);
     const float phi = (t0 + t1) + (t2 + t3);
     const float dphi = -inv_a * ((3.2f * t0 + 0.9423f * t1) + (0.4029f * t2 + 0.2016f * t3));
     const float rinv = 1.0f / r;
@@ -504,7 +517,7 @@ __device__ __forceinline__ void zbl_term(float r, float kzz, float inv_a, float 
     if (r >= r1) {
         const float w = r2 - r1;
         float sn, cs;
-        sincosf(PI_F * (r - r1) / w, &sn, &cs);
+        __sincosf(PI_F * (r - r1) / w, &sn, &cs);  // argument in [0, pi]
         f = 0.5f * (1.0f + cs);
         fp = -0.5f * sn * PI_F / w;
     }

@@ -590,6 +590,13 @@ static AtomArgs atom_args(Ctx *c) {
     a.om = c->om.as<float>();
     a.dqt = c->dqt.as<float>();
     a.cpart = c->cpart.as<float>();
+    a.chunks = c->chunk_begin.as<int>();
+    a.n_chunks = c->n_chunks;
+    a.NDP = c->NDP;
+    a.st_D = c->st_D.as<float>();
+    a.st_S = c->st_S.as<float>();
+    a.st_b = c->st_b.as<float>();
+    a.st_ab = c->st_ab.as<float>();
     return a;
 }
 
@@ -629,13 +636,12 @@ int launch_forward(Ctx *c, float *q_raw) {
     return NEP_OK;
 }
 
-int launch_adjoint(Ctx *c) {
+int launch_adjoint(Ctx *c, int stage) {
     if (c->n_atoms == 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.warp_begin = c->adj.warp_begin.as<int>();
-    const size_t smem = c->ks->adj_smem[c->adj.var](c->T, c->NN) * c->adj.wpb;
-    c->ks->launch_adj[c->adj.var](a, c->adj.blocks, c->adj.wpb, smem, c->stream);
-    CK_LAUNCH("k_adjoint");
+    c->ks->launch_adj[c->adj.var](a, c->adj.blocks, c->adj.wpb, stage, c->stream);
+    CK_LAUNCH("adjoint stages");
     return NEP_OK;
 }
 
@@ -650,14 +656,16 @@ int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blo
     return NEP_OK;
 }
 
-int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb) {
+int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
+                         const int *chunks, int n_chunks) {
     if (blocks <= 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.work = work;
     a.warp_begin = warp_begin;
-    const size_t smem = c->ks->adj_smem[var](c->T, c->NN) * wpb;
-    c->ks->launch_adj[var](a, blocks, wpb, smem, c->stream);
-    CK_LAUNCH("k_adjoint");
+    a.chunks = chunks;
+    a.n_chunks = n_chunks;
+    c->ks->launch_adj[var](a, blocks, wpb, -1, c->stream);
+    CK_LAUNCH("adjoint stages");
     return NEP_OK;
 }
 
@@ -885,7 +893,7 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
     if ((rc = launch_count_hasw(c, hw))) return rc;
     CK(cudaMemsetAsync(c->p_acc.ptr, 0, sizeof(double) * c->P, c->stream));
     const int pv = 2;  // one warp per atom: lanes-per-atom 16, 168-register variant
-    const size_t fs = c->ks->fwd_smem[pv](c->T, c->NN), as = c->ks->adj_smem[pv](c->T, c->NN);
+    const size_t fs = c->ks->fwd_smem[pv](c->T, c->NN);
     const size_t gsm = ann_smem(c);
     const int groups = ann_groups(c);
     for (int64_t s = 0; s < ns; ++s) {
@@ -899,9 +907,11 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, s, s + 1,
                                 ps + s * 3, 1)))
             return rc;
-        c->ks->launch_adj[pv](a, (int)n, 1, as, c->stream);
-        CK_LAUNCH("k_adjoint (plain)");
         const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
+        a.chunks = c->p_chunks.as<int>() + c->p_cofs[s];
+        a.n_chunks = nch;
+        c->ks->launch_adj[pv](a, (int)n, 1, -1, c->stream);
+        CK_LAUNCH("adjoint stages (plain)");
         if (nch > 0) {
             k_ann_grad<<<dim3(nch, groups), ANN_TILES, gsm, c->stream>>>(c->p_chunks.as<int>() + c->p_cofs[s], c->NN, c->NDP,
                                                                    c->zt.as<float>(), c->ut.as<float>(),

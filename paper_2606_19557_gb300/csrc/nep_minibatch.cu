@@ -273,7 +273,7 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
             break;
         if ((rc = launch_loss_final(c, loss3))) break;
         if ((rc = launch_adjoint_sched(c, c->mb_work.as<int>(), c->mb_wba.as<int>() + m.wa_off, m.Wa / c->mb_used[3],
-                                       c->mb_used[2], c->mb_used[3])))
+                                       c->mb_used[2], c->mb_used[3], c->mb_chunks.as<int>() + m.ck_off, m.n_ck)))
             break;
         if ((rc = launch_ann_grad_chunks(c, c->mb_chunks.as<int>() + m.ck_off, m.n_ck))) break;
         rc = launch_grad_final_sched(c, grad, c->mb_clo.as<int>() + mi * T, c->mb_chi.as<int>() + mi * T,

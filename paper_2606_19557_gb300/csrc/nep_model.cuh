@@ -7,28 +7,32 @@
 // Forward (k_forward):
 //   A_nlm = sum_j g^A_n(r_ij) Y_lm(r^_ij)          pair geometry staged in shared memory,
 //                                                   lanes own (l, m) outputs
-//   q_n   = sum_b sum_k c^{t_i b}_{nk} S^b_k,  S^b_k = sum_{j: t_j = b} f_k(r_ij)
-//                                                   (the radial descriptor is linear in c)
+//   q_n   = sum_j sum_k c^{t_i t_j}_{nk} f_k(r_ij)  (one species: through the sums
+//                                                   S_k = sum_j f_k(r_ij), q being linear in c)
 //   q_nl  = sum_m A_nlm^2, q4_n, q5_n               (Methods, Eq. "q3b"; 4-/5-body readings)
 //   E_i   = w1 . tanh(W0 q~ - b0) - b1              (Eq. "ann"), e = dE_i/dq~
 //   G_p   = dE_i/dd_p                               pair gradients, written per pair
-// Adjoint (k_adjoint), for cotangents fbar = dL/dF, ebar = dL/dE_s, wbar = dL/dW_s:
+// Adjoint (k_adj_jvp -> k_net_rev -> k_adj_cg), for cotangents fbar = dL/dF,
+// ebar = dL/dE_s, wbar = dL/dW_s:
 //   lambda_p = fbar_i - fbar_j - wbar_s d_p
 //   dq_i = sum_p (dq_i/dd_p) lambda_p               forward-mode JVP of the descriptors
 //   reverse through the network (tanh', tanh'') -> per-atom vectors for the network
-//   gradient, abar = dJ/dq; then dJ/dc (radial part factorised over species sums,
-//   angular part per pair).
+//   gradient, abar = dJ/dq (tiled products over chunks of atoms of one species);
+//   then dJ/dc (radial part factorised over species sums, angular part per pair).
 //
 // Work layout.  Per-pair quantities are computed one pair per lane; reductions over
 // the pairs of an atom go through rows staged in shared memory and read by lanes that
 // own outputs, in a fixed order:
 //   * angular moments and their JVP: lanes own (l, m);
-//   * radial species sums S^b_k (more than one species): lanes own k and walk their
-//     atom's rows, which come sorted by neighbour species, adding each species run into
-//     the atom's S^b (one species: every lane sums its own pairs, one reduction per atom);
+//   * radial species sums S^b_k of the adjoint (more than one species): lanes own k and
+//     walk their atom's rows, which come sorted by neighbour species, adding each species
+//     run into the atom's S^b (one species: every lane sums its own pairs, one reduction
+//     per atom); the forward's radial descriptor takes each pair's g_n directly;
 //   * angular coefficient gradient: all 32 lanes own (n, k-range) tiles of the current
 //     (t_i, t_j) block and walk the rows of every atom of the batch; a species change
-//     flushes the tile into the warp's shared accumulator.
+//     flushes the tile into the warp's shared accumulator (one species and a small block:
+//     every lane sums the whole block over its own pairs in registers instead, and the
+//     lanes reduce it once per warp).
 // Per-atom matrices that every pair of an atom reads (dE/dA, dJ/dA) are stored [lm][n]
 // with n padded to a multiple of 4, and the coefficient rows c[n][k] are 16-byte-aligned
 // copies in the parameter buffer, so both are read with 128-bit loads.
@@ -231,13 +235,9 @@ struct FwdL {
         float g[G][SW][NAP];  // g^A_n of each lane's pair
         float Y[G][SW][L3];
     };
-    struct __align__(16) Rad {
-        float f[G][SW][S::KR + 1];  // f_k, then the species bits
-    };
     Atom at[G];
     union {
         Mom m;
-        Rad r;
     } st;
     // runtime tail (floats): u[G][NN], Sr[G][T][KR], beta[G][T][KR]
     __host__ __device__ static size_t tail(int T, int NN) { return (size_t)G * NN + 2 * (size_t)G * T * S::KR; }
@@ -246,21 +246,17 @@ struct FwdL {
     }
 };
 
+// Adjoint, stage 1 (k_adj_jvp): the JVP of the descriptors.
 template <class S, int SW>
-struct AdjL {
+struct JvpL {
     static constexpr int G = 32 / SW;
     static constexpr int NAP = round4(S::NA);
     static constexpr int NLMO = (L3 + SW - 1) / SW;
     struct __align__(16) Atom {
-        float A[L3 * NAP];   // A_nlm at [lm][n]
-        float D[L3 * NAP];   // dA (the JVP), then dJ/dA in place
-        float Ah[L3 * NAP];  // dE_i/dA
-        float b[S::ND];
-        float ab[S::ND];
+        float A[L3 * NAP];  // A_nlm at [lm][n]
+        float D[L3 * NAP];  // dA_nlm, the JVP of the moments, at [lm][n]
         float dqt[S::ND];
         float G4[S::NA * 5];
-        float H4[S::NA * 5];
-        float ad[S::NA];  // sum_m A_n1m dA_n1m (read by every l = 1 lane before dA is overwritten)
     };
     struct __align__(16) Jvp {
         float g[G][SW][NAP];   // g^A_n
@@ -268,26 +264,50 @@ struct AdjL {
         float Y[G][SW][L3];
         float P[G][SW][L3];    // grad Y_lm . p, p the part of lambda / r normal to r^
     };
-    struct __align__(16) Cg {
-        float2 ab[G][SW][S::NA];  // (alpha_n, beta_n) of each lane's pair
-        float2 ff[G][SW][S::KA];  // (f_k, f'_k)
-        int t[G][SW];             // species of the neighbour
-    };
     struct __align__(16) Rad {
         float f[G][SW][2 * S::KR + 1];  // f_k, (r^.lambda) f'_k, then the species bits
     };
     Atom at[G];
     union {
         Jvp j;
-        Cg c;
         Rad r;
     } st;
-    // runtime tail: u[G][NN], Sr[G][T][2 KR], accR[T][NCR], accA[T][NCA]
+    // runtime tail: Sr[G][T][2 KR]
+    __host__ __device__ static size_t tail(int T, int NN) { return 2 * (size_t)G * T * S::KR; }
+    __host__ __device__ static size_t bytes(int T, int NN) {
+        return ((sizeof(JvpL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
+    }
+};
+
+// Adjoint, stage 3 (k_adj_cg): dJ/dA and the coefficient gradient.
+template <class S, int SW>
+struct CgL {
+    static constexpr int G = 32 / SW;
+    static constexpr int NAP = round4(S::NA);
+    static constexpr int NLMO = (L3 + SW - 1) / SW;
+    struct __align__(16) Atom {
+        float A[L3 * NAP];   // A_nlm at [lm][n]
+        float D[L3 * NAP];   // dA, then dJ/dA in place
+        float Ah[L3 * NAP];  // dE_i/dA
+        float b[S::ND];
+        float ab[S::ND];
+        float G4[S::NA * 5];
+        float H4[S::NA * 5];
+        float ad[S::NA];  // sum_m A_n1m dA_n1m (read by every l = 1 lane before dA is overwritten)
+    };
+    struct __align__(16) Cg {
+        float2 ab[G][SW][S::NA];  // (alpha_n, beta_n) of each lane's pair
+        float2 ff[G][SW][S::KA];  // (f_k, f'_k)
+        int t[G][SW];             // species of the neighbour
+    };
+    Atom at[G];
+    Cg st;
+    // runtime tail: Sr[G][T][2 KR], accR[T][NCR], accA[T][NCA]
     __host__ __device__ static size_t tail(int T, int NN) {
-        return (size_t)G * NN + 2 * (size_t)G * T * S::KR + (size_t)T * (S::NCR + S::NCA);
+        return 2 * (size_t)G * T * S::KR + (size_t)T * (S::NCR + S::NCA);
     }
     __host__ __device__ static size_t bytes(int T, int NN) {
-        return ((sizeof(AdjL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
+        return ((sizeof(CgL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
     }
 };
 
@@ -300,7 +320,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
     constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
     constexpr int KR4 = round4(KR), KA4 = round4(KA);
     constexpr int VR = pow2ceil(KR);
-    constexpr int RC = (KR + SW - 1) / SW;
+    constexpr int VRN = pow2ceil(NR);
     extern __shared__ __align__(16) float smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int grp = lane / SW, sl = lane % SW;
@@ -412,9 +432,10 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                 }
             }
             if (__any_sync(FULL, nRad > 0)) flush_groups<VR, SW>(v, Sr, KR, nRad > 0, lane, false);
-        } else {
-            float v[RC];
-            int bcur = -1;
+        } else {  // several species: every lane adds g_n = sum_k c^{t_i t_j}_nk f_k of its own pairs
+            float qv[VRN];
+#pragma unroll
+            for (int n = 0; n < VRN; ++n) qv[n] = 0.0f;
             float4 nxr = pair_or_zero(prs, sl, nRad);
             for (int c0 = 0; c0 < maxR; c0 += SW) {
                 const int k = c0 + sl;
@@ -422,27 +443,28 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
                 nxr = pair_or_zero(prs, k + SW, nRad);
                 if (k < nRad) {
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                    float *row = sm.st.r.f[grp][sl];
-                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, row);
-                    row[KR] = __int_as_float(pair_t(pd));
+                    float f[KR], g[NR];
+                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
+                    contract_c<NR, KR>(cRi + pair_t(pd) * NR * KR4, f, g);
+#pragma unroll
+                    for (int n = 0; n < NR; ++n) qv[n] += g[n];
                 }
-                __syncwarp();
-                walk_species_rows<KR, SW>(sm.st.r.f[grp], min(SW, nRad - c0), sl, Sr, v, bcur);
-                __syncwarp();
             }
-            close_species_run<KR, SW>(sl, Sr, v, bcur);
+            for (int n = sl; n < NR; n += SW) at.q[n] = 0.0f;
+            __syncwarp();
+            if (__any_sync(FULL, nRad > 0)) flush_groups<VRN, SW>(qv, at.q, NR, nRad > 0, lane, false);
         }
         __syncwarp();
 
         // ---------------------------------------------------------------- descriptors
-        for (int n = sl; n < NR; n += SW) {
-            float q = 0.0f;
-            for (int bb = 0; bb < T; ++bb) {
-                const float *cr = cRi + (bb * NR + n) * KR4;
+        if (T == 1) {
+            for (int n = sl; n < NR; n += SW) {
+                float q = 0.0f;
+                const float *cr = cRi + n * KR4;
 #pragma unroll
-                for (int kk = 0; kk < KR; ++kk) q += __ldg(cr + kk) * Sr[bb * KR + kk];
+                for (int kk = 0; kk < KR; ++kk) q += __ldg(cr + kk) * Sr[kk];
+                at.q[n] = q;
             }
-            at.q[n] = q;
         }
         for (int e = sl; e < 4 * NA; e += SW) {
             const int n = e % NA, l = e / NA + 1;
@@ -676,19 +698,39 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forw
 }
 
 // ============================================================================= adjoint
+// Three stages, for cotangents fbar = dL/dF, ebar = dL/dE_s, wbar = dL/dW_s:
+//   k_adj_jvp  (per atom)  lambda_p = fbar_i - fbar_j - wbar_s d_p; the JVP dq~ of the
+//                          descriptors along lambda; stores dq~, dA and the radial
+//                          species sums S^b_k, S'^b_k;
+//   k_net_rev  (per chunk of atoms of one species, tiled products) the reverse pass through
+//                          the network: zeta, u, omega and abar = dJ/dq~, b = dE/dq~;
+//   k_adj_cg   (per atom)  dJ/dA and the gradient into the coefficients c.
+
+// Loads a [lm][n]-packed per-atom matrix (NA x 24 floats) into a [lm][NAP] shared row set.
+template <int NA, int NAP, int SW>
+__device__ __forceinline__ void load_lm_rows(const float *src, float *dst, int sl) {
+    for (int e = sl; e < L3 * NA; e += SW) {
+        const int lm = e / NA, n = e - lm * NA;
+        dst[lm * NAP + n] = src[e];
+    }
+}
+
+// lambda_p of a pair (record pd, neighbour j) of an atom with cotangent fbi and structure wbar
+__device__ __forceinline__ void pair_lambda(const AtomArgs &a, float4 pd, float fbx, float fby, float fbz,
+                                            const float *Wb, float &lx, float &ly, float &lz) {
+    const float4 fbj = a.fbar[pair_j(pd)];
+    lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
+    ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
+    lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+}
 
 template <class S, int SW, int VAR>
-__global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjoint(AtomArgs a) {
-    using L = AdjL<S, SW>;
+__global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adj_jvp(AtomArgs a) {
+    using L = JvpL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
-    constexpr int NCR = S::NCR, NCA = S::NCA, NC = S::NC;
     constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
     constexpr int KR4 = round4(KR), KA4 = round4(KA);
     constexpr int VR2 = pow2ceil(2 * KR);
-    constexpr int RC2 = (2 * KR + SW - 1) / SW;
-    // angular coefficient-gradient tiles: lane -> (n, k-range of width TW), 32 lanes
-    constexpr int NKT = 32 / NA;
-    constexpr int TW = (KA + NKT - 1) / NKT;
     extern __shared__ __align__(16) float smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int grp = lane / SW, sl = lane % SW;
@@ -696,61 +738,19 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
     float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
     L &sm = *reinterpret_cast<L *>(base_ptr);
     float *tail = base_ptr + sizeof(L) / sizeof(float);
-    float *Sr = tail + G * NN + grp * T * 2 * KR;  // [T][2 KR] S^b_k | S'^b_k of this group
-    float *accR = tail + G * NN + G * T * 2 * KR;  // [T][NCR] (warp)
-    float *accA = accR + T * NCR;                  // [T][NCA] (warp)
-    const int tn = lane % NA, tk0 = (lane / NA) * TW;
-    const bool tile_own = lane / NA < NKT && tk0 < KA;
+    float *Sr = tail + grp * T * 2 * KR;  // [T][2 KR] S^b_k | S'^b_k of this group
 
     const int w = blockIdx.x * (blockDim.x >> 5) + wib;
     const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
     const ParOff po = par_offsets(T, NN, NR, KR, NA, KA);
-    const float *W0 = a.par + po.w0;
-    const float *W0T = a.par + po.w0t;
-    const float *w1 = a.par + po.w1;
     const float *scale = a.par + po.scale;
-
-    int cur_t = -1;
-    // open (t_i, t_j) tile of the angular coefficient gradient, carried across batches
-    float X[TW];
-#pragma unroll
-    for (int jj = 0; jj < TW; ++jj) X[jj] = 0.0f;
-    int xb = -1;
-    auto close_tile = [&]() {
-        if (xb >= 0 && tile_own) {
-#pragma unroll
-            for (int jj = 0; jj < TW; ++jj)
-                if (tk0 + jj < KA) accA[xb * NCA + tn * KA + tk0 + jj] += X[jj];
-        }
-#pragma unroll
-        for (int jj = 0; jj < TW; ++jj) X[jj] = 0.0f;
-    };
-    auto flush_slot = [&](int t) {
-        float *dst = a.cpart + (size_t)(w + t) * T * NC;
-        for (int bb = 0; bb < T; ++bb) {
-            for (int e = lane; e < NCR; e += 32) dst[(size_t)bb * NC + e] = accR[bb * NCR + e];
-            for (int e = lane; e < NCA; e += 32) dst[(size_t)bb * NC + NCR + e] = accA[bb * NCA + e];
-        }
-    };
 
     for (int bp = wbeg; bp < wend;) {
         int ti, nb, i;
         load_batch<SW>(a, bp, wend, lane, ti, nb, i);
         const bool act = grp < nb;
-        const int bp0 = bp;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
-        if (ti != cur_t) {
-            __syncwarp();
-            close_tile();
-            xb = -1;
-            __syncwarp();
-            if (cur_t >= 0) flush_slot(cur_t);
-            for (int e = lane; e < T * NCR; e += 32) accR[e] = 0.0f;
-            for (int e = lane; e < T * NCA; e += 32) accA[e] = 0.0f;
-            cur_t = ti;
-            __syncwarp();
-        }
         const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;
         const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;
         const int s = a.struct_of[i];
@@ -765,73 +765,13 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
             const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
             prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
         }
-
-        // ---------------------------------------------------------------- state of the forward pass
-        for (int e = sl; e < L3 * NA; e += SW) {  // stored [lm][n], n packed
-            const int lm = e / NA, n = e - lm * NA;
-            at.A[lm * NAP + n] = a.st_A[(size_t)wi * NA * L3 + e];
-        }
-        for (int mu = lane; mu < NN; mu += 32) {
-            const float wo = w1[ti * NN + mu];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const float h = a.st_h[(size_t)(bp0 + (g < nb ? g : 0)) * NN + mu];
-                tail[g * NN + mu] = wo * (1.0f - h * h);
-            }
-        }
-        __syncwarp();
-        for (int v = lane; v < ND; v += 32) {
-            float e[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) e[g] = 0.0f;
-            const float *wr = W0 + (size_t)ti * NN * ND + v;
-#pragma unroll 10
-            for (int mu = 0; mu < NN; ++mu) {
-                const float wv = wr[(size_t)mu * ND];
-#pragma unroll
-                for (int g = 0; g < G; ++g) e[g] += wv * tail[g * NN + mu];
-            }
-            const float sc = scale[v];
-#pragma unroll
-            for (int g = 0; g < G; ++g) sm.at[g].b[v] = e[g] * sc;
-        }
-        for (int n = sl; n < NA; n += SW) {
-            float a2[5], Mt[6], M2[6], pr[5];
-            l2_block<NAP>(at.A, n, a2);
-            l2_matrix(a2, Mt);
-            sym_prod(Mt, Mt, M2);
-            l2_project(M2, pr);
-#pragma unroll
-            for (int m = 0; m < 5; ++m) at.G4[n * 5 + m] = 3.0f * KAPPA_REAL * pr[m];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < NLMO; ++j) {
-            const int lm = sl + j * SW;
-            if (lm < L3) {
-                const int l = l_of_lm(lm);
-                float ah[NA];
-#pragma unroll
-                for (int n = 0; n < NA; ++n) {
-                    const float av = at.A[lm * NAP + n];
-                    float x = 2.0f * at.b[NR + (l - 1) * NA + n] * av;
-                    if (l == 2) x += at.b[NR + 4 * NA + n] * at.G4[n * 5 + (lm - 3)];
-                    if (l == 1) {
-                        const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
-                        x += at.b[NR + 5 * NA + n] * 4.0f * (x0 * x0 + x1 * x1 + x2 * x2) * av;
-                    }
-                    ah[n] = x;
-                }
-                store_row4<NA>(at.Ah + lm * NAP, ah);
-            }
-        }
+        load_lm_rows<NA, NAP, SW>(a.st_A + (size_t)wi * NA * L3, at.A, sl);
         const float4 *prs = a.pair + beg;
         const float4 fbi = a.fbar[i];
         const float fbx = fbi.x, fby = fbi.y, fbz = fbi.z;
         float Wb[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Wb[k] = a.wbar[(size_t)s * 9 + k];
-        const float eb = a.ebar[s];
         __syncwarp();
 
         // ---------------------------------------------------------------- angular JVP: dA_nlm
@@ -847,11 +787,9 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                 const float4 pd = nxt;
                 nxt = pair_or_zero(prs, k + SW, nAng);
                 if (k < nAng) {
-                    const int j = pair_j(pd), tj = pair_t(pd);
-                    const float4 fbj = a.fbar[j];
-                    const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
-                    const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
-                    const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+                    const int tj = pair_t(pd);
+                    float lx, ly, lz;
+                    pair_lambda(a, pd, fbx, fby, fbz, Wb, lx, ly, lz);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     const float rinv = inv_norm(r2);
                     const float r = r2 * rinv;
@@ -892,7 +830,13 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
 #pragma unroll
             for (int jj = 0; jj < NLMO; ++jj) {
                 const int lm = sl + jj * SW;
-                if (lm < L3) store_row4<NA>(at.D + lm * NAP, accd[jj]);
+                if (lm < L3) {
+                    store_row4<NA>(at.D + lm * NAP, accd[jj]);
+                    if (act) {
+#pragma unroll
+                        for (int n = 0; n < NA; ++n) a.st_D[(size_t)wi * NA * L3 + lm * NA + n] = accd[jj][n];
+                    }
+                }
             }
         }
 
@@ -909,11 +853,8 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                 const float4 pd = nxt;
                 nxt = pair_or_zero(prs, k + SW, nRad);
                 if (k < nRad) {
-                    const int j = pair_j(pd);
-                    const float4 fbj = a.fbar[j];
-                    const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
-                    const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
-                    const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+                    float lx, ly, lz;
+                    pair_lambda(a, pd, fbx, fby, fbz, Wb, lx, ly, lz);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     const float rinv = inv_norm(r2);
                     const float rl = (pd.x * lx + pd.y * ly + pd.z * lz) * rinv;
@@ -928,6 +869,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
             }
             if (__any_sync(FULL, nRad > 0)) flush_groups<VR2, SW>(v, Sr, 2 * KR, nRad > 0, lane, false);
         } else {
+            constexpr int RC2 = (2 * KR + SW - 1) / SW;
             float v[RC2];
             int bcur = -1;
             float4 nxt = pair_or_zero(prs, sl, nRad);
@@ -936,11 +878,8 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                 const float4 pd = nxt;
                 nxt = pair_or_zero(prs, k + SW, nRad);
                 if (k < nRad) {
-                    const int j = pair_j(pd);
-                    const float4 fbj = a.fbar[j];
-                    const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
-                    const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
-                    const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+                    float lx, ly, lz;
+                    pair_lambda(a, pd, fbx, fby, fbz, Wb, lx, ly, lz);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     const float rinv = inv_norm(r2);
                     const float rl = (pd.x * lx + pd.y * ly + pd.z * lz) * rinv;
@@ -958,8 +897,19 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
             close_species_run<2 * KR, SW>(sl, Sr, v, bcur);
         }
         __syncwarp();
+        if (act)
+            for (int e = sl; e < T * 2 * KR; e += SW) a.st_S[(size_t)wi * T * 2 * KR + e] = Sr[e];
 
         // ---------------------------------------------------------------- JVP of the descriptors
+        for (int n = sl; n < NA; n += SW) {
+            float a2[5], Mt[6], M2[6], pr[5];
+            l2_block<NAP>(at.A, n, a2);
+            l2_matrix(a2, Mt);
+            sym_prod(Mt, Mt, M2);
+            l2_project(M2, pr);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) at.G4[n * 5 + m] = 3.0f * KAPPA_REAL * pr[m];
+        }
         for (int n = sl; n < NR; n += SW) {
             float d = 0.0f;
             for (int bb = 0; bb < T; ++bb) {
@@ -979,113 +929,320 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
             const int v = NR + (l - 1) * NA + n;
             at.dqt[v] = 2.0f * s2 * scale[v];
         }
+        __syncwarp();
         for (int n = sl; n < NA; n += SW) {
-            float a2[5], d2[5];
-            l2_block<NAP>(at.A, n, a2);
+            float d2[5];
             l2_block<NAP>(at.D, n, d2);
             float d4 = 0.0f;
 #pragma unroll
             for (int m = 0; m < 5; ++m) d4 += at.G4[n * 5 + m] * d2[m];
             at.dqt[NR + 4 * NA + n] = d4 * scale[NR + 4 * NA + n];
-            float Mt[6], dMt[6], Pm[6], pr[5];
+            const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
+            const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
+            const float ad = x0 * at.D[n] + x1 * at.D[NAP + n] + x2 * at.D[2 * NAP + n];
+            at.dqt[NR + 5 * NA + n] = 4.0f * q1 * ad * scale[NR + 5 * NA + n];
+        }
+        __syncwarp();
+        if (act)
+            for (int v = sl; v < ND; v += SW) a.dqt[(size_t)wi * ND + v] = at.dqt[v];
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------- network reverse
+// Per chunk of <= 128 work positions of one species t, in tiles of 64 atoms (Eq. "ann"):
+//   v = W0 dq~,  h' = 1 - h^2,  h'' = -2 h h',
+//   zeta = ebar w1 h' + w1 h'' v,  u = w1 h',  omega = ebar h + h' v,
+//   abar = s (W0^T zeta),  b = s (W0^T u).
+// 256 threads as 16 x 16; each owns 4 atoms x 4 columns of a 64 x 64 output block, and the
+// operands come from shared memory with 128-bit loads (atoms along the fast axis).
+constexpr int NETR = 64;  // atoms per tile
+
+template <class S>
+__host__ __device__ inline size_t net_rev_smem(int NN) {
+    const size_t NDQ = round4(S::ND), NNP = round4(NN);
+    return sizeof(float) * (NDQ * NETR + 2 * NNP * NETR + (size_t)S::ND * NNP + (size_t)NN * NDQ);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
+    constexpr int ND = S::ND, NDQ = round4(ND);
+    extern __shared__ __align__(16) float smn[];
+    const int NN = a.NN, NNP = round4(NN), T = a.T;
+    float *Q = smn;                 // [NDQ][NETR] dq~, transposed
+    float *Z = Q + NDQ * NETR;      // [NNP][NETR] zeta, transposed
+    float *U = Z + NNP * NETR;      // [NNP][NETR] u, transposed
+    float *Wt = U + NNP * NETR;     // [ND][NNP]  W0^T of the species
+    float *Wn = Wt + ND * NNP;      // [NN][NDQ]  W0 of the species
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int rc0 = a.chunks[blockIdx.x], rc1 = a.chunks[blockIdx.x + 1];
+    if (rc0 >= rc1) return;
+    const int t = a.type[a.work[rc0]];
+    const ParOff po = par_offsets(T, NN, S::NR, S::KR, S::NA, S::KA);
+    const float *W0 = a.par + po.w0 + (size_t)t * NN * ND;
+    const float *W0T = a.par + po.w0t + (size_t)t * ND * NN;
+    const float *w1 = a.par + po.w1 + (size_t)t * NN;
+    const float *scale = a.par + po.scale;
+    for (int e = threadIdx.x; e < ND * NNP; e += 256) {
+        const int k = e / NNP, mu = e - k * NNP;
+        Wt[e] = mu < NN ? W0T[(size_t)k * NN + mu] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < NN * NDQ; e += 256) {
+        const int mu = e / NDQ, v = e - mu * NDQ;
+        Wn[e] = v < ND ? W0[(size_t)mu * ND + v] : 0.0f;
+    }
+    for (int rb = rc0; rb < rc1; rb += NETR) {
+        const int nr = min(NETR, rc1 - rb);
+        __syncthreads();  // the weights are staged; the previous tile is done with Q, Z, U
+        for (int e = threadIdx.x; e < NETR * NDQ; e += 256) {
+            const int r = e / NDQ, k = e - r * NDQ;
+            Q[k * NETR + r] = (r < nr && k < ND) ? a.dqt[(size_t)(rb + r) * ND + k] : 0.0f;
+        }
+        __syncthreads();
+        const int r0 = ty * 4;
+        for (int cb = 0; cb < NNP; cb += 64) {
+            const int mu0 = cb + tx * 4;
+            if (mu0 < NNP) {
+                float acc[4][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
+#pragma unroll 7
+                for (int k = 0; k < ND; ++k) {
+                    const float4 q4 = *reinterpret_cast<const float4 *>(Q + k * NETR + r0);
+                    const float4 w4 = *reinterpret_cast<const float4 *>(Wt + k * NNP + mu0);
+                    const float q[4] = {q4.x, q4.y, q4.z, q4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] += q[x] * wv[y];
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int r = r0 + x;
+                    const bool row = r < nr;
+                    const int wpos = rb + (row ? r : 0);
+                    const float eb = row ? a.ebar[a.struct_of[a.work[wpos]]] : 0.0f;
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        const int mu = mu0 + y;
+                        float ze = 0.0f, uu = 0.0f;
+                        if (row && mu < NN) {
+                            const float h = a.st_h[(size_t)wpos * NN + mu];
+                            const float wo = w1[mu];
+                            const float hp = 1.0f - h * h;
+                            const float hpp = -2.0f * h * hp;
+                            ze = eb * wo * hp + wo * hpp * acc[x][y];
+                            uu = wo * hp;
+                            a.zt[(size_t)wpos * NN + mu] = ze;
+                            a.ut[(size_t)wpos * NN + mu] = uu;
+                            a.om[(size_t)wpos * NN + mu] = eb * h + hp * acc[x][y];
+                        }
+                        Z[mu * NETR + r] = ze;
+                        U[mu * NETR + r] = uu;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int cb = 0; cb < NDQ; cb += 64) {
+            const int v0 = cb + tx * 4;
+            if (v0 < NDQ) {
+                float aa[4][4], ab[4][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) aa[x][y] = ab[x][y] = 0.0f;
+#pragma unroll 5
+                for (int mu = 0; mu < NN; ++mu) {
+                    const float4 z4 = *reinterpret_cast<const float4 *>(Z + mu * NETR + r0);
+                    const float4 u4 = *reinterpret_cast<const float4 *>(U + mu * NETR + r0);
+                    const float4 w4 = *reinterpret_cast<const float4 *>(Wn + mu * NDQ + v0);
+                    const float z[4] = {z4.x, z4.y, z4.z, z4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) {
+                            aa[x][y] += z[x] * wv[y];
+                            ab[x][y] += uu[x] * wv[y];
+                        }
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int r = r0 + x;
+                    if (r < nr) {
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) {
+                            const int v = v0 + y;
+                            if (v < ND) {
+                                const float sc = scale[v];
+                                a.st_ab[(size_t)(rb + r) * ND + v] = aa[x][y] * sc;
+                                a.st_b[(size_t)(rb + r) * ND + v] = ab[x][y] * sc;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <class S, int SW, int VAR>
+__global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adj_cg(AtomArgs a) {
+    using L = CgL<S, SW>;
+    constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
+    constexpr int NCR = S::NCR, NCA = S::NCA, NC = S::NC;
+    constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
+    // angular coefficient-gradient tiles: lane -> (n, k-range of width TW), 32 lanes
+    constexpr int NKT = 32 / NA;
+    constexpr int TW = (KA + NKT - 1) / NKT;
+    extern __shared__ __align__(16) float smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane / SW, sl = lane % SW;
+    const int T = a.T, NN = a.NN;
+    float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
+    L &sm = *reinterpret_cast<L *>(base_ptr);
+    float *tail = base_ptr + sizeof(L) / sizeof(float);
+    float *Sr = tail + grp * T * 2 * KR;       // [T][2 KR] S^b_k | S'^b_k of this group
+    float *accR = tail + G * T * 2 * KR;       // [T][NCR] (warp)
+    float *accA = accR + T * NCR;              // [T][NCA] (warp)
+    const int tn = lane % NA, tk0 = (lane / NA) * TW;
+    const bool tile_own = lane / NA < NKT && tk0 < KA;
+
+    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
+
+    int cur_t = -1;
+    // One species (and a coefficient block of at most 64 values): every lane keeps the whole
+    // (0, 0) block of the angular coefficient gradient for its own pairs, across all the
+    // warp's atoms, and the group lanes reduce it once at the end of the warp's range.
+    constexpr bool REG1 = S::NCA <= 64;
+    constexpr int V1 = REG1 ? pow2ceil(NCA) : 1;
+    const bool one_species = REG1 && T == 1;
+    float X1[V1];
+#pragma unroll
+    for (int e = 0; e < V1; ++e) X1[e] = 0.0f;
+    // open (t_i, t_j) tile of the angular coefficient gradient, carried across batches
+    float X[TW];
+#pragma unroll
+    for (int jj = 0; jj < TW; ++jj) X[jj] = 0.0f;
+    int xb = -1;
+    auto close_tile = [&]() {
+        if (xb >= 0 && tile_own) {
+#pragma unroll
+            for (int jj = 0; jj < TW; ++jj)
+                if (tk0 + jj < KA) accA[xb * NCA + tn * KA + tk0 + jj] += X[jj];
+        }
+#pragma unroll
+        for (int jj = 0; jj < TW; ++jj) X[jj] = 0.0f;
+    };
+    auto flush_slot = [&](int t) {
+        float *dst = a.cpart + (size_t)(w + t) * T * NC;
+        for (int bb = 0; bb < T; ++bb) {
+            for (int e = lane; e < NCR; e += 32) dst[(size_t)bb * NC + e] = accR[bb * NCR + e];
+            for (int e = lane; e < NCA; e += 32) dst[(size_t)bb * NC + NCR + e] = accA[bb * NCA + e];
+        }
+    };
+
+    for (int bp = wbeg; bp < wend;) {
+        int ti, nb, i;
+        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
+        const bool act = grp < nb;
+        const int wi = bp + (act ? grp : 0);
+        bp += nb;
+        if (ti != cur_t) {
+            __syncwarp();
+            close_tile();
+            xb = -1;
+            __syncwarp();
+            if (cur_t >= 0) flush_slot(cur_t);
+            for (int e = lane; e < T * NCR; e += 32) accR[e] = 0.0f;
+            for (int e = lane; e < T * NCA; e += 32) accA[e] = 0.0f;
+            cur_t = ti;
+            __syncwarp();
+        }
+        const int s = a.struct_of[i];
+        const int64_t beg = a.nbr_off[i];
+        const int nAng = act ? a.n_ang[i] : 0;
+        const int maxA = __reduce_max_sync(FULL, nAng);
+        typename L::Atom &at = sm.at[grp];
+        if (bp + grp < wend) {  // the atoms after this batch: bring their angular records into L2
+            const int ni = a.work[bp + grp];
+            prefetch_l2(a.pair + a.nbr_off[ni], sizeof(float4) * (size_t)a.n_ang[ni], sl, SW);
+        }
+
+        // ---------------------------------------------------------------- state of the earlier stages
+        load_lm_rows<NA, NAP, SW>(a.st_A + (size_t)wi * NA * L3, at.A, sl);
+        load_lm_rows<NA, NAP, SW>(a.st_D + (size_t)wi * NA * L3, at.D, sl);
+        for (int v = sl; v < ND; v += SW) {
+            at.b[v] = a.st_b[(size_t)wi * ND + v];
+            at.ab[v] = a.st_ab[(size_t)wi * ND + v];
+        }
+        for (int e = sl; e < T * 2 * KR; e += SW) Sr[e] = act ? a.st_S[(size_t)wi * T * 2 * KR + e] : 0.0f;
+        __syncwarp();
+        for (int n = sl; n < NA; n += SW) {
+            float a2[5], d2[5], Mt[6], dMt[6], M2[6], Pm[6], pr[5];
+            l2_block<NAP>(at.A, n, a2);
+            l2_block<NAP>(at.D, n, d2);
             l2_matrix(a2, Mt);
             l2_matrix(d2, dMt);
+            sym_prod(Mt, Mt, M2);
+            l2_project(M2, pr);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) at.G4[n * 5 + m] = 3.0f * KAPPA_REAL * pr[m];
             sym_prod(Mt, dMt, Pm);
             l2_project(Pm, pr);
 #pragma unroll
             for (int m = 0; m < 5; ++m) at.H4[n * 5 + m] = 6.0f * KAPPA_REAL * pr[m];
-            const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
-            const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
-            const float ad = x0 * at.D[n] + x1 * at.D[NAP + n] + x2 * at.D[2 * NAP + n];
-            at.ad[n] = ad;
-            at.dqt[NR + 5 * NA + n] = 4.0f * q1 * ad * scale[NR + 5 * NA + n];
+            at.ad[n] = at.A[n] * at.D[n] + at.A[NAP + n] * at.D[NAP + n] + at.A[2 * NAP + n] * at.D[2 * NAP + n];
         }
         __syncwarp();
 
-        // ---------------------------------------------------------------- reverse through the network
-        // ebar of every atom of the batch (one structure per atom)
-        float ebg[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) ebg[g] = __shfl_sync(FULL, eb, g * SW);
-        for (int mu = lane; mu < NN; mu += 32) {
-            float v[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) v[g] = 0.0f;
-            const float *wt = W0T + (size_t)ti * ND * NN + mu;
-#pragma unroll
-            for (int q = 0; q < ND; ++q) {
-                const float wv = wt[(size_t)q * NN];
-#pragma unroll
-                for (int g = 0; g < G; ++g) v[g] += wv * sm.at[g].dqt[q];
-            }
-            const float wo = w1[ti * NN + mu];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const int wg = bp0 + (g < nb ? g : 0);
-                const float h = a.st_h[(size_t)wg * NN + mu];
-                const float hp = 1.0f - h * h;
-                const float hpp = -2.0f * h * hp;
-                const float ze = ebg[g] * wo * hp + wo * hpp * v[g];
-                tail[g * NN + mu] = ze;  // zeta of atom g
-                if (g < nb) {
-                    a.zt[(size_t)wg * NN + mu] = ze;
-                    a.ut[(size_t)wg * NN + mu] = wo * hp;
-                    a.om[(size_t)wg * NN + mu] = ebg[g] * h + hp * v[g];
-                }
-            }
-        }
-        __syncwarp();
-        for (int v = lane; v < ND; v += 32) {
-            float e[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) e[g] = 0.0f;
-            const float *wr = W0 + (size_t)ti * NN * ND + v;
-#pragma unroll 10
-            for (int mu = 0; mu < NN; ++mu) {
-                const float wv = wr[(size_t)mu * ND];
-#pragma unroll
-                for (int g = 0; g < G; ++g) e[g] += wv * tail[g * NN + mu];
-            }
-            const float sc = scale[v];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                sm.at[g].ab[v] = e[g] * sc;
-                if (g < nb) a.dqt[(size_t)(bp0 + g) * ND + v] = sm.at[g].dqt[v];
-            }
-        }
-        __syncwarp();
-
-        // ---------------------------------------------------------------- dJ/dA (in place of dA)
+        // ---------------------------------------------------------------- dE/dA and dJ/dA (in place of dA)
 #pragma unroll
         for (int jj = 0; jj < NLMO; ++jj) {
             const int lm = sl + jj * SW;
             if (lm < L3) {
                 const int l = l_of_lm(lm);
-                float xr[NA];
+                float ah[NA], xr[NA];
 #pragma unroll
                 for (int n = 0; n < NA; ++n) {
                     const float av = at.A[lm * NAP + n], dv = at.D[lm * NAP + n];
+                    const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
+                    const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
                     const int v3 = NR + (l - 1) * NA + n;
+                    float h = 2.0f * at.b[v3] * av;
                     float x = 2.0f * at.ab[v3] * av + 2.0f * at.b[v3] * dv;
-                    if (l == 2)
+                    if (l == 2) {
+                        h += at.b[NR + 4 * NA + n] * at.G4[n * 5 + lm - 3];
                         x += at.ab[NR + 4 * NA + n] * at.G4[n * 5 + lm - 3] + at.b[NR + 4 * NA + n] * at.H4[n * 5 + lm - 3];
+                    }
                     if (l == 1) {
-                        const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
-                        const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
                         const int v5 = NR + 5 * NA + n;
+                        h += at.b[v5] * 4.0f * q1 * av;
                         x += at.ab[v5] * 4.0f * q1 * av + at.b[v5] * (8.0f * at.ad[n] * av + 4.0f * q1 * dv);
                     }
+                    ah[n] = h;
                     xr[n] = x;
                 }
+                store_row4<NA>(at.Ah + lm * NAP, ah);
                 store_row4<NA>(at.D + lm * NAP, xr);  // only this lane reads or writes row lm here
             }
         }
+        const float4 *prs = a.pair + beg;
+        const float4 fbi = a.fbar[i];
+        const float fbx = fbi.x, fby = fbi.y, fbz = fbi.z;
+        float Wb[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Wb[k] = a.wbar[(size_t)s * 9 + k];
         __syncwarp();
 
         // ---------------------------------------------------------------- radial coefficient gradient
 #pragma unroll 1
         for (int g2 = 0; g2 < G; ++g2) {
-            if (grp == g2) {
+            if (grp == g2 && act) {
                 for (int e = sl; e < T * NCR; e += SW) {
                     const int bb = e / NCR, rr = e - bb * NCR, n = rr / KR, kk = rr - n * KR;
                     accR[e] += at.ab[n] * Sr[bb * 2 * KR + kk] + at.b[n] * Sr[bb * 2 * KR + KR + kk];
@@ -1105,11 +1262,9 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                 const float4 pd = nxt;
                 nxt = pair_or_zero(prs, k + SW, nAng);
                 if (k < nAng) {
-                    const int j = pair_j(pd), tj = pair_t(pd);
-                    const float4 fbj = a.fbar[j];
-                    const float lx = fbx - fbj.x - (Wb[0] * pd.x + Wb[1] * pd.y + Wb[2] * pd.z);
-                    const float ly = fby - fbj.y - (Wb[3] * pd.x + Wb[4] * pd.y + Wb[5] * pd.z);
-                    const float lz = fbz - fbj.z - (Wb[6] * pd.x + Wb[7] * pd.y + Wb[8] * pd.z);
+                    const int tj = pair_t(pd);
+                    float lx, ly, lz;
+                    pair_lambda(a, pd, fbx, fby, fbz, Wb, lx, ly, lz);
                     const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
                     const float rinv = inv_norm(r2);
                     const float r = r2 * rinv;
@@ -1139,29 +1294,38 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
                     });
                     float f[KA], fp[KA];
                     basis_val_der<KA>(r, a.inv_rcA, f, fp);
+                    if (one_species) {
 #pragma unroll
-                    for (int n = 0; n < NA; ++n) sm.st.c.ab[grp][sl][n] = make_float2(al[n], be[n] * rl);
+                        for (int n = 0; n < NA; ++n)
 #pragma unroll
-                    for (int kk = 0; kk < KA; ++kk) sm.st.c.ff[grp][sl][kk] = make_float2(f[kk], fp[kk]);
-                    sm.st.c.t[grp][sl] = tj;
+                            for (int kk = 0; kk < KA; ++kk)
+                                X1[REG1 ? n * KA + kk : 0] += al[n] * f[kk] + (be[n] * rl) * fp[kk];
+                    } else {
+#pragma unroll
+                        for (int n = 0; n < NA; ++n) sm.st.ab[grp][sl][n] = make_float2(al[n], be[n] * rl);
+#pragma unroll
+                        for (int kk = 0; kk < KA; ++kk) sm.st.ff[grp][sl][kk] = make_float2(f[kk], fp[kk]);
+                        sm.st.t[grp][sl] = tj;
+                    }
                 }
+                if (one_species) continue;
                 __syncwarp();
                 // every lane walks the rows of every atom of the batch (uniform control flow)
 #pragma unroll 1
                 for (int g2 = 0; g2 < G; ++g2) {
                     const int cnt = min(SW, __shfl_sync(FULL, nAng, g2 * SW) - c0);
                     for (int pp = 0; pp < cnt; ++pp) {
-                        const int t = sm.st.c.t[g2][pp];
+                        const int t = sm.st.t[g2][pp];
                         if (t != xb) {
                             close_tile();
                             xb = t;
                         }
                         if (tile_own) {
-                            const float2 abv = sm.st.c.ab[g2][pp][tn];
+                            const float2 abv = sm.st.ab[g2][pp][tn];
 #pragma unroll
                             for (int jj = 0; jj < TW; ++jj) {
                                 if (tk0 + jj < KA) {
-                                    const float2 ffv = sm.st.c.ff[g2][pp][tk0 + jj];
+                                    const float2 ffv = sm.st.ff[g2][pp][tk0 + jj];
                                     X[jj] += abv.x * ffv.x + abv.y * ffv.y;
                                 }
                             }
@@ -1174,6 +1338,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adjo
         __syncwarp();
     }
     __syncwarp();
+    if (one_species && cur_t >= 0) flush_groups<V1, SW>(X1, accA, NCA, true, lane, true);
     close_tile();
     __syncwarp();
     if (cur_t >= 0) flush_slot(cur_t);
@@ -1185,14 +1350,21 @@ template <class S, int SW, int VAR>
 void launch_fwd_t(const AtomArgs &a, int blocks, int wpb, size_t smem, cudaStream_t st) {
     k_forward<S, SW, VAR><<<blocks, wpb * 32, smem, st>>>(a);
 }
+// Adjoint stages: 0 = JVP, 1 = network reverse, 2 = coefficient gradient, -1 = all three.
 template <class S, int SW, int VAR>
-void launch_adj_t(const AtomArgs &a, int blocks, int wpb, size_t smem, cudaStream_t st) {
-    k_adjoint<S, SW, VAR><<<blocks, wpb * 32, smem, st>>>(a);
+void launch_adj_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_t st) {
+    if (stage < 0 || stage == 0) k_adj_jvp<S, SW, VAR><<<blocks, wpb * 32, JvpL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
+    if ((stage < 0 || stage == 1) && a.n_chunks > 0) k_net_rev<S><<<a.n_chunks, 256, net_rev_smem<S>(a.NN), st>>>(a);
+    if (stage < 0 || stage == 2) k_adj_cg<S, SW, VAR><<<blocks, wpb * 32, CgL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
 }
 template <class S, int SW>
 size_t fwd_bytes_t(int T, int NN) { return FwdL<S, SW>::bytes(T, NN); }
+// per-warp shared memory of the larger of the two per-atom adjoint stages
 template <class S, int SW>
-size_t adj_bytes_t(int T, int NN) { return AdjL<S, SW>::bytes(T, NN); }
+size_t adj_bytes_t(int T, int NN) {
+    const size_t j = JvpL<S, SW>::bytes(T, NN), c = CgL<S, SW>::bytes(T, NN);
+    return j > c ? j : c;
+}
 
 // Variant v: SW = 8 (v < 2) or 16, register budget VAR = v & 1.
 template <int NR, int KR, int NA, int KA>
@@ -1207,10 +1379,16 @@ KernelSet make_set() {
     k.fwd_fn[1] = (const void *)k_forward<S, 8, 1>;
     k.fwd_fn[2] = (const void *)k_forward<S, 16, 0>;
     k.fwd_fn[3] = (const void *)k_forward<S, 16, 1>;
-    k.adj_fn[0] = (const void *)k_adjoint<S, 8, 0>;
-    k.adj_fn[1] = (const void *)k_adjoint<S, 8, 1>;
-    k.adj_fn[2] = (const void *)k_adjoint<S, 16, 0>;
-    k.adj_fn[3] = (const void *)k_adjoint<S, 16, 1>;
+    k.adj_fn[0] = (const void *)k_adj_cg<S, 8, 0>;
+    k.adj_fn[1] = (const void *)k_adj_cg<S, 8, 1>;
+    k.adj_fn[2] = (const void *)k_adj_cg<S, 16, 0>;
+    k.adj_fn[3] = (const void *)k_adj_cg<S, 16, 1>;
+    k.jvp_fn[0] = (const void *)k_adj_jvp<S, 8, 0>;
+    k.jvp_fn[1] = (const void *)k_adj_jvp<S, 8, 1>;
+    k.jvp_fn[2] = (const void *)k_adj_jvp<S, 16, 0>;
+    k.jvp_fn[3] = (const void *)k_adj_jvp<S, 16, 1>;
+    k.net_rev_fn = (const void *)k_net_rev<S>;
+    k.net_rev_smem = net_rev_smem<S>;
     k.launch_fwd[0] = launch_fwd_t<S, 8, 0>;
     k.launch_fwd[1] = launch_fwd_t<S, 8, 1>;
     k.launch_fwd[2] = launch_fwd_t<S, 16, 0>;

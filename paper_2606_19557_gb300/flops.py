@@ -8,16 +8,19 @@ Per radial pair (K = K_R):
   forward : basis values (4K + 8) and species sums (K); basis + derivatives (9K + 10),
             sum_k beta_k f'_k (2K), pair gradient (4), force/virial accumulation (21),
             two distance evaluations (2 x 7)                              -> 16K + 57
-  adjoint : lambda_p (24), distance (7), r^.lambda (6), basis + derivatives (9K + 10),
+  adjoint JVP : lambda_p (24), distance (7), r^.lambda (6), basis + derivatives (9K + 10),
             two species sums (3K)                                          -> 12K + 47
 Per angular pair (K = K_A, N = N_A, L3 = 24):
   forward : distance, basis, g_n = sum_k c f_k (2NK), 24 harmonics (72), moments
             (2 N L3); then basis + derivatives, g and g' (4NK), harmonics + gradients
             (172), dE/dA contractions (4 N L3), force assembly (8 L3 + 36)
-  adjoint : two passes of lambda / distance / basis / harmonics, the JVP of the
-            moments (6 L3 + 4 N L3), alpha/beta (6 N L3), coefficient terms (4NK)
-Per atom: descriptor contractions, the network forward (4 N_des N_neu) and its
-reverse (6 N_des N_neu), and the network-gradient contraction (4 N_des N_neu).
+  adjoint JVP : lambda / distance / basis / harmonics (9K + 225), g and g' (4NK), the
+            projected gradients (6 L3) and the JVP of the moments (4 N L3)
+  adjoint coefficient gradient : lambda / distance / basis / harmonics again (9K + 225),
+            alpha/beta (6 N L3 + 6 L3), coefficient terms (4NK)
+Per atom: descriptor contractions, the network forward (4 N_des N_neu), the network
+reverse pass (6 N_des N_neu: v = W0 dq~, abar = W0^T zeta, b = W0^T u), dJ/dA and the
+radial coefficient gradient, and the network-gradient contraction (4 N_des N_neu).
 """
 from __future__ import annotations
 
@@ -38,24 +41,24 @@ def per_unit(spec) -> dict:
         "fwd_angular_pair": (7 + 4 * KA + 8 + 2 * NA * KA + 72 + 2 * NA * L3)
         + (7 + 9 * KA + 10 + 4 * NA * KA + 172 + 4 * NA * L3 + 8 * L3 + 36),
         "fwd_atom": 2 * T * KR * NR + 2 * L3 * NA + 70 * NA + 4 * ND * NN + 6 * NN + 4 * NA * L3 + 2 * T * KR * NR,
-        "adj_radial_pair": 12 * KR + 47,
-        "adj_angular_pair": 2 * (24 + 7 + 12 + 9 * KA + 10 + 72 + 100) + 4 * NA * KA + NA + 6 * L3
-        + 4 * NA * L3 + 6 * L3 + 6 * NA * L3 + 4 * NA * KA,
-        "adj_atom": 2 * ND * NN + 2 * T * KR * NR + 4 * NA * L3 + 120 * NA + 4 * ND * NN + 12 * NN
-        + 8 * NA * L3 + 4 * T * NR * KR,
+        "jvp_radial_pair": 12 * KR + 47,
+        "jvp_angular_pair": (24 + 7 + 12 + 9 * KA + 10 + 72 + 100) + 4 * NA * KA + NA + 6 * L3 + 4 * NA * L3,
+        "jvp_atom": 2 * T * KR * NR + 4 * NA * L3 + 60 * NA,
+        "netrev_atom": 6 * ND * NN + 12 * NN,
+        "cg_angular_pair": (24 + 7 + 12 + 9 * KA + 10 + 72 + 100) + 6 * L3 + 6 * NA * L3 + 4 * NA * KA,
+        "cg_atom": 60 * NA + 8 * NA * L3 + 4 * T * NR * KR,
         "net_atom": 4 * ND * NN + 2 * NN,
     }
 
 
 def per_kernel(spec, n_atoms: int, n_radial: int, n_angular: int) -> dict:
     u = per_unit(spec)
-    return {
+    out = {
         "forward": u["fwd_radial_pair"] * n_radial + u["fwd_angular_pair"] * n_angular + u["fwd_atom"] * n_atoms,
-        "adjoint": u["adj_radial_pair"] * n_radial + u["adj_angular_pair"] * n_angular + u["adj_atom"] * n_atoms,
+        "adjoint_jvp": u["jvp_radial_pair"] * n_radial + u["jvp_angular_pair"] * n_angular + u["jvp_atom"] * n_atoms,
+        "net_reverse": u["netrev_atom"] * n_atoms,
+        "adjoint_cgrad": u["cg_angular_pair"] * n_angular + u["cg_atom"] * n_atoms,
         "net_grad": u["net_atom"] * n_atoms,
     }
-
-
-def fp32_peak_tflops(n_sm: int = 152, clock_mhz: float = 2070.0) -> float:
-    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
-    return n_sm * 128 * 2 * clock_mhz * 1e6 / 1e12
+    out["adjoint"] = out["adjoint_jvp"] + out["net_reverse"] + out["adjoint_cgrad"]
+    return out
