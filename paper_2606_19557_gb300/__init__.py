@@ -27,7 +27,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "nep_gb300.h")
 
 NEP_OK, NEP_EINVAL, NEP_ENOMEM, NEP_ECUDA, NEP_ESTATE, NEP_EINTERNAL = 0, -1, -2, -3, -4, -5
 SCHED_PERSISTENT, SCHED_PLAIN = 0, 1
-KERNEL_COUNT = 10
+KERNEL_COUNT = 12
 
 _lib = None
 _lock = threading.Lock()

@@ -26,9 +26,9 @@ Ctx::~Ctx() {
 
 static thread_local std::string g_create_err;
 
-static const char *kernel_names[KID_COUNT] = {"expand_params", "forward",     "force_gather",  "struct_sums",
-                                              "loss_final",    "adjoint_jvp", "net_reverse",   "adjoint_cgrad",
-                                              "net_grad",      "grad_reduce"};
+static const char *kernel_names[KID_COUNT] = {"expand_params", "forward_desc", "net_forward",   "forward_pair",
+                                              "force_gather",  "struct_sums",  "loss_final",    "adjoint_jvp",
+                                              "net_reverse",   "adjoint_cgrad", "net_grad",     "grad_reduce"};
 
 // ----------------------------------------------------------------------------- helpers
 
@@ -205,9 +205,12 @@ static int set_smem_attr(Ctx *c) {
     CK(cudaDeviceGetAttribute(&maxo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
     if (c->ks->fwd_smem[2](c->T, c->NN) > (size_t)maxo || c->ks->adj_smem[2](c->T, c->NN) > (size_t)maxo)
         return c->fail(NEP_EINVAL, "model too large for shared memory");
-    if (c->ks->net_rev_smem(c->NN) > (size_t)maxo) return c->fail(NEP_EINVAL, "model too large for shared memory");
+    if (c->ks->net_rev_smem(c->NN) > (size_t)maxo || c->ks->net_fwd_smem(c->NN) > (size_t)maxo)
+        return c->fail(NEP_EINVAL, "model too large for shared memory");
+    CK(cudaFuncSetAttribute(c->ks->net_fwd_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     for (int v = 0; v < NVAR; ++v) {
         CK(cudaFuncSetAttribute(c->ks->fwd_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+        CK(cudaFuncSetAttribute(c->ks->desc_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
         CK(cudaFuncSetAttribute(c->ks->adj_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
         CK(cudaFuncSetAttribute(c->ks->jvp_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     }
@@ -271,27 +274,31 @@ static int body_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr
     mark(c, 0);
     if ((rc = launch_expand(c))) return rc;
     mark(c, 1);
-    if ((rc = launch_forward(c, nullptr))) return rc;
+    if ((rc = launch_forward(c, nullptr, 0))) return rc;
     mark(c, 2);
+    if ((rc = launch_forward(c, nullptr, 1))) return rc;
+    mark(c, 3);
+    if ((rc = launch_forward(c, nullptr, 2))) return rc;
+    mark(c, 4);
     if ((rc = launch_count_hasw(c, hw))) return rc;
     if ((rc = launch_gather(c, c->F_int.as<float>(), Fr, lF, true, 0, c->n_atoms))) return rc;
-    mark(c, 3);
+    mark(c, 5);
     if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, 0,
                             c->n_struct)))
         return rc;
-    mark(c, 4);
-    if ((rc = launch_loss_final(c, loss3))) return rc;
-    mark(c, 5);
-    if ((rc = launch_adjoint(c, 0))) return rc;
     mark(c, 6);
-    if ((rc = launch_adjoint(c, 1))) return rc;
+    if ((rc = launch_loss_final(c, loss3))) return rc;
     mark(c, 7);
-    if ((rc = launch_adjoint(c, 2))) return rc;
+    if ((rc = launch_adjoint(c, 0))) return rc;
     mark(c, 8);
-    if ((rc = launch_ann_grad(c))) return rc;
+    if ((rc = launch_adjoint(c, 1))) return rc;
     mark(c, 9);
-    if ((rc = launch_grad_final(c, grad))) return rc;
+    if ((rc = launch_adjoint(c, 2))) return rc;
     mark(c, 10);
+    if ((rc = launch_ann_grad(c))) return rc;
+    mark(c, 11);
+    if ((rc = launch_grad_final(c, grad))) return rc;
+    mark(c, 12);
     return NEP_OK;
 }
 
@@ -521,7 +528,7 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
         c->F_int.ensure<float>(na * 3) || c->E_int.ensure<double>(ns) || c->W_int.ensure<double>(ns * 9) ||
         c->loss_part.ensure<double>(nlp) || c->st_D.ensure<float>(na * NAL) ||
         c->st_S.ensure<float>(na * 2 * (int64_t)c->T * c->ks->KR) || c->st_b.ensure<float>(na * NDP) ||
-        c->st_ab.ensure<float>(na * NDP))
+        c->st_ab.ensure<float>(na * NDP) || c->st_E.ensure<float>(na))
         return c->fail(NEP_ENOMEM, "step buffers");
     if ((rc = default_shapes(c))) return rc;
     CK(cudaDeviceSynchronize());
@@ -637,7 +644,7 @@ int nep_descriptors(nep_ctx *c, float *q) {
     DevBuf qp;
     if (qp.ensure<float>(c->n_atoms * c->NDP)) return c->fail(NEP_ENOMEM, "descriptor buffer");
     if ((rc = launch_expand(c))) return rc;
-    if ((rc = launch_forward(c, qp.as<float>()))) return rc;
+    if ((rc = launch_forward(c, qp.as<float>(), 0))) return rc;
     if ((rc = launch_compact_q(c, qp.as<float>(), q))) return rc;
     CK(cudaStreamSynchronize(c->stream));
     return NEP_OK;
@@ -652,7 +659,7 @@ int nep_descriptor_range(nep_ctx *c, float *qmin, float *qmax) {
     DevBuf qp;
     if (qp.ensure<float>(c->n_atoms * c->NDP)) return c->fail(NEP_ENOMEM, "descriptor buffer");
     if ((rc = launch_expand(c))) return rc;
-    if ((rc = launch_forward(c, qp.as<float>()))) return rc;
+    if ((rc = launch_forward(c, qp.as<float>(), 0))) return rc;
     if ((rc = launch_range(c, qp.as<float>(), qmin, qmax))) return rc;
     CK(cudaStreamSynchronize(c->stream));
     return NEP_OK;
@@ -1008,9 +1015,9 @@ int nep_get_launch(const nep_ctx *c, int *fw, int *fb, int *aw, int *ab) {
 int nep_get_variant(const nep_ctx *c, int *fwd_lanes, int *fwd_regs, int *adj_lanes, int *adj_regs) {
     if (!c || !c->ks) return NEP_EINVAL;
     if (fwd_lanes) *fwd_lanes = c->ks->sw[c->fwd.var];
-    if (fwd_regs) *fwd_regs = (c->fwd.var & 1) ? 128 : 168;
+    if (fwd_regs) *fwd_regs = (c->fwd.var & 1) ? 96 : 128;
     if (adj_lanes) *adj_lanes = c->ks->sw[c->adj.var];
-    if (adj_regs) *adj_regs = (c->adj.var & 1) ? 128 : 168;
+    if (adj_regs) *adj_regs = (c->adj.var & 1) ? 96 : 128;
     return NEP_OK;
 }
 
@@ -1036,14 +1043,14 @@ int nep_set_variant(nep_ctx *c, int fwd_var, int adj_var) {
 int nep_set_launch(nep_ctx *c, int fw, int fb, int aw, int ab) {
     if (!c) return NEP_EINVAL;
     if (!c->have_batch) return c->fail(NEP_ESTATE, "no structures");
-    if (fw < 0 || fb < 0 || aw < 0 || ab < 0 || fw > 8 || aw > 8) return c->fail(NEP_EINVAL, "bad launch shape");
+    if (fw < 0 || fb < 0 || aw < 0 || ab < 0 || fw > 4 || aw > 4)
+        return c->fail(NEP_EINVAL, "bad launch shape (at most 4 warps per block)");
     CK(cudaSetDevice(c->dev));
     CK(cudaStreamSynchronize(c->stream));
     int rc;
     fw = fw ? fw : c->fwd.wpb;
     aw = aw ? aw : c->adj.wpb;
-    const int vf = (fw > c->ks->max_wpb[c->fwd.var]) ? (c->fwd.var | 1) : c->fwd.var;
-    const int va = (aw > c->ks->max_wpb[c->adj.var]) ? (c->adj.var | 1) : c->adj.var;
+    const int vf = c->fwd.var, va = c->adj.var;
     const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[vf], fw, c->ks->fwd_smem[vf](c->T, c->NN) * fw);
     const int ma = max_blocks_per_sm(c, c->ks->adj_fn[va], aw, c->ks->adj_smem[va](c->T, c->NN) * aw);
     if (mf < 1 || ma < 1) return c->fail(NEP_EINVAL, "launch shape does not fit");
@@ -1078,7 +1085,7 @@ int nep_autotune(nep_ctx *c) {
     CK(cudaEventCreate(&e1));
     float best_f = 1e30f, best_a = 1e30f;
     int bfw = c->fwd.wpb, bfb = c->fwd.blocks, bfv = c->fwd.var, baw = c->adj.wpb, bab = c->adj.blocks, bav = c->adj.var;
-    const int wpbs[3] = {2, 4, 8};
+    const int wpbs[3] = {1, 2, 4};
     for (int var = 0; var < NVAR && !rc; ++var) {
         for (int wpb : wpbs) {
             if (wpb > c->ks->max_wpb[var]) continue;

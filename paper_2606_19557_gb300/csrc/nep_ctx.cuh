@@ -57,8 +57,8 @@ struct Sched {
 constexpr int NVAR = 4;
 
 enum KernelId {
-    KID_EXPAND = 0, KID_FWD, KID_GATHER, KID_STRUCT, KID_LOSS, KID_ADJ, KID_NETREV, KID_ADJCG, KID_ANN, KID_GRAD,
-    KID_COUNT
+    KID_EXPAND = 0, KID_DESC, KID_NETFWD, KID_PAIR, KID_GATHER, KID_STRUCT, KID_LOSS, KID_ADJ, KID_NETREV, KID_ADJCG,
+    KID_ANN, KID_GRAD, KID_COUNT
 };
 
 struct Ctx;
@@ -67,8 +67,11 @@ struct Ctx;
 struct KernelSet {
     int NR, KR, NA, KA;
     // variants v = 0..3: lanes per atom sw[v] (8 or 16), register budget v & 1
-    // (0: 128 threads x 3 blocks per SM, 168 registers; 1: 256 x 2, 128 registers)
-    const void *fwd_fn[NVAR];
+    // (0: blocks of <= 128 threads, 4 per SM, 128 registers; 1: 5 per SM, 96 registers)
+    const void *fwd_fn[NVAR];   // forward pair-gradient stage
+    const void *desc_fn[NVAR];  // forward descriptor stage
+    const void *net_fwd_fn;     // network forward pass (one block per chunk)
+    size_t (*net_fwd_smem)(int NN);
     const void *adj_fn[NVAR];   // adjoint coefficient-gradient stage (the larger footprint)
     const void *jvp_fn[NVAR];   // adjoint JVP stage
     const void *net_rev_fn;     // network reverse pass (one block per chunk)
@@ -77,7 +80,8 @@ struct KernelSet {
     int sw[NVAR];
     size_t (*fwd_smem[NVAR])(int T, int NN);  // bytes per warp
     size_t (*adj_smem[NVAR])(int T, int NN);
-    void (*launch_fwd[NVAR])(const AtomArgs &, int blocks, int wpb, size_t smem, cudaStream_t);
+    // forward stages (0 descriptors, 1 network, 2 pair gradients; -1 all)
+    void (*launch_fwd[NVAR])(const AtomArgs &, int blocks, int wpb, int stage, cudaStream_t);
     // adjoint stages (0 JVP, 1 network reverse, 2 coefficient gradient; -1 all)
     void (*launch_adj[NVAR])(const AtomArgs &, int blocks, int wpb, int stage, cudaStream_t);
 };
@@ -133,6 +137,7 @@ struct Ctx {
     // per-step buffers
     DevBuf E_atom, F_own, W_atom, G, st_qt, st_h, st_A;
     DevBuf st_D, st_S, st_b, st_ab;   // adjoint stage outputs (JVP of A, radial species sums, b, abar)
+    DevBuf st_E;                      // network energy per work position
     DevBuf fbar, ebar, wbar, zt, ut, om, dqt, cpart, annpart;
     DevBuf F_int, E_int, W_int;       // internal outputs for nep_loss_grad
     DevBuf loss_part, gb1, n_sv, loss3_int, grad_int;
@@ -225,9 +230,10 @@ int fetch_host_lists(Ctx *c);
 
 // step pieces (nep_loss.cu)
 int launch_expand(Ctx *c);
-int launch_forward(Ctx *c, float *q_raw);
+int launch_forward(Ctx *c, float *q_raw, int stage = -1);
 // explicit schedules (mini-batch mode)
-int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb);
+int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
+                         const int *chunks, int n_chunks);
 int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
                          const int *chunks, int n_chunks);
 int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks);

@@ -97,10 +97,10 @@ struct AtomArgs {
     float *st_S;            // [Na_work][T][2 KR] radial species sums S^b_k | S'^b_k
     float *st_b;            // [Na_work][ND] s * dE_i/dq~
     float *st_ab;           // [Na_work][ND] abar = dJ/dq (scaled)
+    float *st_E;            // [Na_work] network energy of each atom (without the ZBL term)
 };
 
-// Network reverse pass over the chunks (nep_net.cu).
-void launch_net_rev(const AtomArgs &a, cudaStream_t st);
+
 
 // ----------------------------------------------------------------------------- warp helpers
 

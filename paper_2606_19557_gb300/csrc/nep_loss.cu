@@ -597,6 +597,7 @@ static AtomArgs atom_args(Ctx *c) {
     a.st_S = c->st_S.as<float>();
     a.st_b = c->st_b.as<float>();
     a.st_ab = c->st_ab.as<float>();
+    a.st_E = c->st_E.as<float>();
     return a;
 }
 
@@ -625,14 +626,13 @@ int launch_expand(Ctx *c) {
     return NEP_OK;
 }
 
-int launch_forward(Ctx *c, float *q_raw) {
+int launch_forward(Ctx *c, float *q_raw, int stage) {
     if (c->n_atoms == 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.warp_begin = c->fwd.warp_begin.as<int>();
     a.q_raw = q_raw;
-    const size_t smem = c->ks->fwd_smem[c->fwd.var](c->T, c->NN) * c->fwd.wpb;
-    c->ks->launch_fwd[c->fwd.var](a, c->fwd.blocks, c->fwd.wpb, smem, c->stream);
-    CK_LAUNCH("k_forward");
+    c->ks->launch_fwd[c->fwd.var](a, c->fwd.blocks, c->fwd.wpb, stage, c->stream);
+    CK_LAUNCH("forward stages");
     return NEP_OK;
 }
 
@@ -645,14 +645,16 @@ int launch_adjoint(Ctx *c, int stage) {
     return NEP_OK;
 }
 
-int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb) {
+int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
+                         const int *chunks, int n_chunks) {
     if (blocks <= 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.work = work;
     a.warp_begin = warp_begin;
-    const size_t smem = c->ks->fwd_smem[var](c->T, c->NN) * wpb;
-    c->ks->launch_fwd[var](a, blocks, wpb, smem, c->stream);
-    CK_LAUNCH("k_forward");
+    a.chunks = chunks;
+    a.n_chunks = n_chunks;
+    c->ks->launch_fwd[var](a, blocks, wpb, -1, c->stream);
+    CK_LAUNCH("forward stages");
     return NEP_OK;
 }
 
@@ -892,8 +894,7 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
     if ((rc = launch_expand(c))) return rc;
     if ((rc = launch_count_hasw(c, hw))) return rc;
     CK(cudaMemsetAsync(c->p_acc.ptr, 0, sizeof(double) * c->P, c->stream));
-    const int pv = 2;  // one warp per atom: lanes-per-atom 16, 168-register variant
-    const size_t fs = c->ks->fwd_smem[pv](c->T, c->NN);
+    const int pv = 2;  // one warp per atom: lanes-per-atom 16, 128-register variant
     const size_t gsm = ann_smem(c);
     const int groups = ann_groups(c);
     for (int64_t s = 0; s < ns; ++s) {
@@ -901,15 +902,15 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         AtomArgs a = atom_args(c);
         a.work = c->p_work.as<int>();
         a.warp_begin = c->p_ident.as<int>() + a0;
-        c->ks->launch_fwd[pv](a, (int)n, 1, fs, c->stream);
-        CK_LAUNCH("k_forward (plain)");
+        const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
+        a.chunks = c->p_chunks.as<int>() + c->p_cofs[s];
+        a.n_chunks = nch;
+        c->ks->launch_fwd[pv](a, (int)n, 1, -1, c->stream);
+        CK_LAUNCH("forward stages (plain)");
         if ((rc = launch_gather(c, c->F_int.as<float>(), Fr, lF, true, a0, a0 + n, pg + s * GB, GB))) return rc;
         if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, s, s + 1,
                                 ps + s * 3, 1)))
             return rc;
-        const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
-        a.chunks = c->p_chunks.as<int>() + c->p_cofs[s];
-        a.n_chunks = nch;
         c->ks->launch_adj[pv](a, (int)n, 1, -1, c->stream);
         CK_LAUNCH("adjoint stages (plain)");
         if (nch > 0) {

@@ -264,7 +264,7 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
     do {
         if ((rc = launch_expand(c))) break;
         if ((rc = launch_forward_sched(c, c->mb_work.as<int>(), c->mb_wbf.as<int>() + m.wf_off, m.Wf / c->mb_used[1],
-                                       c->mb_used[0], c->mb_used[1])))
+                                       c->mb_used[0], c->mb_used[1], c->mb_chunks.as<int>() + m.ck_off, m.n_ck)))
             break;
         if ((rc = launch_count_hasw(c, hw, m.s0, m.s1))) break;
         if ((rc = launch_gather(c, c->F_int.as<float>(), c->tgt_F.as<float>(), lF, true, m.a0, m.a1))) break;

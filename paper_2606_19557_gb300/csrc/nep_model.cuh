@@ -4,7 +4,7 @@
 // atoms of one species, one group of SW lanes per atom, so that the ~15-20 angular
 // and ~60-80 radial neighbours of an atom keep most lanes busy.
 //
-// Forward (k_forward):
+// Forward (k_fwd_desc -> k_net_fwd -> k_fwd_pair):
 //   A_nlm = sum_j g^A_n(r_ij) Y_lm(r^_ij)          pair geometry staged in shared memory,
 //                                                   lanes own (l, m) outputs
 //   q_n   = sum_j sum_k c^{t_i t_j}_{nk} f_k(r_ij)  (one species: through the sums
@@ -218,31 +218,46 @@ __device__ __forceinline__ void l2_block(const float *M, int n, float *a) {
 
 // ============================================================================= layouts
 
+// Forward, stage 1 (k_fwd_desc): descriptors.
 template <class S, int SW>
-struct FwdL {
+struct DescL {
     static constexpr int G = 32 / SW;
     static constexpr int NAP = round4(S::NA);
     static constexpr int NLMO = (L3 + SW - 1) / SW;  // (l, m) outputs owned per lane
     struct __align__(16) Atom {
-        float A[L3 * NAP];   // A_nlm at [lm][n]
-        float Ah[L3 * NAP];  // dE_i/dA_nlm at [lm][n]
+        float A[L3 * NAP];  // A_nlm at [lm][n]
         float q[S::ND];
-        float qt[S::ND];
-        float b[S::ND];
-        float G4[S::NA * 5];
     };
     struct __align__(16) Mom {
         float g[G][SW][NAP];  // g^A_n of each lane's pair
         float Y[G][SW][L3];
     };
     Atom at[G];
-    union {
-        Mom m;
-    } st;
-    // runtime tail (floats): u[G][NN], Sr[G][T][KR], beta[G][T][KR]
-    __host__ __device__ static size_t tail(int T, int NN) { return (size_t)G * NN + 2 * (size_t)G * T * S::KR; }
+    Mom st;
+    // runtime tail (floats): S[G][KR] (one species)
+    __host__ __device__ static size_t tail(int T, int NN) { return (size_t)G * S::KR; }
     __host__ __device__ static size_t bytes(int T, int NN) {
-        return ((sizeof(FwdL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
+        return ((sizeof(DescL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
+    }
+};
+
+// Forward, stage 3 (k_fwd_pair): pair gradients.
+template <class S, int SW>
+struct PairL {
+    static constexpr int G = 32 / SW;
+    static constexpr int NAP = round4(S::NA);
+    static constexpr int NLMO = (L3 + SW - 1) / SW;
+    struct __align__(16) Atom {
+        float A[L3 * NAP];   // A_nlm at [lm][n]
+        float Ah[L3 * NAP];  // dE_i/dA_nlm at [lm][n]
+        float b[S::ND];
+        float G4[S::NA * 5];
+    };
+    Atom at[G];
+    // runtime tail (floats): beta[G][T][KR]
+    __host__ __device__ static size_t tail(int T, int NN) { return (size_t)G * T * S::KR; }
+    __host__ __device__ static size_t bytes(int T, int NN) {
+        return ((sizeof(PairL) + sizeof(float) * tail(T, NN)) + 15) & ~(size_t)15;
     }
 };
 
@@ -311,392 +326,6 @@ struct CgL {
     }
 };
 
-// ============================================================================= forward
-
-template <class S, int SW, int VAR>
-__global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_forward(AtomArgs a) {
-    using L = FwdL<S, SW>;
-    constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
-    constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
-    constexpr int KR4 = round4(KR), KA4 = round4(KA);
-    constexpr int VR = pow2ceil(KR);
-    constexpr int VRN = pow2ceil(NR);
-    extern __shared__ __align__(16) float smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int grp = lane / SW, sl = lane % SW;
-    const int T = a.T, NN = a.NN;
-    float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
-    L &sm = *reinterpret_cast<L *>(base_ptr);
-    float *tail = base_ptr + sizeof(L) / sizeof(float);
-    float *Sr = tail + G * NN + grp * T * KR;                 // [T][KR] of this group
-    float *beta = tail + G * NN + G * T * KR + grp * T * KR;  // [T][KR] of this group
-
-    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-    const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
-    const ParOff po = par_offsets(T, NN, NR, KR, NA, KA);
-    const float *W0 = a.par + po.w0;
-    const float *W0T = a.par + po.w0t;
-    const float *b0 = a.par + po.b0;
-    const float *w1 = a.par + po.w1;
-    const float b1 = a.par[po.b1];
-    const float *scale = a.par + po.scale;
-
-    for (int bp = wbeg; bp < wend;) {
-        int ti, nb, i;
-        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
-        const bool act = grp < nb;
-        const int bp0 = bp;
-        const int wi = bp + (act ? grp : 0);
-        bp += nb;
-        const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;  // [b][n][KR4]
-        const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;  // [b][n][KA4]
-        const int64_t beg = a.nbr_off[i];
-        const int nRad = act ? (int)(a.nbr_off[i + 1] - beg) : 0;
-        const int nAng = act ? a.n_ang[i] : 0;
-        const int maxR = __reduce_max_sync(FULL, nRad);
-        const int maxA = __reduce_max_sync(FULL, nAng);
-        typename L::Atom &at = sm.at[grp];
-        if (bp + grp < wend) {  // the atoms after this batch: bring their pair records into L2
-            const int ni = a.work[bp + grp];
-            const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
-            prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
-        }
-
-        // ---------------------------------------------------------------- angular moments A_nlm
-        float accA[NLMO][NA];
-#pragma unroll
-        for (int j = 0; j < NLMO; ++j)
-#pragma unroll
-            for (int n = 0; n < NA; ++n) accA[j][n] = 0.0f;
-        const float4 *prs = a.pair + beg;
-        float4 nxt = pair_or_zero(prs, sl, nAng);
-        for (int c0 = 0; c0 < maxA; c0 += SW) {
-            const int k = c0 + sl;
-            const float4 pd = nxt;
-            nxt = pair_or_zero(prs, k + SW, nAng);
-            if (k < nAng) {
-                const int tj = pair_t(pd);
-                const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                const float rinv = inv_norm(r2);
-                const float r = r2 * rinv;
-                float f[KA], g[NA];
-                basis_val<KA>(r, a.inv_rcA, f);
-                contract_c<NA, KA>(cAi + tj * NA * KA4, f, g);
-                store_row4<NA>(sm.st.m.g[grp][sl], g);
-                float Y[L3];
-                ylm_val(pd.x * rinv, pd.y * rinv, pd.z * rinv, Y);
-#pragma unroll
-                for (int lm = 0; lm < L3; ++lm) sm.st.m.Y[grp][sl][lm] = Y[lm];
-            }
-            __syncwarp();
-            const int cnt = min(SW, nAng - c0);
-            for (int pp = 0; pp < cnt; ++pp) {
-                float gv[NAP];
-                load_row<NAP>(sm.st.m.g[grp][pp], gv);
-#pragma unroll
-                for (int j = 0; j < NLMO; ++j) {
-                    const int lm = sl + j * SW;
-                    if (lm < L3) {
-                        const float y = sm.st.m.Y[grp][pp][lm];
-#pragma unroll
-                        for (int n = 0; n < NA; ++n) accA[j][n] += gv[n] * y;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-#pragma unroll
-        for (int j = 0; j < NLMO; ++j) {
-            const int lm = sl + j * SW;
-            if (lm < L3) store_row4<NA>(at.A + lm * NAP, accA[j]);
-        }
-
-        // ---------------------------------------------------------------- radial species sums S^b_k
-        for (int e = sl; e < T * KR; e += SW) Sr[e] = 0.0f;
-        __syncwarp();
-        if (T == 1) {  // one species: every lane sums its own pairs, one reduction per atom
-            float v[VR];
-#pragma unroll
-            for (int k = 0; k < VR; ++k) v[k] = 0.0f;
-            float4 nxr = pair_or_zero(prs, sl, nRad);
-            for (int c0 = 0; c0 < maxR; c0 += SW) {
-                const int k = c0 + sl;
-                const float4 pd = nxr;
-                nxr = pair_or_zero(prs, k + SW, nRad);
-                if (k < nRad) {
-                    const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                    float f[KR];
-                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
-#pragma unroll
-                    for (int kk = 0; kk < KR; ++kk) v[kk] += f[kk];
-                }
-            }
-            if (__any_sync(FULL, nRad > 0)) flush_groups<VR, SW>(v, Sr, KR, nRad > 0, lane, false);
-        } else {  // several species: every lane adds g_n = sum_k c^{t_i t_j}_nk f_k of its own pairs
-            float qv[VRN];
-#pragma unroll
-            for (int n = 0; n < VRN; ++n) qv[n] = 0.0f;
-            float4 nxr = pair_or_zero(prs, sl, nRad);
-            for (int c0 = 0; c0 < maxR; c0 += SW) {
-                const int k = c0 + sl;
-                const float4 pd = nxr;
-                nxr = pair_or_zero(prs, k + SW, nRad);
-                if (k < nRad) {
-                    const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-                    float f[KR], g[NR];
-                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
-                    contract_c<NR, KR>(cRi + pair_t(pd) * NR * KR4, f, g);
-#pragma unroll
-                    for (int n = 0; n < NR; ++n) qv[n] += g[n];
-                }
-            }
-            for (int n = sl; n < NR; n += SW) at.q[n] = 0.0f;
-            __syncwarp();
-            if (__any_sync(FULL, nRad > 0)) flush_groups<VRN, SW>(qv, at.q, NR, nRad > 0, lane, false);
-        }
-        __syncwarp();
-
-        // ---------------------------------------------------------------- descriptors
-        if (T == 1) {
-            for (int n = sl; n < NR; n += SW) {
-                float q = 0.0f;
-                const float *cr = cRi + n * KR4;
-#pragma unroll
-                for (int kk = 0; kk < KR; ++kk) q += __ldg(cr + kk) * Sr[kk];
-                at.q[n] = q;
-            }
-        }
-        for (int e = sl; e < 4 * NA; e += SW) {
-            const int n = e % NA, l = e / NA + 1;
-            float s2 = 0.0f;
-            for (int m = 0; m < 2 * l + 1; ++m) {
-                const float v = at.A[(l * l - 1 + m) * NAP + n];
-                s2 += v * v;
-            }
-            at.q[NR + (l - 1) * NA + n] = s2;
-        }
-        for (int n = sl; n < NA; n += SW) {
-            float a2[5], Mt[6], M2[6], pr[5];
-            l2_block<NAP>(at.A, n, a2);
-            l2_matrix(a2, Mt);
-            sym_prod(Mt, Mt, M2);
-            at.q[NR + 4 * NA + n] = KAPPA_REAL * sym_trace_prod(M2, Mt);
-            l2_project(M2, pr);
-#pragma unroll
-            for (int m = 0; m < 5; ++m) at.G4[n * 5 + m] = 3.0f * KAPPA_REAL * pr[m];
-            const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
-            const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
-            at.q[NR + 5 * NA + n] = q1 * q1;
-        }
-        __syncwarp();
-        for (int e = sl; e < ND; e += SW) at.qt[e] = at.q[e] * scale[e];
-        __syncwarp();
-
-        // ---------------------------------------------------------------- network (Eq. "ann")
-        // The G atoms of the batch share the species, so the layer runs as a small
-        // batched product: lanes index neurons (then descriptor components) and each
-        // weight is loaded once for all G atoms.
-        float Eg[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) Eg[g] = 0.0f;
-        for (int mu = lane; mu < NN; mu += 32) {
-            float z[G];
-            const float bz = -b0[ti * NN + mu];
-#pragma unroll
-            for (int g = 0; g < G; ++g) z[g] = bz;
-            const float *wt = W0T + (size_t)ti * ND * NN + mu;
-#pragma unroll
-            for (int v = 0; v < ND; ++v) {
-                const float wv = wt[(size_t)v * NN];
-#pragma unroll
-                for (int g = 0; g < G; ++g) z[g] += wv * sm.at[g].qt[v];
-            }
-            const float wo = w1[ti * NN + mu];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const float h = tanhf(z[g]);
-                if (g < nb) a.st_h[(size_t)(bp0 + g) * NN + mu] = h;
-                Eg[g] += wo * h;
-                tail[g * NN + mu] = wo * (1.0f - h * h);  // u of atom g
-            }
-        }
-        float Ei = 0.0f;
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const float e = warp_sum(Eg[g]);
-            if (g == grp) Ei = e - b1;
-        }
-        __syncwarp();
-        for (int v = lane; v < ND; v += 32) {
-            float e[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) e[g] = 0.0f;
-            const float *wr = W0 + (size_t)ti * NN * ND + v;
-#pragma unroll 10
-            for (int mu = 0; mu < NN; ++mu) {
-                const float wv = wr[(size_t)mu * ND];
-#pragma unroll
-                for (int g = 0; g < G; ++g) e[g] += wv * tail[g * NN + mu];
-            }
-            const float sc = scale[v];
-#pragma unroll
-            for (int g = 0; g < G; ++g) sm.at[g].b[v] = e[g] * sc;
-        }
-        __syncwarp();
-
-        // ---------------------------------------------------------------- dE_i/dA and radial factors
-#pragma unroll
-        for (int j = 0; j < NLMO; ++j) {
-            const int lm = sl + j * SW;
-            if (lm < L3) {
-                const int l = l_of_lm(lm);
-                float ah[NA];
-#pragma unroll
-                for (int n = 0; n < NA; ++n) {
-                    const float av = at.A[lm * NAP + n];
-                    float x = 2.0f * at.b[NR + (l - 1) * NA + n] * av;
-                    if (l == 2) x += at.b[NR + 4 * NA + n] * at.G4[n * 5 + (lm - 3)];
-                    if (l == 1) x += at.b[NR + 5 * NA + n] * 4.0f * at.q[NR + n] * av;
-                    ah[n] = x;
-                }
-                store_row4<NA>(at.Ah + lm * NAP, ah);
-            }
-        }
-        for (int e = sl; e < T * KR; e += SW) {
-            const int bb = e / KR, kk = e - bb * KR;
-            float s2 = 0.0f;
-#pragma unroll
-            for (int n = 0; n < NR; ++n) s2 += at.b[n] * __ldg(cRi + (bb * NR + n) * KR4 + kk);
-            beta[e] = s2;
-        }
-        __syncwarp();
-
-        // ---------------------------------------------------------------- pair gradients
-        const float *zbl_ti = a.zbl ? a.zbl + (size_t)ti * T * 2 : nullptr;
-        float Ez = 0.0f;  // ZBL energy of this lane's pairs (half of each pair term)
-        float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
-        float W9[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) W9[k] = 0.0f;
-        // angular neighbours: angular and radial parts of G_p together
-        float4 nxf = pair_or_zero(prs, sl, nAng);
-        for (int k = sl; k < nAng; k += SW) {
-            const int64_t p = beg + k;
-            const float4 pd = nxf;
-            nxf = pair_or_zero(prs, k + SW, nAng);
-            const int tj = pair_t(pd);
-            const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-            const float rinv = inv_norm(r2);
-            const float r = r2 * rinv;
-            const float ux = pd.x * rinv, uy = pd.y * rinv, uz = pd.z * rinv;
-            float f[KA], fp[KA], g[NA], gp[NA];
-            basis_val_der<KA>(r, a.inv_rcA, f, fp);
-            contract_c2<NA, KA>(cAi + tj * NA * KA4, f, fp, g, gp);
-            float srad = 0.0f, Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
-            ylm_each(ux, uy, uz, [&](int lm, float Y, float gx, float gy, float gz) {
-                const float4 *h4 = reinterpret_cast<const float4 *>(at.Ah + lm * NAP);
-                float a1 = 0.0f, a2 = 0.0f;
-#pragma unroll
-                for (int q = 0; q < NAP / 4; ++q) {
-                    const float4 h = h4[q];
-                    const float hv[4] = {h.x, h.y, h.z, h.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (4 * q + e < NA) {
-                            a1 += hv[e] * at_k<NA>(g, 4 * q + e);
-                            a2 += hv[e] * at_k<NA>(gp, 4 * q + e);
-                        }
-                    }
-                }
-                srad += a2 * Y;
-                Vx += a1 * gx;
-                Vy += a1 * gy;
-                Vz += a1 * gz;
-            });
-            {
-                float fr[KR], fpr[KR];
-                basis_val_der<KR>(r, a.inv_rcR, fr, fpr);
-                const float *be = beta + tj * KR;
-#pragma unroll
-                for (int kk = 0; kk < KR; ++kk) srad += be[kk] * fpr[kk];
-            }
-            if (r < a.zbl_r2) {
-                float ez, dez;
-                zbl_term(r, zbl_ti[2 * tj], zbl_ti[2 * tj + 1], a.zbl_r1, a.zbl_r2, ez, dez);
-                Ez += 0.5f * ez;
-                srad += 0.5f * dez;
-            }
-            const float uv = ux * Vx + uy * Vy + uz * Vz;
-            const float Gx = srad * ux + (Vx - ux * uv) * rinv;
-            const float Gy = srad * uy + (Vy - uy * uv) * rinv;
-            const float Gz = srad * uz + (Vz - uz * uv) * rinv;
-            a.G[p] = make_float4(Gx, Gy, Gz, 0.0f);
-            Fx += Gx;
-            Fy += Gy;
-            Fz += Gz;
-            W9[0] -= Gx * pd.x; W9[1] -= Gx * pd.y; W9[2] -= Gx * pd.z;
-            W9[3] -= Gy * pd.x; W9[4] -= Gy * pd.y; W9[5] -= Gy * pd.z;
-            W9[6] -= Gz * pd.x; W9[7] -= Gz * pd.y; W9[8] -= Gz * pd.z;
-        }
-        // radial-only neighbours
-        nxf = pair_or_zero(prs, nAng + sl, nRad);
-        for (int k = nAng + sl; k < nRad; k += SW) {
-            const int64_t p = beg + k;
-            const float4 pd = nxf;
-            nxf = pair_or_zero(prs, k + SW, nRad);
-            const int tj = pair_t(pd);
-            const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
-            const float rinv = inv_norm(r2);
-            float f[KR], fp[KR];
-            basis_val_der<KR>(r2 * rinv, a.inv_rcR, f, fp);
-            const float *be = beta + tj * KR;
-            float s2 = 0.0f;
-#pragma unroll
-            for (int kk = 0; kk < KR; ++kk) s2 += be[kk] * fp[kk];
-            if (r2 * rinv < a.zbl_r2) {
-                float ez, dez;
-                zbl_term(r2 * rinv, zbl_ti[2 * tj], zbl_ti[2 * tj + 1], a.zbl_r1, a.zbl_r2, ez, dez);
-                Ez += 0.5f * ez;
-                s2 += 0.5f * dez;
-            }
-            s2 *= rinv;
-            const float Gx = s2 * pd.x, Gy = s2 * pd.y, Gz = s2 * pd.z;
-            a.G[p] = make_float4(Gx, Gy, Gz, 0.0f);
-            Fx += Gx;
-            Fy += Gy;
-            Fz += Gz;
-            W9[0] -= Gx * pd.x; W9[1] -= Gx * pd.y; W9[2] -= Gx * pd.z;
-            W9[3] -= Gy * pd.x; W9[4] -= Gy * pd.y; W9[5] -= Gy * pd.z;
-            W9[6] -= Gz * pd.x; W9[7] -= Gz * pd.y; W9[8] -= Gz * pd.z;
-        }
-        {
-            float v[16] = {Fx, Fy, Fz, W9[0], W9[1], W9[2], W9[3], W9[4], W9[5], W9[6], W9[7], W9[8],
-                           Ez, 0.0f, 0.0f, 0.0f};
-            group_reduce_scatter<16, SW>(v, lane);
-            const int base = grs_base<16, SW>(lane);
-            if (act && (lane & GRS<16, SW>::DUP_MASK) == 0) {
-#pragma unroll
-                for (int o = 0; o < GRS<16, SW>::OUT; ++o) {
-                    const int idx = base + o;
-                    if (idx < 3) a.F_own[(size_t)i * 3 + idx] = v[o];
-                    else if (idx < 12) a.W_atom[(size_t)i * 9 + idx - 3] = v[o];
-                    else if (idx == 12) a.E_atom[i] = Ei + v[o];
-                }
-            }
-        }
-        if (act) {
-            for (int e = sl; e < ND; e += SW) a.st_qt[(size_t)wi * ND + e] = at.qt[e];
-            for (int e = sl; e < L3 * NA; e += SW) {  // [lm][n], n packed
-                const int lm = e / NA, n = e - lm * NA;
-                a.st_A[(size_t)wi * NA * L3 + e] = at.A[lm * NAP + n];
-            }
-            if (a.q_raw)
-                for (int e = sl; e < ND; e += SW) a.q_raw[(size_t)i * ND + e] = at.q[e];
-        }
-        __syncwarp();
-    }
-}
-
 // ============================================================================= adjoint
 // Three stages, for cotangents fbar = dL/dF, ebar = dL/dE_s, wbar = dL/dW_s:
 //   k_adj_jvp  (per atom)  lambda_p = fbar_i - fbar_j - wbar_s d_p; the JVP dq~ of the
@@ -725,7 +354,7 @@ __device__ __forceinline__ void pair_lambda(const AtomArgs &a, float4 pd, float 
 }
 
 template <class S, int SW, int VAR>
-__global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adj_jvp(AtomArgs a) {
+__global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_jvp(AtomArgs a) {
     using L = JvpL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
@@ -953,7 +582,7 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adj_
 // Per chunk of <= 128 work positions of one species t, in tiles of 64 atoms (Eq. "ann"):
 //   v = W0 dq~,  h' = 1 - h^2,  h'' = -2 h h',
 //   zeta = ebar w1 h' + w1 h'' v,  u = w1 h',  omega = ebar h + h' v,
-//   abar = s (W0^T zeta),  b = s (W0^T u).
+//   abar = s (W0^T zeta)   (b = s (W0^T u) comes from the network forward pass).
 // 256 threads as 16 x 16; each owns 4 atoms x 4 columns of a 64 x 64 output block, and the
 // operands come from shared memory with 128-bit loads (atoms along the fast axis).
 constexpr int NETR = 64;  // atoms per tile
@@ -961,7 +590,7 @@ constexpr int NETR = 64;  // atoms per tile
 template <class S>
 __host__ __device__ inline size_t net_rev_smem(int NN) {
     const size_t NDQ = round4(S::ND), NNP = round4(NN);
-    return sizeof(float) * (NDQ * NETR + 2 * NNP * NETR + (size_t)S::ND * NNP + (size_t)NN * NDQ);
+    return sizeof(float) * (NDQ * NETR + NNP * NETR + (size_t)S::ND * NNP + (size_t)NN * NDQ);
 }
 
 template <class S>
@@ -971,8 +600,7 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
     const int NN = a.NN, NNP = round4(NN), T = a.T;
     float *Q = smn;                 // [NDQ][NETR] dq~, transposed
     float *Z = Q + NDQ * NETR;      // [NNP][NETR] zeta, transposed
-    float *U = Z + NNP * NETR;      // [NNP][NETR] u, transposed
-    float *Wt = U + NNP * NETR;     // [ND][NNP]  W0^T of the species
+    float *Wt = Z + NNP * NETR;     // [ND][NNP]  W0^T of the species
     float *Wn = Wt + ND * NNP;      // [NN][NDQ]  W0 of the species
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int rc0 = a.chunks[blockIdx.x], rc1 = a.chunks[blockIdx.x + 1];
@@ -1027,20 +655,18 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
 #pragma unroll
                     for (int y = 0; y < 4; ++y) {
                         const int mu = mu0 + y;
-                        float ze = 0.0f, uu = 0.0f;
+                        float ze = 0.0f;
                         if (row && mu < NN) {
                             const float h = a.st_h[(size_t)wpos * NN + mu];
                             const float wo = w1[mu];
                             const float hp = 1.0f - h * h;
                             const float hpp = -2.0f * h * hp;
                             ze = eb * wo * hp + wo * hpp * acc[x][y];
-                            uu = wo * hp;
                             a.zt[(size_t)wpos * NN + mu] = ze;
-                            a.ut[(size_t)wpos * NN + mu] = uu;
+                            a.ut[(size_t)wpos * NN + mu] = wo * hp;
                             a.om[(size_t)wpos * NN + mu] = eb * h + hp * acc[x][y];
                         }
                         Z[mu * NETR + r] = ze;
-                        U[mu * NETR + r] = uu;
                     }
                 }
             }
@@ -1049,25 +675,20 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
         for (int cb = 0; cb < NDQ; cb += 64) {
             const int v0 = cb + tx * 4;
             if (v0 < NDQ) {
-                float aa[4][4], ab[4][4];
+                float aa[4][4];
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) aa[x][y] = ab[x][y] = 0.0f;
+                    for (int y = 0; y < 4; ++y) aa[x][y] = 0.0f;
 #pragma unroll 5
                 for (int mu = 0; mu < NN; ++mu) {
                     const float4 z4 = *reinterpret_cast<const float4 *>(Z + mu * NETR + r0);
-                    const float4 u4 = *reinterpret_cast<const float4 *>(U + mu * NETR + r0);
                     const float4 w4 = *reinterpret_cast<const float4 *>(Wn + mu * NDQ + v0);
-                    const float z[4] = {z4.x, z4.y, z4.z, z4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
-                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                    const float z[4] = {z4.x, z4.y, z4.z, z4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                     for (int x = 0; x < 4; ++x)
 #pragma unroll
-                        for (int y = 0; y < 4; ++y) {
-                            aa[x][y] += z[x] * wv[y];
-                            ab[x][y] += uu[x] * wv[y];
-                        }
+                        for (int y = 0; y < 4; ++y) aa[x][y] += z[x] * wv[y];
                 }
 #pragma unroll
                 for (int x = 0; x < 4; ++x) {
@@ -1076,11 +697,7 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
 #pragma unroll
                         for (int y = 0; y < 4; ++y) {
                             const int v = v0 + y;
-                            if (v < ND) {
-                                const float sc = scale[v];
-                                a.st_ab[(size_t)(rb + r) * ND + v] = aa[x][y] * sc;
-                                a.st_b[(size_t)(rb + r) * ND + v] = ab[x][y] * sc;
-                            }
+                            if (v < ND) a.st_ab[(size_t)(rb + r) * ND + v] = aa[x][y] * scale[v];
                         }
                     }
                 }
@@ -1090,7 +707,7 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
 }
 
 template <class S, int SW, int VAR>
-__global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adj_cg(AtomArgs a) {
+__global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_cg(AtomArgs a) {
     using L = CgL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int NCR = S::NCR, NCA = S::NCA, NC = S::NC;
@@ -1344,11 +961,529 @@ __global__ void __launch_bounds__(VAR == 0 ? 128 : 256, VAR == 0 ? 3 : 2) k_adj_
     if (cur_t >= 0) flush_slot(cur_t);
 }
 
-// ============================================================================= dispatch
+// ============================================================================= forward
+// Three stages:
+//   k_fwd_desc (per atom)  angular moments, radial descriptor, invariants -> q~, A;
+//   k_net_fwd  (per chunk of atoms of one species, tiled products) the network (Eq. "ann"):
+//                          h = tanh(W0 q~ - b0), E_i = w1.h - b1, b = s (W0^T (w1 (1 - h^2)));
+//   k_fwd_pair (per atom)  dE_i/dA, the radial factors beta, pair gradients G_p, the
+//                          atom's own force and virial sums.
 
 template <class S, int SW, int VAR>
-void launch_fwd_t(const AtomArgs &a, int blocks, int wpb, size_t smem, cudaStream_t st) {
-    k_forward<S, SW, VAR><<<blocks, wpb * 32, smem, st>>>(a);
+__global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_desc(AtomArgs a) {
+    using L = DescL<S, SW>;
+    constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
+    constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
+    constexpr int KR4 = round4(KR), KA4 = round4(KA);
+    constexpr int VR = pow2ceil(KR);
+    constexpr int VRN = pow2ceil(NR);
+    extern __shared__ __align__(16) float smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane / SW, sl = lane % SW;
+    const int T = a.T, NN = a.NN;
+    float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
+    L &sm = *reinterpret_cast<L *>(base_ptr);
+    float *Sr = base_ptr + sizeof(L) / sizeof(float) + grp * KR;  // [KR] of this group (one species)
+
+    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
+    const ParOff po = par_offsets(T, NN, NR, KR, NA, KA);
+    const float *scale = a.par + po.scale;
+
+    for (int bp = wbeg; bp < wend;) {
+        int ti, nb, i;
+        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
+        const bool act = grp < nb;
+        const int wi = bp + (act ? grp : 0);
+        bp += nb;
+        const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;  // [b][n][KR4]
+        const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;  // [b][n][KA4]
+        const int64_t beg = a.nbr_off[i];
+        const int nRad = act ? (int)(a.nbr_off[i + 1] - beg) : 0;
+        const int nAng = act ? a.n_ang[i] : 0;
+        const int maxR = __reduce_max_sync(FULL, nRad);
+        const int maxA = __reduce_max_sync(FULL, nAng);
+        typename L::Atom &at = sm.at[grp];
+        if (bp + grp < wend) {  // the atoms after this batch: bring their pair records into L2
+            const int ni = a.work[bp + grp];
+            const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
+            prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
+        }
+
+        // ---------------------------------------------------------------- angular moments A_nlm
+        float accA[NLMO][NA];
+#pragma unroll
+        for (int j = 0; j < NLMO; ++j)
+#pragma unroll
+            for (int n = 0; n < NA; ++n) accA[j][n] = 0.0f;
+        const float4 *prs = a.pair + beg;
+        float4 nxt = pair_or_zero(prs, sl, nAng);
+        for (int c0 = 0; c0 < maxA; c0 += SW) {
+            const int k = c0 + sl;
+            const float4 pd = nxt;
+            nxt = pair_or_zero(prs, k + SW, nAng);
+            if (k < nAng) {
+                const int tj = pair_t(pd);
+                const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
+                const float rinv = inv_norm(r2);
+                const float r = r2 * rinv;
+                float f[KA], g[NA];
+                basis_val<KA>(r, a.inv_rcA, f);
+                contract_c<NA, KA>(cAi + tj * NA * KA4, f, g);
+                store_row4<NA>(sm.st.g[grp][sl], g);
+                float Y[L3];
+                ylm_val(pd.x * rinv, pd.y * rinv, pd.z * rinv, Y);
+#pragma unroll
+                for (int lm = 0; lm < L3; ++lm) sm.st.Y[grp][sl][lm] = Y[lm];
+            }
+            __syncwarp();
+            const int cnt = min(SW, nAng - c0);
+            for (int pp = 0; pp < cnt; ++pp) {
+                float gv[NAP];
+                load_row<NAP>(sm.st.g[grp][pp], gv);
+#pragma unroll
+                for (int j = 0; j < NLMO; ++j) {
+                    const int lm = sl + j * SW;
+                    if (lm < L3) {
+                        const float y = sm.st.Y[grp][pp][lm];
+#pragma unroll
+                        for (int n = 0; n < NA; ++n) accA[j][n] += gv[n] * y;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < NLMO; ++j) {
+            const int lm = sl + j * SW;
+            if (lm < L3) store_row4<NA>(at.A + lm * NAP, accA[j]);
+        }
+
+        // ---------------------------------------------------------------- radial descriptor q_n
+        if (T == 1) {  // one species: S_k = sum_j f_k(r_ij), one reduction per atom, q = c S
+            float v[VR];
+#pragma unroll
+            for (int k = 0; k < VR; ++k) v[k] = 0.0f;
+            float4 nxr = pair_or_zero(prs, sl, nRad);
+            for (int c0 = 0; c0 < maxR; c0 += SW) {
+                const int k = c0 + sl;
+                const float4 pd = nxr;
+                nxr = pair_or_zero(prs, k + SW, nRad);
+                if (k < nRad) {
+                    const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
+                    float f[KR];
+                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) v[kk] += f[kk];
+                }
+            }
+            for (int e = sl; e < KR; e += SW) Sr[e] = 0.0f;
+            __syncwarp();
+            if (__any_sync(FULL, nRad > 0)) flush_groups<VR, SW>(v, Sr, KR, nRad > 0, lane, false);
+            __syncwarp();
+            for (int n = sl; n < NR; n += SW) {
+                float q = 0.0f;
+                const float *cr = cRi + n * KR4;
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) q += __ldg(cr + kk) * Sr[kk];
+                at.q[n] = q;
+            }
+        } else {  // several species: every lane adds g_n = sum_k c^{t_i t_j}_nk f_k of its own pairs
+            float qv[VRN];
+#pragma unroll
+            for (int n = 0; n < VRN; ++n) qv[n] = 0.0f;
+            float4 nxr = pair_or_zero(prs, sl, nRad);
+            for (int c0 = 0; c0 < maxR; c0 += SW) {
+                const int k = c0 + sl;
+                const float4 pd = nxr;
+                nxr = pair_or_zero(prs, k + SW, nRad);
+                if (k < nRad) {
+                    const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
+                    float f[KR], g[NR];
+                    basis_val<KR>(r2 * inv_norm(r2), a.inv_rcR, f);
+                    contract_c<NR, KR>(cRi + pair_t(pd) * NR * KR4, f, g);
+#pragma unroll
+                    for (int n = 0; n < NR; ++n) qv[n] += g[n];
+                }
+            }
+            for (int n = sl; n < NR; n += SW) at.q[n] = 0.0f;
+            __syncwarp();
+            if (__any_sync(FULL, nRad > 0)) flush_groups<VRN, SW>(qv, at.q, NR, nRad > 0, lane, false);
+        }
+        __syncwarp();
+
+        // ---------------------------------------------------------------- invariants (Eq. "q3b", 4-/5-body)
+        for (int e = sl; e < 4 * NA; e += SW) {
+            const int n = e % NA, l = e / NA + 1;
+            float s2 = 0.0f;
+            for (int m = 0; m < 2 * l + 1; ++m) {
+                const float v = at.A[(l * l - 1 + m) * NAP + n];
+                s2 += v * v;
+            }
+            at.q[NR + (l - 1) * NA + n] = s2;
+        }
+        for (int n = sl; n < NA; n += SW) {
+            float a2[5], Mt[6], M2[6];
+            l2_block<NAP>(at.A, n, a2);
+            l2_matrix(a2, Mt);
+            sym_prod(Mt, Mt, M2);
+            at.q[NR + 4 * NA + n] = KAPPA_REAL * sym_trace_prod(M2, Mt);
+            const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
+            const float q1 = x0 * x0 + x1 * x1 + x2 * x2;
+            at.q[NR + 5 * NA + n] = q1 * q1;
+        }
+        __syncwarp();
+        if (act) {
+            for (int e = sl; e < ND; e += SW) a.st_qt[(size_t)wi * ND + e] = at.q[e] * scale[e];
+            for (int e = sl; e < L3 * NA; e += SW) {  // [lm][n], n packed
+                const int lm = e / NA, n = e - lm * NA;
+                a.st_A[(size_t)wi * NA * L3 + e] = at.A[lm * NAP + n];
+            }
+            if (a.q_raw)
+                for (int e = sl; e < ND; e += SW) a.q_raw[(size_t)i * ND + e] = at.q[e];
+        }
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------- network forward
+// Per chunk of <= 128 work positions of one species t, in tiles of 64 atoms (Eq. "ann"):
+//   h = tanh(W0 q~ - b0),  E = w1 . h - b1,  u = w1 (1 - h^2),  b = s (W0^T u).
+// Same tiling as the network reverse pass.
+template <class S>
+__host__ __device__ inline size_t net_fwd_smem(int NN) {
+    const size_t NDQ = round4(S::ND), NNP = round4(NN);
+    return sizeof(float) * (NDQ * NETR + NNP * NETR + (size_t)S::ND * NNP + (size_t)NN * NDQ + NETR);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
+    constexpr int ND = S::ND, NDQ = round4(ND);
+    extern __shared__ __align__(16) float smn[];
+    const int NN = a.NN, NNP = round4(NN), T = a.T;
+    float *Q = smn;                 // [NDQ][NETR] q~, transposed
+    float *U = Q + NDQ * NETR;      // [NNP][NETR] u, transposed
+    float *Wt = U + NNP * NETR;     // [ND][NNP]  W0^T of the species
+    float *Wn = Wt + ND * NNP;      // [NN][NDQ]  W0 of the species
+    float *Es = Wn + NN * NDQ;      // [NETR]     energies of the tile's atoms
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int rc0 = a.chunks[blockIdx.x], rc1 = a.chunks[blockIdx.x + 1];
+    if (rc0 >= rc1) return;
+    const int t = a.type[a.work[rc0]];
+    const ParOff po = par_offsets(T, NN, S::NR, S::KR, S::NA, S::KA);
+    const float *W0 = a.par + po.w0 + (size_t)t * NN * ND;
+    const float *W0T = a.par + po.w0t + (size_t)t * ND * NN;
+    const float *b0 = a.par + po.b0 + (size_t)t * NN;
+    const float *w1 = a.par + po.w1 + (size_t)t * NN;
+    const float b1 = a.par[po.b1];
+    const float *scale = a.par + po.scale;
+    for (int e = threadIdx.x; e < ND * NNP; e += 256) {
+        const int k = e / NNP, mu = e - k * NNP;
+        Wt[e] = mu < NN ? W0T[(size_t)k * NN + mu] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < NN * NDQ; e += 256) {
+        const int mu = e / NDQ, v = e - mu * NDQ;
+        Wn[e] = v < ND ? W0[(size_t)mu * ND + v] : 0.0f;
+    }
+    for (int rb = rc0; rb < rc1; rb += NETR) {
+        const int nr = min(NETR, rc1 - rb);
+        __syncthreads();  // the weights are staged; the previous tile is done with Q, U, Es
+        for (int e = threadIdx.x; e < NETR * NDQ; e += 256) {
+            const int r = e / NDQ, k = e - r * NDQ;
+            Q[k * NETR + r] = (r < nr && k < ND) ? a.st_qt[(size_t)(rb + r) * ND + k] : 0.0f;
+        }
+        if (threadIdx.x < NETR) Es[threadIdx.x] = 0.0f;
+        __syncthreads();
+        const int r0 = ty * 4;
+        for (int cb = 0; cb < NNP; cb += 64) {
+            const int mu0 = cb + tx * 4;
+            float ep[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // w1 . h over this thread's 4 neurons
+            if (mu0 < NNP) {
+                float acc[4][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
+#pragma unroll 7
+                for (int k = 0; k < ND; ++k) {
+                    const float4 q4 = *reinterpret_cast<const float4 *>(Q + k * NETR + r0);
+                    const float4 w4 = *reinterpret_cast<const float4 *>(Wt + k * NNP + mu0);
+                    const float q[4] = {q4.x, q4.y, q4.z, q4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] += q[x] * wv[y];
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int r = r0 + x;
+                    const bool row = r < nr;
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        const int mu = mu0 + y;
+                        float uu = 0.0f;
+                        if (row && mu < NN) {
+                            const float h = tanhf(acc[x][y] - b0[mu]);
+                            const float wo = w1[mu];
+                            a.st_h[(size_t)(rb + r) * NN + mu] = h;
+                            ep[x] += wo * h;
+                            uu = wo * (1.0f - h * h);
+                        }
+                        U[mu * NETR + r] = uu;
+                    }
+                }
+            }
+            // energies: the 16 column threads of a row group add their neuron sums in a fixed order
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                float v = ep[x];
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                if (tx == 0) Es[r0 + x] += v;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nr) a.st_E[rb + threadIdx.x] = Es[threadIdx.x] - b1;
+        for (int cb = 0; cb < NDQ; cb += 64) {
+            const int v0 = cb + tx * 4;
+            if (v0 < NDQ) {
+                float ab[4][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) ab[x][y] = 0.0f;
+#pragma unroll 5
+                for (int mu = 0; mu < NN; ++mu) {
+                    const float4 u4 = *reinterpret_cast<const float4 *>(U + mu * NETR + r0);
+                    const float4 w4 = *reinterpret_cast<const float4 *>(Wn + mu * NDQ + v0);
+                    const float uu[4] = {u4.x, u4.y, u4.z, u4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) ab[x][y] += uu[x] * wv[y];
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int r = r0 + x;
+                    if (r < nr) {
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) {
+                            const int v = v0 + y;
+                            if (v < ND) a.st_b[(size_t)(rb + r) * ND + v] = ab[x][y] * scale[v];
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <class S, int SW, int VAR>
+__global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_pair(AtomArgs a) {
+    using L = PairL<S, SW>;
+    constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
+    constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
+    constexpr int KR4 = round4(KR), KA4 = round4(KA);
+    extern __shared__ __align__(16) float smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane / SW, sl = lane % SW;
+    const int T = a.T, NN = a.NN;
+    float *base_ptr = smem_raw + wib * (L::bytes(T, NN) / sizeof(float));
+    L &sm = *reinterpret_cast<L *>(base_ptr);
+    float *beta = base_ptr + sizeof(L) / sizeof(float) + grp * T * KR;  // [T][KR] of this group
+
+    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int wbeg = a.warp_begin[w], wend = a.warp_begin[w + 1];
+    const ParOff po = par_offsets(T, NN, NR, KR, NA, KA);
+
+    for (int bp = wbeg; bp < wend;) {
+        int ti, nb, i;
+        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
+        const bool act = grp < nb;
+        const int wi = bp + (act ? grp : 0);
+        bp += nb;
+        const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;
+        const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;
+        const int64_t beg = a.nbr_off[i];
+        const int nRad = act ? (int)(a.nbr_off[i + 1] - beg) : 0;
+        const int nAng = act ? a.n_ang[i] : 0;
+        typename L::Atom &at = sm.at[grp];
+        if (bp + grp < wend) {  // the atoms after this batch: bring their pair records into L2
+            const int ni = a.work[bp + grp];
+            const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
+            prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
+        }
+        load_lm_rows<NA, NAP, SW>(a.st_A + (size_t)wi * NA * L3, at.A, sl);
+        for (int v = sl; v < ND; v += SW) at.b[v] = a.st_b[(size_t)wi * ND + v];
+        __syncwarp();
+
+        // ---------------------------------------------------------------- dE_i/dA and radial factors
+        for (int n = sl; n < NA; n += SW) {
+            float a2[5], Mt[6], M2[6], pr[5];
+            l2_block<NAP>(at.A, n, a2);
+            l2_matrix(a2, Mt);
+            sym_prod(Mt, Mt, M2);
+            l2_project(M2, pr);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) at.G4[n * 5 + m] = 3.0f * KAPPA_REAL * pr[m];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < NLMO; ++j) {
+            const int lm = sl + j * SW;
+            if (lm < L3) {
+                const int l = l_of_lm(lm);
+                float ah[NA];
+#pragma unroll
+                for (int n = 0; n < NA; ++n) {
+                    const float av = at.A[lm * NAP + n];
+                    float x = 2.0f * at.b[NR + (l - 1) * NA + n] * av;
+                    if (l == 2) x += at.b[NR + 4 * NA + n] * at.G4[n * 5 + (lm - 3)];
+                    if (l == 1) {
+                        const float x0 = at.A[n], x1 = at.A[NAP + n], x2 = at.A[2 * NAP + n];
+                        x += at.b[NR + 5 * NA + n] * 4.0f * (x0 * x0 + x1 * x1 + x2 * x2) * av;
+                    }
+                    ah[n] = x;
+                }
+                store_row4<NA>(at.Ah + lm * NAP, ah);
+            }
+        }
+        for (int e = sl; e < T * KR; e += SW) {
+            const int bb = e / KR, kk = e - bb * KR;
+            float s2 = 0.0f;
+#pragma unroll
+            for (int n = 0; n < NR; ++n) s2 += at.b[n] * __ldg(cRi + (bb * NR + n) * KR4 + kk);
+            beta[e] = s2;
+        }
+        __syncwarp();
+
+        // ---------------------------------------------------------------- pair gradients
+        const float4 *prs = a.pair + beg;
+        const float *zbl_ti = a.zbl ? a.zbl + (size_t)ti * T * 2 : nullptr;
+        float Ez = 0.0f;  // ZBL energy of this lane's pairs (half of each pair term)
+        float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+        float W9[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) W9[k] = 0.0f;
+        // angular neighbours: angular and radial parts of G_p together
+        float4 nxf = pair_or_zero(prs, sl, nAng);
+        for (int k = sl; k < nAng; k += SW) {
+            const int64_t p = beg + k;
+            const float4 pd = nxf;
+            nxf = pair_or_zero(prs, k + SW, nAng);
+            const int tj = pair_t(pd);
+            const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
+            const float rinv = inv_norm(r2);
+            const float r = r2 * rinv;
+            const float ux = pd.x * rinv, uy = pd.y * rinv, uz = pd.z * rinv;
+            float f[KA], fp[KA], g[NA], gp[NA];
+            basis_val_der<KA>(r, a.inv_rcA, f, fp);
+            contract_c2<NA, KA>(cAi + tj * NA * KA4, f, fp, g, gp);
+            float srad = 0.0f, Vx = 0.0f, Vy = 0.0f, Vz = 0.0f;
+            ylm_each(ux, uy, uz, [&](int lm, float Y, float gx, float gy, float gz) {
+                const float4 *h4 = reinterpret_cast<const float4 *>(at.Ah + lm * NAP);
+                float a1 = 0.0f, a2 = 0.0f;
+#pragma unroll
+                for (int q = 0; q < NAP / 4; ++q) {
+                    const float4 h = h4[q];
+                    const float hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (4 * q + e < NA) {
+                            a1 += hv[e] * at_k<NA>(g, 4 * q + e);
+                            a2 += hv[e] * at_k<NA>(gp, 4 * q + e);
+                        }
+                    }
+                }
+                srad += a2 * Y;
+                Vx += a1 * gx;
+                Vy += a1 * gy;
+                Vz += a1 * gz;
+            });
+            {
+                float fr[KR], fpr[KR];
+                basis_val_der<KR>(r, a.inv_rcR, fr, fpr);
+                const float *be = beta + tj * KR;
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) srad += be[kk] * fpr[kk];
+            }
+            if (r < a.zbl_r2) {
+                float ez, dez;
+                zbl_term(r, zbl_ti[2 * tj], zbl_ti[2 * tj + 1], a.zbl_r1, a.zbl_r2, ez, dez);
+                Ez += 0.5f * ez;
+                srad += 0.5f * dez;
+            }
+            const float uv = ux * Vx + uy * Vy + uz * Vz;
+            const float Gx = srad * ux + (Vx - ux * uv) * rinv;
+            const float Gy = srad * uy + (Vy - uy * uv) * rinv;
+            const float Gz = srad * uz + (Vz - uz * uv) * rinv;
+            a.G[p] = make_float4(Gx, Gy, Gz, 0.0f);
+            Fx += Gx;
+            Fy += Gy;
+            Fz += Gz;
+            W9[0] -= Gx * pd.x; W9[1] -= Gx * pd.y; W9[2] -= Gx * pd.z;
+            W9[3] -= Gy * pd.x; W9[4] -= Gy * pd.y; W9[5] -= Gy * pd.z;
+            W9[6] -= Gz * pd.x; W9[7] -= Gz * pd.y; W9[8] -= Gz * pd.z;
+        }
+        // radial-only neighbours
+        nxf = pair_or_zero(prs, nAng + sl, nRad);
+        for (int k = nAng + sl; k < nRad; k += SW) {
+            const int64_t p = beg + k;
+            const float4 pd = nxf;
+            nxf = pair_or_zero(prs, k + SW, nRad);
+            const int tj = pair_t(pd);
+            const float r2 = pd.x * pd.x + pd.y * pd.y + pd.z * pd.z;
+            const float rinv = inv_norm(r2);
+            float f[KR], fp[KR];
+            basis_val_der<KR>(r2 * rinv, a.inv_rcR, f, fp);
+            const float *be = beta + tj * KR;
+            float s2 = 0.0f;
+#pragma unroll
+            for (int kk = 0; kk < KR; ++kk) s2 += be[kk] * fp[kk];
+            if (r2 * rinv < a.zbl_r2) {
+                float ez, dez;
+                zbl_term(r2 * rinv, zbl_ti[2 * tj], zbl_ti[2 * tj + 1], a.zbl_r1, a.zbl_r2, ez, dez);
+                Ez += 0.5f * ez;
+                s2 += 0.5f * dez;
+            }
+            s2 *= rinv;
+            const float Gx = s2 * pd.x, Gy = s2 * pd.y, Gz = s2 * pd.z;
+            a.G[p] = make_float4(Gx, Gy, Gz, 0.0f);
+            Fx += Gx;
+            Fy += Gy;
+            Fz += Gz;
+            W9[0] -= Gx * pd.x; W9[1] -= Gx * pd.y; W9[2] -= Gx * pd.z;
+            W9[3] -= Gy * pd.x; W9[4] -= Gy * pd.y; W9[5] -= Gy * pd.z;
+            W9[6] -= Gz * pd.x; W9[7] -= Gz * pd.y; W9[8] -= Gz * pd.z;
+        }
+        {
+            const float Ei = a.st_E[wi];
+            float v[16] = {Fx, Fy, Fz, W9[0], W9[1], W9[2], W9[3], W9[4], W9[5], W9[6], W9[7], W9[8],
+                           Ez, 0.0f, 0.0f, 0.0f};
+            group_reduce_scatter<16, SW>(v, lane);
+            const int base = grs_base<16, SW>(lane);
+            if (act && (lane & GRS<16, SW>::DUP_MASK) == 0) {
+#pragma unroll
+                for (int o = 0; o < GRS<16, SW>::OUT; ++o) {
+                    const int idx = base + o;
+                    if (idx < 3) a.F_own[(size_t)i * 3 + idx] = v[o];
+                    else if (idx < 12) a.W_atom[(size_t)i * 9 + idx - 3] = v[o];
+                    else if (idx == 12) a.E_atom[i] = Ei + v[o];
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ============================================================================= dispatch
+
+// Forward stages: 0 = descriptors, 1 = network, 2 = pair gradients, -1 = all three.
+template <class S, int SW, int VAR>
+void launch_fwd_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_t st) {
+    if (stage < 0 || stage == 0) k_fwd_desc<S, SW, VAR><<<blocks, wpb * 32, DescL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
+    if ((stage < 0 || stage == 1) && a.n_chunks > 0) k_net_fwd<S><<<a.n_chunks, 256, net_fwd_smem<S>(a.NN), st>>>(a);
+    if (stage < 0 || stage == 2) k_fwd_pair<S, SW, VAR><<<blocks, wpb * 32, PairL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
 }
 // Adjoint stages: 0 = JVP, 1 = network reverse, 2 = coefficient gradient, -1 = all three.
 template <class S, int SW, int VAR>
@@ -1357,8 +1492,12 @@ void launch_adj_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_
     if ((stage < 0 || stage == 1) && a.n_chunks > 0) k_net_rev<S><<<a.n_chunks, 256, net_rev_smem<S>(a.NN), st>>>(a);
     if (stage < 0 || stage == 2) k_adj_cg<S, SW, VAR><<<blocks, wpb * 32, CgL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
 }
+// per-warp shared memory of the larger of the two per-atom forward stages
 template <class S, int SW>
-size_t fwd_bytes_t(int T, int NN) { return FwdL<S, SW>::bytes(T, NN); }
+size_t fwd_bytes_t(int T, int NN) {
+    const size_t d = DescL<S, SW>::bytes(T, NN), p = PairL<S, SW>::bytes(T, NN);
+    return d > p ? d : p;
+}
 // per-warp shared memory of the larger of the two per-atom adjoint stages
 template <class S, int SW>
 size_t adj_bytes_t(int T, int NN) {
@@ -1366,7 +1505,8 @@ size_t adj_bytes_t(int T, int NN) {
     return j > c ? j : c;
 }
 
-// Variant v: SW = 8 (v < 2) or 16, register budget VAR = v & 1.
+// Variant v: SW = 8 (v < 2) or 16, register budget VAR = v & 1 (blocks of at most 128 threads;
+// 0: four blocks per SM, 128 registers; 1: five blocks per SM, 96 registers).
 template <int NR, int KR, int NA, int KA>
 KernelSet make_set() {
     using S = Shape<NR, KR, NA, KA>;
@@ -1375,10 +1515,16 @@ KernelSet make_set() {
     k.KR = KR;
     k.NA = NA;
     k.KA = KA;
-    k.fwd_fn[0] = (const void *)k_forward<S, 8, 0>;
-    k.fwd_fn[1] = (const void *)k_forward<S, 8, 1>;
-    k.fwd_fn[2] = (const void *)k_forward<S, 16, 0>;
-    k.fwd_fn[3] = (const void *)k_forward<S, 16, 1>;
+    k.fwd_fn[0] = (const void *)k_fwd_pair<S, 8, 0>;
+    k.fwd_fn[1] = (const void *)k_fwd_pair<S, 8, 1>;
+    k.fwd_fn[2] = (const void *)k_fwd_pair<S, 16, 0>;
+    k.fwd_fn[3] = (const void *)k_fwd_pair<S, 16, 1>;
+    k.desc_fn[0] = (const void *)k_fwd_desc<S, 8, 0>;
+    k.desc_fn[1] = (const void *)k_fwd_desc<S, 8, 1>;
+    k.desc_fn[2] = (const void *)k_fwd_desc<S, 16, 0>;
+    k.desc_fn[3] = (const void *)k_fwd_desc<S, 16, 1>;
+    k.net_fwd_fn = (const void *)k_net_fwd<S>;
+    k.net_fwd_smem = net_fwd_smem<S>;
     k.adj_fn[0] = (const void *)k_adj_cg<S, 8, 0>;
     k.adj_fn[1] = (const void *)k_adj_cg<S, 8, 1>;
     k.adj_fn[2] = (const void *)k_adj_cg<S, 16, 0>;
@@ -1402,7 +1548,7 @@ KernelSet make_set() {
     k.adj_smem[0] = k.adj_smem[1] = adj_bytes_t<S, 8>;
     k.adj_smem[2] = k.adj_smem[3] = adj_bytes_t<S, 16>;
     for (int v = 0; v < NVAR; ++v) {
-        k.max_wpb[v] = (v & 1) ? 8 : 4;
+        k.max_wpb[v] = 4;
         k.sw[v] = v < 2 ? 8 : 16;
     }
     return k;

@@ -55,9 +55,9 @@ extern "C" int nep_descriptor_range_noalloc(nep_ctx *c, float *qmin, float *qmax
     float *q = nullptr;
     int rc = scratch_address(c, &q);
     if (rc) return rc;
-    // Every scratch entry the range kernel reads is written by the forward kernel in
-    // this same call, so nothing has to be cleared between calls.
+    // Every scratch entry the range kernel reads is written by the forward's descriptor
+    // stage in this same call, so nothing has to be cleared between calls.
     if ((rc = launch_expand(c))) return rc;
-    if ((rc = launch_forward(c, q))) return rc;
+    if ((rc = launch_forward(c, q, 0))) return rc;
     return launch_range(c, q, qmin, qmax);
 }

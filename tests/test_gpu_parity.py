@@ -281,8 +281,11 @@ def test_launch_shapes_agree():
     c = get_case("scale_t5")
     g0 = c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref)[1].cpu().numpy()
     shape = c.nep.launch_shape()
-    c.nep.set_launch(2, 152, 8, 152 * 2)
+    c.nep.set_launch(2, 152, 4, 152 * 2)
     g1 = c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref)[1].cpu().numpy()
+    from paper_2606_19557_gb300 import NepError
+    with pytest.raises(NepError):  # blocks hold at most 4 warps
+        c.nep.set_launch(8, 152, 4, 152)
     c.nep.set_launch(*shape)
     assert rel(g1, g0) < 1e-6
 
