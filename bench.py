@@ -478,7 +478,7 @@ def minibatch_epochs(device: int, args, flush):
     nep.close()
     return {"workload": WORKLOADS["fcc_bcc_t1"]["desc"], "batch_structures": args.mb_size, "steps_per_epoch": nmb,
             "epoch_ms": ep_ms, "atoms_per_s": batch.n_atoms / (ep_ms / 1e3), "epochs_timed": args.mb_epochs,
-            "kernels_per_step": 16}
+            "kernels_per_step": 9}
 
 
 def run_ours(args):
@@ -628,7 +628,7 @@ def run_ours(args):
         "kernel_ms": kavg,
         "kernel_tflops": {k: fl[k] / (kavg[k] * 1e-3) / 1e12 for k in fl if kavg.get(k)},
         "e2e": {"value": e2e_value, "unit": "atoms/s", "h2d_bytes_per_step": 4 * P, "d2h_bytes_per_step": 24 + 4 * P},
-        "gpu_launches": 14 * args.steps,  # kernels of one loss + gradient graph
+        "gpu_launches": 10 * args.steps,  # kernels of one loss + gradient graph
         "clocks": clocks,
         "cpu_baseline": cb,
         "err_vs_oracle": err,

@@ -310,12 +310,13 @@ int nep_autotune(nep_ctx *ctx);
 /* Current launch shape: warps per block and blocks of the forward and adjoint kernels. */
 int nep_get_launch(const nep_ctx *ctx, int *fwd_warps, int *fwd_blocks, int *adj_warps, int *adj_blocks);
 
-/* Kernel variant of the forward and adjoint kernels: lanes that share one atom (8 or 16)
- * and the register budget per thread (128 or 96). */
+/* Kernel variant of the forward and adjoint kernels: lanes that share one atom (8, 16 or
+ * 32) and the register budget per thread (128 or 96). */
 int nep_get_variant(const nep_ctx *ctx, int *fwd_lanes, int *fwd_regs, int *adj_lanes, int *adj_regs);
 
-/* Selects kernel variants v in [0, 4): lanes per atom 8 (v < 2) or 16, register
- * budget 128 (v even) or 96 (v odd); the grid is reset to the occupancy limit. */
+/* Selects kernel variants v in [0, 6): lanes per atom 8 (v < 2), 16 (v < 4) or 32,
+ * register budget 128 (v even) or 96 (v odd); the grid is reset to the occupancy limit.
+ * nep_autotune tries v < 4; mini-batch setup also tries the 32-lane variants. */
 int nep_set_variant(nep_ctx *ctx, int fwd_var, int adj_var);
 
 /* Sets the launch shape explicitly (0 keeps a value); at most 4 warps per block. */

@@ -27,7 +27,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "nep_gb300.h")
 
 NEP_OK, NEP_EINVAL, NEP_ENOMEM, NEP_ECUDA, NEP_ESTATE, NEP_EINTERNAL = 0, -1, -2, -3, -4, -5
 SCHED_PERSISTENT, SCHED_PLAIN = 0, 1
-KERNEL_COUNT = 12
+KERNEL_COUNT = 10
 
 _lib = None
 _lock = threading.Lock()
@@ -432,7 +432,8 @@ class NEP:
         return tuple(int(x.value) for x in v)
 
     def set_variant(self, fwd_var: int, adj_var: int):
-        """Kernel variants (0-3): lanes per atom 8 for 0-1 and 16 for 2-3; odd = 128 registers."""
+        """Kernel variants (0-5): lanes per atom 8 for 0-1, 16 for 2-3, 32 for 4-5; even = 128
+        registers per thread, odd = 96."""
         self._call(self.lib.nep_set_variant, int(fwd_var), int(adj_var))
 
     def set_launch(self, fwd_warps=0, fwd_blocks=0, adj_warps=0, adj_blocks=0):

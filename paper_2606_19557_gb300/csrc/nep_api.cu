@@ -26,9 +26,9 @@ Ctx::~Ctx() {
 
 static thread_local std::string g_create_err;
 
-static const char *kernel_names[KID_COUNT] = {"expand_params", "forward_desc", "net_forward",   "forward_pair",
-                                              "force_gather",  "struct_sums",  "loss_final",    "adjoint_jvp",
-                                              "net_reverse",   "adjoint_cgrad", "net_grad",     "grad_reduce"};
+static const char *kernel_names[KID_COUNT] = {"expand_params", "forward_desc", "net_forward", "forward_pair",
+                                              "loss_terms",    "adjoint_jvp",  "net_reverse", "adjoint_cgrad",
+                                              "net_grad",      "grad_reduce"};
 
 // ----------------------------------------------------------------------------- helpers
 
@@ -244,7 +244,7 @@ static int default_shapes(Ctx *c) {
     return alloc_sched_buffers(c);
 }
 
-static void drop_graphs(Ctx *c) {
+void nep::drop_graphs(Ctx *c) {
     for (Ctx::Graph *g : {&c->g_loss, &c->g_eval, &c->g_train}) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         g->exec = nullptr;
@@ -263,13 +263,18 @@ static int body_eval(Ctx *c, double *E, float *F, double *W) {
     int rc;
     if ((rc = launch_expand(c))) return rc;
     if ((rc = launch_forward(c, nullptr))) return rc;
-    if ((rc = launch_gather(c, F, nullptr, 0.0, false, 0, c->n_atoms))) return rc;
-    if ((rc = launch_struct(c, E, W, nullptr, nullptr, nullptr, 0.0, 0.0, false, 0, c->n_struct))) return rc;
-    return NEP_OK;
+    TermsCall t;
+    t.a1 = c->n_atoms;
+    t.s1 = c->n_struct;
+    t.F_out = F;
+    t.E_out = E;
+    t.W_out = W;
+    return launch_terms(c, t);
 }
 
+// opt: training step, the optimiser update fused into the gradient reduction
 static int body_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
-                     double lF, double lV, double *loss3, float *grad) {
+                     double lF, double lV, double *loss3, float *grad, bool opt = false) {
     int rc;
     mark(c, 0);
     if ((rc = launch_expand(c))) return rc;
@@ -280,25 +285,34 @@ static int body_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr
     mark(c, 3);
     if ((rc = launch_forward(c, nullptr, 2))) return rc;
     mark(c, 4);
-    if ((rc = launch_count_hasw(c, hw))) return rc;
-    if ((rc = launch_gather(c, c->F_int.as<float>(), Fr, lF, true, 0, c->n_atoms))) return rc;
+    TermsCall t;
+    t.a1 = c->n_atoms;
+    t.s1 = c->n_struct;
+    t.F_out = c->F_int.as<float>();
+    t.E_out = c->E_int.as<double>();
+    t.W_out = c->W_int.as<double>();
+    t.loss = true;
+    t.F_ref = Fr;
+    t.E_ref = Er;
+    t.W_ref = Wr;
+    t.has_W = hw;
+    t.lE = lE;
+    t.lF = lF;
+    t.lV = lV;
+    t.nsv = c->ov_NsV > 0.0 ? c->ov_NsV : host_nsv(c, hw, 0, c->n_struct);
+    t.loss3 = loss3;
+    if ((rc = launch_terms(c, t))) return rc;
     mark(c, 5);
-    if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, 0,
-                            c->n_struct)))
-        return rc;
-    mark(c, 6);
-    if ((rc = launch_loss_final(c, loss3))) return rc;
-    mark(c, 7);
     if ((rc = launch_adjoint(c, 0))) return rc;
-    mark(c, 8);
+    mark(c, 6);
     if ((rc = launch_adjoint(c, 1))) return rc;
-    mark(c, 9);
+    mark(c, 7);
     if ((rc = launch_adjoint(c, 2))) return rc;
-    mark(c, 10);
+    mark(c, 8);
     if ((rc = launch_ann_grad(c))) return rc;
-    mark(c, 11);
-    if ((rc = launch_grad_final(c, grad))) return rc;
-    mark(c, 12);
+    mark(c, 9);
+    if ((rc = launch_grad_final(c, grad, opt, loss3, lE, lF, lV))) return rc;
+    mark(c, 10);
     return NEP_OK;
 }
 
@@ -402,19 +416,21 @@ int nep_create(const nep_config *cfg, void *cuda_stream, nep_ctx **out) {
         c->qscale.ensure<float>(c->ND) || c->par.ensure<float>(c->po.total) || c->d_err.ensure<int>(4) ||
         c->n_sv.ensure<int>(4) || c->gb1.ensure<double>(4) || c->loss3_int.ensure<double>(4) ||
         c->grad_int.ensure<float>(c->P) || c->hostbuf_theta.ensure<float>(c->P) ||
-        c->gpart.ensure<double>(8 * c->P)) {
+        c->gpart.ensure<double>(8 * c->P) || c->counters.ensure<unsigned>(3 + (c->P + 31) / 32)) {
         g_create_err = "device allocation failed";
         delete c;
         return NEP_ENOMEM;
     }
     if (cudaMemcpy(c->d_desc_map.ptr, c->desc_map.data(), sizeof(int) * c->ND, cudaMemcpyHostToDevice) ||
-        cudaMemcpy(c->d_desc_inv.ptr, inv.data(), sizeof(int) * c->NDP, cudaMemcpyHostToDevice)) {
+        cudaMemcpy(c->d_desc_inv.ptr, inv.data(), sizeof(int) * c->NDP, cudaMemcpyHostToDevice) ||
+        cudaMemset(c->counters.ptr, 0, c->counters.bytes)) {
         g_create_err = "cudaMemcpy failed";
         delete c;
         return NEP_ECUDA;
     }
     for (int k = 0; k <= KID_COUNT; ++k) cudaEventCreate(&c->ev[k]);
     c->ev_made = true;
+    if (const char *e = getenv("NEP_PDL")) c->use_pdl = std::strcmp(e, "1") == 0;
     *out = c;
     return NEP_OK;
 }
@@ -447,6 +463,9 @@ int nep_set_params(nep_ctx *c, const float *theta, const float *qscale) {
     CK(cudaSetDevice(c->dev));
     CK(cudaMemcpyAsync(c->theta.ptr, theta, sizeof(float) * c->P, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(c->qscale.ptr, qscale, sizeof(float) * c->ND, cudaMemcpyDeviceToDevice, c->stream));
+    // the padded copies follow theta from here on (every optimiser update refreshes them)
+    int rc = launch_expand(c);
+    if (rc) return rc;
     c->have_params = true;
     c->state_valid = false;
     return NEP_OK;
@@ -763,8 +782,19 @@ int nep_set_targets(nep_ctx *c, const double *Er, const float *Fr, const double 
         if (hw) CK(cudaMemcpyAsync(c->tgt_hw.ptr, hw, ns, cudaMemcpyDeviceToDevice, c->stream));
     }
     if (na > 0) CK(cudaMemcpyAsync(c->tgt_F.ptr, Fr, sizeof(float) * na * 3, cudaMemcpyDeviceToDevice, c->stream));
+    // N_s^V of any structure range from a host prefix count (loss normaliser of a group)
+    c->tgt_nsv_pre.assign(ns + 1, 0);
+    if (hw && ns > 0) {
+        std::vector<uint8_t> h(ns);
+        CK(cudaMemcpyAsync(h.data(), hw, ns, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int64_t s = 0; s < ns; ++s) c->tgt_nsv_pre[s + 1] = c->tgt_nsv_pre[s] + (h[s] ? 1 : 0);
+    } else {
+        for (int64_t s = 0; s < ns; ++s) c->tgt_nsv_pre[s + 1] = s + 1;
+    }
     c->tgt_has_hw = hw != nullptr;
     c->have_targets = true;
+    drop_graphs(c);  // the step graphs carry the normalisers of the previous targets
     return NEP_OK;
 }
 
@@ -819,10 +849,9 @@ int nep_optim_step(nep_ctx *c, const float *grad, const double *loss) {
 }
 
 static int body_train(Ctx *c, double lE, double lF, double lV, double *loss3) {
-    int rc = body_loss(c, c->tgt_E.as<double>(), c->tgt_F.as<float>(), c->tgt_W.as<double>(),
-                       c->tgt_has_hw ? c->tgt_hw.as<uint8_t>() : nullptr, lE, lF, lV, loss3, c->grad_int.as<float>());
-    if (rc) return rc;
-    return launch_opt_step(c, c->grad_int.as<float>(), loss3, lE, lF, lV, nullptr);
+    return body_loss(c, c->tgt_E.as<double>(), c->tgt_F.as<float>(), c->tgt_W.as<double>(),
+                     c->tgt_has_hw ? c->tgt_hw.as<uint8_t>() : nullptr, lE, lF, lV, loss3, c->grad_int.as<float>(),
+                     true);
 }
 
 int nep_train_step(nep_ctx *c, double lE, double lF, double lV, double *loss3) {
@@ -931,9 +960,7 @@ int nep_minibatch_loss_grad(nep_ctx *c, int64_t m, double lE, double lF, double 
 
 static int mb_train_step(nep_ctx *c, int64_t m, double lE, double lF, double lV, double *loss3) {
     double *l3 = loss3 ? loss3 : c->loss3_int.as<double>();
-    int rc = run_minibatch_loss(c, m, lE, lF, lV, l3, c->grad_int.as<float>());
-    if (rc) return rc;
-    return launch_opt_step(c, c->grad_int.as<float>(), l3, lE, lF, lV, nullptr);
+    return run_minibatch_loss(c, m, lE, lF, lV, l3, c->grad_int.as<float>(), true);
 }
 
 int nep_minibatch_train_step(nep_ctx *c, int64_t m, double lE, double lF, double lV, double *loss3) {
@@ -1086,7 +1113,7 @@ int nep_autotune(nep_ctx *c) {
     float best_f = 1e30f, best_a = 1e30f;
     int bfw = c->fwd.wpb, bfb = c->fwd.blocks, bfv = c->fwd.var, baw = c->adj.wpb, bab = c->adj.blocks, bav = c->adj.var;
     const int wpbs[3] = {1, 2, 4};
-    for (int var = 0; var < NVAR && !rc; ++var) {
+    for (int var = 0; var < NVAR_TUNE && !rc; ++var) {
         for (int wpb : wpbs) {
             if (wpb > c->ks->max_wpb[var]) continue;
             const int mf = max_blocks_per_sm(c, c->ks->fwd_fn[var], wpb, c->ks->fwd_smem[var](c->T, c->NN) * wpb);

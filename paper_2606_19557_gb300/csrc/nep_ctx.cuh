@@ -54,11 +54,13 @@ struct Sched {
     DevBuf type_wlo, type_whi;  // [T] first / last warp holding each species (adjoint slots)
 };
 
-constexpr int NVAR = 4;
+constexpr int NVAR = 6;
+constexpr int NVAR_TUNE = 4;  // variants the whole-batch autotune tries (32 lanes per atom pays only
+                              // for small mini-batch groups, whose own tuning includes it)
 
 enum KernelId {
-    KID_EXPAND = 0, KID_DESC, KID_NETFWD, KID_PAIR, KID_GATHER, KID_STRUCT, KID_LOSS, KID_ADJ, KID_NETREV, KID_ADJCG,
-    KID_ANN, KID_GRAD, KID_COUNT
+    KID_EXPAND = 0, KID_DESC, KID_NETFWD, KID_PAIR, KID_TERMS, KID_ADJ, KID_NETREV, KID_ADJCG, KID_ANN, KID_GRAD,
+    KID_COUNT
 };
 
 struct Ctx;
@@ -66,7 +68,7 @@ struct Ctx;
 // Per-bucket kernel entry points (compile-time shapes).
 struct KernelSet {
     int NR, KR, NA, KA;
-    // variants v = 0..3: lanes per atom sw[v] (8 or 16), register budget v & 1
+    // variants v = 0..5: lanes per atom sw[v] (8, 16 or 32), register budget v & 1
     // (0: blocks of <= 128 threads, 4 per SM, 128 registers; 1: 5 per SM, 96 registers)
     const void *fwd_fn[NVAR];   // forward pair-gradient stage
     const void *desc_fn[NVAR];  // forward descriptor stage
@@ -81,9 +83,9 @@ struct KernelSet {
     size_t (*fwd_smem[NVAR])(int T, int NN);  // bytes per warp
     size_t (*adj_smem[NVAR])(int T, int NN);
     // forward stages (0 descriptors, 1 network, 2 pair gradients; -1 all)
-    void (*launch_fwd[NVAR])(const AtomArgs &, int blocks, int wpb, int stage, cudaStream_t);
+    void (*launch_fwd[NVAR])(const AtomArgs &, int blocks, int wpb, int stage, cudaStream_t, bool pdl);
     // adjoint stages (0 JVP, 1 network reverse, 2 coefficient gradient; -1 all)
-    void (*launch_adj[NVAR])(const AtomArgs &, int blocks, int wpb, int stage, cudaStream_t);
+    void (*launch_adj[NVAR])(const AtomArgs &, int blocks, int wpb, int stage, cudaStream_t, bool pdl);
 };
 
 const KernelSet *select_kernels(int nR, int kR, int nA, int kA);
@@ -142,8 +144,16 @@ struct Ctx {
     DevBuf F_int, E_int, W_int;       // internal outputs for nep_loss_grad
     DevBuf loss_part, gb1, n_sv, loss3_int, grad_int;
     DevBuf gpart;                     // [8][P] FP64 segment sums of the gradient reduction
+    // arrival counters of the last-block reductions (zero between launches; the last block
+    // of a launch resets its counter): [0] loss terms, [1] optimiser, [2..] gradient columns
+    DevBuf counters;
     DevBuf tgt_E, tgt_F, tgt_W, tgt_hw;  // nep_set_targets copies
     bool have_targets = false, tgt_has_hw = false;
+    std::vector<int64_t> tgt_nsv_pre;    // [ns + 1] prefix count of the structures with virial targets
+    // programmatic dependent launch between the step's kernels (NEP_PDL=1): measured no
+    // faster on the step graphs, whose kernels are long against the launch gaps
+    bool use_pdl = false;
+    bool pdl() const { return use_pdl && !timing; }
     DevBuf hostbuf_theta;             // device copy target of nep_loss_grad_host
 
     // ZBL short-range term (nep_set_zbl): per species pair e^2/(4 pi eps0) Z_i Z_j and 1/a_ij
@@ -237,26 +247,169 @@ int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blo
 int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
                          const int *chunks, int n_chunks);
 int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks);
+// opt: apply the optimiser step to each parameter as its gradient completes (training)
 int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi, const int *wlo, const int *whi,
-                            const int *warp_begin);
-int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1,
-                  double *part = nullptr, int nblocks = 0);
-int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, const double *W_ref,
-                  const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1,
-                  double *part = nullptr, int nblocks = 0);
-int launch_count_hasw(Ctx *c, const uint8_t *has_W, int64_t s0 = 0, int64_t s1 = -1);
-int launch_loss_final(Ctx *c, double *loss3, const double *fpart = nullptr, int nf = -1,
-                      const double *spart = nullptr, int nsb = -1);
+                            const int *warp_begin, bool opt, const double *loss3, double lE, double lF, double lV);
+// One launch of the force gather (atoms [a0, a1)), the per-structure sums (structures
+// [s0, s1)) and, with loss3, the loss reduction by the launch's last block.
+struct TermsCall {
+    int64_t a0 = 0, a1 = 0, s0 = 0, s1 = 0;
+    float *F_out = nullptr;
+    double *E_out = nullptr, *W_out = nullptr;
+    bool loss = false;  // loss terms and cotangents against the references below
+    const float *F_ref = nullptr;
+    const double *E_ref = nullptr, *W_ref = nullptr;
+    const uint8_t *has_W = nullptr;
+    double lE = 0.0, lF = 0.0, lV = 0.0;
+    double nsv = 0.0;         // N_s^V: > 0 given; 0 counted here from has_W over [s0, s1); < 0 the
+                              // count an earlier launch_count_hasw left on the device
+    double *loss3 = nullptr;  // null: partials only (reduced later by launch_loss_final)
+    double *fpart = nullptr;  // force partials, one per gather block (null: the context's loss_part)
+    double *spart = nullptr;  // structure partials, 3 per structure (null: after the force partials)
+    int gather_blocks = 0;    // 0: the default
+    bool pdl = true;          // programmatic dependent launch (when the context allows it)
+};
+int launch_terms(Ctx *c, const TermsCall &t);
+// N_s^V of structures [s0, s1) for the loss, known on the host: has_W absent or the
+// targets' copy; 0 if it must be counted on the device.  A range without virial targets
+// gives 1 (any positive value: no virial term enters then).
+double host_nsv(Ctx *c, const uint8_t *has_W, int64_t s0, int64_t s1);
+int launch_loss_final(Ctx *c, double *loss3, const double *fpart, int nf, const double *spart, int nsb, double nsv);
+int launch_count_hasw(Ctx *c, const uint8_t *has_W, int64_t s0, int64_t s1);
 int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, const uint8_t *hw, double lE,
                    double lF, double lV, double *loss3, float *grad);
 int launch_cotangents(Ctx *c, const double *dE, const float *dF, const double *dW);
 int launch_adjoint(Ctx *c, int stage = -1);
 int launch_ann_grad(Ctx *c);
-int launch_grad_final(Ctx *c, float *grad);
+int launch_grad_final(Ctx *c, float *grad, bool opt = false, const double *loss3 = nullptr, double lE = 0.0,
+                      double lF = 0.0, double lV = 0.0);
 int launch_range(Ctx *c, const float *q, float *qmin, float *qmax);
 
 // optimiser (nep_optim.cu); device state slots
 enum { OPT_T, OPT_B1T, OPT_B2T, OPT_LR, OPT_BEST, OPT_BAD, OPT_ACC, OPT_NACC, OPT_LAST, OPT_NRED, OPT_NST };
+
+// Refresh of the padded parameter copies (par) from one compact parameter theta[k]: the
+// inverse of the expansion, so an update keeps par in step with theta without a launch.
+struct ParScatter {
+    ParOff po;
+    int T, NN, ND, NDP, nR, kR, nA, kA, NRP, KRP, NAP, KAP;
+    const int *map;  // [ND] compact -> padded descriptor index
+    float *par;
+};
+
+__device__ inline void scatter_param(const ParScatter &s, int64_t k, float v) {
+    const int T = s.T, NN = s.NN, ND = s.ND;
+    const int64_t cb0 = (int64_t)T * NN * ND, cw1 = cb0 + (int64_t)T * NN, cb1 = cw1 + (int64_t)T * NN;
+    const int64_t ccR = cb1 + 1, ccA = ccR + (int64_t)T * T * s.nR * s.kR;
+    if (k < cb0) {
+        const int64_t tm = k / ND;  // t * NN + mu
+        const int vp = s.map[(int)(k - tm * ND)];
+        const int t = (int)(tm / NN), mu = (int)(tm - (int64_t)t * NN);
+        s.par[s.po.w0 + tm * s.NDP + vp] = v;
+        s.par[s.po.w0t + ((int64_t)t * s.NDP + vp) * NN + mu] = v;
+    } else if (k < cw1) {
+        s.par[s.po.b0 + (k - cb0)] = v;
+    } else if (k < cb1) {
+        s.par[s.po.w1 + (k - cw1)] = v;
+    } else if (k == cb1) {
+        s.par[s.po.b1] = v;
+    } else if (k < ccA) {
+        const int64_t r = k - ccR;
+        const int kk = (int)(r % s.kR), n = (int)((r / s.kR) % s.nR);
+        const int64_t ab = r / ((int64_t)s.kR * s.nR);
+        s.par[s.po.cR + (ab * s.NRP + n) * s.KRP + kk] = v;
+        s.par[s.po.cRp + (ab * s.NRP + n) * round4(s.KRP) + kk] = v;
+    } else {
+        const int64_t r = k - ccA;
+        const int kk = (int)(r % s.kA), n = (int)((r / s.kA) % s.nA);
+        const int64_t ab = r / ((int64_t)s.kA * s.nA);
+        s.par[s.po.cA + (ab * s.NAP + n) * s.KAP + kk] = v;
+        s.par[s.po.cAp + (ab * s.NAP + n) * round4(s.KAP) + kk] = v;
+    }
+}
+
+// One AMSGrad step (the update rule of the optimiser file) inside another kernel.
+struct OptArgs {
+    float *theta;
+    double *m, *v, *vmax, *st;
+    double b1, b2, eps;
+    const double *loss3;  // the step's loss terms for the epoch mean (or loss1, or neither)
+    double lE, lF, lV;
+    const double *loss1;
+    ParScatter ps;
+};
+
+// State of this step as every element sees it (the tick is written once, afterwards).
+struct OptStep {
+    double bc1, bc2, lr;
+};
+__device__ inline OptStep opt_step_state(const OptArgs &o) {
+    OptStep s;
+    s.bc1 = 1.0 - o.st[OPT_B1T] * o.b1;
+    s.bc2 = 1.0 - o.st[OPT_B2T] * o.b2;
+    s.lr = o.st[OPT_LR];
+    return s;
+}
+__device__ inline void amsgrad_elem(const OptArgs &o, const OptStep &s, int64_t i, double gi) {
+    const double mi = __dadd_rn(__dmul_rn(o.b1, o.m[i]), __dmul_rn(1.0 - o.b1, gi));
+    const double vi = __dadd_rn(__dmul_rn(o.b2, o.v[i]), __dmul_rn(__dmul_rn(1.0 - o.b2, gi), gi));
+    o.m[i] = mi;
+    o.v[i] = vi;
+    const double vh = vi / s.bc2;
+    const double vm = o.vmax[i] > vh ? o.vmax[i] : vh;
+    o.vmax[i] = vm;
+    const double step = __dmul_rn(s.lr, mi / s.bc1) / __dadd_rn(sqrt(vm), o.eps);
+    const float th = (float)__dadd_rn((double)o.theta[i], -step);
+    o.theta[i] = th;
+    scatter_param(o.ps, i, th);
+}
+// Step counter, beta powers and the epoch loss sum: one thread, after every element's update.
+__device__ inline void opt_tick(const OptArgs &o) {
+    o.st[OPT_T] += 1.0;
+    o.st[OPT_B1T] *= o.b1;
+    o.st[OPT_B2T] *= o.b2;
+    if (o.loss3) {
+        o.st[OPT_ACC] += o.lE * o.loss3[0] + o.lF * o.loss3[1] + o.lV * o.loss3[2];
+        o.st[OPT_NACC] += 1.0;
+    } else if (o.loss1) {
+        o.st[OPT_ACC] += o.loss1[0];
+        o.st[OPT_NACC] += 1.0;
+    }
+}
+
+// Last-block arrival: every thread of the block calls it, wrote = this thread stored data
+// that the last block will read; true in the block that arrived last (it reads the other
+// blocks' data through L2, __ldcg).
+__device__ inline bool last_block_arrival(unsigned *counter, unsigned nblocks, bool wrote) {
+    __shared__ unsigned s_last;
+    if (wrote) __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const bool last = atomicAdd(counter, 1u) == nblocks - 1u;
+        if (last) *counter = 0u;  // every other block has arrived: ready for the next launch
+        s_last = last ? 1u : 0u;
+    }
+    __syncthreads();
+    return s_last != 0u;
+}
+
+// Unevaluated pair sums in FP32 (hi + lo): the FP32 pipes run 64x the FP64 rate on this
+// part, and a compensated sum of FP32 terms keeps the error of an FP64 sum (Knuth's
+// TwoSum: the rounding error of each addition is carried in lo).  Fixed order, so
+// deterministic like the FP64 reductions they replace.
+__device__ __forceinline__ void f2_add(float &hi, float &lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+__device__ __forceinline__ void f2_merge(float &hi, float &lo, float h2, float l2) {
+    f2_add(hi, lo, h2);
+    lo += l2;
+}
+
+OptArgs opt_args(Ctx *c, const double *loss3, double lE, double lF, double lV, const double *loss1);
+ParScatter par_scatter(Ctx *c);
 int launch_opt_reset(Ctx *c);
 int launch_opt_set_lr(Ctx *c, double lr);
 int launch_opt_step(Ctx *c, const float *grad, const double *loss3, double lE, double lF, double lV,
@@ -268,7 +421,10 @@ int build_minibatches(Ctx *c, int batch_size);
 int minibatch_shape_check(Ctx *c);  // rebuilds the schedules if the launch shape changed
 int minibatch_tune(Ctx *c);         // picks the kernel variants of the group steps by timing
 void drop_minibatch_graphs(Ctx *c);
-int run_minibatch_loss(Ctx *c, int64_t m, double lE, double lF, double lV, double *loss3, float *grad);
+void drop_graphs(Ctx *c);  // every cached graph (whole-batch and mini-batch)
+// opt: training step (optimiser update fused into the gradient reduction)
+int run_minibatch_loss(Ctx *c, int64_t m, double lE, double lF, double lV, double *loss3, float *grad,
+                       bool opt = false);
 int prepare_loss_kernels(Ctx *c);
 
 }  // namespace nep

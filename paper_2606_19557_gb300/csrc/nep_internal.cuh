@@ -116,6 +116,32 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// Programmatic dependent launch.  Every kernel of the step calls grid_dep_wait() before
+// its first global-memory access: it returns once the kernel launched before it in the
+// stream has completed and its writes are visible (at once when launched without the
+// attribute).  grid_dep_launch() lets the next kernel's blocks be scheduled early; they
+// wait in grid_dep_wait(), so only launch latency overlaps, never memory traffic.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch of a kernel that starts with grid_dep_wait(); pdl allows it to be scheduled while
+// the previous kernel of the stream drains (also inside a captured graph).
+template <typename... P, typename... A>
+inline cudaError_t launch_k(bool pdl, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<A &&>(args)...);
+}
+
 // Transposing warp reduction of V values per lane (V a power of two).  Recursive
 // halving: at each step a lane keeps one half of its values and adds the half
 // its partner kept.  After min(log2 V, 5) steps lane l holds V/32 fully reduced

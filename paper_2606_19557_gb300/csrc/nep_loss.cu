@@ -24,6 +24,8 @@ struct ExpandArgs {
 };
 
 __global__ void k_expand(ExpandArgs x) {
+    grid_dep_wait();
+    grid_dep_launch();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const ParOff &po = x.po;
     if (e >= po.total) return;
@@ -84,30 +86,54 @@ __global__ void k_expand(ExpandArgs x) {
     x.par[e] = v;
 }
 
-// --------------------------------------------------------------------------- forces
+// --------------------------------------------------------------------------- loss terms
+struct TermsArgs {
+    int64_t a0, a1, s0, s1;
+    int nG;  // the first nG blocks gather forces, the next s1 - s0 sum one structure each
+    const int64_t *nbr_off;
+    const int *rev;
+    const float4 *G;
+    const float *F_own;
+    float *F_out;
+    const int64_t *atom_off;
+    const float *E_atom, *W_atom;
+    double *E_out, *W_out;
+    int loss;
+    const float *F_ref;
+    float coefF;
+    float *fbar;
+    const double *E_ref, *W_ref;
+    const uint8_t *has_W;
+    const int *n_sv;  // device count of N_s^V when nsv <= 0
+    double nsv, lamE, lamV, Ns, Na;
+    float *ebar, *wbar;
+    double *fpart, *spart;  // [nG] force partials; [3 (s1 - s0)] structure partials
+    double *loss3, *gb1;    // loss3: the last block reduces the partials
+    unsigned *counter;
+};
+
 // F_i = sum_{p in N(i)} G_p - sum_{p in N(i)} G_{rev(p)}: the second sum visits the pairs
-// (j, i, -S) of which i is the neighbour, through the reverse index (no atomics).
-__global__ void k_gather(int64_t a0, int64_t a1, const int64_t *nbr_off, const int *rev, const float4 *G,
-                         const float *F_own, float *F_out, const float *F_ref, float coefF, int loss, float *fbar,
-                         double *part) {
-    __shared__ double wpart[32];
+// (j, i, -S) of which i is the neighbour, through the reverse index (no atomics).  Warps
+// stride over the atoms; the block's squared force residuals go to fpart[block].
+__device__ void gather_block(const TermsArgs &x, int blk) {
+    __shared__ float2 wpart[32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * nw + wib, W = (int64_t)gridDim.x * nw;
-    double acc = 0.0;
-    for (int64_t i = a0 + gw; i < a1; i += W) {
-        const int64_t beg = nbr_off[i], end = nbr_off[i + 1];
+    const int64_t gw = (int64_t)blk * nw + wib, W = (int64_t)x.nG * nw;
+    float ah = 0.0f, al = 0.0f;  // sum of d^2: each square exact as p + e (FMA), then TwoSum
+    for (int64_t i = x.a0 + gw; i < x.a1; i += W) {
+        const int64_t beg = x.nbr_off[i], end = x.nbr_off[i + 1];
         float sx = 0.0f, sy = 0.0f, sz = 0.0f;
         for (int64_t p0 = beg; p0 < end; p0 += 128) {  // 4 index loads, then 4 gathers, in flight
             int r[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int64_t p = p0 + lane + 32 * k;
-                r[k] = p < end ? rev[p] : -1;
+                r[k] = p < end ? x.rev[p] : -1;
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (r[k] >= 0) {
-                    const float4 g = G[r[k]];
+                    const float4 g = x.G[r[k]];
                     sx += g.x;
                     sy += g.y;
                     sz += g.z;
@@ -118,93 +144,144 @@ __global__ void k_gather(int64_t a0, int64_t a1, const int64_t *nbr_off, const i
         sy = warp_sum(sy);
         sz = warp_sum(sz);
         if (lane < 3) {
-            const float own = F_own[i * 3 + lane];
+            const float own = x.F_own[i * 3 + lane];
             const float F = own - (lane == 0 ? sx : lane == 1 ? sy : sz);
-            F_out[i * 3 + lane] = F;
-            if (loss) {
-                const float d = F - F_ref[i * 3 + lane];
-                fbar[i * 4 + lane] = coefF * d;  // float4 rows (x, y, z, unused)
-                acc += (double)d * (double)d;
+            x.F_out[i * 3 + lane] = F;
+            if (x.loss) {
+                const float d = F - x.F_ref[i * 3 + lane];
+                x.fbar[i * 4 + lane] = x.coefF * d;  // float4 rows (x, y, z, unused)
+                const float p = d * d;
+                f2_add(ah, al, p);
+                al += fmaf(d, d, -p);
             }
         }
     }
-    if (loss) {
-        acc += __shfl_down_sync(FULL, acc, 1);
-        acc += __shfl_down_sync(FULL, acc, 2);  // lanes 0..2 hold the sums; lane 0 gets 0+1+2(+3=0)
-        if (lane == 0) wpart[wib] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int k = 0; k < nw; ++k) s += wpart[k];
-            part[blockIdx.x] = s;
-        }
+    if (!x.loss) return;
+    // lanes 0..2 hold the sums (the others zero): lane 0 takes 1 and 2 in a fixed order
+    f2_merge(ah, al, __shfl_down_sync(FULL, ah, 1), __shfl_down_sync(FULL, al, 1));
+    f2_merge(ah, al, __shfl_down_sync(FULL, ah, 2), __shfl_down_sync(FULL, al, 2));
+    if (lane == 0) wpart[wib] = make_float2(ah, al);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float h = 0.0f, l = 0.0f;
+        for (int k = 0; k < nw; ++k) f2_merge(h, l, wpart[k].x, wpart[k].y);
+        x.fpart[blk] = (double)h + (double)l;
     }
 }
 
-// --------------------------------------------------------------------------- structures
-// E_s = sum_i E_i and W_s = sum_i W_i in FP64 (Eq. 1); loss terms and cotangents of Eq. "loss".
-// One block per structure: its threads stride over the structure's atoms, then a fixed-order
-// reduction (lanes, then warps in order), so a 10,000-atom cell is summed by 256 threads.
-// The block size (~4 atoms per thread, from the launch's mean structure size) fixes the
-// summation order.  part[3 * (s - s0) + q]: the structure's loss terms.
-__global__ void k_struct(int64_t s0, int64_t s1, const int64_t *atom_off, const float *E_atom, const float *W_atom,
-                         double *E_out, double *W_out, int loss, const double *E_ref, const double *W_ref,
-                         const uint8_t *has_W, const int *n_sv, double nsv_over, double lamE, double lamV, double Ns,
-                         float *ebar, float *wbar, double *part /*[s1 - s0][3]*/) {
-    __shared__ double red[32][10];
+// E_s = sum_i E_i and W_s = sum_i W_i (Eq. 1) as compensated FP32 pair sums, returned in
+// FP64; loss terms and cotangents of Eq. "loss".  The block's threads stride over the
+// structure's atoms, then a fixed-order reduction (lanes, then warps in order), so a
+// 10,000-atom cell is summed by all 256 threads.  Lanes k = 0..9 of warp 0 finish one
+// quantity each (0: E, 1..9: W).  spart[3 (s - s0) + q]: the structure's loss terms.
+__device__ void struct_block(const TermsArgs &x, int64_t s) {
+    __shared__ float2 red[10][33];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t s = s0 + blockIdx.x;
-    if (s >= s1) return;
-    const int64_t b = atom_off[s], e = atom_off[s + 1];
-    double v[10];
+    const int64_t b = x.atom_off[s], e = x.atom_off[s + 1];
+    float h[10], l[10];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) v[k] = 0.0;
+    for (int k = 0; k < 10; ++k) h[k] = l[k] = 0.0f;
     for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-        v[0] += (double)E_atom[i];
+        f2_add(h[0], l[0], x.E_atom[i]);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) v[1 + k] += (double)W_atom[i * 9 + k];
+        for (int k = 0; k < 9; ++k) f2_add(h[1 + k], l[1 + k], x.W_atom[i * 9 + k]);
     }
 #pragma unroll
-    for (int k = 0; k < 10; ++k) v[k] = warp_sum_d(v[k]);
-    if (lane == 0)
-        for (int k = 0; k < 10; ++k) red[wib][k] = v[k];
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+            f2_merge(h[k], l[k], __shfl_xor_sync(FULL, h[k], o), __shfl_xor_sync(FULL, l[k], o));
+    if (lane < 10) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+            if (k == lane) red[k][wib] = make_float2(h[k], l[k]);
+    }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double E = 0.0, Wv[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int w = 0; w < nw; ++w) {
-        E += red[w][0];
-        for (int k = 0; k < 9; ++k) Wv[k] += red[w][1 + k];
+    if (wib != 0) return;
+    double v = 0.0;  // lane k: the finished quantity k
+    if (lane < 10) {
+        float hh = 0.0f, ll = 0.0f;
+        for (int w = 0; w < nw; ++w) f2_merge(hh, ll, red[lane][w].x, red[lane][w].y);
+        v = (double)hh + (double)ll;
+        if (lane == 0) x.E_out[s] = v;
+        else x.W_out[s * 9 + lane - 1] = v;
     }
-    E_out[s] = E;
-    for (int k = 0; k < 9; ++k) W_out[s * 9 + k] = Wv[k];
-    if (!loss) return;
-    // FP64 division is slow on this part: one reciprocal per structure, coefficients once
-    const double NsV = nsv_over > 0.0 ? nsv_over : (double)(*n_sv);
+    if (!x.loss) return;
+    // FP64 division is slow on this part: one reciprocal per lane, coefficients once
+    const double NsV = x.nsv > 0.0 ? x.nsv : (double)(*x.n_sv);
     const double na = (double)(e - b);
     const double inv_na = 1.0 / na, inv_na2 = inv_na * inv_na;
-    const double dE = E - E_ref[s];
-    const double aE = (dE * inv_na) * (dE * inv_na);
-    const double eb = (lamE * 2.0 / Ns) * dE * inv_na2;
-    ebar[s] = (float)eb;
-    const double ab1 = -na * eb;
+    const bool hw = x.has_W == nullptr || x.has_W[s] != 0;
     double aV = 0.0;
-    const bool hw = has_W == nullptr || has_W[s] != 0;
-    const double cV = NsV > 0.0 ? lamV * 2.0 / (9.0 * NsV) : 0.0;
-    for (int k = 0; k < 9; ++k) {
+    if (lane >= 1 && lane < 10) {
         double wb = 0.0;
         if (hw && NsV > 0.0) {
-            const double dW = Wv[k] - W_ref[s * 9 + k];
-            aV += (dW * inv_na) * (dW * inv_na);
-            wb = cV * dW * inv_na2;
+            const double dW = v - x.W_ref[s * 9 + lane - 1];
+            aV = (dW * inv_na) * (dW * inv_na);
+            wb = (x.lamV * 2.0 / (9.0 * NsV)) * dW * inv_na2;
         }
-        wbar[s * 9 + k] = (float)wb;
+        x.wbar[s * 9 + lane - 1] = (float)wb;
     }
-    part[3 * (s - s0) + 0] = aE;
-    part[3 * (s - s0) + 1] = aV;
-    part[3 * (s - s0) + 2] = ab1;
+    // lanes 1..9 in order onto lane 0 (fixed order)
+    double tV = 0.0;
+    for (int k = 1; k < 10; ++k) tV += __shfl_sync(FULL, aV, k);
+    if (lane == 0) {
+        const double dE = v - x.E_ref[s];
+        const double eb = (x.lamE * 2.0 / x.Ns) * dE * inv_na2;
+        x.ebar[s] = (float)eb;
+        x.spart[3 * (s - x.s0) + 0] = (dE * inv_na) * (dE * inv_na);
+        x.spart[3 * (s - x.s0) + 1] = tV;
+        x.spart[3 * (s - x.s0) + 2] = -na * eb;
+    }
+}
+
+// The loss terms DeltaE, DeltaF, DeltaV of Eq. "loss" and dL/db1 from the partials, in a
+// fixed order (strided thread sums, lanes, then warps in order).  Partials written by
+// other blocks of the same launch are read through L2.
+__device__ void loss_reduce(const double *fpart, int nf, const double *spart, int nsb, double nsv, double Ns,
+                            double Na, double *loss3, double *gb1) {
+    __shared__ double sh[32][4];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nsb; k += blockDim.x) {
+        a[0] += __ldcg(spart + 3 * k);
+        a[2] += __ldcg(spart + 3 * k + 1);
+        a[3] += __ldcg(spart + 3 * k + 2);
+    }
+    for (int k = threadIdx.x; k < nf; k += blockDim.x) a[1] += __ldcg(fpart + k);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q] = warp_sum_d(a[q]);
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) sh[wib][q] = a[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < nw; ++w)
+            for (int q = 0; q < 4; ++q) t[q] += sh[w][q];
+        loss3[0] = Ns > 0 ? t[0] / Ns : 0.0;
+        loss3[1] = Na > 0 ? t[1] / (3.0 * Na) : 0.0;
+        loss3[2] = nsv > 0 ? t[2] / (9.0 * nsv) : 0.0;
+        *gb1 = t[3];
+    }
+}
+
+// Force gather, structure sums and (with loss3) the loss reduction in one launch of
+// 256-thread blocks: the reduction runs in the block that finishes last.
+__global__ void __launch_bounds__(256) k_loss_terms(TermsArgs x) {
+    grid_dep_wait();
+    grid_dep_launch();
+    const int blk = blockIdx.x;
+    if (blk < x.nG) gather_block(x, blk);
+    else struct_block(x, x.s0 + (blk - x.nG));
+    if (!x.loss || !x.loss3) return;
+    if (!last_block_arrival(x.counter, gridDim.x, threadIdx.x == 0)) return;
+    const double nsv = x.nsv > 0.0 ? x.nsv : (double)__ldcg(x.n_sv);
+    loss_reduce(x.fpart, x.nG, x.spart, (int)(x.s1 - x.s0), nsv, x.Ns, x.Na, x.loss3, x.gb1);
 }
 
 __global__ void k_count_hasw(int64_t ns, const uint8_t *has_W, int *n_sv) {
+    grid_dep_wait();
+    grid_dep_launch();
     __shared__ int sh[256];
     int c = 0;
     for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) c += (has_W == nullptr || has_W[s]) ? 1 : 0;
@@ -217,30 +294,11 @@ __global__ void k_count_hasw(int64_t ns, const uint8_t *has_W, int *n_sv) {
     }
 }
 
+// Loss reduction over partials left by several launches (plain form).
 __global__ void k_loss_final(const double *fpart, int nf, const double *spart, int nsb, const int *n_sv,
-                             double nsv_over, double Ns, double Na, double *loss3, double *gb1) {
-    __shared__ double sh[4][256];
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int k = threadIdx.x; k < nsb; k += blockDim.x) {
-        a[0] += spart[3 * k];
-        a[2] += spart[3 * k + 1];
-        a[3] += spart[3 * k + 2];
-    }
-    for (int k = threadIdx.x; k < nf; k += blockDim.x) a[1] += fpart[k];
-    for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = a[q];
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double nsv = nsv_over > 0.0 ? nsv_over : (double)(*n_sv);
-        loss3[0] = Ns > 0 ? sh[0][0] / Ns : 0.0;
-        loss3[1] = Na > 0 ? sh[1][0] / (3.0 * Na) : 0.0;
-        loss3[2] = nsv > 0 ? sh[2][0] / (9.0 * nsv) : 0.0;
-        *gb1 = sh[3][0];
-    }
+                             double nsv, double Ns, double Na, double *loss3, double *gb1) {
+    const double v = nsv > 0.0 ? nsv : (double)(*n_sv);
+    loss_reduce(fpart, nf, spart, nsb, v, Ns, Na, loss3, gb1);
 }
 
 // dL/dF rows into the float4 layout the adjoint gathers.
@@ -322,6 +380,8 @@ __device__ __forceinline__ void ann_stage(const AnnTile &t, int rr, int nr, int 
 
 __global__ void k_ann_grad(const int *chunk_begin, int NN, int NDP, const float *zt, const float *ut,
                            const float *om, const float *qt, const float *dqt, float *part) {
+    grid_dep_wait();
+    grid_dep_launch();
     extern __shared__ __align__(16) float sm[];
     const int NNP = (NN + 3) & ~3, NDQ = (NDP + 3) & ~3;
     const int tile_floats = ANN_ROWS * (3 * NNP + 2 * NDQ);
@@ -399,15 +459,20 @@ struct GradArgs {
     const double *gb1;
     float *grad;
     double *acc;           // plain form: add the partial sums here (FP64), b1 left out
+    unsigned *counters;    // [0] all columns done, [1 + x] segments of column x done
+    int opt;               // training: AMSGrad step on each parameter once its gradient is final
+    OptArgs o;
 };
 
-// Two passes.  k_grad_part: one block per (32 consecutive parameters, row segment), with
-// GF_RG row groups (threadIdx.y); the threads of a warp read 32 neighbouring parameters of
-// one partial row (coalesced), each thread keeps four FP64 chains, the row groups are added
-// in a fixed order and each segment's sum goes to gpart[seg][k].  k_grad_sum adds the
-// GF_SEG segments of each parameter in order.  Spreading the rows over segments keeps
-// every SM busy with the FP64 additions.
-constexpr int GF_RG = 32;
+// One launch, one block per (32 consecutive parameters = a column, row segment), with
+// GF_RG row groups (threadIdx.y): the threads of a warp read 32 neighbouring parameters of
+// one partial row (coalesced), each thread keeps two compensated FP32 pair sums, the row
+// groups are merged pairwise in a fixed order and each segment's sum goes to gpart[seg][k].
+// The last of a column's GF_SEG blocks to finish merges the segments in order (the final
+// gradient), and in training applies the optimiser step to those parameters; the last
+// column then advances the optimiser state.  Spreading the rows over segments keeps every
+// SM busy.
+constexpr int GF_RG = 16;
 constexpr int GF_SEG = 8;
 
 struct GradSource {  // where parameter k's partials live
@@ -469,48 +534,79 @@ __device__ __forceinline__ GradSource grad_source(const GradArgs &g, int64_t k) 
     return r;
 }
 
-__global__ void k_grad_part(GradArgs g, double *gpart /*[GF_SEG][P]*/) {
-    __shared__ double red[GF_RG][33];
+__global__ void __launch_bounds__(32 * GF_RG) k_grad_reduce(GradArgs g, float2 *gpart /*[GF_SEG][P]*/) {
+    grid_dep_wait();
+    grid_dep_launch();
+    __shared__ float2 red[GF_RG][33];
     const int tx = threadIdx.x, ty = threadIdx.y, seg = blockIdx.y;
     const int64_t k = (int64_t)blockIdx.x * 32 + tx;
     const int T = g.T, NC = g.NRP * g.KRP + g.NAP * g.KAP;
     const int annstride = g.NN * g.NDP + 2 * g.NN;
-    double s = 0.0;
+    float h = 0.0f, l = 0.0f;
+    GradSource r{};
     if (k < g.P) {
-        const GradSource r = grad_source(g, k);
+        r = grad_source(g, k);
         if (!r.b1) {
             const int len = (r.hi - r.lo + GF_SEG - 1) / GF_SEG;
             const int lo = r.lo + seg * len, hi = min(r.hi, lo + len);
-            double s4[4] = {0.0, 0.0, 0.0, 0.0};  // four independent chains keep four loads in flight
-            int q = 0;
+            // two compensated chains keep two loads in flight, merged in a fixed order
+            float h2 = 0.0f, l2 = 0.0f;
             if (r.net) {
-                for (int c = lo + ty; c < hi; c += GF_RG, q = (q + 1) & 3)
-                    s4[q] += (double)g.annpart[(size_t)c * annstride + r.off];
+                int c = lo + ty;
+                for (; c + GF_RG < hi; c += 2 * GF_RG) {
+                    f2_add(h, l, g.annpart[(size_t)c * annstride + r.off]);
+                    f2_add(h2, l2, g.annpart[(size_t)(c + GF_RG) * annstride + r.off]);
+                }
+                if (c < hi) f2_add(h, l, g.annpart[(size_t)c * annstride + r.off]);
             } else {
-                for (int w = lo + ty; w < hi; w += GF_RG, q = (q + 1) & 3)
+                int w = lo + ty;
+                for (; w + GF_RG < hi; w += 2 * GF_RG) {
                     if (g.warp_begin[w] < g.warp_begin[w + 1])
-                        s4[q] += (double)g.cpart[((size_t)(w + r.a) * T + r.b) * NC + r.off];
+                        f2_add(h, l, g.cpart[((size_t)(w + r.a) * T + r.b) * NC + r.off]);
+                    const int w2 = w + GF_RG;
+                    if (g.warp_begin[w2] < g.warp_begin[w2 + 1])
+                        f2_add(h2, l2, g.cpart[((size_t)(w2 + r.a) * T + r.b) * NC + r.off]);
+                }
+                if (w < hi && g.warp_begin[w] < g.warp_begin[w + 1])
+                    f2_add(h, l, g.cpart[((size_t)(w + r.a) * T + r.b) * NC + r.off]);
             }
-            s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+            f2_merge(h, l, h2, l2);
         }
     }
-    red[ty][tx] = s;
+    red[ty][tx] = make_float2(h, l);
     __syncthreads();
-    if (ty != 0 || k >= g.P) return;
-    double tot = 0.0;
-    for (int rr = 0; rr < GF_RG; ++rr) tot += red[rr][tx];
-    gpart[(size_t)seg * g.P + k] = tot;
-}
-
-__global__ void k_grad_sum(GradArgs g, const double *gpart) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.P) return;
-    const GradSource r = grad_source(g, k);
-    double tot = 0.0;
-    for (int seg = 0; seg < GF_SEG; ++seg) tot += gpart[(size_t)seg * g.P + k];
-    if (r.b1) tot = g.acc ? 0.0 : *g.gb1;
-    if (g.acc) g.acc[k] += r.sign * tot;
-    else g.grad[k] = (float)(r.sign * tot);
+#pragma unroll
+    for (int o = GF_RG / 2; o > 0; o >>= 1) {  // row groups pairwise, fixed pairing
+        if (ty < o) {
+            float2 a = red[ty][tx];
+            const float2 b = red[ty + o][tx];
+            f2_merge(a.x, a.y, b.x, b.y);
+            red[ty][tx] = a;
+        }
+        __syncthreads();
+    }
+    const bool writer = ty == 0 && k < g.P;
+    if (writer) gpart[(size_t)seg * g.P + k] = red[0][tx];
+    if (!last_block_arrival(g.counters + 1 + blockIdx.x, GF_SEG, writer)) return;
+    OptStep os{};
+    if (g.opt) os = opt_step_state(g.o);
+    if (writer) {
+        float th = 0.0f, tl = 0.0f;
+        for (int sg = 0; sg < GF_SEG; ++sg) {
+            const float2 v = __ldcg(gpart + (size_t)sg * g.P + k);
+            f2_merge(th, tl, v.x, v.y);
+        }
+        if (g.acc) {
+            if (!r.b1) g.acc[k] += r.sign * ((double)th + (double)tl);
+        } else {
+            const float gk = r.b1 ? (float)*g.gb1 : (float)r.sign * (th + tl);
+            g.grad[k] = gk;
+            if (g.opt) amsgrad_elem(g.o, os, k, (double)gk);
+        }
+    }
+    if (!g.opt) return;
+    if (!last_block_arrival(g.counters, gridDim.x, false)) return;
+    if (tx == 0 && ty == 0) opt_tick(g.o);
 }
 
 // Plain form: gradient = FP64 accumulator, b1 from the loss reduction.
@@ -621,8 +717,7 @@ int launch_expand(Ctx *c) {
     x.KAP = c->ks->KA;
     x.inv = c->d_desc_inv.as<int>();
     const int64_t n = c->po.total;
-    k_expand<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x);
-    CK_LAUNCH("k_expand");
+    CK(launch_k(c->pdl(), k_expand, (unsigned)((n + 255) / 256), 256, 0, c->stream, x));
     return NEP_OK;
 }
 
@@ -631,7 +726,7 @@ int launch_forward(Ctx *c, float *q_raw, int stage) {
     AtomArgs a = atom_args(c);
     a.warp_begin = c->fwd.warp_begin.as<int>();
     a.q_raw = q_raw;
-    c->ks->launch_fwd[c->fwd.var](a, c->fwd.blocks, c->fwd.wpb, stage, c->stream);
+    c->ks->launch_fwd[c->fwd.var](a, c->fwd.blocks, c->fwd.wpb, stage, c->stream, c->pdl());
     CK_LAUNCH("forward stages");
     return NEP_OK;
 }
@@ -640,7 +735,7 @@ int launch_adjoint(Ctx *c, int stage) {
     if (c->n_atoms == 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.warp_begin = c->adj.warp_begin.as<int>();
-    c->ks->launch_adj[c->adj.var](a, c->adj.blocks, c->adj.wpb, stage, c->stream);
+    c->ks->launch_adj[c->adj.var](a, c->adj.blocks, c->adj.wpb, stage, c->stream, c->pdl());
     CK_LAUNCH("adjoint stages");
     return NEP_OK;
 }
@@ -653,7 +748,7 @@ int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blo
     a.warp_begin = warp_begin;
     a.chunks = chunks;
     a.n_chunks = n_chunks;
-    c->ks->launch_fwd[var](a, blocks, wpb, -1, c->stream);
+    c->ks->launch_fwd[var](a, blocks, wpb, -1, c->stream, c->pdl());
     CK_LAUNCH("forward stages");
     return NEP_OK;
 }
@@ -666,7 +761,7 @@ int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blo
     a.warp_begin = warp_begin;
     a.chunks = chunks;
     a.n_chunks = n_chunks;
-    c->ks->launch_adj[var](a, blocks, wpb, -1, c->stream);
+    c->ks->launch_adj[var](a, blocks, wpb, -1, c->stream, c->pdl());
     CK_LAUNCH("adjoint stages");
     return NEP_OK;
 }
@@ -674,56 +769,72 @@ int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blo
 static int gather_blocks(Ctx *c) { return c->n_sm * 4; }
 
 
-int launch_gather(Ctx *c, float *F_out, const float *F_ref, double lamF, bool loss, int64_t a0, int64_t a1,
-                  double *part, int nblocks) {
-    if (a1 <= a0) return NEP_OK;
-    const int nb = nblocks > 0 ? nblocks : gather_blocks(c);
-    const float coef = (float)(lamF * 2.0 / (3.0 * c->norm_Na()));
-    k_gather<<<nb, 256, 0, c->stream>>>(a0, a1, c->nbr_off.as<int64_t>(), c->rev.as<int>(), (const float4 *)c->G.ptr,
-                                        c->F_own.as<float>(), F_out, F_ref, coef, loss ? 1 : 0, c->fbar.as<float>(),
-                                        part ? part : c->loss_part.as<double>());
-    CK_LAUNCH("k_gather");
-    return NEP_OK;
+double host_nsv(Ctx *c, const uint8_t *has_W, int64_t s0, int64_t s1) {
+    int64_t n;
+    if (!has_W) n = s1 - s0;
+    else if (has_W == c->tgt_hw.as<uint8_t>() && c->tgt_has_hw && (int64_t)c->tgt_nsv_pre.size() > s1)
+        n = c->tgt_nsv_pre[s1] - c->tgt_nsv_pre[s0];
+    else return 0.0;
+    return n > 0 ? (double)n : 1.0;
 }
 
 int launch_count_hasw(Ctx *c, const uint8_t *has_W, int64_t s0, int64_t s1) {
-    if (s1 < 0) s1 = c->n_struct;
-    k_count_hasw<<<1, 256, 0, c->stream>>>(s1 - s0, has_W ? has_W + s0 : nullptr, c->n_sv.as<int>());
-    CK_LAUNCH("k_count_hasw");
+    CK(launch_k(c->pdl(), k_count_hasw, 1, 256, 0, c->stream, s1 - s0, has_W ? has_W + s0 : nullptr,
+                c->n_sv.as<int>()));
     return NEP_OK;
 }
 
-static int64_t pow2ceil_host(int64_t n) {
-    int64_t p = 1;
-    while (p < n) p <<= 1;
-    return p;
-}
-
-int launch_struct(Ctx *c, double *E_out, double *W_out, const double *E_ref, const double *W_ref,
-                  const uint8_t *has_W, double lamE, double lamV, bool loss, int64_t s0, int64_t s1, double *part,
-                  int nblocks) {
-    if (s1 <= s0) return NEP_OK;
-    (void)nblocks;  // one block per structure, ~4 atoms per thread (32 to 256 threads)
-    c->struct_parts = s1 - s0;
-    const int64_t mean = (c->h_atom_off[s1] - c->h_atom_off[s0]) / (s1 - s0);
-    const int threads = (int)std::min<int64_t>(256, std::max<int64_t>(32, pow2ceil_host(mean / 4)));
-    k_struct<<<(unsigned)(s1 - s0), threads, 0, c->stream>>>(s0, s1, c->atom_off.as<int64_t>(), c->E_atom.as<float>(),
-                                        c->W_atom.as<float>(), E_out, W_out, loss ? 1 : 0, E_ref, W_ref, has_W,
-                                        c->n_sv.as<int>(), c->ov_NsV, lamE, lamV, c->norm_Ns(), c->ebar.as<float>(),
-                                        c->wbar.as<float>(), part ? part : c->loss_part.as<double>() + gather_blocks(c));
-    CK_LAUNCH("k_struct");
-    return NEP_OK;
-}
-
-int launch_loss_final(Ctx *c, double *loss3, const double *fpart, int nf, const double *spart, int nsb) {
-    if (!fpart) {
-        fpart = c->loss_part.as<double>();
-        nf = c->n_atoms > 0 ? gather_blocks(c) : 0;
-        spart = c->loss_part.as<double>() + gather_blocks(c);
-        nsb = c->n_struct > 0 ? (int)c->struct_parts : 0;
+int launch_terms(Ctx *c, const TermsCall &t) {
+    const int64_t ns = t.s1 - t.s0;
+    const int nG = t.a1 > t.a0 ? (t.gather_blocks > 0 ? t.gather_blocks : gather_blocks(c)) : 0;
+    if (nG + ns == 0)  // nothing to sum: the loss terms and dL/db1 are zero
+        return t.loss && t.loss3 ? launch_loss_final(c, t.loss3, nullptr, 0, nullptr, 0, 1.0) : NEP_OK;
+    TermsArgs x{};
+    x.a0 = t.a0;
+    x.a1 = t.a1;
+    x.s0 = t.s0;
+    x.s1 = t.s1;
+    x.nG = nG;
+    x.nbr_off = c->nbr_off.as<int64_t>();
+    x.rev = c->rev.as<int>();
+    x.G = (const float4 *)c->G.ptr;
+    x.F_own = c->F_own.as<float>();
+    x.F_out = t.F_out;
+    x.atom_off = c->atom_off.as<int64_t>();
+    x.E_atom = c->E_atom.as<float>();
+    x.W_atom = c->W_atom.as<float>();
+    x.E_out = t.E_out;
+    x.W_out = t.W_out;
+    x.loss = t.loss ? 1 : 0;
+    x.F_ref = t.F_ref;
+    x.coefF = (float)(t.lF * 2.0 / (3.0 * c->norm_Na()));
+    x.fbar = c->fbar.as<float>();
+    x.E_ref = t.E_ref;
+    x.W_ref = t.W_ref;
+    x.has_W = t.has_W;
+    x.n_sv = c->n_sv.as<int>();
+    x.nsv = t.nsv;
+    x.lamE = t.lE;
+    x.lamV = t.lV;
+    x.Ns = c->norm_Ns();
+    x.Na = c->norm_Na();
+    x.ebar = c->ebar.as<float>();
+    x.wbar = c->wbar.as<float>();
+    x.fpart = t.fpart ? t.fpart : c->loss_part.as<double>();
+    x.spart = t.spart ? t.spart : x.fpart + nG;
+    x.loss3 = t.loss ? t.loss3 : nullptr;
+    x.gb1 = c->gb1.as<double>();
+    x.counter = c->counters.as<unsigned>();
+    if (t.loss && t.nsv == 0.0) {
+        if (int rc = launch_count_hasw(c, t.has_W, t.s0, t.s1)) return rc;
     }
-    k_loss_final<<<1, 256, 0, c->stream>>>(fpart, nf, spart, nsb, c->n_sv.as<int>(), c->ov_NsV, c->norm_Ns(),
-                                           c->norm_Na(), loss3, c->gb1.as<double>());
+    CK(launch_k(t.pdl && c->pdl(), k_loss_terms, (unsigned)(nG + ns), 256, 0, c->stream, x));
+    return NEP_OK;
+}
+
+int launch_loss_final(Ctx *c, double *loss3, const double *fpart, int nf, const double *spart, int nsb, double nsv) {
+    k_loss_final<<<1, 256, 0, c->stream>>>(fpart, nf, spart, nsb, c->n_sv.as<int>(), nsv, c->norm_Ns(), c->norm_Na(),
+                                           loss3, c->gb1.as<double>());
     CK_LAUNCH("k_loss_final");
     return NEP_OK;
 }
@@ -755,30 +866,19 @@ int prepare_loss_kernels(Ctx *c) {
     return NEP_OK;
 }
 
-int launch_ann_grad(Ctx *c) {
-    if (c->n_chunks == 0) return NEP_OK;
-    k_ann_grad<<<dim3(c->n_chunks, ann_groups(c)), ANN_TILES, ann_smem(c), c->stream>>>(c->chunk_begin.as<int>(), c->NN, c->NDP, c->zt.as<float>(),
-                                                      c->ut.as<float>(), c->om.as<float>(), c->st_qt.as<float>(),
-                                                      c->dqt.as<float>(), c->annpart.as<float>());
-    CK_LAUNCH("k_ann_grad");
-    return NEP_OK;
-}
-
 int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks) {
     if (n_chunks <= 0) return NEP_OK;
-    k_ann_grad<<<dim3(n_chunks, ann_groups(c)), ANN_TILES, ann_smem(c), c->stream>>>(
-        chunks, c->NN, c->NDP, c->zt.as<float>(), c->ut.as<float>(), c->om.as<float>(), c->st_qt.as<float>(),
-        c->dqt.as<float>(), c->annpart.as<float>());
-    CK_LAUNCH("k_ann_grad");
+    CK(launch_k(c->pdl(), k_ann_grad, dim3(n_chunks, ann_groups(c)), ANN_TILES, ann_smem(c), c->stream, chunks,
+                c->NN, c->NDP, c->zt.as<float>(), c->ut.as<float>(), c->om.as<float>(), c->st_qt.as<float>(),
+                c->dqt.as<float>(), c->annpart.as<float>()));
     return NEP_OK;
 }
 
-static int run_grad_final(Ctx *c, const GradArgs &g) {
-    double *gp = c->gpart.as<double>();
-    k_grad_part<<<dim3((unsigned)((c->P + 31) / 32), GF_SEG), dim3(32, GF_RG), 0, c->stream>>>(g, gp);
-    CK_LAUNCH("k_grad_part");
-    k_grad_sum<<<(unsigned)((c->P + 255) / 256), 256, 0, c->stream>>>(g, gp);
-    CK_LAUNCH("k_grad_sum");
+int launch_ann_grad(Ctx *c) { return launch_ann_grad_chunks(c, c->chunk_begin.as<int>(), c->n_chunks); }
+
+static int run_grad_final(Ctx *c, const GradArgs &g, bool pdl) {
+    CK(launch_k(pdl, k_grad_reduce, dim3((unsigned)((c->P + 31) / 32), GF_SEG), dim3(32, GF_RG), 0, c->stream, g,
+                c->gpart.as<float2>()));
     return NEP_OK;
 }
 
@@ -808,23 +908,33 @@ static GradArgs grad_args(Ctx *c, float *grad) {
     g.gb1 = c->gb1.as<double>();
     g.grad = grad;
     g.acc = nullptr;
+    g.counters = c->counters.as<unsigned>() + 2;
+    g.opt = 0;
     return g;
 }
 
 int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi, const int *wlo, const int *whi,
-                            const int *warp_begin) {
+                            const int *warp_begin, bool opt, const double *loss3, double lE, double lF, double lV) {
     GradArgs g = grad_args(c, grad);
     g.clo = clo;
     g.chi = chi;
     g.wlo = wlo;
     g.whi = whi;
     g.warp_begin = warp_begin;
-    return run_grad_final(c, g);
+    if (opt) {
+        g.opt = 1;
+        g.o = opt_args(c, loss3, lE, lF, lV, nullptr);
+    }
+    return run_grad_final(c, g, c->pdl());
 }
 
-int launch_grad_final(Ctx *c, float *grad) {
+int launch_grad_final(Ctx *c, float *grad, bool opt, const double *loss3, double lE, double lF, double lV) {
     GradArgs g = grad_args(c, grad);
-    return run_grad_final(c, g);
+    if (opt) {
+        g.opt = 1;
+        g.o = opt_args(c, loss3, lE, lF, lV, nullptr);
+    }
+    return run_grad_final(c, g, c->pdl());
 }
 
 // ----------------------------------------------------------------------------- plain form
@@ -892,7 +1002,11 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
     double *pg = c->p_part.as<double>();
     double *ps = pg + ns * GB;
     if ((rc = launch_expand(c))) return rc;
-    if ((rc = launch_count_hasw(c, hw))) return rc;
+    double nsv = c->ov_NsV > 0.0 ? c->ov_NsV : host_nsv(c, hw, 0, ns);
+    if (nsv == 0.0) {  // counted once over the whole batch
+        if ((rc = launch_count_hasw(c, hw, 0, ns))) return rc;
+        nsv = -1.0;
+    }
     CK(cudaMemsetAsync(c->p_acc.ptr, 0, sizeof(double) * c->P, c->stream));
     const int pv = 2;  // one warp per atom: lanes-per-atom 16, 128-register variant
     const size_t gsm = ann_smem(c);
@@ -905,13 +1019,31 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
         a.chunks = c->p_chunks.as<int>() + c->p_cofs[s];
         a.n_chunks = nch;
-        c->ks->launch_fwd[pv](a, (int)n, 1, -1, c->stream);
+        c->ks->launch_fwd[pv](a, (int)n, 1, -1, c->stream, false);
         CK_LAUNCH("forward stages (plain)");
-        if ((rc = launch_gather(c, c->F_int.as<float>(), Fr, lF, true, a0, a0 + n, pg + s * GB, GB))) return rc;
-        if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), Er, Wr, hw, lE, lV, true, s, s + 1,
-                                ps + s * 3, 1)))
-            return rc;
-        c->ks->launch_adj[pv](a, (int)n, 1, -1, c->stream);
+        TermsCall t;
+        t.a0 = a0;
+        t.a1 = a0 + n;
+        t.s0 = s;
+        t.s1 = s + 1;
+        t.F_out = c->F_int.as<float>();
+        t.E_out = c->E_int.as<double>();
+        t.W_out = c->W_int.as<double>();
+        t.loss = true;
+        t.F_ref = Fr;
+        t.E_ref = Er;
+        t.W_ref = Wr;
+        t.has_W = hw;
+        t.lE = lE;
+        t.lF = lF;
+        t.lV = lV;
+        t.nsv = nsv;
+        t.fpart = pg + s * GB;
+        t.spart = ps + 3 * s;
+        t.gather_blocks = GB;
+        t.pdl = false;
+        if ((rc = launch_terms(c, t))) return rc;
+        c->ks->launch_adj[pv](a, (int)n, 1, -1, c->stream, false);
         CK_LAUNCH("adjoint stages (plain)");
         if (nch > 0) {
             k_ann_grad<<<dim3(nch, groups), ANN_TILES, gsm, c->stream>>>(c->p_chunks.as<int>() + c->p_cofs[s], c->NN, c->NDP,
@@ -927,9 +1059,9 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         g.whi = c->p_whi.as<int>() + s * c->T;
         g.warp_begin = c->p_ident.as<int>() + a0;
         g.acc = c->p_acc.as<double>();
-        if ((rc = run_grad_final(c, g))) return rc;
+        if ((rc = run_grad_final(c, g, false))) return rc;
     }
-    if ((rc = launch_loss_final(c, loss3, pg, (int)(ns * GB), ps, (int)ns))) return rc;
+    if ((rc = launch_loss_final(c, loss3, pg, (int)(ns * GB), ps, (int)ns, nsv))) return rc;
     k_grad_convert<<<(unsigned)((c->P + 255) / 256), 256, 0, c->stream>>>(c->P, (int64_t)c->T * c->NN * c->ND +
                                                                           2 * (int64_t)c->T * c->NN,
                                                                           c->p_acc.as<double>(), c->gb1.as<double>(),

@@ -123,7 +123,6 @@ int build_minibatches(Ctx *c, int B) {
     group_launch(c, 0, fvar, fwpb, fcap);
     group_launch(c, 1, avar, awpb, acap);
     const int gf = 32 / c->ks->sw[fvar], ga = 32 / c->ks->sw[avar];
-    const int CH = 128;  // work positions per network-gradient chunk
     std::vector<int> work(na);
     std::vector<int> wbf, wba, wlo, whi, chunks, clo, chi;
     std::vector<Ctx::MiniBatch> mbs;
@@ -163,7 +162,9 @@ int build_minibatches(Ctx *c, int B) {
         wlo.resize(tofs + T);
         whi.resize(tofs + T);
         species_warps(ba, tb, T, wlo.data() + tofs, whi.data() + tofs);
-        // network-gradient chunks of one species each
+        // network chunks of one species each: about one per SM in a small group (the network
+        // kernels run one block per chunk), 128 work positions at most
+        const int CH = std::max(16, std::min(128, n / std::max(1, c->n_sm) / 16 * 16));
         m.ck_off = (int64_t)chunks.size();
         clo.resize(tofs + T);
         chi.resize(tofs + T);
@@ -177,6 +178,13 @@ int build_minibatches(Ctx *c, int B) {
         mbs.push_back(m);
     }
     const int64_t nm = (int64_t)mbs.size();
+    int max_ck = 0;
+    for (const Ctx::MiniBatch &m : mbs) max_ck = std::max(max_ck, m.n_ck);
+    const size_t arow = sizeof(float) * (size_t)(c->NN * c->NDP + 2 * c->NN);
+    if (c->annpart.bytes < arow * (size_t)(max_ck + 1)) {
+        drop_graphs(c);  // the whole-batch graphs hold the old partial buffer
+        if (c->annpart.ensure_bytes(arow * (size_t)(max_ck + 1))) return c->fail(NEP_ENOMEM, "network partials");
+    }
     if (c->mb_work.ensure<int>(std::max<int64_t>(na, 1)) || c->mb_wbf.ensure<int>((int64_t)wbf.size() + 1) ||
         c->mb_wba.ensure<int>((int64_t)wba.size() + 1) || c->mb_wlo.ensure<int>(nm * T + 1) ||
         c->mb_whi.ensure<int>(nm * T + 1) || c->mb_chunks.ensure<int>((int64_t)chunks.size() + 1) ||
@@ -209,14 +217,15 @@ int build_minibatches(Ctx *c, int B) {
 // fastest.  Needs parameters and targets; otherwise the batch's own variants stay.
 int minibatch_tune(Ctx *c) {
     if (!c->have_targets || !c->have_params || c->mb.empty()) return NEP_OK;
-    const int cand[][2] = {{-1, -1}, {2, 2}, {3, 2}, {3, 3}, {0, 0}};
+    const int cand[][2] = {{-1, -1}, {2, 2}, {3, 2}, {3, 3}, {0, 0}, {4, 4}, {5, 5}, {4, 5}};
+    const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
     const int ng = (int)std::min<size_t>(8, c->mb.size());
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     int bi = 0, rc = NEP_OK;
-    for (int k = 0; k < 5 && !rc; ++k) {
+    for (int k = 0; k < ncand && !rc; ++k) {
         c->mb_var[0] = cand[k][0];
         c->mb_var[1] = cand[k][1];
         if ((rc = build_minibatches(c, c->mb_B))) break;
@@ -248,8 +257,10 @@ int minibatch_tune(Ctx *c) {
     return build_minibatches(c, c->mb_B);
 }
 
-// Loss and gradient of group m against the references of nep_set_targets.
-int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, double *loss3, float *grad) {
+// Loss and gradient of group m against the references of nep_set_targets.  The padded
+// parameter copies are current (nep_set_params expands them, every optimiser update
+// refreshes them), so the step starts with the descriptors.
+int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, double *loss3, float *grad, bool opt) {
     int rc0 = minibatch_shape_check(c);  // the launch shape may have changed since the setup
     if (rc0) return rc0;
     const Ctx::MiniBatch &m = c->mb[mi];
@@ -262,23 +273,35 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
     c->ov_NsV = 0.0;
     int rc = NEP_OK;
     do {
-        if ((rc = launch_expand(c))) break;
         if ((rc = launch_forward_sched(c, c->mb_work.as<int>(), c->mb_wbf.as<int>() + m.wf_off, m.Wf / c->mb_used[1],
                                        c->mb_used[0], c->mb_used[1], c->mb_chunks.as<int>() + m.ck_off, m.n_ck)))
             break;
-        if ((rc = launch_count_hasw(c, hw, m.s0, m.s1))) break;
-        if ((rc = launch_gather(c, c->F_int.as<float>(), c->tgt_F.as<float>(), lF, true, m.a0, m.a1))) break;
-        if ((rc = launch_struct(c, c->E_int.as<double>(), c->W_int.as<double>(), c->tgt_E.as<double>(),
-                                c->tgt_W.as<double>(), hw, lE, lV, true, m.s0, m.s1)))
-            break;
-        if ((rc = launch_loss_final(c, loss3))) break;
+        TermsCall t;
+        t.a0 = m.a0;
+        t.a1 = m.a1;
+        t.s0 = m.s0;
+        t.s1 = m.s1;
+        t.F_out = c->F_int.as<float>();
+        t.E_out = c->E_int.as<double>();
+        t.W_out = c->W_int.as<double>();
+        t.loss = true;
+        t.F_ref = c->tgt_F.as<float>();
+        t.E_ref = c->tgt_E.as<double>();
+        t.W_ref = c->tgt_W.as<double>();
+        t.has_W = hw;
+        t.lE = lE;
+        t.lF = lF;
+        t.lV = lV;
+        t.nsv = host_nsv(c, hw, m.s0, m.s1);
+        t.loss3 = loss3;
+        if ((rc = launch_terms(c, t))) break;
         if ((rc = launch_adjoint_sched(c, c->mb_work.as<int>(), c->mb_wba.as<int>() + m.wa_off, m.Wa / c->mb_used[3],
                                        c->mb_used[2], c->mb_used[3], c->mb_chunks.as<int>() + m.ck_off, m.n_ck)))
             break;
         if ((rc = launch_ann_grad_chunks(c, c->mb_chunks.as<int>() + m.ck_off, m.n_ck))) break;
         rc = launch_grad_final_sched(c, grad, c->mb_clo.as<int>() + mi * T, c->mb_chi.as<int>() + mi * T,
                                      c->mb_wlo.as<int>() + mi * T, c->mb_whi.as<int>() + mi * T,
-                                     c->mb_wba.as<int>() + m.wa_off);
+                                     c->mb_wba.as<int>() + m.wa_off, opt, loss3, lE, lF, lV);
     } while (0);
     c->ov_Ns = sNs;
     c->ov_Na = sNa;

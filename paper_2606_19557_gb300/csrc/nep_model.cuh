@@ -355,6 +355,8 @@ __device__ __forceinline__ void pair_lambda(const AtomArgs &a, float4 pd, float 
 
 template <class S, int SW, int VAR>
 __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_jvp(AtomArgs a) {
+    grid_dep_wait();
+    grid_dep_launch();
     using L = JvpL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
@@ -595,6 +597,8 @@ __host__ __device__ inline size_t net_rev_smem(int NN) {
 
 template <class S>
 __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
+    grid_dep_wait();
+    grid_dep_launch();
     constexpr int ND = S::ND, NDQ = round4(ND);
     extern __shared__ __align__(16) float smn[];
     const int NN = a.NN, NNP = round4(NN), T = a.T;
@@ -708,6 +712,8 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
 
 template <class S, int SW, int VAR>
 __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_cg(AtomArgs a) {
+    grid_dep_wait();
+    grid_dep_launch();
     using L = CgL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int NCR = S::NCR, NCA = S::NCA, NC = S::NC;
@@ -971,6 +977,8 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_cg(AtomArgs a) {
 
 template <class S, int SW, int VAR>
 __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_desc(AtomArgs a) {
+    grid_dep_wait();
+    grid_dep_launch();
     using L = DescL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
@@ -1158,6 +1166,8 @@ __host__ __device__ inline size_t net_fwd_smem(int NN) {
 
 template <class S>
 __global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
+    grid_dep_wait();
+    grid_dep_launch();
     constexpr int ND = S::ND, NDQ = round4(ND);
     extern __shared__ __align__(16) float smn[];
     const int NN = a.NN, NNP = round4(NN), T = a.T;
@@ -1280,6 +1290,8 @@ __global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
 
 template <class S, int SW, int VAR>
 __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_pair(AtomArgs a) {
+    grid_dep_wait();
+    grid_dep_launch();
     using L = PairL<S, SW>;
     constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, ND = S::ND;
     constexpr int G = L::G, NAP = L::NAP, NLMO = L::NLMO;
@@ -1480,17 +1492,23 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_pair(AtomArgs a) 
 
 // Forward stages: 0 = descriptors, 1 = network, 2 = pair gradients, -1 = all three.
 template <class S, int SW, int VAR>
-void launch_fwd_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_t st) {
-    if (stage < 0 || stage == 0) k_fwd_desc<S, SW, VAR><<<blocks, wpb * 32, DescL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
-    if ((stage < 0 || stage == 1) && a.n_chunks > 0) k_net_fwd<S><<<a.n_chunks, 256, net_fwd_smem<S>(a.NN), st>>>(a);
-    if (stage < 0 || stage == 2) k_fwd_pair<S, SW, VAR><<<blocks, wpb * 32, PairL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
+void launch_fwd_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_t st, bool pdl) {
+    if (stage < 0 || stage == 0)
+        launch_k(pdl, k_fwd_desc<S, SW, VAR>, blocks, wpb * 32, DescL<S, SW>::bytes(a.T, a.NN) * wpb, st, a);
+    if ((stage < 0 || stage == 1) && a.n_chunks > 0)
+        launch_k(pdl, k_net_fwd<S>, a.n_chunks, 256, net_fwd_smem<S>(a.NN), st, a);
+    if (stage < 0 || stage == 2)
+        launch_k(pdl, k_fwd_pair<S, SW, VAR>, blocks, wpb * 32, PairL<S, SW>::bytes(a.T, a.NN) * wpb, st, a);
 }
 // Adjoint stages: 0 = JVP, 1 = network reverse, 2 = coefficient gradient, -1 = all three.
 template <class S, int SW, int VAR>
-void launch_adj_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_t st) {
-    if (stage < 0 || stage == 0) k_adj_jvp<S, SW, VAR><<<blocks, wpb * 32, JvpL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
-    if ((stage < 0 || stage == 1) && a.n_chunks > 0) k_net_rev<S><<<a.n_chunks, 256, net_rev_smem<S>(a.NN), st>>>(a);
-    if (stage < 0 || stage == 2) k_adj_cg<S, SW, VAR><<<blocks, wpb * 32, CgL<S, SW>::bytes(a.T, a.NN) * wpb, st>>>(a);
+void launch_adj_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_t st, bool pdl) {
+    if (stage < 0 || stage == 0)
+        launch_k(pdl, k_adj_jvp<S, SW, VAR>, blocks, wpb * 32, JvpL<S, SW>::bytes(a.T, a.NN) * wpb, st, a);
+    if ((stage < 0 || stage == 1) && a.n_chunks > 0)
+        launch_k(pdl, k_net_rev<S>, a.n_chunks, 256, net_rev_smem<S>(a.NN), st, a);
+    if (stage < 0 || stage == 2)
+        launch_k(pdl, k_adj_cg<S, SW, VAR>, blocks, wpb * 32, CgL<S, SW>::bytes(a.T, a.NN) * wpb, st, a);
 }
 // per-warp shared memory of the larger of the two per-atom forward stages
 template <class S, int SW>
@@ -1505,7 +1523,7 @@ size_t adj_bytes_t(int T, int NN) {
     return j > c ? j : c;
 }
 
-// Variant v: SW = 8 (v < 2) or 16, register budget VAR = v & 1 (blocks of at most 128 threads;
+// Variant v: SW = 8 (v < 2), 16 (v < 4) or 32, register budget VAR = v & 1 (blocks of at most 128 threads;
 // 0: four blocks per SM, 128 registers; 1: five blocks per SM, 96 registers).
 template <int NR, int KR, int NA, int KA>
 KernelSet make_set() {
@@ -1519,37 +1537,51 @@ KernelSet make_set() {
     k.fwd_fn[1] = (const void *)k_fwd_pair<S, 8, 1>;
     k.fwd_fn[2] = (const void *)k_fwd_pair<S, 16, 0>;
     k.fwd_fn[3] = (const void *)k_fwd_pair<S, 16, 1>;
+    k.fwd_fn[4] = (const void *)k_fwd_pair<S, 32, 0>;
+    k.fwd_fn[5] = (const void *)k_fwd_pair<S, 32, 1>;
     k.desc_fn[0] = (const void *)k_fwd_desc<S, 8, 0>;
     k.desc_fn[1] = (const void *)k_fwd_desc<S, 8, 1>;
     k.desc_fn[2] = (const void *)k_fwd_desc<S, 16, 0>;
     k.desc_fn[3] = (const void *)k_fwd_desc<S, 16, 1>;
+    k.desc_fn[4] = (const void *)k_fwd_desc<S, 32, 0>;
+    k.desc_fn[5] = (const void *)k_fwd_desc<S, 32, 1>;
     k.net_fwd_fn = (const void *)k_net_fwd<S>;
     k.net_fwd_smem = net_fwd_smem<S>;
     k.adj_fn[0] = (const void *)k_adj_cg<S, 8, 0>;
     k.adj_fn[1] = (const void *)k_adj_cg<S, 8, 1>;
     k.adj_fn[2] = (const void *)k_adj_cg<S, 16, 0>;
     k.adj_fn[3] = (const void *)k_adj_cg<S, 16, 1>;
+    k.adj_fn[4] = (const void *)k_adj_cg<S, 32, 0>;
+    k.adj_fn[5] = (const void *)k_adj_cg<S, 32, 1>;
     k.jvp_fn[0] = (const void *)k_adj_jvp<S, 8, 0>;
     k.jvp_fn[1] = (const void *)k_adj_jvp<S, 8, 1>;
     k.jvp_fn[2] = (const void *)k_adj_jvp<S, 16, 0>;
     k.jvp_fn[3] = (const void *)k_adj_jvp<S, 16, 1>;
+    k.jvp_fn[4] = (const void *)k_adj_jvp<S, 32, 0>;
+    k.jvp_fn[5] = (const void *)k_adj_jvp<S, 32, 1>;
     k.net_rev_fn = (const void *)k_net_rev<S>;
     k.net_rev_smem = net_rev_smem<S>;
     k.launch_fwd[0] = launch_fwd_t<S, 8, 0>;
     k.launch_fwd[1] = launch_fwd_t<S, 8, 1>;
     k.launch_fwd[2] = launch_fwd_t<S, 16, 0>;
     k.launch_fwd[3] = launch_fwd_t<S, 16, 1>;
+    k.launch_fwd[4] = launch_fwd_t<S, 32, 0>;
+    k.launch_fwd[5] = launch_fwd_t<S, 32, 1>;
     k.launch_adj[0] = launch_adj_t<S, 8, 0>;
     k.launch_adj[1] = launch_adj_t<S, 8, 1>;
     k.launch_adj[2] = launch_adj_t<S, 16, 0>;
     k.launch_adj[3] = launch_adj_t<S, 16, 1>;
+    k.launch_adj[4] = launch_adj_t<S, 32, 0>;
+    k.launch_adj[5] = launch_adj_t<S, 32, 1>;
     k.fwd_smem[0] = k.fwd_smem[1] = fwd_bytes_t<S, 8>;
     k.fwd_smem[2] = k.fwd_smem[3] = fwd_bytes_t<S, 16>;
+    k.fwd_smem[4] = k.fwd_smem[5] = fwd_bytes_t<S, 32>;
     k.adj_smem[0] = k.adj_smem[1] = adj_bytes_t<S, 8>;
     k.adj_smem[2] = k.adj_smem[3] = adj_bytes_t<S, 16>;
+    k.adj_smem[4] = k.adj_smem[5] = adj_bytes_t<S, 32>;
     for (int v = 0; v < NVAR; ++v) {
         k.max_wpb[v] = 4;
-        k.sw[v] = v < 2 ? 8 : 16;
+        k.sw[v] = v < 2 ? 8 : v < 4 ? 16 : 32;
     }
     return k;
 }

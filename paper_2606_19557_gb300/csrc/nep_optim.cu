@@ -13,6 +13,8 @@
 // FP64.  The P-element update is a few tens of kilobytes: one short elementwise launch.
 #include <math_constants.h>
 
+#include <algorithm>
+
 #include "nep_ctx.cuh"
 
 namespace nep {
@@ -42,40 +44,16 @@ __global__ void k_opt_set_lr(double *st, double lr) {
     }
 }
 
-// Step counter and the powers beta^t (running products), and the epoch loss sum:
-// L = lamE DE + lamF DF + lamV DV of this step when loss3 is given, else loss1[0].
-__global__ void k_opt_tick(double *st, double b1, double b2, const double *loss3, double lE, double lF, double lV,
-                           const double *loss1) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        st[OPT_T] += 1.0;
-        st[OPT_B1T] *= b1;
-        st[OPT_B2T] *= b2;
-        if (loss3) {
-            st[OPT_ACC] += lE * loss3[0] + lF * loss3[1] + lV * loss3[2];
-            st[OPT_NACC] += 1.0;
-        } else if (loss1) {
-            st[OPT_ACC] += loss1[0];
-            st[OPT_NACC] += 1.0;
-        }
-    }
-}
-
-__global__ void k_amsgrad(int64_t P, float *__restrict__ theta, const float *__restrict__ g, double *__restrict__ m,
-                          double *__restrict__ v, double *__restrict__ vmax, const double *__restrict__ st, double b1,
-                          double b2, double eps) {
+// One AMSGrad step over the P parameters (the padded copies follow each update); the
+// block that finishes last advances the step counter, the powers beta^t and the epoch loss
+// sum (L = lamE DE + lamF DF + lamV DV of this step when loss3 is given, else loss1[0]).
+__global__ void k_opt_step(int64_t P, const float *__restrict__ g, OptArgs o, unsigned *counter) {
+    grid_dep_wait();
+    grid_dep_launch();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
-    const double bc1 = 1.0 - st[OPT_B1T], bc2 = 1.0 - st[OPT_B2T], lr = st[OPT_LR];
-    const double gi = (double)g[i];
-    const double mi = __dadd_rn(__dmul_rn(b1, m[i]), __dmul_rn(1.0 - b1, gi));
-    const double vi = __dadd_rn(__dmul_rn(b2, v[i]), __dmul_rn(__dmul_rn(1.0 - b2, gi), gi));
-    m[i] = mi;
-    v[i] = vi;
-    const double vh = vi / bc2;
-    const double vm = vmax[i] > vh ? vmax[i] : vh;
-    vmax[i] = vm;
-    const double step = __dmul_rn(lr, mi / bc1) / __dadd_rn(sqrt(vm), eps);
-    theta[i] = (float)__dadd_rn((double)theta[i], -step);
+    const OptStep s = opt_step_state(o);
+    if (i < P) amsgrad_elem(o, s, i, (double)g[i]);
+    if (last_block_arrival(counter, gridDim.x, false) && threadIdx.x == 0) opt_tick(o);
 }
 
 // Epoch boundary: mean loss of the epoch's steps, improvement test, rate reduction.
@@ -119,17 +97,51 @@ int launch_opt_set_lr(Ctx *c, double lr) {
     return NEP_OK;
 }
 
+ParScatter par_scatter(Ctx *c) {
+    ParScatter p;
+    p.po = c->po;
+    p.T = c->T;
+    p.NN = c->NN;
+    p.ND = c->ND;
+    p.NDP = c->NDP;
+    p.nR = c->nR;
+    p.kR = c->kR;
+    p.nA = c->nA;
+    p.kA = c->kA;
+    p.NRP = c->ks->NR;
+    p.KRP = c->ks->KR;
+    p.NAP = c->ks->NA;
+    p.KAP = c->ks->KA;
+    p.map = c->d_desc_map.as<int>();
+    p.par = c->par.as<float>();
+    return p;
+}
+
+OptArgs opt_args(Ctx *c, const double *loss3, double lE, double lF, double lV, const double *loss1) {
+    const nep_optim_config &cf = c->ocfg;
+    OptArgs o;
+    o.theta = c->theta.as<float>();
+    o.m = c->opt_m.as<double>();
+    o.v = c->opt_v.as<double>();
+    o.vmax = c->opt_vmax.as<double>();
+    o.st = c->opt_st.as<double>();
+    o.b1 = cf.beta1;
+    o.b2 = cf.beta2;
+    o.eps = cf.eps;
+    o.loss3 = loss3;
+    o.lE = lE;
+    o.lF = lF;
+    o.lV = lV;
+    o.loss1 = loss1;
+    o.ps = par_scatter(c);
+    return o;
+}
+
 int launch_opt_step(Ctx *c, const float *grad, const double *loss3, double lE, double lF, double lV,
                     const double *loss1) {
-    const nep_optim_config &o = c->ocfg;
-    k_opt_tick<<<1, 32, 0, c->stream>>>(c->opt_st.as<double>(), o.beta1, o.beta2, loss3, lE, lF, lV, loss1);
-    CK_LAUNCH("k_opt_tick");
-    if (c->P > 0) {
-        k_amsgrad<<<(unsigned)((c->P + 255) / 256), 256, 0, c->stream>>>(
-            c->P, c->theta.as<float>(), grad, c->opt_m.as<double>(), c->opt_v.as<double>(), c->opt_vmax.as<double>(),
-            c->opt_st.as<double>(), o.beta1, o.beta2, o.eps);
-        CK_LAUNCH("k_amsgrad");
-    }
+    const unsigned nb = (unsigned)std::max<int64_t>(1, (c->P + 255) / 256);
+    CK(launch_k(c->pdl(), k_opt_step, nb, 256, 0, c->stream, c->P, grad, opt_args(c, loss3, lE, lF, lV, loss1),
+                c->counters.as<unsigned>() + 1));
     return NEP_OK;
 }
 

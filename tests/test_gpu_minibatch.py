@@ -127,6 +127,29 @@ def test_minibatch_train_step_and_epochs():
     np.testing.assert_allclose(l3d, c.oracle_group(0, 4, lam, theta=th)[0], rtol=TOL)
 
 
+def test_padded_copies_follow_updates():
+    """A group's pass starts from the padded parameter copies, which every optimiser update
+    refreshes in place of a new expansion: after a stand-alone update and a fused training
+    step, the pass equals the one after nep_set_params expands the same parameters afresh."""
+    c = case("alloy_t4")
+    c.nep.minibatch_setup(4)
+    qs = torch.tensor(c.qs, dtype=torch.float32)
+    c.nep.set_params(torch.tensor(c.theta, dtype=torch.float32), qs)
+    c.nep.optim_init(lr=1e-2)
+    lam = (1.0, 2.0, 0.3)
+    g = np.random.default_rng(7).normal(size=c.nep.P).astype(np.float32)
+    c.nep.optim_step(torch.tensor(g))
+    c.nep.minibatch_train_step(1, lam)
+    th = c.nep.get_params().clone()
+    assert not np.array_equal(th.cpu().numpy(), c.theta.astype(np.float32))
+    la, ga = c.nep.minibatch_loss_grad(2, lam)
+    la, ga = la.cpu().numpy(), ga.cpu().numpy()
+    c.nep.set_params(th, qs)
+    lb, gb = c.nep.minibatch_loss_grad(2, lam)
+    assert np.array_equal(la, lb.cpu().numpy()) and np.array_equal(ga, gb.cpu().numpy())
+    c.nep.set_params(torch.tensor(c.theta, dtype=torch.float32), qs)
+
+
 def test_minibatch_errors():
     from paper_2606_19557_gb300 import NEP, NepError
     spec = synth.SPECS["fcc32_t1"]

@@ -290,6 +290,34 @@ def test_launch_shapes_agree():
     assert rel(g1, g0) < 1e-6
 
 
+@pytest.mark.parametrize("name", ["alloy_t4", "scale_t5"])
+def test_every_kernel_variant_matches_oracle(name):
+    """Each kernel variant (8, 16 or 32 lanes per atom; 128 or 96 registers), forward and
+    adjoint alike, against the oracle: E/F/W, the loss and the gradient block by block."""
+    c = get_case(name)
+    lam = (1.0, 2.0, 0.3)
+    Eo, Fo, Wo = oracle.evaluate(c.spec, c.theta, c.qs, c.batch)
+    l3o, go = oracle.loss_grad(c.spec, c.theta, c.qs, c.batch, c.E_ref, c.F_ref, c.W_ref, None, lam)[:2]
+    shape, var = c.nep.launch_shape(), c.nep.variant()
+    lanes = []
+    for v in range(6):
+        c.nep.set_variant(v, v)
+        lanes.append(c.nep.variant()[0])
+        E, F, W = [x.cpu().numpy() for x in c.nep.eval()]
+        assert rel(E, Eo) < TOL and rel(F, Fo) < TOL and rel(W, Wo) < TOL, v
+        l3, g = c.nep.loss_grad(c.E_ref, c.F_ref, c.W_ref, None, lam)
+        np.testing.assert_allclose(l3.cpu().numpy(), l3o, rtol=TOL)
+        assert_grad_close(g.cpu().numpy(), go, c.spec, TOL)
+    assert lanes == [8, 8, 16, 16, 32, 32]
+    # back to the earlier variants and shape for the other tests
+
+    def index(lanes, regs):
+        return {8: 0, 16: 2, 32: 4}[lanes] + (1 if regs == 96 else 0)
+
+    c.nep.set_variant(index(var[0], var[1]), index(var[2], var[3]))
+    c.nep.set_launch(*shape)
+
+
 def test_empty_batch():
     from paper_2606_19557_gb300 import NEP
     spec = synth.SPECS["fcc32_t1"]
