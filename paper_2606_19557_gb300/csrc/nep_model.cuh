@@ -335,13 +335,73 @@ struct CgL {
 //                          the network: zeta, u, omega and abar = dJ/dq~, b = dE/dq~;
 //   k_adj_cg   (per atom)  dJ/dA and the gradient into the coefficients c.
 
+// Copy of N floats of per-atom state (written by an earlier stage) by the SW lanes of a
+// group: up to eight loads of a lane are issued before their stores, so the copy costs
+// about N / (8 SW) memory round trips instead of N / SW.  st(e, value) places element e.
+template <int N, int SW, class St>
+__device__ __forceinline__ void gather_rows(const float *src, int sl, St st) {
+    constexpr int IT = (N + SW - 1) / SW;
+    constexpr int B = IT < 8 ? IT : 8;
+#pragma unroll
+    for (int i0 = 0; i0 < IT; i0 += B) {
+        float v[B];
+#pragma unroll
+        for (int it = 0; it < B; ++it) {
+            const int e = sl + (i0 + it) * SW;
+            v[it] = (i0 + it < IT && e < N) ? __ldg(src + e) : 0.0f;
+        }
+#pragma unroll
+        for (int it = 0; it < B; ++it) {
+            const int e = sl + (i0 + it) * SW;
+            if (i0 + it < IT && e < N) st(e, v[it]);
+        }
+    }
+}
+
+// The same for a run-time length n, eight loads per lane in flight at a time.
+template <int SW, class St>
+__device__ __forceinline__ void gather_rows_n(const float *src, int n, int sl, St st) {
+    for (int e0 = 0; e0 < n; e0 += 8 * SW) {
+        float v[8];
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int e = e0 + sl + it * SW;
+            v[it] = e < n ? __ldg(src + e) : 0.0f;
+        }
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int e = e0 + sl + it * SW;
+            if (e < n) st(e, v[it]);
+        }
+    }
+}
+
+// Block-wide staging of n elements by NT threads, eight loads per thread in flight:
+// ld(e) returns element e (or the padding value), st(e, value) places it.
+template <int NT, class Ld, class St>
+__device__ __forceinline__ void block_stage(int n, Ld ld, St st) {
+    for (int e0 = 0; e0 < n; e0 += 8 * NT) {
+        float v[8];
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int e = e0 + (int)threadIdx.x + it * NT;
+            v[it] = e < n ? ld(e) : 0.0f;
+        }
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int e = e0 + (int)threadIdx.x + it * NT;
+            if (e < n) st(e, v[it]);
+        }
+    }
+}
+
 // Loads a [lm][n]-packed per-atom matrix (NA x 24 floats) into a [lm][NAP] shared row set.
 template <int NA, int NAP, int SW>
 __device__ __forceinline__ void load_lm_rows(const float *src, float *dst, int sl) {
-    for (int e = sl; e < L3 * NA; e += SW) {
+    gather_rows<L3 * NA, SW>(src, sl, [&](int e, float x) {
         const int lm = e / NA, n = e - lm * NA;
-        dst[lm * NAP + n] = src[e];
-    }
+        dst[lm * NAP + n] = x;
+    });
 }
 
 // lambda_p of a pair (record pd, neighbour j) of an atom with cotangent fbi and structure wbar
@@ -615,21 +675,33 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
     const float *W0T = a.par + po.w0t + (size_t)t * ND * NN;
     const float *w1 = a.par + po.w1 + (size_t)t * NN;
     const float *scale = a.par + po.scale;
-    for (int e = threadIdx.x; e < ND * NNP; e += 256) {
-        const int k = e / NNP, mu = e - k * NNP;
-        Wt[e] = mu < NN ? W0T[(size_t)k * NN + mu] : 0.0f;
-    }
-    for (int e = threadIdx.x; e < NN * NDQ; e += 256) {
-        const int mu = e / NDQ, v = e - mu * NDQ;
-        Wn[e] = v < ND ? W0[(size_t)mu * ND + v] : 0.0f;
-    }
+    block_stage<256>(
+        ND * NNP,
+        [&](int e) {
+            const int k = e / NNP, mu = e - k * NNP;
+            return mu < NN ? __ldg(W0T + (size_t)k * NN + mu) : 0.0f;
+        },
+        [&](int e, float x) { Wt[e] = x; });
+    block_stage<256>(
+        NN * NDQ,
+        [&](int e) {
+            const int mu = e / NDQ, v = e - mu * NDQ;
+            return v < ND ? __ldg(W0 + (size_t)mu * ND + v) : 0.0f;
+        },
+        [&](int e, float x) { Wn[e] = x; });
     for (int rb = rc0; rb < rc1; rb += NETR) {
         const int nr = min(NETR, rc1 - rb);
         __syncthreads();  // the weights are staged; the previous tile is done with Q, Z, U
-        for (int e = threadIdx.x; e < NETR * NDQ; e += 256) {
-            const int r = e / NDQ, k = e - r * NDQ;
-            Q[k * NETR + r] = (r < nr && k < ND) ? a.dqt[(size_t)(rb + r) * ND + k] : 0.0f;
-        }
+        block_stage<256>(
+            NETR * NDQ,
+            [&](int e) {
+                const int r = e / NDQ, k = e - r * NDQ;
+                return (r < nr && k < ND) ? __ldg(a.dqt + (size_t)(rb + r) * ND + k) : 0.0f;
+            },
+            [&](int e, float x) {
+                const int r = e / NDQ, k = e - r * NDQ;
+                Q[k * NETR + r] = x;
+            });
         __syncthreads();
         const int r0 = ty * 4;
         for (int cb = 0; cb < NNP; cb += 64) {
@@ -799,11 +871,10 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_cg(AtomArgs a) {
         // ---------------------------------------------------------------- state of the earlier stages
         load_lm_rows<NA, NAP, SW>(a.st_A + (size_t)wi * NA * L3, at.A, sl);
         load_lm_rows<NA, NAP, SW>(a.st_D + (size_t)wi * NA * L3, at.D, sl);
-        for (int v = sl; v < ND; v += SW) {
-            at.b[v] = a.st_b[(size_t)wi * ND + v];
-            at.ab[v] = a.st_ab[(size_t)wi * ND + v];
-        }
-        for (int e = sl; e < T * 2 * KR; e += SW) Sr[e] = act ? a.st_S[(size_t)wi * T * 2 * KR + e] : 0.0f;
+        gather_rows<ND, SW>(a.st_b + (size_t)wi * ND, sl, [&](int v, float x) { at.b[v] = x; });
+        gather_rows<ND, SW>(a.st_ab + (size_t)wi * ND, sl, [&](int v, float x) { at.ab[v] = x; });
+        gather_rows_n<SW>(a.st_S + (size_t)wi * T * 2 * KR, T * 2 * KR, sl,
+                          [&](int e, float x) { Sr[e] = act ? x : 0.0f; });
         __syncwarp();
         for (int n = sl; n < NA; n += SW) {
             float a2[5], d2[5], Mt[6], dMt[6], M2[6], Pm[6], pr[5];
@@ -1187,21 +1258,33 @@ __global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
     const float *w1 = a.par + po.w1 + (size_t)t * NN;
     const float b1 = a.par[po.b1];
     const float *scale = a.par + po.scale;
-    for (int e = threadIdx.x; e < ND * NNP; e += 256) {
-        const int k = e / NNP, mu = e - k * NNP;
-        Wt[e] = mu < NN ? W0T[(size_t)k * NN + mu] : 0.0f;
-    }
-    for (int e = threadIdx.x; e < NN * NDQ; e += 256) {
-        const int mu = e / NDQ, v = e - mu * NDQ;
-        Wn[e] = v < ND ? W0[(size_t)mu * ND + v] : 0.0f;
-    }
+    block_stage<256>(
+        ND * NNP,
+        [&](int e) {
+            const int k = e / NNP, mu = e - k * NNP;
+            return mu < NN ? __ldg(W0T + (size_t)k * NN + mu) : 0.0f;
+        },
+        [&](int e, float x) { Wt[e] = x; });
+    block_stage<256>(
+        NN * NDQ,
+        [&](int e) {
+            const int mu = e / NDQ, v = e - mu * NDQ;
+            return v < ND ? __ldg(W0 + (size_t)mu * ND + v) : 0.0f;
+        },
+        [&](int e, float x) { Wn[e] = x; });
     for (int rb = rc0; rb < rc1; rb += NETR) {
         const int nr = min(NETR, rc1 - rb);
         __syncthreads();  // the weights are staged; the previous tile is done with Q, U, Es
-        for (int e = threadIdx.x; e < NETR * NDQ; e += 256) {
-            const int r = e / NDQ, k = e - r * NDQ;
-            Q[k * NETR + r] = (r < nr && k < ND) ? a.st_qt[(size_t)(rb + r) * ND + k] : 0.0f;
-        }
+        block_stage<256>(
+            NETR * NDQ,
+            [&](int e) {
+                const int r = e / NDQ, k = e - r * NDQ;
+                return (r < nr && k < ND) ? __ldg(a.st_qt + (size_t)(rb + r) * ND + k) : 0.0f;
+            },
+            [&](int e, float x) {
+                const int r = e / NDQ, k = e - r * NDQ;
+                Q[k * NETR + r] = x;
+            });
         if (threadIdx.x < NETR) Es[threadIdx.x] = 0.0f;
         __syncthreads();
         const int r0 = ty * 4;
@@ -1326,7 +1409,7 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_pair(AtomArgs a) 
             prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
         }
         load_lm_rows<NA, NAP, SW>(a.st_A + (size_t)wi * NA * L3, at.A, sl);
-        for (int v = sl; v < ND; v += SW) at.b[v] = a.st_b[(size_t)wi * ND + v];
+        gather_rows<ND, SW>(a.st_b + (size_t)wi * ND, sl, [&](int v, float x) { at.b[v] = x; });
         __syncwarp();
 
         // ---------------------------------------------------------------- dE_i/dA and radial factors
