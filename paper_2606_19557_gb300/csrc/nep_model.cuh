@@ -934,16 +934,22 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_cg(AtomArgs a) {
         __syncwarp();
 
         // ---------------------------------------------------------------- radial coefficient gradient
+        // accR[b][n][k] += abar_n S^b_k + b_n S'^b_k for each atom of the batch in turn, all 32
+        // lanes on one atom: lane -> (b, n), the K_R products of the row unrolled
 #pragma unroll 1
-        for (int g2 = 0; g2 < G; ++g2) {
-            if (grp == g2 && act) {
-                for (int e = sl; e < T * NCR; e += SW) {
-                    const int bb = e / NCR, rr = e - bb * NCR, n = rr / KR, kk = rr - n * KR;
-                    accR[e] += at.ab[n] * Sr[bb * 2 * KR + kk] + at.b[n] * Sr[bb * 2 * KR + KR + kk];
-                }
+        for (int g2 = 0; g2 < nb; ++g2) {
+            const typename L::Atom &a2 = sm.at[g2];
+            const float *S2 = tail + g2 * T * 2 * KR;
+            for (int q = lane; q < T * NR; q += 32) {
+                const int bb = q / NR, n = q - bb * NR;
+                const float x = a2.ab[n], y = a2.b[n];
+                const float *sb = S2 + bb * 2 * KR;
+                float *dst = accR + q * KR;  // = accR[b * NCR + n * KR]
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) dst[kk] += x * sb[kk] + y * sb[KR + kk];
             }
-            __syncwarp();
         }
+        __syncwarp();
 
         // ---------------------------------------------------------------- angular coefficient gradient
         // per pair p (species b): X^b_nk += alpha_n f_k + beta_n f'_k with
