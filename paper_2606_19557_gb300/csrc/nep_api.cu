@@ -517,6 +517,7 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
     for (int t = 0; t < c->T; ++t) c->type_begin[t + 1] += c->type_begin[t];
     if (c->work.ensure<int>(na)) return c->fail(NEP_ENOMEM, "work order");
     if (na > 0) CK(cudaMemcpy(c->work.ptr, c->h_work.data(), sizeof(int) * na, cudaMemcpyHostToDevice));
+    if ((rc = build_work_rec(c, c->work.as<int>(), c->rec, c->rec2))) return rc;
     // network-gradient chunks (single species each)
     {
         const int CH = 128;  // work positions per network-gradient chunk
@@ -572,6 +573,7 @@ int nep_update_positions(nep_ctx *c, const float *pos, const float *cell) {
     int rc = build_neighbors(c, cell == nullptr, host_lists);
     if (rc) return rc;
     if (c->G.ensure_bytes(sizeof(float4) * (size_t)(c->n_pairs + 1))) return c->fail(NEP_ENOMEM, "pair gradients");
+    if ((rc = build_work_rec(c, c->work.as<int>(), c->rec, c->rec2))) return rc;  // new pair ranges
     // re-balance the kernel schedules for the new neighbour counts (same sizes, same
     // buffers): the result is then the one a fresh context computes, bit for bit
     if (host_lists) {

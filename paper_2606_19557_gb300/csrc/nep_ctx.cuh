@@ -130,6 +130,7 @@ struct Ctx {
     // schedule
     DevBuf work;                 // [Na] atom per work position (species-sorted)
     std::vector<int> h_work, type_begin;  // type_begin [T+1] work positions
+    DevBuf rec, rec2;  // work records of `work` (int4 atom / first pair / pair counts, int2 species / structure)
     Sched fwd, adj;
     DevBuf sched_cost, sched_pre;  // [Na + 1] work cost per position and its exclusive prefix
     // network-gradient contraction chunks
@@ -185,6 +186,7 @@ struct Ctx {
     int mb_key[6] = {-1, -1, -1, -1, -1, -1};  // launch shapes the schedules were built for
     std::vector<MiniBatch> mb;
     DevBuf mb_work, mb_wbf, mb_wba, mb_wlo, mb_whi, mb_chunks, mb_clo, mb_chi;
+    DevBuf mb_rec, mb_rec2;  // work records of mb_work
     std::vector<cudaGraphExec_t> mb_graphs;  // per group: training step, captured on first use
     std::vector<uint64_t> mb_gkey;           // loss weights the graphs were captured with
 
@@ -193,6 +195,7 @@ struct Ctx {
     bool plain_ready = false;
     std::vector<int64_t> p_cofs;
     DevBuf p_work, p_ident, p_wlo, p_whi, p_clo, p_chi, p_chunks, p_acc, p_part;
+    DevBuf p_rec, p_rec2;  // work records of p_work
     bool state_valid = false;
 
     // graphs
@@ -239,13 +242,16 @@ int build_neighbors(Ctx *c, bool same_cells = false, bool host_lists = true);
 int fetch_host_lists(Ctx *c);
 
 // step pieces (nep_loss.cu)
+// Work records of a work order (after the neighbour lists and the order are final): per
+// position the atom, its first pair and pair counts, its species and structure.
+int build_work_rec(Ctx *c, const int *work, DevBuf &rec, DevBuf &rec2);
 int launch_expand(Ctx *c);
 int launch_forward(Ctx *c, float *q_raw, int stage = -1);
 // explicit schedules (mini-batch mode)
-int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
-                         const int *chunks, int n_chunks);
-int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
-                         const int *chunks, int n_chunks);
+int launch_forward_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBuf &rec2, const int *warp_begin,
+                         int blocks, int var, int wpb, const int *chunks, int n_chunks);
+int launch_adjoint_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBuf &rec2, const int *warp_begin,
+                         int blocks, int var, int wpb, const int *chunks, int n_chunks);
 int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks);
 // opt: apply the optimiser step to each parameter as its gradient completes (training)
 int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi, const int *wlo, const int *whi,

@@ -58,6 +58,8 @@ __host__ __device__ inline ParOff par_offsets(int T, int NN, int NR, int KR, int
 struct AtomArgs {
     // schedule
     const int *work;        // [Na] atom index at each work position (atoms sorted by species)
+    const int4 *rec;        // [Na] per work position: atom i, first pair, radial and angular pair counts
+    const int2 *rec2;       // [Na] per work position: species and structure of the atom
     const int *warp_begin;  // [W+1] work-position range of each warp
     // geometry (cached by the neighbour build)
     const int64_t *nbr_off; // [Na+1]

@@ -657,6 +657,8 @@ __global__ void k_compact_q(int64_t na, int NDP, int ND, const int *desc_map, co
 static AtomArgs atom_args(Ctx *c) {
     AtomArgs a{};
     a.work = c->work.as<int>();
+    a.rec = c->rec.as<int4>();
+    a.rec2 = c->rec2.as<int2>();
     a.nbr_off = c->nbr_off.as<int64_t>();
     a.n_ang = c->n_ang.as<int>();
     a.pair = (const float4 *)c->pair.ptr;
@@ -695,6 +697,29 @@ static AtomArgs atom_args(Ctx *c) {
     a.st_ab = c->st_ab.as<float>();
     a.st_E = c->st_E.as<float>();
     return a;
+}
+
+namespace {
+__global__ void k_work_rec(int64_t n, const int *work, const int *type, const int *struct_of, const int64_t *nbr_off,
+                           const int *n_ang, int4 *rec, int2 *rec2) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int i = work[q];
+    const int64_t b = nbr_off[i];
+    rec[q] = make_int4(i, (int)b, (int)(nbr_off[i + 1] - b), n_ang[i]);
+    rec2[q] = make_int2(type[i], struct_of[i]);
+}
+}  // namespace
+
+int build_work_rec(Ctx *c, const int *work, DevBuf &rec, DevBuf &rec2) {
+    const int64_t na = c->n_atoms;
+    if (rec.ensure<int4>(na) || rec2.ensure<int2>(na)) return c->fail(NEP_ENOMEM, "work records");
+    if (na == 0) return NEP_OK;
+    k_work_rec<<<(unsigned)((na + 255) / 256), 256, 0, c->stream>>>(na, work, c->type.as<int>(), c->struct_of.as<int>(),
+                                                                    c->nbr_off.as<int64_t>(), c->n_ang.as<int>(),
+                                                                    rec.as<int4>(), rec2.as<int2>());
+    CK_LAUNCH("k_work_rec");
+    return NEP_OK;
 }
 
 int launch_expand(Ctx *c) {
@@ -740,11 +765,13 @@ int launch_adjoint(Ctx *c, int stage) {
     return NEP_OK;
 }
 
-int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
-                         const int *chunks, int n_chunks) {
+int launch_forward_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBuf &rec2, const int *warp_begin,
+                         int blocks, int var, int wpb, const int *chunks, int n_chunks) {
     if (blocks <= 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.work = work;
+    a.rec = rec.as<int4>();
+    a.rec2 = rec2.as<int2>();
     a.warp_begin = warp_begin;
     a.chunks = chunks;
     a.n_chunks = n_chunks;
@@ -753,11 +780,13 @@ int launch_forward_sched(Ctx *c, const int *work, const int *warp_begin, int blo
     return NEP_OK;
 }
 
-int launch_adjoint_sched(Ctx *c, const int *work, const int *warp_begin, int blocks, int var, int wpb,
-                         const int *chunks, int n_chunks) {
+int launch_adjoint_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBuf &rec2, const int *warp_begin,
+                         int blocks, int var, int wpb, const int *chunks, int n_chunks) {
     if (blocks <= 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.work = work;
+    a.rec = rec.as<int4>();
+    a.rec2 = rec2.as<int2>();
     a.warp_begin = warp_begin;
     a.chunks = chunks;
     a.n_chunks = n_chunks;
@@ -989,6 +1018,7 @@ static int build_plain(Ctx *c) {
     CK(cudaMemcpy(c->p_clo.ptr, clo.data(), sizeof(int) * ns * T, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->p_chi.ptr, chi.data(), sizeof(int) * ns * T, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->p_chunks.ptr, cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice));
+    if (int rc = build_work_rec(c, c->p_work.as<int>(), c->p_rec, c->p_rec2)) return rc;
     c->plain_ready = true;
     return NEP_OK;
 }
@@ -1015,6 +1045,8 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         const int64_t a0 = c->h_atom_off[s], n = c->h_atom_off[s + 1] - a0;
         AtomArgs a = atom_args(c);
         a.work = c->p_work.as<int>();
+        a.rec = c->p_rec.as<int4>();
+        a.rec2 = c->p_rec2.as<int2>();
         a.warp_begin = c->p_ident.as<int>() + a0;
         const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
         a.chunks = c->p_chunks.as<int>() + c->p_cofs[s];

@@ -194,6 +194,7 @@ int build_minibatches(Ctx *c, int B) {
         return h.empty() ? cudaSuccess : cudaMemcpy(d.ptr, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
     };
     CK(up(c->mb_work, work));
+    if (int rc = build_work_rec(c, c->mb_work.as<int>(), c->mb_rec, c->mb_rec2)) return rc;
     CK(up(c->mb_wbf, wbf));
     CK(up(c->mb_wba, wba));
     CK(up(c->mb_wlo, wlo));
@@ -273,7 +274,8 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
     c->ov_NsV = 0.0;
     int rc = NEP_OK;
     do {
-        if ((rc = launch_forward_sched(c, c->mb_work.as<int>(), c->mb_wbf.as<int>() + m.wf_off, m.Wf / c->mb_used[1],
+        if ((rc = launch_forward_sched(c, c->mb_work.as<int>(), c->mb_rec, c->mb_rec2, c->mb_wbf.as<int>() + m.wf_off,
+                                       m.Wf / c->mb_used[1],
                                        c->mb_used[0], c->mb_used[1], c->mb_chunks.as<int>() + m.ck_off, m.n_ck)))
             break;
         TermsCall t;
@@ -295,7 +297,8 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
         t.nsv = host_nsv(c, hw, m.s0, m.s1);
         t.loss3 = loss3;
         if ((rc = launch_terms(c, t))) break;
-        if ((rc = launch_adjoint_sched(c, c->mb_work.as<int>(), c->mb_wba.as<int>() + m.wa_off, m.Wa / c->mb_used[3],
+        if ((rc = launch_adjoint_sched(c, c->mb_work.as<int>(), c->mb_rec, c->mb_rec2, c->mb_wba.as<int>() + m.wa_off,
+                                       m.Wa / c->mb_used[3],
                                        c->mb_used[2], c->mb_used[3], c->mb_chunks.as<int>() + m.ck_off, m.n_ck)))
             break;
         if ((rc = launch_ann_grad_chunks(c, c->mb_chunks.as<int>() + m.ck_off, m.n_ck))) break;

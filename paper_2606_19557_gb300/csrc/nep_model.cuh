@@ -122,25 +122,36 @@ __device__ __forceinline__ void load_row(const float *src, float *dst) {
 }
 
 // Batch of up to G = 32/SW consecutive work positions of one species, starting at `base`
-// (< wend): group g reads position base + g, so the loads of all groups are in flight
-// together.  Returns the species ti, the batch size nb and this group's atom i (the
-// batch's first atom for groups beyond nb).
+// (< wend): group g reads the work record of position base + g, so the loads of all groups
+// are one round trip together.  Returns the species ti, the batch size nb and this group's
+// atom with its pair range and structure (the batch's first atom, with no pairs, for
+// groups beyond nb).
+struct BatchAtom {
+    int ti, nb, i, beg, nRad, nAng, s;
+};
 template <int SW>
-__device__ __forceinline__ void load_batch(const AtomArgs &a, int base, int wend, int lane, int &ti, int &nb,
-                                           int &i) {
+__device__ __forceinline__ BatchAtom load_batch(const AtomArgs &a, int base, int wend, int lane) {
     constexpr int G = 32 / SW;
     const int grp = lane / SW;
     const int q = base + grp;
-    const int iq = (grp < G && q < wend) ? a.work[q] : -1;
-    const int tq = iq >= 0 ? a.type[iq] : -1;
-    ti = __shfl_sync(FULL, tq, 0);
-    const unsigned same = __ballot_sync(FULL, tq == ti);
+    const bool valid = grp < G && q < wend;
+    const int4 r = valid ? __ldg(a.rec + q) : make_int4(-1, 0, 0, 0);
+    const int2 r2 = valid ? __ldg(a.rec2 + q) : make_int2(-1, 0);
+    BatchAtom b;
+    b.ti = __shfl_sync(FULL, r2.x, 0);
+    const unsigned same = __ballot_sync(FULL, r2.x == b.ti);
     unsigned gm = 0;
 #pragma unroll
     for (int g = 0; g < G; ++g) gm |= ((same >> (g * SW)) & 1u) << g;
-    nb = min(G, __ffs(~gm) - 1);
-    const int i0 = __shfl_sync(FULL, iq, 0);
-    i = grp < nb ? iq : i0;
+    b.nb = min(G, __ffs(~gm) - 1);
+    const int i0 = __shfl_sync(FULL, r.x, 0), beg0 = __shfl_sync(FULL, r.y, 0), s0 = __shfl_sync(FULL, r2.y, 0);
+    const bool act = grp < b.nb;
+    b.i = act ? r.x : i0;
+    b.beg = act ? r.y : beg0;
+    b.nRad = act ? r.z : 0;
+    b.nAng = act ? r.w : 0;
+    b.s = act ? r2.y : s0;
+    return b;
 }
 
 // Reduce-scatter the V-vector of every group and add the totals of group `grp` into
@@ -437,24 +448,23 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_jvp(AtomArgs a) {
     const float *scale = a.par + po.scale;
 
     for (int bp = wbeg; bp < wend;) {
-        int ti, nb, i;
-        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
+        const BatchAtom ba = load_batch<SW>(a, bp, wend, lane);
+        const int ti = ba.ti, nb = ba.nb, i = ba.i;
         const bool act = grp < nb;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
         const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;
         const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;
-        const int s = a.struct_of[i];
-        const int64_t beg = a.nbr_off[i];
-        const int nRad = act ? (int)(a.nbr_off[i + 1] - beg) : 0;
-        const int nAng = act ? a.n_ang[i] : 0;
+        const int s = ba.s;
+        const int64_t beg = ba.beg;
+        const int nRad = ba.nRad;
+        const int nAng = ba.nAng;
         const int maxR = __reduce_max_sync(FULL, nRad);
         const int maxA = __reduce_max_sync(FULL, nAng);
         typename L::Atom &at = sm.at[grp];
         if (bp + grp < wend) {  // the atoms after this batch: bring their pair records into L2
-            const int ni = a.work[bp + grp];
-            const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
-            prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
+            const int4 nr = __ldg(a.rec + bp + grp);
+            prefetch_l2(a.pair + nr.y, sizeof(float4) * (size_t)nr.z, sl, SW);
         }
         load_lm_rows<NA, NAP, SW>(a.st_A + (size_t)wi * NA * L3, at.A, sl);
         const float4 *prs = a.pair + beg;
@@ -669,7 +679,7 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int rc0 = a.chunks[blockIdx.x], rc1 = a.chunks[blockIdx.x + 1];
     if (rc0 >= rc1) return;
-    const int t = a.type[a.work[rc0]];
+    const int t = __ldg(a.rec2 + rc0).x;
     const ParOff po = par_offsets(T, NN, S::NR, S::KR, S::NA, S::KA);
     const float *W0 = a.par + po.w0 + (size_t)t * NN * ND;
     const float *W0T = a.par + po.w0t + (size_t)t * ND * NN;
@@ -727,7 +737,7 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
                     const int r = r0 + x;
                     const bool row = r < nr;
                     const int wpos = rb + (row ? r : 0);
-                    const float eb = row ? a.ebar[a.struct_of[a.work[wpos]]] : 0.0f;
+                    const float eb = row ? a.ebar[__ldg(a.rec2 + wpos).y] : 0.0f;
 #pragma unroll
                     for (int y = 0; y < 4; ++y) {
                         const int mu = mu0 + y;
@@ -842,8 +852,8 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_cg(AtomArgs a) {
     };
 
     for (int bp = wbeg; bp < wend;) {
-        int ti, nb, i;
-        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
+        const BatchAtom ba = load_batch<SW>(a, bp, wend, lane);
+        const int ti = ba.ti, nb = ba.nb, i = ba.i;
         const bool act = grp < nb;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
@@ -858,14 +868,14 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_cg(AtomArgs a) {
             cur_t = ti;
             __syncwarp();
         }
-        const int s = a.struct_of[i];
-        const int64_t beg = a.nbr_off[i];
-        const int nAng = act ? a.n_ang[i] : 0;
+        const int s = ba.s;
+        const int64_t beg = ba.beg;
+        const int nAng = ba.nAng;
         const int maxA = __reduce_max_sync(FULL, nAng);
         typename L::Atom &at = sm.at[grp];
         if (bp + grp < wend) {  // the atoms after this batch: bring their angular records into L2
-            const int ni = a.work[bp + grp];
-            prefetch_l2(a.pair + a.nbr_off[ni], sizeof(float4) * (size_t)a.n_ang[ni], sl, SW);
+            const int4 nr = __ldg(a.rec + bp + grp);
+            prefetch_l2(a.pair + nr.y, sizeof(float4) * (size_t)nr.w, sl, SW);
         }
 
         // ---------------------------------------------------------------- state of the earlier stages
@@ -1076,23 +1086,22 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_desc(AtomArgs a) 
     const float *scale = a.par + po.scale;
 
     for (int bp = wbeg; bp < wend;) {
-        int ti, nb, i;
-        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
+        const BatchAtom ba = load_batch<SW>(a, bp, wend, lane);
+        const int ti = ba.ti, nb = ba.nb, i = ba.i;
         const bool act = grp < nb;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
         const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;  // [b][n][KR4]
         const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;  // [b][n][KA4]
-        const int64_t beg = a.nbr_off[i];
-        const int nRad = act ? (int)(a.nbr_off[i + 1] - beg) : 0;
-        const int nAng = act ? a.n_ang[i] : 0;
+        const int64_t beg = ba.beg;
+        const int nRad = ba.nRad;
+        const int nAng = ba.nAng;
         const int maxR = __reduce_max_sync(FULL, nRad);
         const int maxA = __reduce_max_sync(FULL, nAng);
         typename L::Atom &at = sm.at[grp];
         if (bp + grp < wend) {  // the atoms after this batch: bring their pair records into L2
-            const int ni = a.work[bp + grp];
-            const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
-            prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
+            const int4 nr = __ldg(a.rec + bp + grp);
+            prefetch_l2(a.pair + nr.y, sizeof(float4) * (size_t)nr.z, sl, SW);
         }
 
         // ---------------------------------------------------------------- angular moments A_nlm
@@ -1256,7 +1265,7 @@ __global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int rc0 = a.chunks[blockIdx.x], rc1 = a.chunks[blockIdx.x + 1];
     if (rc0 >= rc1) return;
-    const int t = a.type[a.work[rc0]];
+    const int t = __ldg(a.rec2 + rc0).x;
     const ParOff po = par_offsets(T, NN, S::NR, S::KR, S::NA, S::KA);
     const float *W0 = a.par + po.w0 + (size_t)t * NN * ND;
     const float *W0T = a.par + po.w0t + (size_t)t * ND * NN;
@@ -1398,21 +1407,20 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_pair(AtomArgs a) 
     const ParOff po = par_offsets(T, NN, NR, KR, NA, KA);
 
     for (int bp = wbeg; bp < wend;) {
-        int ti, nb, i;
-        load_batch<SW>(a, bp, wend, lane, ti, nb, i);
+        const BatchAtom ba = load_batch<SW>(a, bp, wend, lane);
+        const int ti = ba.ti, nb = ba.nb, i = ba.i;
         const bool act = grp < nb;
         const int wi = bp + (act ? grp : 0);
         bp += nb;
         const float *cRi = a.par + po.cRp + (size_t)ti * T * NR * KR4;
         const float *cAi = a.par + po.cAp + (size_t)ti * T * NA * KA4;
-        const int64_t beg = a.nbr_off[i];
-        const int nRad = act ? (int)(a.nbr_off[i + 1] - beg) : 0;
-        const int nAng = act ? a.n_ang[i] : 0;
+        const int64_t beg = ba.beg;
+        const int nRad = ba.nRad;
+        const int nAng = ba.nAng;
         typename L::Atom &at = sm.at[grp];
         if (bp + grp < wend) {  // the atoms after this batch: bring their pair records into L2
-            const int ni = a.work[bp + grp];
-            const int64_t nb0 = a.nbr_off[ni], nb1 = a.nbr_off[ni + 1];
-            prefetch_l2(a.pair + nb0, sizeof(float4) * (size_t)(nb1 - nb0), sl, SW);
+            const int4 nr = __ldg(a.rec + bp + grp);
+            prefetch_l2(a.pair + nr.y, sizeof(float4) * (size_t)nr.z, sl, SW);
         }
         load_lm_rows<NA, NAP, SW>(a.st_A + (size_t)wi * NA * L3, at.A, sl);
         gather_rows<ND, SW>(a.st_b + (size_t)wi * ND, sl, [&](int v, float x) { at.b[v] = x; });
