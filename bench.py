@@ -508,7 +508,11 @@ def run_ours(args):
     dist = None
     name = args.config
     # host work first: the batch, and the oracle leg (before any GPU work of this process)
-    spec, batch = build_workload(name, rank)
+    if args.stride > 1:  # a profiling cut: every stride-th structure of the workload
+        n_all = {"scale_t5": 20000, "alloy_t4": 5000, "fcc_bcc_t1": 1000}[name]
+        spec, batch = build_workload(name, rank, only=list(range(0, n_all, args.stride)))
+    else:
+        spec, batch = build_workload(name, rank)
     cb, ref = cpu_baseline(name, args.sample_structures) if (rank == 0 and ws == 1 and args.cpu_sample) \
         else (None, None)
     torch.cuda.set_device(local)
@@ -625,6 +629,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     cfg = config_block(name)
+    if args.stride > 1:
+        cfg["workload"] += f"; profiling cut: every {args.stride}th structure only"
     cfg.update({"structures_per_gpu": batch.n_struct, "atoms_per_gpu": batch.n_atoms, "radial_pairs": n_rad,
                 "angular_pairs": n_ang, "launch_shape": list(shape), "kernel_variant": variant,
                 "neighbor_build_ms": 1e3 * t_nbr, "neighbor_rebuild_ms": t_rebuild})
@@ -677,6 +683,8 @@ def main():
     ap.add_argument("--mb-size", dest="mb_size", type=int, default=16)
     ap.add_argument("--md-steps", dest="md_steps", type=int, default=5)
     ap.add_argument("--launch", default="", help="fixed kernel variants and shape: fv,av,fwarps,fblocks,awarps,ablocks")
+    ap.add_argument("--stride", type=int, default=1,
+                    help="profiling cut: only every stride-th structure of the headline workload (1: all)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
