@@ -77,7 +77,15 @@ def build_workload(name: str, rank: int, only=None):
 # shape, scaled to a launch by its atoms.  Valid only for the kernel sources with the
 # recorded SHA-256; otherwise the bench reports null.
 KERNEL_SOURCES = ("paper_2606_19557_gb300/csrc/nep_model.cuh", "paper_2606_19557_gb300/csrc/nep_internal.cuh")
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --set full on every 50th structure of the headline workload (131,591 atoms, 71.6
+    # radial pairs per atom against 71.4 in the full batch), launch 0,2,4,608,1,2128
+    "scale_t5": {
+        "sha256": "3c597117db6f0d3a5c8448ba979d97083286a2cf32a4a6b550cde76290a915ab",
+        "bytes_per_atom": {"forward_desc": 1817.2, "forward_pair": 3279.9, "adjoint_jvp": 2974.4,
+                           "adjoint_cgrad": 2683.1},
+    },
+}
 
 
 def kernel_traffic(workload: str, kernel: str, n_atoms: int):

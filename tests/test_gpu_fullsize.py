@@ -4,9 +4,11 @@ bench times (autotuned shape).
 Structures are independent, so a structure's E_s, F_i and W_s come out of the full batched
 pass exactly as from that structure alone: sampled structures are checked one by one
 against the FP64 oracle.  The loss and gradient are checked against the oracle on the whole
-1000-structure batch (seconds of oracle time), and at the larger sizes through a property
-that holds at any size: the batch's gradient equals the sum over two shards evaluated with
-the batch's normalisers, with each shard's own parity covered by the smaller tests.
+1000-structure batch (seconds of oracle time).  At the larger sizes the gradient is checked
+twice: against the oracle, block by block, through the full-batch adjoint with the
+cotangents restricted to a sample of structures (including a 10,000-atom cell), and through
+a property that holds at any size: the batch's gradient equals the sum over two shards
+evaluated with the batch's normalisers.
 """
 import numpy as np
 import pytest
@@ -54,6 +56,27 @@ def _check_sampled_structures(spec, theta, qs, nep, batch, idx):
     assert np.max(np.abs(F[a_idx] - Fo)) * 1e3 < 1.0       # meV/A
 
 
+def _subset_backward(spec, theta, qs, nep, batch, idx, seed):
+    """The full-batch adjoint (every kernel path the full size reaches: warp ranges spanning
+    species runs, per-warp partial slots, the reduction's row groups) with the cotangents
+    dE, dF, dW zero outside the structures idx.  Structures are independent, so the result
+    is the gradient of those structures alone, which the oracle computes on the subset."""
+    rng = np.random.default_rng(seed)
+    off = batch.atom_off
+    dE = np.zeros(batch.n_struct)
+    dF = np.zeros((batch.n_atoms, 3), np.float32)
+    dW = np.zeros((batch.n_struct, 9))
+    for s in idx:
+        dE[s] = rng.normal()
+        dF[off[s]:off[s + 1]] = rng.normal(size=(off[s + 1] - off[s], 3)).astype(np.float32)
+        dW[s] = rng.normal(size=9)
+    nep.eval()
+    g = nep.backward(dE, dF, dW).cpu().numpy()
+    a_idx = np.concatenate([np.arange(off[s], off[s + 1]) for s in idx])
+    go = oracle.backward(spec, theta, qs, batch.subset(idx), dE[idx], dF[a_idx].astype(np.float64), dW[idx])
+    assert_grad_close(g, go, spec, TOL)
+
+
 def _shard_sum_property(spec, theta, qs, nep, batch, Er, Fr, Wr, lam):
     from paper_2606_19557_gb300 import NEP, shard
     l3, g = nep.loss_grad(Er, Fr, Wr, None, lam)
@@ -96,7 +119,9 @@ def test_alloy_5000_structures():
     b = synth.batch_alloy(seed=3, n_struct=5000)
     spec, theta, qs, nep = _setup("alloy_t4", b, 3, qs_sample=np.arange(0, 5000, 25))
     rng = np.random.default_rng(1)
-    _check_sampled_structures(spec, theta, qs, nep, b, np.sort(rng.choice(5000, 25, replace=False)))
+    idx = np.sort(rng.choice(5000, 25, replace=False))
+    _check_sampled_structures(spec, theta, qs, nep, b, idx)
+    _subset_backward(spec, theta, qs, nep, b, idx, 40)
     Er, Fr, Wr = synth.random_targets(b, 4)
     _shard_sum_property(spec, theta, qs, nep, b, Er, Fr, Wr, (1.0, 2.0, 0.3))
 
@@ -104,10 +129,11 @@ def test_alloy_5000_structures():
 def test_scale_20000_structures_and_10000_atom_cells():
     """5 species, 20,000 structures of 2-2000 atoms plus ten 10,000-atom cells, 4- and
     5-body terms, 50 neurons."""
-    b = synth.batch_scale(seed=5, n_struct=20000, n_big=10)
+    b = synth.batch_scale(seed=5, n_struct=20000, n_big=10, workers=8)
     spec, theta, qs, nep = _setup("scale_t5", b, 5, qs_sample=np.arange(0, 20000, 100))
     rng = np.random.default_rng(2)
     idx = np.concatenate([np.sort(rng.choice(20000, 20, replace=False)), [20000 + int(rng.integers(10))]])
     _check_sampled_structures(spec, theta, qs, nep, b, idx)
+    _subset_backward(spec, theta, qs, nep, b, idx, 50)
     Er, Fr, Wr = synth.random_targets(b, 6)
     _shard_sum_property(spec, theta, qs, nep, b, Er, Fr, Wr, (1.0, 1.0, 0.1))
