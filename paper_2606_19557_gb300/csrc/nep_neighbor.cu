@@ -208,9 +208,9 @@ __global__ void k_atom_bin(int64_t na, const float *pos, const int *type, int T,
                            int64_t *bin_cnt, float4 *pos4, int *err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= na) return;
-    pos4[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], 0.0f);
     const int t = type[i];
     if (t < 0 || t >= T) atomic_err(err, 3);
+    pos4[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], __int_as_float(t & 15));
     const int s = struct_of[i];
     const SGeom &g = geom[s];
     const double p[3] = {(double)pos[3 * i], (double)pos[3 * i + 1], (double)pos[3 * i + 2]};
@@ -247,15 +247,15 @@ __global__ void k_bin_fill(int64_t na, const int64_t *atom_bin, const int64_t *b
     bin_atoms[bin_start[bin] + slot] = (int)i;
 }
 
-// The atoms of every bin in bin order: (x, y, z, bits(j)) and the wrap offsets, so that the
-// lanes scanning a bin read consecutive entries.
+// The atoms of every bin in bin order: (x, y, z, bits(j << 4 | t_j)) and the wrap offsets,
+// so that the lanes scanning a bin read consecutive entries and no species table.
 __global__ void k_bin_pack(int64_t na, const int *bin_atoms, const float4 *pos4, const int4 *atom_wrap,
                            float4 *bin_pos, int4 *bin_wrap) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= na) return;
     const int j = bin_atoms[t];
     const float4 p = pos4[j];
-    bin_pos[t] = make_float4(p.x, p.y, p.z, __int_as_float(j));
+    bin_pos[t] = make_float4(p.x, p.y, p.z, __int_as_float((j << 4) | __float_as_int(p.w)));
     bin_wrap[t] = atom_wrap[j];
 }
 
@@ -365,7 +365,7 @@ __device__ __forceinline__ uint32_t pack_shift(int Sa, int Sb, int Sc) {
     return ((uint32_t)(Sa + 128) << 16) | ((uint32_t)(Sb + 128) << 8) | (uint32_t)(Sc + 128);
 }
 
-// Warp-cooperative candidate scan of atom i (one warp per atom).  Calls hit(j, Sa, Sb, Sc, ang)
+// Warp-cooperative candidate scan of atom i (one warp per atom).  Calls hit(j, t_j, Sa, Sb, Sc, ang)
 // for every pair within rcR (ang: also within rcA), from any lane, in no particular order
 // (the lists are sorted afterwards).  Two ways to enumerate candidates, chosen per structure:
 //   * a structure held in one bin per axis (a cell narrower than 2 rc): the lanes take the
@@ -392,7 +392,7 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
     const float *pi = pos + 3 * i;
     const float hf[9] = {(float)g.h[0], (float)g.h[1], (float)g.h[2], (float)g.h[3], (float)g.h[4],
                          (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
-    auto test = [&](int j, int Sa, int Sb, int Sc, float4 pj4) {
+    auto test = [&](int j, int tj, int Sa, int Sb, int Sc, float4 pj4) {
         if (j == (int)i && Sa == 0 && Sb == 0 && Sc == 0) return;
         const float fa = (float)Sa, fb = (float)Sb, fc = (float)Sc;
         float q[3], B[3];
@@ -427,7 +427,7 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
             inR = r2 < rc2R;
             inA = r2 < rc2A;
         }
-        if (inR) hit(j, Sa, Sb, Sc, inA);
+        if (inR) hit(j, tj, Sa, Sb, Sc, inA);
     };
     if (g.n[0] == 1 && g.n[1] == 1 && g.n[2] == 1) {
         // Image box of each candidate j in FP32, widened by more than the FP32 rounding of
@@ -464,7 +464,7 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
             }
             for (int Sa = lo[0]; Sa <= hi[0]; ++Sa)
                 for (int Sb = lo[1]; Sb <= hi[1]; ++Sb)
-                    for (int Sc = lo[2]; Sc <= hi[2]; ++Sc) test((int)j, Sa, Sb, Sc, pj);
+                    for (int Sc = lo[2]; Sc <= hi[2]; ++Sc) test((int)j, __float_as_int(pj.w), Sa, Sb, Sc, pj);
         }
         return;
     }
@@ -479,16 +479,21 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
             int bb = bi[1] + db;
             const int sb = (bb >= 0) ? bb / g.n[1] : -((-bb + g.n[1] - 1) / g.n[1]);
             bb -= sb * g.n[1];
-            for (int dc = -g.m[2]; dc <= g.m[2]; ++dc) {
+            // the bins along c in runs of consecutive bins with one shift: their atoms are
+            // consecutive in bin order, so the lanes take each run as one range
+            for (int dc = -g.m[2]; dc <= g.m[2];) {
                 int bc = bi[2] + dc;
                 const int sc = (bc >= 0) ? bc / g.n[2] : -((-bc + g.n[2] - 1) / g.n[2]);
                 bc -= sc * g.n[2];
+                const int run = min(g.m[2] - dc, g.n[2] - 1 - bc);  // further bins in this run
                 const int64_t bin = bin_off[s] + ((int64_t)ba * g.n[1] + bb) * g.n[2] + bc;
-                for (int64_t t = bin_start[bin] + lane; t < bin_start[bin + 1]; t += 32) {
-                    const float4 bp = bin_pos[t];  // the bin's atoms in bin order: coalesced
+                for (int64_t t = bin_start[bin] + lane; t < bin_start[bin + run + 1]; t += 32) {
+                    const float4 bp = bin_pos[t];  // the bins' atoms in bin order: coalesced
                     const int4 wj = bin_wrap[t];
-                    test(__float_as_int(bp.w), sa + wi.x - wj.x, sb + wi.y - wj.y, sc + wi.z - wj.z, bp);
+                    const int jt = __float_as_int(bp.w);
+                    test(jt >> 4, jt & 15, sa + wi.x - wj.x, sb + wi.y - wj.y, sc + wi.z - wj.z, bp);
                 }
+                dc += run + 1;
             }
         }
     }
@@ -502,7 +507,7 @@ __device__ __forceinline__ uint64_t pair_key(bool ang, int tj, int j, int Sa, in
 // Pair counts per atom (one warp per atom), and the sort keys of the first `cap` pairs
 // of each atom in scratch[i * cap ...] (unordered): when no atom has more, the keys need
 // no second scan.  *overflow is set when some atom has more than cap pairs.
-__global__ void __launch_bounds__(256, 4) k_count_w(int64_t na, const float *pos, const float4 *pos4, const int *type, const int *struct_of,
+__global__ void __launch_bounds__(256, 4) k_count_w(int64_t na, const float *pos, const float4 *pos4, const int *struct_of,
                           const int64_t *atom_off, const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin,
                           const int4 *atom_wrap, const int64_t *bin_start, const float4 *bin_pos,
                           const int4 *bin_wrap, float rc2R,
@@ -517,9 +522,9 @@ __global__ void __launch_bounds__(256, 4) k_count_w(int64_t na, const float *pos
     int nang = 0;
     uint64_t *dst = scratch + i * (int64_t)cap;
     scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_pos, bin_wrap,
-                   rc2R, rc2A, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, bool ang) {
+                   rc2R, rc2A, rcq * rcq, rcq, err, [&](int j, int tj, int Sa, int Sb, int Sc, bool ang) {
                        const int k = atomicAdd(&slot[wib], 1);
-                       if (k < cap) dst[k] = pair_key(ang, type[j], j, Sa, Sb, Sc);
+                       if (k < cap) dst[k] = pair_key(ang, tj, j, Sa, Sb, Sc);
                        if (ang) ++nang;
                    });
     nang = __reduce_add_sync(FULL, nang);
@@ -533,7 +538,7 @@ __global__ void __launch_bounds__(256, 4) k_count_w(int64_t na, const float *pos
 }
 
 // Sort keys of every pair (one warp per atom); slots taken through a shared counter.
-__global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const int *type, const int *struct_of,
+__global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const int *struct_of,
                          const int64_t *atom_off,
                          const SGeom *geom, const int64_t *bin_off, const int64_t *atom_bin, const int4 *atom_wrap,
                          const int64_t *bin_start, const float4 *bin_pos, const int4 *bin_wrap, float rc2R,
@@ -547,9 +552,9 @@ __global__ void k_fill_w(int64_t na, const float *pos, const float4 *pos4, const
     __syncwarp();
     const int64_t o = nbr_off[i], n = nbr_off[i + 1] - o;
     scan_atom_warp(i, lane, pos, pos4, struct_of, atom_off, geom, bin_off, atom_bin, atom_wrap, bin_start, bin_pos, bin_wrap,
-                   rc2R, rc2A, rcq * rcq, rcq, err, [&](int j, int Sa, int Sb, int Sc, bool ang) {
+                   rc2R, rc2A, rcq * rcq, rcq, err, [&](int j, int tj, int Sa, int Sb, int Sc, bool ang) {
                        const int k = atomicAdd(&slot[wib], 1);
-                       if (k < n) keys[o + k] = pair_key(ang, type[j], j, Sa, Sb, Sc);
+                       if (k < n) keys[o + k] = pair_key(ang, tj, j, Sa, Sb, Sc);
                    });
     __syncwarp();
     if (lane == 0 && slot[wib] != n) atomic_err(err, 5);
@@ -796,7 +801,7 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
         k_bin_pack<<<gA, 256, 0, st>>>(na, c->bin_atoms.as<int>(), c->pos4.as<float4>(),
                                        (const int4 *)c->atom_wrap.ptr, c->bin_pos.as<float4>(),
                                        (int4 *)c->bin_wrap.ptr);
-        k_count_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(), c->type.as<int>(),
+        k_count_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(),
                                       c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
                                       c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
                                       (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
@@ -824,7 +829,7 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
     c->n_pairs = M;
     if (na > 0) {
         if (overflow)  // some atom has more than `cap` pairs: a second scan writes the keys
-            k_fill_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(), c->type.as<int>(),
+            k_fill_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(),
                                          c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
                                          c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
                                          (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
