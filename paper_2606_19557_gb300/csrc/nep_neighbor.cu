@@ -693,21 +693,27 @@ __global__ void k_sort_decode(int64_t na, const uint64_t *keys_in, const uint64_
     }
 }
 
-// One thread per pair: index of (j, i, -S) in j's sorted list.
+// Reverse-pair index, one thread per pair (the lanes of a warp over one atom's list).  Each
+// unordered pair {(i, j, S), (j, i, -S)} is searched once, from the entry with i < j (or,
+// for an atom's own images, the larger packed shift): a binary search of j's sorted keys,
+// then rev set on both entries and the displacements checked for antisymmetry.  Every found pair adds one to *found; the host checks 2 found == M, so an
+// entry without a partner cannot pass unnoticed.
 __global__ void k_reverse(int64_t na, const int64_t *nbr_off, const uint64_t *keys, const int *type, int *rev,
-                          const float4 *pair, int *err) {
+                          const float4 *pair, unsigned long long *found, int *err) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= na) return;
     const int64_t beg = nbr_off[i], end = nbr_off[i + 1];
     const int ti = type[i];
+    unsigned nf = 0;
     for (int64_t p = beg + lane; p < end; p += 32) {
         const uint64_t k = keys[p];
         const int j = (int)((k >> 24) & ((1ull << 35) - 1));
         const uint32_t sp = (uint32_t)(k & 0xffffffull);
         const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
-        const uint64_t want = (k & (1ull << 63)) | ((uint64_t)ti << 59) | ((uint64_t)i << 24) |
-                              (uint64_t)pack_shift(-Sa, -Sb, -Sc);
+        const uint32_t spn = pack_shift(-Sa, -Sb, -Sc);
+        if (!(j > (int)i || (j == (int)i && sp > spn))) continue;  // the partner's entry searches
+        const uint64_t want = (k & (1ull << 63)) | ((uint64_t)ti << 59) | ((uint64_t)i << 24) | (uint64_t)spn;
         int64_t lo = nbr_off[j], hi = nbr_off[j + 1];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
@@ -716,13 +722,16 @@ __global__ void k_reverse(int64_t na, const int64_t *nbr_off, const uint64_t *ke
         }
         if (lo >= nbr_off[j + 1] || keys[lo] != want) {
             atomic_err(err, 6);
-            rev[p] = (int)p;
             continue;
         }
         rev[p] = (int)lo;
+        rev[lo] = (int)p;
+        ++nf;
         const float4 a = pair[p], b = pair[lo];
         if (a.x != -b.x || a.y != -b.y || a.z != -b.z) atomic_err(err, 7);
     }
+    nf = __reduce_add_sync(FULL, nf);
+    if (lane == 0 && nf) atomicAdd(found, (unsigned long long)nf);
 }
 
 // out += sum of v[0..n) (integer atomics: the total does not depend on the order)
@@ -745,7 +754,7 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
     int *err = c->d_err.as<int>();
     CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     if (c->geom.ensure_bytes(sizeof(SGeom) * (size_t)(ns > 0 ? ns : 1)) || c->nbins.ensure<int64_t>(ns + 1) ||
-        c->bin_off.ensure<int64_t>(ns + 1) || c->d_total.ensure<int64_t>(4))
+        c->bin_off.ensure<int64_t>(ns + 1) || c->d_total.ensure<int64_t>(6))
         return c->fail(NEP_ENOMEM, "geometry buffers");
     SGeom *geom = (SGeom *)c->geom.ptr;
     int rc = 0, herr = 0;
@@ -842,20 +851,26 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
                                           c->nbr_off.as<int64_t>(),
                                           c->pos.as<float>(), c->struct_of.as<int>(), geom, c->keys.as<uint64_t>(),
                                           (float4 *)c->pair.ptr, c->shift.as<int32_t>());
+    }
+    // found reverse pairs and the angular pair count (integer sums: exact in any order)
+    int64_t *found_dev = c->d_total.as<int64_t>() + 4;
+    int64_t *nang_dev = c->d_total.as<int64_t>() + 5;
+    CK(cudaMemsetAsync(found_dev, 0, 2 * sizeof(int64_t), st));
+    if (na > 0) {
+        const unsigned gw = (unsigned)((na * 32 + 255) / 256);
         k_reverse<<<gw, 256, 0, st>>>(na, c->nbr_off.as<int64_t>(), c->keys.as<uint64_t>(), c->type.as<int>(),
-                                      c->rev.as<int>(), (const float4 *)c->pair.ptr, err);
+                                      c->rev.as<int>(), (const float4 *)c->pair.ptr,
+                                      (unsigned long long *)found_dev, err);
         CK(cudaGetLastError());
     }
-    // angular pair count (an integer sum: exact in any order)
-    int64_t *nang_dev = c->d_total.as<int64_t>() + 3;
-    CK(cudaMemsetAsync(nang_dev, 0, sizeof(int64_t), st));
     if (na > 0) k_sum_int<<<(unsigned)std::min<int64_t>((na + 255) / 256, 1024), 256, 0, st>>>(na, c->n_ang.as<int>(), nang_dev);
     CK(cudaGetLastError());
-    int64_t nang_total = 0;
-    CK(cudaMemcpyAsync(&nang_total, nang_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    int64_t fin[2] = {0, 0};  // found reverse pairs, angular pairs
+    CK(cudaMemcpyAsync(fin, found_dev, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (herr) return c->fail(NEP_EINTERNAL, "neighbour list is not symmetric");
+    if (herr || 2 * fin[0] != M) return c->fail(NEP_EINTERNAL, "neighbour list is not symmetric");
+    const int64_t nang_total = fin[1];
     c->n_pairs_ang = nang_total;
     c->h_lists_ok = false;
     return host_lists ? fetch_host_lists(c) : NEP_OK;
