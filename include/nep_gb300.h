@@ -120,11 +120,23 @@ int nep_set_structures(nep_ctx *ctx, int64_t n_struct, const int64_t *atom_off_d
  * launch shapes, so every later result equals that of a fresh context on the new
  * geometry, bit for bit.  Without mini-batches the schedules are built on the device;
  * with them (nep_minibatch_setup) the group schedules are rebuilt on the host.
- * Synchronizes with the list build; the schedule kernels are queued on the context's
- * stream after it.  Errors: NEP_ESTATE (no batch), NEP_EINVAL (bad geometry: the batch
- * is then unusable, and later calls return NEP_ESTATE, until nep_set_structures),
- * NEP_ENOMEM, NEP_ECUDA. */
+ * With the cells kept and a nonzero skin (nep_set_skin) the lists come from candidate
+ * lists: every pair within r_c^R + skin of the positions at the last candidate scan.
+ * While no atom has moved half the skin from those positions, the lists are the
+ * candidates that pass the pair predicate at the new positions (a filter, no scan); the
+ * filter keeps the scan's order, so the lists are the scan's, bit for bit.  Otherwise
+ * the candidates are rebuilt first.  The candidate lists take about 17 bytes per
+ * candidate pair.  Synchronizes with the list build; the schedule kernels are queued on
+ * the context's stream after it.  Errors: NEP_ESTATE (no batch), NEP_EINVAL (bad
+ * geometry: the batch is then unusable, and later calls return NEP_ESTATE, until
+ * nep_set_structures), NEP_ENOMEM, NEP_ECUDA. */
 int nep_update_positions(nep_ctx *ctx, const float *pos_dev, const float *cell_dev);
+
+/* Skin (Angstrom, in [0, 10]; default 0.5) of the candidate lists of nep_update_positions
+ * with the cells kept; 0 scans on every update.  The paper keeps neighbour lists on the
+ * GPU (Sec. "Training efficiency"); the skin is this implementation's way to refresh them
+ * between MD-style steps.  Errors: NEP_EINVAL. */
+int nep_set_skin(nep_ctx *ctx, float skin);
 
 /* Radial and angular neighbour-pair counts of the cached batch. */
 int nep_num_pairs(const nep_ctx *ctx, int64_t *n_radial, int64_t *n_angular);

@@ -85,6 +85,7 @@ def load_library():
             "nep_set_structures": (I, [P, I64, P, P, P, P]),
             "nep_num_pairs": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
             "nep_update_positions": (I, [P, P, P]),
+            "nep_set_skin": (I, [P, ctypes.c_float]),
             "nep_get_neighbors": (I, [P, P, P, P, P]),
             "nep_eval": (I, [P, P, P, P]),
             "nep_descriptors": (I, [P, P]),
@@ -234,6 +235,10 @@ class NEP:
         if p.numel() != 3 * self.n_atoms or (cl is not None and cl.numel() != 9 * self.n_struct):
             raise ValueError("positions [N_a, 3] and cells [n_struct, 9] of the cached batch expected")
         self._call(self.lib.nep_update_positions, _ptr(p), _ptr(cl))
+
+    def set_skin(self, skin: float):
+        """Skin (Angstrom) of the candidate lists behind update_positions with the cells kept; 0 scans every time."""
+        self._call(self.lib.nep_set_skin, float(skin))
 
     def num_pairs(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()

@@ -570,8 +570,25 @@ int nep_update_positions(nep_ctx *c, const float *pos, const float *cell) {
     c->state_valid = false;
     // the mini-batch schedules are built on the host from host copies of the lists
     const bool host_lists = c->mb_B > 0;
-    int rc = build_neighbors(c, cell == nullptr, host_lists);
-    if (rc) return rc;
+    int rc = NEP_OK;
+    bool done = false;
+    if (!cell && c->skin > 0.0f) {  // cells kept: filter the candidate lists (rescan when stale)
+        bool far = true;
+        if (c->cand_ok && (rc = filter_candidates(c, host_lists, far))) return rc;
+        if (!far) {
+            done = true;
+        } else if ((rc = build_candidates(c)) == NEP_OK) {
+            if ((rc = filter_candidates(c, host_lists, far))) return rc;
+            if (far) return c->fail(NEP_EINTERNAL, "candidate filter after a fresh scan");
+            done = true;
+        } else if (rc != NEP_EINVAL) {
+            return rc;
+        }
+        // NEP_EINVAL: cells too thin for the wider cutoff (or bad positions, which the scan
+        // below reports): this context scans from now on
+        if (!done) c->skin = 0.0f;
+    }
+    if (!done && (rc = build_neighbors(c, cell == nullptr, host_lists))) return rc;
     if (c->G.ensure_bytes(sizeof(float4) * (size_t)(c->n_pairs + 1))) return c->fail(NEP_ENOMEM, "pair gradients");
     if ((rc = build_work_rec(c, c->work.as<int>(), c->rec, c->rec2))) return rc;  // new pair ranges
     // re-balance the kernel schedules for the new neighbour counts (same sizes, same
@@ -587,6 +604,14 @@ int nep_update_positions(nep_ctx *c, const float *pos, const float *cell) {
     if (!std::equal(before, before + 5, after)) drop_graphs(c);  // graphs hold the old addresses
     c->plain_ready = false;
     c->have_batch = true;
+    return NEP_OK;
+}
+
+int nep_set_skin(nep_ctx *c, float skin) {
+    if (!c) return NEP_EINVAL;
+    if (!(skin >= 0.0f) || !(skin <= 10.0f)) return c->fail(NEP_EINVAL, "skin must be in [0, 10] Angstrom");
+    c->skin = skin;
+    c->cand_ok = c->cgeom_ok = false;
     return NEP_OK;
 }
 

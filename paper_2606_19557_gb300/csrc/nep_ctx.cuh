@@ -126,6 +126,12 @@ struct Ctx {
     DevBuf bin_pos, bin_wrap;          // atoms in bin order: (x, y, z, bits(j)) and wrap offsets
     int64_t nbin_total = 0;            // bins of the current cells
     bool geom_ok = false;              // geom / nbins / bin_off / struct_of hold the current cells
+    // candidate lists for position updates with the cells kept (pairs within r_c + skin of
+    // the reference positions cand_ref); grid for the wider cutoff in cgeom / cnbins / cbin_off
+    float skin = 0.5f;                 // Angstrom; 0: every position update scans
+    bool cand_ok = false, cgeom_ok = false;
+    int64_t cand_M = 0, cnbin_total = 0;
+    DevBuf cgeom, cnbins, cbin_off, cand_off, cand_key, cand_rev, cand_pidx, cand_flag, cand_ref;
 
     // schedule
     DevBuf work;                 // [Na] atom per work position (species-sorted)
@@ -239,6 +245,10 @@ int scan_exclusive(Ctx *c, const int64_t *in, int64_t n, int64_t *out, int64_t *
 // same_cells: the cells are those of the previous successful build (geometry kept);
 // host_lists: copy the per-atom counts and offsets to h_nang / h_nbr_off.
 int build_neighbors(Ctx *c, bool same_cells = false, bool host_lists = true);
+// candidate lists (nep_neighbor.cu): build at the current positions, and the exact lists
+// from them; moved_too_far: some atom moved half the skin or more (nothing valid written)
+int build_candidates(Ctx *c);
+int filter_candidates(Ctx *c, bool host_lists, bool &moved_too_far);
 int fetch_host_lists(Ctx *c);
 
 // step pieces (nep_loss.cu)

@@ -18,6 +18,8 @@
 // Negating S negates every operation exactly, so d(j,i,-S) = -d(i,j,S) bit for bit
 // and the radial/angular lists are symmetric.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "nep_ctx.cuh"
@@ -586,12 +588,10 @@ __device__ __forceinline__ void pair_d0(const float *pi, const float *pj, const 
     }
 }
 
-// Pair record of key k from the predicate's displacement.
-__device__ __forceinline__ void emit_pair(uint64_t k, int64_t slot, int64_t i, const float *pos, const SGeom &g,
-                                          uint64_t *keys_out, float4 *pair, int32_t *shift) {
+// The predicate's displacement (c7's float) of the pair of key k from atom i.
+__device__ __forceinline__ void decode_key(uint64_t k, int64_t i, const float *pos, const SGeom &g, float *d32) {
     const int j = (int)((k >> 24) & ((1ull << 35) - 1));
     const uint32_t sp = (uint32_t)(k & 0xffffffull);
-    float d32[3];
     if (sp == SHIFT0) {
         pair_d0(pos + 3 * i, pos + 3 * j, g.h, d32);
     } else {
@@ -600,6 +600,13 @@ __device__ __forceinline__ void emit_pair(uint64_t k, int64_t slot, int64_t i, c
                              (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
         if (!pair_d_fp32(pos + 3 * i, pos + 3 * j, hf, Sa, Sb, Sc, d32)) pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
     }
+}
+
+// Pair record of key k from the predicate's displacement.
+__device__ __forceinline__ void emit_pair(uint64_t k, int64_t slot, int64_t i, const float *pos, const SGeom &g,
+                                          uint64_t *keys_out, float4 *pair, int32_t *shift) {
+    float d32[3];
+    decode_key(k, i, pos, g, d32);
     store_pair(k, slot, d32, keys_out, pair, shift);
 }
 
@@ -727,11 +734,134 @@ __global__ void k_reverse(int64_t na, const int64_t *nbr_off, const uint64_t *ke
         rev[p] = (int)lo;
         rev[lo] = (int)p;
         ++nf;
-        const float4 a = pair[p], b = pair[lo];
-        if (a.x != -b.x || a.y != -b.y || a.z != -b.z) atomic_err(err, 7);
+        if (pair) {  // candidate lists carry no records
+            const float4 a = pair[p], b = pair[lo];
+            if (a.x != -b.x || a.y != -b.y || a.z != -b.z) atomic_err(err, 7);
+        }
     }
     nf = __reduce_add_sync(FULL, nf);
     if (lane == 0 && nf) atomicAdd(found, (unsigned long long)nf);
+}
+
+// Candidate keys of each atom in ascending order (one warp per atom, rank sort).
+__global__ void k_sort_keys(int64_t na, const uint64_t *keys_in, const uint64_t *scratch, int cap,
+                            const int64_t *off, uint64_t *keys_out) {
+    constexpr int STAGE = 256;  // keys per warp staged in shared memory
+    __shared__ __align__(16) uint64_t sk[8][STAGE];
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (i >= na) return;
+    const int64_t beg = off[i], n = off[i + 1] - beg;
+    const uint64_t *src = scratch ? scratch + i * (int64_t)cap : keys_in + beg;
+    if (n <= STAGE) {
+        uint64_t *s = sk[wib];
+        for (int64_t e = lane; e < n; e += 32) s[e] = src[e];
+        __syncwarp();
+        for (int64_t e = lane; e < n; e += 32) {
+            const uint64_t k = s[e];
+            int rank = 0;
+            for (int e2 = 0; e2 < (int)n; ++e2) rank += s[e2] < k ? 1 : 0;
+            keys_out[beg + rank] = k;
+        }
+        return;
+    }
+    for (int64_t e = lane; e < n; e += 32) {
+        const uint64_t k = src[e];
+        int64_t rank = 0;
+        for (int64_t e2 = 0; e2 < n; ++e2) rank += (src[e2] < k) ? 1 : 0;
+        keys_out[beg + rank] = k;
+    }
+}
+
+// max_i |p_i - r_i|^2 in FP64 (as the bits of a non-negative double: integer order).
+__global__ void k_max_disp(int64_t na, const float *pos, const float *ref, unsigned long long *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double d2 = 0.0;
+    if (i < na) {
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            const double d = (double)pos[3 * i + x] - (double)ref[3 * i + x];
+            d2 += d * d;
+        }
+        if (!(d2 <= 1e30)) d2 = 1e30;  // a non-finite position: the scan rejects it
+    }
+    unsigned long long b = (unsigned long long)__double_as_longlong(d2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(FULL, b, o);
+        b = y > b ? y : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, b);
+}
+
+// Candidate filter, one warp per atom.  Pass 1 (WRITE = false): the pair predicate (c7) of
+// every candidate at the current positions, as flags (bit 0 within r_c^R, bit 1 within
+// r_c^A), and the atom's radial and angular counts.  Pass 2: the pair records of the kept
+// candidates at their list positions (angular ones first, each group in candidate order)
+// and each candidate's position (pidx, -1 if dropped).
+template <bool WRITE>
+__global__ void k_filter(int64_t na, const int64_t *coff, const uint64_t *ckey, const float *pos,
+                         const int *struct_of, const SGeom *geom, float rc2R, float rc2A, uint8_t *cflag,
+                         int64_t *cnt, int *n_ang, const int64_t *nbr_off, float4 *pair, int32_t *shift,
+                         int *pidx) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= na) return;
+    const int64_t beg = coff[i], n = coff[i + 1] - beg;
+    const SGeom &g = geom[struct_of[i]];
+    if (!WRITE) {
+        int nr = 0, nang = 0;
+        for (int64_t e = lane; e < n; e += 32) {
+            float d32[3];
+            decode_key(ckey[beg + e], i, pos, g, d32);
+            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(d32[0], d32[0]), __fmul_rn(d32[1], d32[1])),
+                                       __fmul_rn(d32[2], d32[2]));
+            const bool inR = r2 < rc2R, inA = r2 < rc2A;
+            cflag[beg + e] = (uint8_t)((inR ? 1 : 0) | (inA ? 2 : 0));
+            nr += inR ? 1 : 0;
+            nang += inA ? 1 : 0;
+        }
+        nr = __reduce_add_sync(FULL, nr);
+        nang = __reduce_add_sync(FULL, nang);
+        if (lane == 0) {
+            cnt[i] = nr;
+            n_ang[i] = nang;
+        }
+        return;
+    }
+    const int64_t pbeg = nbr_off[i];
+    const int nA = n_ang[i];
+    int ca = 0, cr = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t e0 = 0; e0 < n; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const int f = e < n ? cflag[beg + e] : 0;
+        const bool isA = (f & 2) != 0, isR = (f & 1) != 0 && !isA;
+        const unsigned mA = __ballot_sync(FULL, isA), mR = __ballot_sync(FULL, isR);
+        int64_t slot = -1;
+        if (isA) slot = pbeg + ca + __popc(mA & below);
+        else if (isR) slot = pbeg + nA + cr + __popc(mR & below);
+        if (slot >= 0) {
+            const uint64_t k = ckey[beg + e];
+            float d32[3];
+            decode_key(k, i, pos, g, d32);
+            const int j = (int)((k >> 24) & ((1ull << 35) - 1));
+            const int tj = (int)((k >> 59) & 15ull);
+            pair[slot] = make_float4(d32[0], d32[1], d32[2], __int_as_float((j << 4) | tj));
+            shift[slot] = (int32_t)(k & 0xffffffull);
+        }
+        if (e < n) pidx[beg + e] = (int)slot;
+        ca += __popc(mA);
+        cr += __popc(mR);
+    }
+}
+
+// rev of the filtered lists from the candidates' reverse index.
+__global__ void k_filter_rev(int64_t Mc, const int *pidx, const int *crev, int *rev) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Mc) return;
+    const int p = pidx[q];
+    if (p >= 0) rev[p] = pidx[crev[q]];
 }
 
 // out += sum of v[0..n) (integer atomics: the total does not depend on the order)
@@ -745,48 +875,63 @@ __global__ void k_sum_int(int64_t n, const int *v, int64_t *out) {
 
 }  // namespace
 
-int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
-    const int64_t ns = c->n_struct, na = c->n_atoms;
+namespace {
+
+// Per-structure bin grids for a cutoff rc (they depend on the cells only).
+struct Grid {
+    DevBuf *geom, *nbins, *bin_off;
+    int64_t *nbin_total;
+    bool *ok;
+};
+
+int grid_setup(Ctx *c, const Grid &gr, float rc, bool same_cells, bool with_struct_of) {
+    const int64_t ns = c->n_struct;
     const cudaStream_t st = c->stream;
-    const float rcR = c->cfg.rc_R, rcA = c->cfg.rc_A;
+    int *err = c->d_err.as<int>();
+    if (gr.geom->ensure_bytes(sizeof(SGeom) * (size_t)(ns > 0 ? ns : 1)) || gr.nbins->ensure<int64_t>(ns + 1) ||
+        gr.bin_off->ensure<int64_t>(ns + 1) || c->d_total.ensure<int64_t>(8))
+        return c->fail(NEP_ENOMEM, "geometry buffers");
+    if (same_cells && *gr.ok) return NEP_OK;
+    *gr.ok = false;
+    if (ns > 0) {
+        k_struct_geom<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(ns, c->cell.as<float>(), (double)rc,
+                                                                    (SGeom *)gr.geom->ptr, gr.nbins->as<int64_t>(), err);
+        if (with_struct_of)
+            k_struct_of<<<(unsigned)ns, 128, 0, st>>>(ns, c->atom_off.as<int64_t>(), c->struct_of.as<int>());
+    }
+    CK(cudaGetLastError());
+    int rc_ = scan_exclusive(c, gr.nbins->as<int64_t>(), ns, gr.bin_off->as<int64_t>(), c->d_total.as<int64_t>());
+    if (rc_) return rc_;
+    int64_t nbt = 0;
+    int herr = 0;
+    CK(cudaMemcpyAsync(&nbt, c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return c->fail(NEP_EINVAL, herr == 1 ? "singular or non-finite cell" : "cell too thin for the cutoff (more than 127 images)");
+    *gr.nbin_total = nbt;
+    *gr.ok = true;
+    return NEP_OK;
+}
+
+// Binning and the counting scan at cutoffs (rcR, rcA) over grid gr: the pair counts of the
+// atoms scanned into off [na + 1] (total M), the first `cap` keys of each atom in
+// nbr_scratch, the angular counts in n_ang, and whether some atom has more than cap pairs.
+int scan_count(Ctx *c, const Grid &gr, float rcR, float rcA, int cap, DevBuf &off, int64_t &M, int &overflow) {
+    const int64_t na = c->n_atoms;
+    const cudaStream_t st = c->stream;
     const float rc2R = rcR * rcR, rc2A = rcA * rcA;  // single rounded products
     const float rcq = rcR + 0.05f;
     int *err = c->d_err.as<int>();
-    CK(cudaMemsetAsync(err, 0, sizeof(int), st));
-    if (c->geom.ensure_bytes(sizeof(SGeom) * (size_t)(ns > 0 ? ns : 1)) || c->nbins.ensure<int64_t>(ns + 1) ||
-        c->bin_off.ensure<int64_t>(ns + 1) || c->d_total.ensure<int64_t>(6))
-        return c->fail(NEP_ENOMEM, "geometry buffers");
-    SGeom *geom = (SGeom *)c->geom.ptr;
-    int rc = 0, herr = 0;
-    if (!(same_cells && c->geom_ok)) {  // per-structure bin grids (depend on the cells only)
-        c->geom_ok = false;
-        if (ns > 0) {
-            k_struct_geom<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(ns, c->cell.as<float>(), (double)rcR, geom,
-                                                                        c->nbins.as<int64_t>(), err);
-            k_struct_of<<<(unsigned)ns, 128, 0, st>>>(ns, c->atom_off.as<int64_t>(), c->struct_of.as<int>());
-        }
-        CK(cudaGetLastError());
-        rc = scan_exclusive(c, c->nbins.as<int64_t>(), ns, c->bin_off.as<int64_t>(), c->d_total.as<int64_t>());
-        if (rc) return rc;
-        int64_t nbt = 0;
-        CK(cudaMemcpyAsync(&nbt, c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (herr) return c->fail(NEP_EINVAL, herr == 1 ? "singular or non-finite cell" : "cell too thin for the cutoff (more than 127 images)");
-        c->nbin_total = nbt;
-        c->geom_ok = true;
-    }
-    const int64_t nbin_total = c->nbin_total;
+    const SGeom *geom = (const SGeom *)gr.geom->ptr;
+    const int64_t nbin_total = *gr.nbin_total;
     if (c->bin_cnt.ensure<int64_t>(nbin_total + 1) || c->bin_start.ensure<int64_t>(nbin_total + 1) ||
         c->bin_cur.ensure<int64_t>(nbin_total + 1) || c->atom_bin.ensure<int64_t>(na + 1) ||
         c->atom_wrap.ensure_bytes(sizeof(int4) * (size_t)(na + 1)) || c->bin_atoms.ensure<int>(na + 1) ||
-        c->cnt.ensure<int64_t>(na + 1) || c->n_ang.ensure<int>(na + 1) || c->nbr_off.ensure<int64_t>(na + 1) ||
+        c->cnt.ensure<int64_t>(na + 1) || c->n_ang.ensure<int>(na + 1) || off.ensure<int64_t>(na + 1) ||
         c->pos4.ensure<float4>(na + 1) || c->d_flag.ensure<int>(1) || c->bin_pos.ensure<float4>(na + 1) ||
-        c->bin_wrap.ensure_bytes(sizeof(int4) * (size_t)(na + 1)))
+        c->bin_wrap.ensure_bytes(sizeof(int4) * (size_t)(na + 1)) ||
+        c->nbr_scratch.ensure<uint64_t>(na * (int64_t)cap + 1))
         return c->fail(NEP_ENOMEM, "bin buffers");
-    // keys of up to `cap` pairs per atom are kept from the counting scan (at most 8 GB)
-    const int cap = (int)std::min<int64_t>(128, (int64_t)8e9 / (8 * std::max<int64_t>(na, 1)));
-    if (c->nbr_scratch.ensure<uint64_t>(na * (int64_t)cap + 1)) return c->fail(NEP_ENOMEM, "neighbour scratch");
     CK(cudaMemsetAsync(c->d_flag.ptr, 0, sizeof(int), st));
     CK(cudaMemsetAsync(c->bin_cnt.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
     CK(cudaMemsetAsync(c->bin_cur.ptr, 0, sizeof(int64_t) * (size_t)(nbin_total + 1), st));
@@ -796,13 +941,13 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
     CK(cudaMemsetAsync(c->n_ang.ptr, 0, sizeof(int) * (size_t)(na + 1), st));
     if (na > 0) {
         k_atom_bin<<<gA, 256, 0, st>>>(na, c->pos.as<float>(), c->type.as<int>(), c->cfg.n_types,
-                                       c->struct_of.as<int>(), geom, c->bin_off.as<int64_t>(),
+                                       c->struct_of.as<int>(), geom, gr.bin_off->as<int64_t>(),
                                        c->atom_bin.as<int64_t>(), (int4 *)c->atom_wrap.ptr, c->bin_cnt.as<int64_t>(),
                                        c->pos4.as<float4>(), err);
         CK(cudaGetLastError());
     }
-    rc = scan_exclusive(c, c->bin_cnt.as<int64_t>(), nbin_total, c->bin_start.as<int64_t>(),
-                        c->d_total.as<int64_t>() + 1);
+    int rc = scan_exclusive(c, c->bin_cnt.as<int64_t>(), nbin_total, c->bin_start.as<int64_t>(),
+                            c->d_total.as<int64_t>() + 1);
     if (rc) return rc;
     if (na > 0) {
         k_bin_fill<<<gA, 256, 0, st>>>(na, c->atom_bin.as<int64_t>(), c->bin_start.as<int64_t>(),
@@ -812,17 +957,18 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
                                        (int4 *)c->bin_wrap.ptr);
         k_count_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(),
                                       c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
-                                      c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
+                                      gr.bin_off->as<int64_t>(), c->atom_bin.as<int64_t>(),
                                       (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
                                       c->bin_pos.as<float4>(), (const int4 *)c->bin_wrap.ptr, rc2R, rc2A, rcq,
                                       c->cnt.as<int64_t>(),
                                       c->n_ang.as<int>(), c->nbr_scratch.as<uint64_t>(), cap, c->d_flag.as<int>(), err);
         CK(cudaGetLastError());
     }
-    rc = scan_exclusive(c, c->cnt.as<int64_t>(), na, c->nbr_off.as<int64_t>(), c->d_total.as<int64_t>());
+    rc = scan_exclusive(c, c->cnt.as<int64_t>(), na, off.as<int64_t>(), c->d_total.as<int64_t>());
     if (rc) return rc;
-    int64_t M = 0;
-    int overflow = 0;
+    int herr = 0;
+    M = 0;
+    overflow = 0;
     CK(cudaMemcpyAsync(&M, c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&overflow, c->d_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -831,21 +977,49 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
                                           herr == 4 ? "non-finite or far out-of-cell position" :
                                                       "more than 127 periodic images along a cell vector");
     if (M >= (int64_t)1 << 31) return c->fail(NEP_EINVAL, "more than 2^31 neighbour pairs");
+    return NEP_OK;
+}
+
+// the second scan of the keys when some atom has more than cap pairs
+void fill_keys(Ctx *c, const Grid &gr, float rcR, float rcA, const DevBuf &off, uint64_t *keys) {
+    const int64_t na = c->n_atoms;
+    const unsigned gW = (unsigned)((na * 32 + 255) / 256);
+    k_fill_w<<<gW, 256, 0, c->stream>>>(na, c->pos.as<float>(), c->pos4.as<float4>(), c->struct_of.as<int>(),
+                                        c->atom_off.as<int64_t>(), (const SGeom *)gr.geom->ptr,
+                                        gr.bin_off->as<int64_t>(), c->atom_bin.as<int64_t>(),
+                                        (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
+                                        c->bin_pos.as<float4>(), (const int4 *)c->bin_wrap.ptr, rcR * rcR, rcA * rcA,
+                                        rcR + 0.05f, off.as<int64_t>(), keys, c->d_err.as<int>());
+}
+
+int key_cap(int64_t na) { return (int)std::min<int64_t>(128, (int64_t)8e9 / (8 * std::max<int64_t>(na, 1))); }
+
+}  // namespace
+
+int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
+    const int64_t na = c->n_atoms;
+    const cudaStream_t st = c->stream;
+    const float rcR = c->cfg.rc_R, rcA = c->cfg.rc_A;
+    int *err = c->d_err.as<int>();
+    CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    if (!same_cells) c->cand_ok = c->cgeom_ok = false;  // candidates hold the old cells
+    const Grid gr{&c->geom, &c->nbins, &c->bin_off, &c->nbin_total, &c->geom_ok};
+    int rc = grid_setup(c, gr, rcR, same_cells, true);
+    if (rc) return rc;
+    // keys of up to `cap` pairs per atom are kept from the counting scan (at most 8 GB)
+    const int cap = key_cap(na);
+    int64_t M = 0;
+    int overflow = 0;
+    if ((rc = scan_count(c, gr, rcR, rcA, cap, c->nbr_off, M, overflow))) return rc;
     if ((overflow && c->keys_tmp.ensure<uint64_t>(M + 1)) || c->keys.ensure<uint64_t>(M + 1) ||
         c->pair.ensure_bytes(sizeof(float4) * (size_t)(M + 1)) || c->rev.ensure<int>(M + 1) ||
         c->shift.ensure<int32_t>(M + 1))
         return c->fail(NEP_ENOMEM, "pair buffers");
     c->n_pairs = M;
+    const SGeom *geom = (const SGeom *)c->geom.ptr;
+    const unsigned gw = (unsigned)((na * 32 + 255) / 256);
     if (na > 0) {
-        if (overflow)  // some atom has more than `cap` pairs: a second scan writes the keys
-            k_fill_w<<<gW, 256, 0, st>>>(na, c->pos.as<float>(), c->pos4.as<float4>(),
-                                         c->struct_of.as<int>(), c->atom_off.as<int64_t>(), geom,
-                                         c->bin_off.as<int64_t>(), c->atom_bin.as<int64_t>(),
-                                         (const int4 *)c->atom_wrap.ptr, c->bin_start.as<int64_t>(),
-                                         c->bin_pos.as<float4>(), (const int4 *)c->bin_wrap.ptr, rc2R, rc2A, rcq,
-                                         c->nbr_off.as<int64_t>(),
-                                         c->keys_tmp.as<uint64_t>(), err);
-        const unsigned gw = (unsigned)((na * 32 + 255) / 256);
+        if (overflow) fill_keys(c, gr, rcR, rcA, c->nbr_off, c->keys_tmp.as<uint64_t>());
         k_sort_decode<<<gw, 256, 0, st>>>(na, c->keys_tmp.as<uint64_t>(),
                                           overflow ? nullptr : c->nbr_scratch.as<uint64_t>(), cap,
                                           c->nbr_off.as<int64_t>(),
@@ -857,7 +1031,6 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
     int64_t *nang_dev = c->d_total.as<int64_t>() + 5;
     CK(cudaMemsetAsync(found_dev, 0, 2 * sizeof(int64_t), st));
     if (na > 0) {
-        const unsigned gw = (unsigned)((na * 32 + 255) / 256);
         k_reverse<<<gw, 256, 0, st>>>(na, c->nbr_off.as<int64_t>(), c->keys.as<uint64_t>(), c->type.as<int>(),
                                       c->rev.as<int>(), (const float4 *)c->pair.ptr,
                                       (unsigned long long *)found_dev, err);
@@ -866,12 +1039,121 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
     if (na > 0) k_sum_int<<<(unsigned)std::min<int64_t>((na + 255) / 256, 1024), 256, 0, st>>>(na, c->n_ang.as<int>(), nang_dev);
     CK(cudaGetLastError());
     int64_t fin[2] = {0, 0};  // found reverse pairs, angular pairs
+    int herr = 0;
     CK(cudaMemcpyAsync(fin, found_dev, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (herr || 2 * fin[0] != M) return c->fail(NEP_EINTERNAL, "neighbour list is not symmetric");
-    const int64_t nang_total = fin[1];
-    c->n_pairs_ang = nang_total;
+    c->n_pairs_ang = fin[1];
+    c->h_lists_ok = false;
+    return host_lists ? fetch_host_lists(c) : NEP_OK;
+}
+
+// ----------------------------------------------------------------------------- candidate lists
+// Position updates with the cells kept.  A candidate list holds, for reference positions R,
+// every pair within r_c + s (s the skin).  If no atom has moved more than d from R, a pair
+// within r_c at the new positions was within r_c + 2d at R, so for 2d < s the new lists are
+// the candidates that pass the pair predicate (c7) at the new positions: a filter instead
+// of a scan.  The filter keeps the candidates' order, (t_j, j, S), and puts the angular
+// ones first, which is the order the scan's sort gives: the lists are the scan's, bit for
+// bit.  The reverse index follows from the candidates' own.
+
+int build_candidates(Ctx *c) {
+    const int64_t na = c->n_atoms;
+    const cudaStream_t st = c->stream;
+    const float rcc = c->cfg.rc_R + c->skin;
+    int *err = c->d_err.as<int>();
+    CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    c->cand_ok = false;
+    const Grid gr{&c->cgeom, &c->cnbins, &c->cbin_off, &c->cnbin_total, &c->cgeom_ok};
+    int rc = grid_setup(c, gr, rcc, true, false);
+    if (rc) return rc;
+    const int cap = key_cap(na);
+    int64_t Mc = 0;
+    int overflow = 0;
+    if ((rc = scan_count(c, gr, rcc, rcc, cap, c->cand_off, Mc, overflow))) return rc;
+    // the lists the filter writes are at most the candidates: room for them once
+    if ((overflow && c->keys_tmp.ensure<uint64_t>(Mc + 1)) || c->cand_key.ensure<uint64_t>(Mc + 1) ||
+        c->cand_rev.ensure<int>(Mc + 1) || c->cand_pidx.ensure<int>(Mc + 1) || c->cand_flag.ensure<uint8_t>(Mc + 1) ||
+        c->cand_ref.ensure<float>(3 * na + 1) || c->pair.ensure_bytes(sizeof(float4) * (size_t)(Mc + 1)) ||
+        c->rev.ensure<int>(Mc + 1) || c->shift.ensure<int32_t>(Mc + 1) ||
+        c->G.ensure_bytes(sizeof(float4) * (size_t)(Mc + 1)))
+        return c->fail(NEP_ENOMEM, "candidate buffers");
+    int64_t *found_dev = c->d_total.as<int64_t>() + 4;
+    CK(cudaMemsetAsync(found_dev, 0, sizeof(int64_t), st));
+    if (na > 0) {
+        const unsigned gw = (unsigned)((na * 32 + 255) / 256);
+        if (overflow) fill_keys(c, gr, rcc, rcc, c->cand_off, c->keys_tmp.as<uint64_t>());
+        k_sort_keys<<<gw, 256, 0, st>>>(na, c->keys_tmp.as<uint64_t>(),
+                                        overflow ? nullptr : c->nbr_scratch.as<uint64_t>(), cap,
+                                        c->cand_off.as<int64_t>(), c->cand_key.as<uint64_t>());
+        k_reverse<<<gw, 256, 0, st>>>(na, c->cand_off.as<int64_t>(), c->cand_key.as<uint64_t>(), c->type.as<int>(),
+                                      c->cand_rev.as<int>(), nullptr, (unsigned long long *)found_dev, err);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(c->cand_ref.ptr, c->pos.ptr, sizeof(float) * 3 * na, cudaMemcpyDeviceToDevice, st));
+    }
+    int64_t found = 0;
+    int herr = 0;
+    CK(cudaMemcpyAsync(&found, found_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr || 2 * found != Mc) return c->fail(NEP_EINTERNAL, "candidate list is not symmetric");
+    c->cand_M = Mc;
+    c->cand_ok = true;
+    return NEP_OK;
+}
+
+int filter_candidates(Ctx *c, bool host_lists, bool &moved_too_far) {
+    const int64_t na = c->n_atoms, Mc = c->cand_M;
+    const cudaStream_t st = c->stream;
+    const float rcR = c->cfg.rc_R, rcA = c->cfg.rc_A;
+    int *err = c->d_err.as<int>();
+    moved_too_far = false;
+    CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    int64_t *disp_dev = c->d_total.as<int64_t>() + 6;  // max squared displacement (FP64 bits)
+    int64_t *nang_dev = c->d_total.as<int64_t>() + 5;
+    CK(cudaMemsetAsync(nang_dev, 0, 2 * sizeof(int64_t), st));
+    const unsigned gA = (unsigned)((na + 255) / 256), gw = (unsigned)((na * 32 + 255) / 256);
+    const SGeom *geom = (const SGeom *)c->cgeom.ptr;
+    if (na > 0) {
+        k_max_disp<<<gA, 256, 0, st>>>(na, c->pos.as<float>(), c->cand_ref.as<float>(),
+                                       (unsigned long long *)disp_dev);
+        k_filter<false><<<gw, 256, 0, st>>>(na, c->cand_off.as<int64_t>(), c->cand_key.as<uint64_t>(),
+                                            c->pos.as<float>(), c->struct_of.as<int>(), geom, rcR * rcR, rcA * rcA,
+                                            c->cand_flag.as<uint8_t>(), c->cnt.as<int64_t>(), c->n_ang.as<int>(),
+                                            nullptr, nullptr, nullptr, nullptr);
+        CK(cudaGetLastError());
+    }
+    int rc = scan_exclusive(c, c->cnt.as<int64_t>(), na, c->nbr_off.as<int64_t>(), c->d_total.as<int64_t>());
+    if (rc) return rc;
+    if (na > 0) {
+        k_filter<true><<<gw, 256, 0, st>>>(na, c->cand_off.as<int64_t>(), c->cand_key.as<uint64_t>(),
+                                           c->pos.as<float>(), c->struct_of.as<int>(), geom, rcR * rcR, rcA * rcA,
+                                           c->cand_flag.as<uint8_t>(), nullptr, c->n_ang.as<int>(),
+                                           c->nbr_off.as<int64_t>(), (float4 *)c->pair.ptr, c->shift.as<int32_t>(),
+                                           c->cand_pidx.as<int>());
+        if (Mc > 0)
+            k_filter_rev<<<(unsigned)((Mc + 255) / 256), 256, 0, st>>>(Mc, c->cand_pidx.as<int>(),
+                                                                      c->cand_rev.as<int>(), c->rev.as<int>());
+        k_sum_int<<<(unsigned)std::min<int64_t>((na + 255) / 256, 1024), 256, 0, st>>>(na, c->n_ang.as<int>(), nang_dev);
+        CK(cudaGetLastError());
+    }
+    int64_t tot[3] = {0, 0, 0};  // pairs, angular pairs, max squared displacement
+    int herr = 0;
+    CK(cudaMemcpyAsync(&tot[0], c->d_total.as<int64_t>(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tot[1], nang_dev, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) return c->fail(NEP_EINTERNAL, "candidate filter");
+    double d2;
+    std::memcpy(&d2, &tot[2], sizeof(double));
+    // 2 d < s with a margin far above the rounding of the predicates (relative 1e-7 of r_c)
+    if (!(2.0 * std::sqrt(d2) < (double)c->skin - 1e-5)) {
+        moved_too_far = true;
+        return NEP_OK;
+    }
+    c->n_pairs = tot[0];
+    c->n_pairs_ang = tot[1];
     c->h_lists_ok = false;
     return host_lists ? fetch_host_lists(c) : NEP_OK;
 }

@@ -514,6 +514,45 @@ def test_update_positions_cells_kept_and_minibatches():
         assert_grad_close(ga.cpu().numpy(), go, spec, TOL)
     nep.close()
 
+def test_update_positions_candidate_lists():
+    """Position updates with the cells kept go through candidate lists (every pair within
+    r_c + skin of the positions of the last candidate scan): small moves are filtered from
+    them, a move of more than half the skin rescans first.  After every update the lists
+    equal the brute force's and those of a context that scans (skin 0) entry for entry, and
+    E/F/W equal those of a fresh context bit for bit."""
+    from paper_2606_19557_gb300 import NEP
+    spec = synth.SPECS["scale_t5"]
+    b = synth.batch_scale(seed=23, n_struct=14, n_big=0)
+    P = oracle.num_params(spec)
+    th = torch.tensor(synth.random_theta(P, 23), dtype=torch.float32)
+    qs = torch.tensor(f32(oracle.scale_from_range(oracle.descriptors(spec, th.double().numpy(), b))),
+                      dtype=torch.float32)
+    nep, scan = NEP(spec), NEP(spec)
+    scan.set_skin(0.0)
+    for x in (nep, scan):
+        x.set_structures_batch(b)
+        x.set_params(th, qs)
+    rng = np.random.default_rng(29)
+    pos = np.asarray(b.pos, np.float64)
+    for step, sigma in enumerate((0.02, 0.03, 0.02, 0.4, 0.02)):  # the 0.4 A move rescans
+        pos = pos + rng.normal(scale=sigma, size=pos.shape)
+        p32 = pos.astype(np.float32)
+        nep.update_positions(p32)
+        scan.update_positions(p32)
+        bs = synth.Batch(b.atom_off, p32.astype(np.float64), b.types, b.cell, b.n_types)
+        _check_neighbors(nep, bs, spec.rc_R, spec.rc_A)
+        for u, v in zip(nep.neighbors(), scan.neighbors()):
+            assert torch.equal(u, v), step
+        f = NEP(spec)
+        f.set_structures_batch(bs)
+        f.set_params(th, qs)
+        for u, v in zip(nep.eval(), f.eval()):
+            assert torch.equal(u, v), step
+        f.close()
+    nep.close()
+    scan.close()
+
+
 @pytest.mark.parametrize("name", ["nep44_t16", "nep88_t16"])
 def test_table2_sixteen_species_models(name):
     """The paper's 16-element models (Table 2 sizes; 80 neurons, 4- and 5-body terms) on a
