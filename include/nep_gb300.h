@@ -125,7 +125,7 @@ int nep_set_structures(nep_ctx *ctx, int64_t n_struct, const int64_t *atom_off_d
  * While no atom has moved half the skin from those positions, the lists are the
  * candidates that pass the pair predicate at the new positions (a filter, no scan); the
  * filter keeps the scan's order, so the lists are the scan's, bit for bit.  Otherwise
- * the candidates are rebuilt first.  The candidate lists take about 17 bytes per
+ * the candidates are rebuilt first.  The candidate lists take about 33 bytes per
  * candidate pair.  Synchronizes with the list build; the schedule kernels are queued on
  * the context's stream after it.  Errors: NEP_ESTATE (no batch), NEP_EINVAL (bad
  * geometry: the batch is then unusable, and later calls return NEP_ESTATE, until

@@ -131,7 +131,7 @@ struct Ctx {
     float skin = 0.5f;                 // Angstrom; 0: every position update scans
     bool cand_ok = false, cgeom_ok = false;
     int64_t cand_M = 0, cnbin_total = 0;
-    DevBuf cgeom, cnbins, cbin_off, cand_off, cand_key, cand_rev, cand_pidx, cand_flag, cand_ref;
+    DevBuf cgeom, cnbins, cbin_off, cand_off, cand_key, cand_rev, cand_pidx, cand_flag, cand_ref, cand_rec;
 
     // schedule
     DevBuf work;                 // [Na] atom per work position (species-sorted)

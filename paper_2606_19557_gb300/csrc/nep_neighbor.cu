@@ -148,6 +148,7 @@ constexpr int SMAX = 127;      // |S_a| limit of the packed shift
 struct SGeom {
     double h[9];
     double inv[9];
+    float hf[9];    // h as given (floats)
     float invf[9];  // inv rounded to float
     float nb[3];    // |b_a|, the norms of the columns of inv (reciprocal vectors), in float
     int n[3];
@@ -160,7 +161,10 @@ __global__ void k_struct_geom(int64_t ns, const float *cell, double rc, SGeom *g
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= ns) return;
     SGeom g;
-    for (int k = 0; k < 9; ++k) g.h[k] = (double)cell[9 * s + k];
+    for (int k = 0; k < 9; ++k) {
+        g.hf[k] = cell[9 * s + k];
+        g.h[k] = (double)cell[9 * s + k];
+    }
     const double *h = g.h;
     const double c0[3] = {h[4] * h[8] - h[5] * h[7], h[5] * h[6] - h[3] * h[8], h[3] * h[7] - h[4] * h[6]};
     const double c1[3] = {h[7] * h[2] - h[8] * h[1], h[8] * h[0] - h[6] * h[2], h[6] * h[1] - h[7] * h[0]};
@@ -392,8 +396,7 @@ __device__ __forceinline__ void scan_atom_warp(int64_t i, int lane, const float 
     const int s = struct_of[i];
     const SGeom &g = geom[s];
     const float *pi = pos + 3 * i;
-    const float hf[9] = {(float)g.h[0], (float)g.h[1], (float)g.h[2], (float)g.h[3], (float)g.h[4],
-                         (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
+    const float hf[9] = {g.hf[0], g.hf[1], g.hf[2], g.hf[3], g.hf[4], g.hf[5], g.hf[6], g.hf[7], g.hf[8]};
     auto test = [&](int j, int tj, int Sa, int Sb, int Sc, float4 pj4) {
         if (j == (int)i && Sa == 0 && Sb == 0 && Sc == 0) return;
         const float fa = (float)Sa, fb = (float)Sb, fc = (float)Sc;
@@ -596,9 +599,8 @@ __device__ __forceinline__ void decode_key(uint64_t k, int64_t i, const float *p
         pair_d0(pos + 3 * i, pos + 3 * j, g.h, d32);
     } else {
         const int Sa = (int)((sp >> 16) & 255) - 128, Sb = (int)((sp >> 8) & 255) - 128, Sc = (int)(sp & 255) - 128;
-        const float hf[9] = {(float)g.h[0], (float)g.h[1], (float)g.h[2], (float)g.h[3], (float)g.h[4],
-                             (float)g.h[5], (float)g.h[6], (float)g.h[7], (float)g.h[8]};
-        if (!pair_d_fp32(pos + 3 * i, pos + 3 * j, hf, Sa, Sb, Sc, d32)) pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
+        if (!pair_d_fp32(pos + 3 * i, pos + 3 * j, g.hf, Sa, Sb, Sc, d32))
+            pair_d(pos + 3 * i, pos + 3 * j, g.h, Sa, Sb, Sc, d32);
     }
 }
 
@@ -796,14 +798,14 @@ __global__ void k_max_disp(int64_t na, const float *pos, const float *ref, unsig
 
 // Candidate filter, one warp per atom.  Pass 1 (WRITE = false): the pair predicate (c7) of
 // every candidate at the current positions, as flags (bit 0 within r_c^R, bit 1 within
-// r_c^A), and the atom's radial and angular counts.  Pass 2: the pair records of the kept
-// candidates at their list positions (angular ones first, each group in candidate order)
-// and each candidate's position (pidx, -1 if dropped).
+// r_c^A) and its pair record in crec, and the atom's radial and angular counts.  Pass 2:
+// the kept candidates' records at their list positions (angular ones first, each group in
+// candidate order) and each candidate's position (pidx, -1 if dropped).
 template <bool WRITE>
 __global__ void k_filter(int64_t na, const int64_t *coff, const uint64_t *ckey, const float *pos,
                          const int *struct_of, const SGeom *geom, float rc2R, float rc2A, uint8_t *cflag,
-                         int64_t *cnt, int *n_ang, const int64_t *nbr_off, float4 *pair, int32_t *shift,
-                         int *pidx) {
+                         float4 *crec, int64_t *cnt, int *n_ang, const int64_t *nbr_off, float4 *pair,
+                         int32_t *shift, int *pidx) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= na) return;
@@ -812,12 +814,18 @@ __global__ void k_filter(int64_t na, const int64_t *coff, const uint64_t *ckey, 
     if (!WRITE) {
         int nr = 0, nang = 0;
         for (int64_t e = lane; e < n; e += 32) {
+            const uint64_t k = ckey[beg + e];
             float d32[3];
-            decode_key(ckey[beg + e], i, pos, g, d32);
+            decode_key(k, i, pos, g, d32);
             const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(d32[0], d32[0]), __fmul_rn(d32[1], d32[1])),
                                        __fmul_rn(d32[2], d32[2]));
             const bool inR = r2 < rc2R, inA = r2 < rc2A;
             cflag[beg + e] = (uint8_t)((inR ? 1 : 0) | (inA ? 2 : 0));
+            if (inR) {
+                const int j = (int)((k >> 24) & ((1ull << 35) - 1));
+                const int tj = (int)((k >> 59) & 15ull);
+                crec[beg + e] = make_float4(d32[0], d32[1], d32[2], __int_as_float((j << 4) | tj));
+            }
             nr += inR ? 1 : 0;
             nang += inA ? 1 : 0;
         }
@@ -842,13 +850,8 @@ __global__ void k_filter(int64_t na, const int64_t *coff, const uint64_t *ckey, 
         if (isA) slot = pbeg + ca + __popc(mA & below);
         else if (isR) slot = pbeg + nA + cr + __popc(mR & below);
         if (slot >= 0) {
-            const uint64_t k = ckey[beg + e];
-            float d32[3];
-            decode_key(k, i, pos, g, d32);
-            const int j = (int)((k >> 24) & ((1ull << 35) - 1));
-            const int tj = (int)((k >> 59) & 15ull);
-            pair[slot] = make_float4(d32[0], d32[1], d32[2], __int_as_float((j << 4) | tj));
-            shift[slot] = (int32_t)(k & 0xffffffull);
+            pair[slot] = crec[beg + e];
+            shift[slot] = (int32_t)(ckey[beg + e] & 0xffffffull);
         }
         if (e < n) pidx[beg + e] = (int)slot;
         ca += __popc(mA);
@@ -1075,6 +1078,7 @@ int build_candidates(Ctx *c) {
     // the lists the filter writes are at most the candidates: room for them once
     if ((overflow && c->keys_tmp.ensure<uint64_t>(Mc + 1)) || c->cand_key.ensure<uint64_t>(Mc + 1) ||
         c->cand_rev.ensure<int>(Mc + 1) || c->cand_pidx.ensure<int>(Mc + 1) || c->cand_flag.ensure<uint8_t>(Mc + 1) ||
+        c->cand_rec.ensure_bytes(sizeof(float4) * (size_t)(Mc + 1)) ||
         c->cand_ref.ensure<float>(3 * na + 1) || c->pair.ensure_bytes(sizeof(float4) * (size_t)(Mc + 1)) ||
         c->rev.ensure<int>(Mc + 1) || c->shift.ensure<int32_t>(Mc + 1) ||
         c->G.ensure_bytes(sizeof(float4) * (size_t)(Mc + 1)))
@@ -1120,8 +1124,9 @@ int filter_candidates(Ctx *c, bool host_lists, bool &moved_too_far) {
                                        (unsigned long long *)disp_dev);
         k_filter<false><<<gw, 256, 0, st>>>(na, c->cand_off.as<int64_t>(), c->cand_key.as<uint64_t>(),
                                             c->pos.as<float>(), c->struct_of.as<int>(), geom, rcR * rcR, rcA * rcA,
-                                            c->cand_flag.as<uint8_t>(), c->cnt.as<int64_t>(), c->n_ang.as<int>(),
-                                            nullptr, nullptr, nullptr, nullptr);
+                                            c->cand_flag.as<uint8_t>(), c->cand_rec.as<float4>(),
+                                            c->cnt.as<int64_t>(), c->n_ang.as<int>(), nullptr, nullptr, nullptr,
+                                            nullptr);
         CK(cudaGetLastError());
     }
     int rc = scan_exclusive(c, c->cnt.as<int64_t>(), na, c->nbr_off.as<int64_t>(), c->d_total.as<int64_t>());
@@ -1129,7 +1134,8 @@ int filter_candidates(Ctx *c, bool host_lists, bool &moved_too_far) {
     if (na > 0) {
         k_filter<true><<<gw, 256, 0, st>>>(na, c->cand_off.as<int64_t>(), c->cand_key.as<uint64_t>(),
                                            c->pos.as<float>(), c->struct_of.as<int>(), geom, rcR * rcR, rcA * rcA,
-                                           c->cand_flag.as<uint8_t>(), nullptr, c->n_ang.as<int>(),
+                                           c->cand_flag.as<uint8_t>(), c->cand_rec.as<float4>(), nullptr,
+                                           c->n_ang.as<int>(),
                                            c->nbr_off.as<int64_t>(), (float4 *)c->pair.ptr, c->shift.as<int32_t>(),
                                            c->cand_pidx.as<int>());
         if (Mc > 0)
