@@ -207,14 +207,16 @@ static int set_smem_attr(Ctx *c) {
         return c->fail(NEP_EINVAL, "model too large for shared memory");
     if (c->ks->net_rev_smem(c->NN) > (size_t)maxo || c->ks->net_fwd_smem(c->NN) > (size_t)maxo)
         return c->fail(NEP_EINVAL, "model too large for shared memory");
-    CK(cudaFuncSetAttribute(c->ks->net_fwd_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+    for (int r = 0; r < 2; ++r) {
+        CK(cudaFuncSetAttribute(c->ks->net_fwd_fn[r], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+        CK(cudaFuncSetAttribute(c->ks->net_rev_fn[r], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
+    }
     for (int v = 0; v < NVAR; ++v) {
         CK(cudaFuncSetAttribute(c->ks->fwd_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
         CK(cudaFuncSetAttribute(c->ks->desc_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
         CK(cudaFuncSetAttribute(c->ks->adj_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
         CK(cudaFuncSetAttribute(c->ks->jvp_fn[v], cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     }
-    CK(cudaFuncSetAttribute(c->ks->net_rev_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxo));
     return NEP_OK;
 }
 

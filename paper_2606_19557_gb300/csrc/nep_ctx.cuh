@@ -72,12 +72,12 @@ struct KernelSet {
     // (0: blocks of <= 128 threads, 4 per SM, 128 registers; 1: 5 per SM, 96 registers)
     const void *fwd_fn[NVAR];   // forward pair-gradient stage
     const void *desc_fn[NVAR];  // forward descriptor stage
-    const void *net_fwd_fn;     // network forward pass (one block per chunk)
-    size_t (*net_fwd_smem)(int NN);
+    const void *net_fwd_fn[2];  // network forward pass (one block per chunk): 64- and 16-row tiles
+    size_t (*net_fwd_smem)(int NN);  // of the 64-row tiles (the larger)
     const void *adj_fn[NVAR];   // adjoint coefficient-gradient stage (the larger footprint)
     const void *jvp_fn[NVAR];   // adjoint JVP stage
-    const void *net_rev_fn;     // network reverse pass (one block per chunk)
-    size_t (*net_rev_smem)(int NN);
+    const void *net_rev_fn[2];  // network reverse pass (one block per chunk): 64- and 16-row tiles
+    size_t (*net_rev_smem)(int NN);  // of the 64-row tiles (the larger)
     int max_wpb[NVAR];                   // largest warps per block each variant allows
     int sw[NVAR];
     size_t (*fwd_smem[NVAR])(int T, int NN);  // bytes per warp
@@ -185,6 +185,7 @@ struct Ctx {
         int64_t wf_off, wa_off;  // offsets of the warp_begin slices in mb_wbf / mb_wba
         int64_t ck_off;          // offset of the chunk list in mb_chunks (n_ck + 1 entries)
         int n_ck;
+        int ch;                  // work positions per chunk (the last of a species may be shorter)
     };
     int mb_B = 0;
     int mb_var[2] = {-1, -1};  // forward / adjoint variants of the groups (-1: the batch's own)
@@ -259,9 +260,9 @@ int launch_expand(Ctx *c);
 int launch_forward(Ctx *c, float *q_raw, int stage = -1);
 // explicit schedules (mini-batch mode)
 int launch_forward_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBuf &rec2, const int *warp_begin,
-                         int blocks, int var, int wpb, const int *chunks, int n_chunks);
+                         int blocks, int var, int wpb, const int *chunks, int n_chunks, int chunk_rows);
 int launch_adjoint_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBuf &rec2, const int *warp_begin,
-                         int blocks, int var, int wpb, const int *chunks, int n_chunks);
+                         int blocks, int var, int wpb, const int *chunks, int n_chunks, int chunk_rows);
 int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks);
 // opt: apply the optimiser step to each parameter as its gradient completes (training)
 int launch_grad_final_sched(Ctx *c, float *grad, const int *clo, const int *chi, const int *wlo, const int *whi,

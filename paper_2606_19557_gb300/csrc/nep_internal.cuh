@@ -94,6 +94,7 @@ struct AtomArgs {
     // species) -> coefficient gradient
     const int *chunks;      // [n_chunks + 1] chunk boundaries (work positions)
     int n_chunks;
+    int chunk_rows;         // the longest chunk (<= 16: the network kernels take 16-row tiles)
     int NDP;                // padded descriptor length
     float *st_D;            // [Na_work][NA*24] JVP of the angular moments, [lm][n]
     float *st_S;            // [Na_work][T][2 KR] radial species sums S^b_k | S'^b_k

@@ -690,6 +690,7 @@ static AtomArgs atom_args(Ctx *c) {
     a.cpart = c->cpart.as<float>();
     a.chunks = c->chunk_begin.as<int>();
     a.n_chunks = c->n_chunks;
+    a.chunk_rows = 128;  // the batch's chunks (nep_set_structures)
     a.NDP = c->NDP;
     a.st_D = c->st_D.as<float>();
     a.st_S = c->st_S.as<float>();
@@ -766,7 +767,7 @@ int launch_adjoint(Ctx *c, int stage) {
 }
 
 int launch_forward_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBuf &rec2, const int *warp_begin,
-                         int blocks, int var, int wpb, const int *chunks, int n_chunks) {
+                         int blocks, int var, int wpb, const int *chunks, int n_chunks, int chunk_rows) {
     if (blocks <= 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.work = work;
@@ -775,13 +776,14 @@ int launch_forward_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBu
     a.warp_begin = warp_begin;
     a.chunks = chunks;
     a.n_chunks = n_chunks;
+    a.chunk_rows = chunk_rows;
     c->ks->launch_fwd[var](a, blocks, wpb, -1, c->stream, c->pdl());
     CK_LAUNCH("forward stages");
     return NEP_OK;
 }
 
 int launch_adjoint_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBuf &rec2, const int *warp_begin,
-                         int blocks, int var, int wpb, const int *chunks, int n_chunks) {
+                         int blocks, int var, int wpb, const int *chunks, int n_chunks, int chunk_rows) {
     if (blocks <= 0) return NEP_OK;
     AtomArgs a = atom_args(c);
     a.work = work;
@@ -790,6 +792,7 @@ int launch_adjoint_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBu
     a.warp_begin = warp_begin;
     a.chunks = chunks;
     a.n_chunks = n_chunks;
+    a.chunk_rows = chunk_rows;
     c->ks->launch_adj[var](a, blocks, wpb, -1, c->stream, c->pdl());
     CK_LAUNCH("adjoint stages");
     return NEP_OK;
@@ -1051,6 +1054,7 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         const int nch = (int)(c->p_cofs[s + 1] - c->p_cofs[s] - 1);
         a.chunks = c->p_chunks.as<int>() + c->p_cofs[s];
         a.n_chunks = nch;
+        a.chunk_rows = 512;
         c->ks->launch_fwd[pv](a, (int)n, 1, -1, c->stream, false);
         CK_LAUNCH("forward stages (plain)");
         TermsCall t;

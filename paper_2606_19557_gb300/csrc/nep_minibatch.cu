@@ -165,6 +165,7 @@ int build_minibatches(Ctx *c, int B) {
         // network chunks of one species each: about one per SM in a small group (the network
         // kernels run one block per chunk), 128 work positions at most
         const int CH = std::max(16, std::min(128, n / std::max(1, c->n_sm) / 16 * 16));
+        m.ch = CH;
         m.ck_off = (int64_t)chunks.size();
         clo.resize(tofs + T);
         chi.resize(tofs + T);
@@ -276,7 +277,8 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
     do {
         if ((rc = launch_forward_sched(c, c->mb_work.as<int>(), c->mb_rec, c->mb_rec2, c->mb_wbf.as<int>() + m.wf_off,
                                        m.Wf / c->mb_used[1],
-                                       c->mb_used[0], c->mb_used[1], c->mb_chunks.as<int>() + m.ck_off, m.n_ck)))
+                                       c->mb_used[0], c->mb_used[1], c->mb_chunks.as<int>() + m.ck_off, m.n_ck,
+                                       m.ch)))
             break;
         TermsCall t;
         t.a0 = m.a0;
@@ -299,7 +301,8 @@ int run_minibatch_loss(Ctx *c, int64_t mi, double lE, double lF, double lV, doub
         if ((rc = launch_terms(c, t))) break;
         if ((rc = launch_adjoint_sched(c, c->mb_work.as<int>(), c->mb_rec, c->mb_rec2, c->mb_wba.as<int>() + m.wa_off,
                                        m.Wa / c->mb_used[3],
-                                       c->mb_used[2], c->mb_used[3], c->mb_chunks.as<int>() + m.ck_off, m.n_ck)))
+                                       c->mb_used[2], c->mb_used[3], c->mb_chunks.as<int>() + m.ck_off, m.n_ck,
+                                       m.ch)))
             break;
         if ((rc = launch_ann_grad_chunks(c, c->mb_chunks.as<int>() + m.ck_off, m.n_ck))) break;
         rc = launch_grad_final_sched(c, grad, c->mb_clo.as<int>() + mi * T, c->mb_chi.as<int>() + mi * T,

@@ -657,24 +657,41 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_jvp(AtomArgs a) {
 //   abar = s (W0^T zeta)   (b = s (W0^T u) comes from the network forward pass).
 // 256 threads as 16 x 16; each owns 4 atoms x 4 columns of a 64 x 64 output block, and the
 // operands come from shared memory with 128-bit loads (atoms along the fast axis).
-constexpr int NETR = 64;  // atoms per tile
+constexpr int NETR = 64;  // atoms per tile of chunks longer than 16 work positions
 
-template <class S>
-__host__ __device__ inline size_t net_rev_smem(int NN) {
-    const size_t NDQ = round4(S::ND), NNP = round4(NN);
-    return sizeof(float) * (NDQ * NETR + NNP * NETR + (size_t)S::ND * NNP + (size_t)NN * NDQ);
+// RX consecutive floats of a transposed tile row (RX = 4: one 128-bit load).
+template <int RX>
+__device__ __forceinline__ void ld_rows(const float *p, float *v) {
+    if constexpr (RX == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int x = 0; x < RX; ++x) v[x] = p[x];
+    }
 }
 
-template <class S>
+template <class S, int RX>
+__host__ __device__ inline size_t net_rev_smem(int NN) {
+    constexpr int R = 16 * RX;
+    const size_t NDQ = round4(S::ND), NNP = round4(NN);
+    return sizeof(float) * (NDQ * R + NNP * R + (size_t)S::ND * NNP + (size_t)NN * NDQ);
+}
+
+template <class S, int RX>
 __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
+    constexpr int R = 16 * RX;  // tile rows: 16 row groups of RX
     grid_dep_wait();
     grid_dep_launch();
     constexpr int ND = S::ND, NDQ = round4(ND);
     extern __shared__ __align__(16) float smn[];
     const int NN = a.NN, NNP = round4(NN), T = a.T;
-    float *Q = smn;                 // [NDQ][NETR] dq~, transposed
-    float *Z = Q + NDQ * NETR;      // [NNP][NETR] zeta, transposed
-    float *Wt = Z + NNP * NETR;     // [ND][NNP]  W0^T of the species
+    float *Q = smn;                 // [NDQ][R] dq~, transposed
+    float *Z = Q + NDQ * R;      // [NNP][R] zeta, transposed
+    float *Wt = Z + NNP * R;     // [ND][NNP]  W0^T of the species
     float *Wn = Wt + ND * NNP;      // [NN][NDQ]  W0 of the species
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int rc0 = a.chunks[blockIdx.x], rc1 = a.chunks[blockIdx.x + 1];
@@ -699,41 +716,42 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
             return v < ND ? __ldg(W0 + (size_t)mu * ND + v) : 0.0f;
         },
         [&](int e, float x) { Wn[e] = x; });
-    for (int rb = rc0; rb < rc1; rb += NETR) {
-        const int nr = min(NETR, rc1 - rb);
+    for (int rb = rc0; rb < rc1; rb += R) {
+        const int nr = min(R, rc1 - rb);
         __syncthreads();  // the weights are staged; the previous tile is done with Q, Z, U
         block_stage<256>(
-            NETR * NDQ,
+            R * NDQ,
             [&](int e) {
                 const int r = e / NDQ, k = e - r * NDQ;
                 return (r < nr && k < ND) ? __ldg(a.dqt + (size_t)(rb + r) * ND + k) : 0.0f;
             },
             [&](int e, float x) {
                 const int r = e / NDQ, k = e - r * NDQ;
-                Q[k * NETR + r] = x;
+                Q[k * R + r] = x;
             });
         __syncthreads();
-        const int r0 = ty * 4;
+        const int r0 = ty * RX;
         for (int cb = 0; cb < NNP; cb += 64) {
             const int mu0 = cb + tx * 4;
             if (mu0 < NNP) {
-                float acc[4][4];
+                float acc[RX][4];
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+                for (int x = 0; x < RX; ++x)
 #pragma unroll
                     for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
 #pragma unroll 7
                 for (int k = 0; k < ND; ++k) {
-                    const float4 q4 = *reinterpret_cast<const float4 *>(Q + k * NETR + r0);
+                    float q[RX];
+                    ld_rows<RX>(Q + k * R + r0, q);
                     const float4 w4 = *reinterpret_cast<const float4 *>(Wt + k * NNP + mu0);
-                    const float q[4] = {q4.x, q4.y, q4.z, q4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                    for (int x = 0; x < 4; ++x)
+                    for (int x = 0; x < RX; ++x)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) acc[x][y] += q[x] * wv[y];
                 }
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
+                for (int x = 0; x < RX; ++x) {
                     const int r = r0 + x;
                     const bool row = r < nr;
                     const int wpos = rb + (row ? r : 0);
@@ -752,7 +770,7 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
                             a.ut[(size_t)wpos * NN + mu] = wo * hp;
                             a.om[(size_t)wpos * NN + mu] = eb * h + hp * acc[x][y];
                         }
-                        Z[mu * NETR + r] = ze;
+                        Z[mu * R + r] = ze;
                     }
                 }
             }
@@ -761,23 +779,24 @@ __global__ void __launch_bounds__(256) k_net_rev(AtomArgs a) {
         for (int cb = 0; cb < NDQ; cb += 64) {
             const int v0 = cb + tx * 4;
             if (v0 < NDQ) {
-                float aa[4][4];
+                float aa[RX][4];
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+                for (int x = 0; x < RX; ++x)
 #pragma unroll
                     for (int y = 0; y < 4; ++y) aa[x][y] = 0.0f;
 #pragma unroll 5
                 for (int mu = 0; mu < NN; ++mu) {
-                    const float4 z4 = *reinterpret_cast<const float4 *>(Z + mu * NETR + r0);
+                    float z[RX];
+                    ld_rows<RX>(Z + mu * R + r0, z);
                     const float4 w4 = *reinterpret_cast<const float4 *>(Wn + mu * NDQ + v0);
-                    const float z[4] = {z4.x, z4.y, z4.z, z4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                    for (int x = 0; x < 4; ++x)
+                    for (int x = 0; x < RX; ++x)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) aa[x][y] += z[x] * wv[y];
                 }
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
+                for (int x = 0; x < RX; ++x) {
                     const int r = r0 + x;
                     if (r < nr) {
 #pragma unroll
@@ -1244,24 +1263,26 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_desc(AtomArgs a) 
 // Per chunk of <= 128 work positions of one species t, in tiles of 64 atoms (Eq. "ann"):
 //   h = tanh(W0 q~ - b0),  E = w1 . h - b1,  u = w1 (1 - h^2),  b = s (W0^T u).
 // Same tiling as the network reverse pass.
-template <class S>
+template <class S, int RX>
 __host__ __device__ inline size_t net_fwd_smem(int NN) {
+    constexpr int R = 16 * RX;
     const size_t NDQ = round4(S::ND), NNP = round4(NN);
-    return sizeof(float) * (NDQ * NETR + NNP * NETR + (size_t)S::ND * NNP + (size_t)NN * NDQ + NETR);
+    return sizeof(float) * (NDQ * R + NNP * R + (size_t)S::ND * NNP + (size_t)NN * NDQ + R);
 }
 
-template <class S>
+template <class S, int RX>
 __global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
+    constexpr int R = 16 * RX;  // tile rows: 16 row groups of RX
     grid_dep_wait();
     grid_dep_launch();
     constexpr int ND = S::ND, NDQ = round4(ND);
     extern __shared__ __align__(16) float smn[];
     const int NN = a.NN, NNP = round4(NN), T = a.T;
-    float *Q = smn;                 // [NDQ][NETR] q~, transposed
-    float *U = Q + NDQ * NETR;      // [NNP][NETR] u, transposed
-    float *Wt = U + NNP * NETR;     // [ND][NNP]  W0^T of the species
+    float *Q = smn;                 // [NDQ][R] q~, transposed
+    float *U = Q + NDQ * R;      // [NNP][R] u, transposed
+    float *Wt = U + NNP * R;     // [ND][NNP]  W0^T of the species
     float *Wn = Wt + ND * NNP;      // [NN][NDQ]  W0 of the species
-    float *Es = Wn + NN * NDQ;      // [NETR]     energies of the tile's atoms
+    float *Es = Wn + NN * NDQ;      // [R]     energies of the tile's atoms
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int rc0 = a.chunks[blockIdx.x], rc1 = a.chunks[blockIdx.x + 1];
     if (rc0 >= rc1) return;
@@ -1287,43 +1308,46 @@ __global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
             return v < ND ? __ldg(W0 + (size_t)mu * ND + v) : 0.0f;
         },
         [&](int e, float x) { Wn[e] = x; });
-    for (int rb = rc0; rb < rc1; rb += NETR) {
-        const int nr = min(NETR, rc1 - rb);
+    for (int rb = rc0; rb < rc1; rb += R) {
+        const int nr = min(R, rc1 - rb);
         __syncthreads();  // the weights are staged; the previous tile is done with Q, U, Es
         block_stage<256>(
-            NETR * NDQ,
+            R * NDQ,
             [&](int e) {
                 const int r = e / NDQ, k = e - r * NDQ;
                 return (r < nr && k < ND) ? __ldg(a.st_qt + (size_t)(rb + r) * ND + k) : 0.0f;
             },
             [&](int e, float x) {
                 const int r = e / NDQ, k = e - r * NDQ;
-                Q[k * NETR + r] = x;
+                Q[k * R + r] = x;
             });
-        if (threadIdx.x < NETR) Es[threadIdx.x] = 0.0f;
+        if (threadIdx.x < R) Es[threadIdx.x] = 0.0f;
         __syncthreads();
-        const int r0 = ty * 4;
+        const int r0 = ty * RX;
         for (int cb = 0; cb < NNP; cb += 64) {
             const int mu0 = cb + tx * 4;
-            float ep[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // w1 . h over this thread's 4 neurons
-            if (mu0 < NNP) {
-                float acc[4][4];
+            float ep[RX];
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < RX; ++x) ep[x] = 0.0f;  // w1 . h over this thread's 4 neurons
+            if (mu0 < NNP) {
+                float acc[RX][4];
+#pragma unroll
+                for (int x = 0; x < RX; ++x)
 #pragma unroll
                     for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
 #pragma unroll 7
                 for (int k = 0; k < ND; ++k) {
-                    const float4 q4 = *reinterpret_cast<const float4 *>(Q + k * NETR + r0);
+                    float q[RX];
+                    ld_rows<RX>(Q + k * R + r0, q);
                     const float4 w4 = *reinterpret_cast<const float4 *>(Wt + k * NNP + mu0);
-                    const float q[4] = {q4.x, q4.y, q4.z, q4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                    for (int x = 0; x < 4; ++x)
+                    for (int x = 0; x < RX; ++x)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) acc[x][y] += q[x] * wv[y];
                 }
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
+                for (int x = 0; x < RX; ++x) {
                     const int r = r0 + x;
                     const bool row = r < nr;
 #pragma unroll
@@ -1337,13 +1361,13 @@ __global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
                             ep[x] += wo * h;
                             uu = wo * (1.0f - h * h);
                         }
-                        U[mu * NETR + r] = uu;
+                        U[mu * R + r] = uu;
                     }
                 }
             }
             // energies: the 16 column threads of a row group add their neuron sums in a fixed order
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
+            for (int x = 0; x < RX; ++x) {
                 float v = ep[x];
 #pragma unroll
                 for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -1355,23 +1379,24 @@ __global__ void __launch_bounds__(256) k_net_fwd(AtomArgs a) {
         for (int cb = 0; cb < NDQ; cb += 64) {
             const int v0 = cb + tx * 4;
             if (v0 < NDQ) {
-                float ab[4][4];
+                float ab[RX][4];
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+                for (int x = 0; x < RX; ++x)
 #pragma unroll
                     for (int y = 0; y < 4; ++y) ab[x][y] = 0.0f;
 #pragma unroll 5
                 for (int mu = 0; mu < NN; ++mu) {
-                    const float4 u4 = *reinterpret_cast<const float4 *>(U + mu * NETR + r0);
+                    float uu[RX];
+                    ld_rows<RX>(U + mu * R + r0, uu);
                     const float4 w4 = *reinterpret_cast<const float4 *>(Wn + mu * NDQ + v0);
-                    const float uu[4] = {u4.x, u4.y, u4.z, u4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                    for (int x = 0; x < 4; ++x)
+                    for (int x = 0; x < RX; ++x)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) ab[x][y] += uu[x] * wv[y];
                 }
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
+                for (int x = 0; x < RX; ++x) {
                     const int r = r0 + x;
                     if (r < nr) {
 #pragma unroll
@@ -1592,8 +1617,10 @@ template <class S, int SW, int VAR>
 void launch_fwd_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_t st, bool pdl) {
     if (stage < 0 || stage == 0)
         launch_k(pdl, k_fwd_desc<S, SW, VAR>, blocks, wpb * 32, DescL<S, SW>::bytes(a.T, a.NN) * wpb, st, a);
-    if ((stage < 0 || stage == 1) && a.n_chunks > 0)
-        launch_k(pdl, k_net_fwd<S>, a.n_chunks, 256, net_fwd_smem<S>(a.NN), st, a);
+    if ((stage < 0 || stage == 1) && a.n_chunks > 0) {  // 16-row tiles for chunks of at most 16
+        if (a.chunk_rows <= 16) launch_k(pdl, k_net_fwd<S, 1>, a.n_chunks, 256, net_fwd_smem<S, 1>(a.NN), st, a);
+        else launch_k(pdl, k_net_fwd<S, 4>, a.n_chunks, 256, net_fwd_smem<S, 4>(a.NN), st, a);
+    }
     if (stage < 0 || stage == 2)
         launch_k(pdl, k_fwd_pair<S, SW, VAR>, blocks, wpb * 32, PairL<S, SW>::bytes(a.T, a.NN) * wpb, st, a);
 }
@@ -1602,8 +1629,10 @@ template <class S, int SW, int VAR>
 void launch_adj_t(const AtomArgs &a, int blocks, int wpb, int stage, cudaStream_t st, bool pdl) {
     if (stage < 0 || stage == 0)
         launch_k(pdl, k_adj_jvp<S, SW, VAR>, blocks, wpb * 32, JvpL<S, SW>::bytes(a.T, a.NN) * wpb, st, a);
-    if ((stage < 0 || stage == 1) && a.n_chunks > 0)
-        launch_k(pdl, k_net_rev<S>, a.n_chunks, 256, net_rev_smem<S>(a.NN), st, a);
+    if ((stage < 0 || stage == 1) && a.n_chunks > 0) {
+        if (a.chunk_rows <= 16) launch_k(pdl, k_net_rev<S, 1>, a.n_chunks, 256, net_rev_smem<S, 1>(a.NN), st, a);
+        else launch_k(pdl, k_net_rev<S, 4>, a.n_chunks, 256, net_rev_smem<S, 4>(a.NN), st, a);
+    }
     if (stage < 0 || stage == 2)
         launch_k(pdl, k_adj_cg<S, SW, VAR>, blocks, wpb * 32, CgL<S, SW>::bytes(a.T, a.NN) * wpb, st, a);
 }
@@ -1642,8 +1671,9 @@ KernelSet make_set() {
     k.desc_fn[3] = (const void *)k_fwd_desc<S, 16, 1>;
     k.desc_fn[4] = (const void *)k_fwd_desc<S, 32, 0>;
     k.desc_fn[5] = (const void *)k_fwd_desc<S, 32, 1>;
-    k.net_fwd_fn = (const void *)k_net_fwd<S>;
-    k.net_fwd_smem = net_fwd_smem<S>;
+    k.net_fwd_fn[0] = (const void *)k_net_fwd<S, 4>;
+    k.net_fwd_fn[1] = (const void *)k_net_fwd<S, 1>;
+    k.net_fwd_smem = net_fwd_smem<S, 4>;
     k.adj_fn[0] = (const void *)k_adj_cg<S, 8, 0>;
     k.adj_fn[1] = (const void *)k_adj_cg<S, 8, 1>;
     k.adj_fn[2] = (const void *)k_adj_cg<S, 16, 0>;
@@ -1656,8 +1686,9 @@ KernelSet make_set() {
     k.jvp_fn[3] = (const void *)k_adj_jvp<S, 16, 1>;
     k.jvp_fn[4] = (const void *)k_adj_jvp<S, 32, 0>;
     k.jvp_fn[5] = (const void *)k_adj_jvp<S, 32, 1>;
-    k.net_rev_fn = (const void *)k_net_rev<S>;
-    k.net_rev_smem = net_rev_smem<S>;
+    k.net_rev_fn[0] = (const void *)k_net_rev<S, 4>;
+    k.net_rev_fn[1] = (const void *)k_net_rev<S, 1>;
+    k.net_rev_smem = net_rev_smem<S, 4>;
     k.launch_fwd[0] = launch_fwd_t<S, 8, 0>;
     k.launch_fwd[1] = launch_fwd_t<S, 8, 1>;
     k.launch_fwd[2] = launch_fwd_t<S, 16, 0>;
