@@ -115,7 +115,7 @@ int nep_set_structures(nep_ctx *ctx, int64_t n_struct, const int64_t *atom_off_d
 /* New positions (and optionally cells) for the cached batch: same structures, atom
  * counts and species.  pos_dev [N_a*3] f32 (device); cell_dev [n_struct*9] f32 (device)
  * or NULL to keep the cells (their bin grids are then reused).  Rebuilds the neighbour
- * lists on the device (step a1, as an MD-style evaluation needs every step) and
+ * lists on the device (as an MD-style evaluation needs every step) and
  * re-balances the per-atom kernel schedules for the new neighbour counts with the same
  * launch shapes, so every later result equals that of a fresh context on the new
  * geometry, bit for bit.  Without mini-batches the schedules are built on the device;

@@ -169,7 +169,6 @@ struct Ctx {
 
     // loss normalisers (0 = this batch's own N_s, N_a, N_s^V); set for one shard of a batch
     double ov_Ns = 0.0, ov_Na = 0.0, ov_NsV = 0.0;
-    int64_t struct_parts = 0;  // loss partials written by the latest k_struct launch (one per structure)
     double norm_Ns() const { return ov_Ns > 0.0 ? ov_Ns : (double)n_struct; }
     double norm_Na() const { return ov_Na > 0.0 ? ov_Na : (double)n_atoms; }
 

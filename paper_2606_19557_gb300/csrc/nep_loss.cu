@@ -1,9 +1,11 @@
-// Force gather, per-structure sums, the E/F/W loss, and the deterministic reductions
-// of the parameter gradient (hot-path steps a5-a7 and the reduction halves of a9/a10).
+// Parameter expansion, the force gather, per-structure sums and the E/F/W loss in one
+// launch, the network-gradient contraction, and the deterministic reduction of the
+// parameter gradient (with the optimiser step in training).
 //
-// Fixed-order reductions everywhere: per-warp FP64 sums in a fixed lane order, per-block
-// partials in a fixed warp order, and a final pass over the partials in index order.
-// No floating-point atomics, so two runs with the same launch shape are bit-identical.
+// Fixed-order reductions everywhere: sums in a fixed lane order, per-block partials in a
+// fixed warp order, and a final pass over the partials in index order (compensated FP32
+// pair sums where FP64 would serialise on this part's slow FP64 units).  No floating-point
+// atomics, so two runs with the same launch shape are bit-identical.
 #include <algorithm>
 #include <vector>
 
@@ -798,7 +800,10 @@ int launch_adjoint_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBu
     return NEP_OK;
 }
 
-static int gather_blocks(Ctx *c) { return c->n_sm * 4; }
+// 8-warp gather blocks: four per SM, fewer when the atoms give a warp less than one each
+static int gather_blocks(Ctx *c, int64_t n_atoms) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(c->n_sm * 4, (n_atoms + 7) / 8));
+}
 
 
 double host_nsv(Ctx *c, const uint8_t *has_W, int64_t s0, int64_t s1) {
@@ -818,7 +823,7 @@ int launch_count_hasw(Ctx *c, const uint8_t *has_W, int64_t s0, int64_t s1) {
 
 int launch_terms(Ctx *c, const TermsCall &t) {
     const int64_t ns = t.s1 - t.s0;
-    const int nG = t.a1 > t.a0 ? (t.gather_blocks > 0 ? t.gather_blocks : gather_blocks(c)) : 0;
+    const int nG = t.a1 > t.a0 ? (t.gather_blocks > 0 ? t.gather_blocks : gather_blocks(c, t.a1 - t.a0)) : 0;
     if (nG + ns == 0)  // nothing to sum: the loss terms and dL/db1 are zero
         return t.loss && t.loss3 ? launch_loss_final(c, t.loss3, nullptr, 0, nullptr, 0, 1.0) : NEP_OK;
     TermsArgs x{};

@@ -1,6 +1,6 @@
-// Per-atom kernels of the NEP loss + parameter-gradient pass (hot-path steps a2-a4, a6,
-// a8-a10).  Persistent over a static species-sorted schedule: each warp owns a
-// contiguous range of work positions and processes them in batches of G = 32/SW
+// Per-atom kernels of the NEP loss + parameter-gradient pass (descriptors, network, pair
+// gradients, and the adjoint).  Persistent over a static species-sorted schedule: each
+// warp owns a contiguous range of work positions and processes them in batches of G = 32/SW
 // atoms of one species, one group of SW lanes per atom, so that the ~15-20 angular
 // and ~60-80 radial neighbours of an atom keep most lanes busy.
 //

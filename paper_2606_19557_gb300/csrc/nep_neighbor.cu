@@ -1,4 +1,5 @@
-// Cell-list neighbour search emitting CSR neighbour lists (hot-path step a1).
+// Cell-list neighbour search emitting CSR neighbour lists (kept on the GPU, Sec. "Training
+// efficiency").
 //
 // The paper builds neighbour lists and displacement vectors once and keeps them on
 // the GPU (Sec. "Training efficiency ..."); this file does the same for a whole
