@@ -331,10 +331,11 @@ __global__ void k_cotangents(int64_t ns, const int64_t *atom_off, const double *
 // --------------------------------------------------------------------------- network gradient
 // grad_w0[t] = sum_i zeta_i q~_i^T + u_i dq~_i^T, grad_b0[t] = -sum zeta, grad_w1[t] = sum omega
 // over the atoms of species t: a contraction over atoms ([NN x 2n] . [2n x ND]).  One
-// block per chunk of work positions holding a single species; each thread accumulates
-// a 4 x 4 register tile of the NN x ND output; FP32 partial per chunk.
+// block per chunk of work positions holding a single species (more only when the 4 x 4
+// tiles of the NN x ND output outnumber 256 threads); each thread accumulates one 4 x 4
+// register tile; FP32 partial per chunk.
 constexpr int ANN_ROWS = 32;
-constexpr int ANN_TILES = 128;  // 4x4 tiles per block (blockIdx.y covers the rest)
+constexpr int ANN_MAX_THREADS = 256;
 
 // Asynchronous 4-byte global -> shared copy (zero fill when !pred), so that the next rows
 // of a chunk load while the current ones are contracted.
@@ -391,8 +392,8 @@ __global__ void k_ann_grad(const int *chunk_begin, int NN, int NDP, const float 
     const int c = blockIdx.x;
     const int r0 = chunk_begin[c], r1 = chunk_begin[c + 1];
     const int tn = NDQ / 4, ntiles = (NNP / 4) * tn;
-    const int tile = blockIdx.y * ANN_TILES + threadIdx.x;
-    const bool own = threadIdx.x < ANN_TILES && tile < ntiles;
+    const int tile = blockIdx.y * blockDim.x + threadIdx.x;
+    const bool own = tile < ntiles;
     const int mu0 = own ? 4 * (tile / tn) : 0, v0 = own ? 4 * (tile % tn) : 0;
     const bool first = blockIdx.y == 0;
     float acc[4][4];
@@ -891,9 +892,16 @@ static size_t ann_smem(Ctx *c) {  // two buffers of staged rows
     const int NNP = (c->NN + 3) & ~3, NDQ = (c->NDP + 3) & ~3;
     return 2 * sizeof(float) * ANN_ROWS * (3 * NNP + 2 * NDQ);
 }
+// threads per block: the output tiles (whole warps, at most 256), and at least the neurons
+// (the b0 / w1 sums of the first block take one thread per neuron)
+static int ann_threads(Ctx *c) {
+    const int ntiles = ((c->NN + 3) / 4) * ((c->NDP + 3) / 4);
+    const int t = std::max((ntiles + 31) / 32 * 32, (c->NN + 31) / 32 * 32);
+    return std::min(ANN_MAX_THREADS, t);
+}
 static int ann_groups(Ctx *c) {
     const int ntiles = ((c->NN + 3) / 4) * ((c->NDP + 3) / 4);
-    return (ntiles + ANN_TILES - 1) / ANN_TILES;
+    return (ntiles + ann_threads(c) - 1) / ann_threads(c);
 }
 
 int prepare_loss_kernels(Ctx *c) {
@@ -905,7 +913,7 @@ int prepare_loss_kernels(Ctx *c) {
 
 int launch_ann_grad_chunks(Ctx *c, const int *chunks, int n_chunks) {
     if (n_chunks <= 0) return NEP_OK;
-    CK(launch_k(c->pdl(), k_ann_grad, dim3(n_chunks, ann_groups(c)), ANN_TILES, ann_smem(c), c->stream, chunks,
+    CK(launch_k(c->pdl(), k_ann_grad, dim3(n_chunks, ann_groups(c)), ann_threads(c), ann_smem(c), c->stream, chunks,
                 c->NN, c->NDP, c->zt.as<float>(), c->ut.as<float>(), c->om.as<float>(), c->st_qt.as<float>(),
                 c->dqt.as<float>(), c->annpart.as<float>()));
     return NEP_OK;
@@ -1087,7 +1095,7 @@ int run_plain_loss(Ctx *c, const double *Er, const float *Fr, const double *Wr, 
         c->ks->launch_adj[pv](a, (int)n, 1, -1, c->stream, false);
         CK_LAUNCH("adjoint stages (plain)");
         if (nch > 0) {
-            k_ann_grad<<<dim3(nch, groups), ANN_TILES, gsm, c->stream>>>(c->p_chunks.as<int>() + c->p_cofs[s], c->NN, c->NDP,
+            k_ann_grad<<<dim3(nch, groups), ann_threads(c), gsm, c->stream>>>(c->p_chunks.as<int>() + c->p_cofs[s], c->NN, c->NDP,
                                                                    c->zt.as<float>(), c->ut.as<float>(),
                                                                    c->om.as<float>(), c->st_qt.as<float>(),
                                                                    c->dqt.as<float>(), c->annpart.as<float>());
