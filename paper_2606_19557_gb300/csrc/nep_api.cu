@@ -522,7 +522,7 @@ int nep_set_structures(nep_ctx *c, int64_t ns, const int64_t *atom_off, const fl
     if ((rc = build_work_rec(c, c->work.as<int>(), c->rec, c->rec2))) return rc;
     // network-gradient chunks (single species each)
     {
-        const int CH = 128;  // work positions per network-gradient chunk
+        const int CH = NET_CHUNK;  // work positions per network chunk
         std::vector<int> cb, clo(c->T), chi(c->T);
         for (int t = 0; t < c->T; ++t) {
             clo[t] = (int)cb.size();

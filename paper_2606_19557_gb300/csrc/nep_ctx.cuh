@@ -54,6 +54,7 @@ struct Sched {
     DevBuf type_wlo, type_whi;  // [T] first / last warp holding each species (adjoint slots)
 };
 
+constexpr int NET_CHUNK = 128;  // work positions per network chunk of the whole batch
 constexpr int NVAR = 6;
 constexpr int NVAR_TUNE = 4;  // variants the whole-batch autotune tries (32 lanes per atom pays only
                               // for small mini-batch groups, whose own tuning includes it)

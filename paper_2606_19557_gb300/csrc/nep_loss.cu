@@ -693,7 +693,7 @@ static AtomArgs atom_args(Ctx *c) {
     a.cpart = c->cpart.as<float>();
     a.chunks = c->chunk_begin.as<int>();
     a.n_chunks = c->n_chunks;
-    a.chunk_rows = 128;  // the batch's chunks (nep_set_structures)
+    a.chunk_rows = NET_CHUNK;  // the batch's chunks (nep_set_structures)
     a.NDP = c->NDP;
     a.st_D = c->st_D.as<float>();
     a.st_S = c->st_S.as<float>();

@@ -651,7 +651,8 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_jvp(AtomArgs a) {
 }
 
 // ----------------------------------------------------------------------------- network reverse
-// Per chunk of <= 128 work positions of one species t, in tiles of 64 atoms (Eq. "ann"):
+// Per chunk of <= 128 work positions of one species t, in tiles of 64 atoms (16 for chunks of
+// at most 16) (Eq. "ann"):
 //   v = W0 dq~,  h' = 1 - h^2,  h'' = -2 h h',
 //   zeta = ebar w1 h' + w1 h'' v,  u = w1 h',  omega = ebar h + h' v,
 //   abar = s (W0^T zeta)   (b = s (W0^T u) comes from the network forward pass).
@@ -1260,7 +1261,8 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_desc(AtomArgs a) 
 }
 
 // ----------------------------------------------------------------------------- network forward
-// Per chunk of <= 128 work positions of one species t, in tiles of 64 atoms (Eq. "ann"):
+// Per chunk of <= 128 work positions of one species t, in tiles of 64 atoms (16 for chunks of
+// at most 16) (Eq. "ann"):
 //   h = tanh(W0 q~ - b0),  E = w1 . h - b1,  u = w1 (1 - h^2),  b = s (W0^T u).
 // Same tiling as the network reverse pass.
 template <class S, int RX>
