@@ -191,6 +191,7 @@ template <int C, int SW>
 __device__ __forceinline__ void walk_species_rows(const float (*rows)[C + 1], int cnt, int sl, float *S, float *v,
                                                   int &bcur) {
     constexpr int RC = (C + SW - 1) / SW;
+#pragma unroll 2
     for (int pp = 0; pp < cnt; ++pp) {
         const float *row = rows[pp];
         const int t = __float_as_int(row[C]);
@@ -512,6 +513,7 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_jvp(AtomArgs a) {
                 }
                 __syncwarp();
                 const int cnt = min(SW, nAng - c0);
+#pragma unroll 2
                 for (int pp = 0; pp < cnt; ++pp) {
                     float gv[NAP], gpv[NAP];
                     load_row<NAP>(sm.st.j.g[grp][pp], gv);
@@ -1044,6 +1046,7 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_adj_cg(AtomArgs a) {
 #pragma unroll 1
                 for (int g2 = 0; g2 < G; ++g2) {
                     const int cnt = min(SW, __shfl_sync(FULL, nAng, g2 * SW) - c0);
+#pragma unroll 2
                     for (int pp = 0; pp < cnt; ++pp) {
                         const int t = sm.st.t[g2][pp];
                         if (t != xb) {
@@ -1152,6 +1155,7 @@ __global__ void __launch_bounds__(128, VAR == 0 ? 4 : 5) k_fwd_desc(AtomArgs a) 
             }
             __syncwarp();
             const int cnt = min(SW, nAng - c0);
+#pragma unroll 2
             for (int pp = 0; pp < cnt; ++pp) {
                 float gv[NAP];
                 load_row<NAP>(sm.st.g[grp][pp], gv);
