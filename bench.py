@@ -81,9 +81,9 @@ TRAFFIC = {
     # ncu --set full on every 50th structure of the headline workload (131,591 atoms, 71.6
     # radial pairs per atom against 71.4 in the full batch), launch 0,2,4,608,1,2128
     "scale_t5": {
-        "sha256": "3c597117db6f0d3a5c8448ba979d97083286a2cf32a4a6b550cde76290a915ab",
-        "bytes_per_atom": {"forward_desc": 1817.2, "forward_pair": 3279.9, "adjoint_jvp": 2974.4,
-                           "adjoint_cgrad": 2683.1},
+        "sha256": "9210137feddc88cca1d15b2edd23c4a933c3cf92acb0ff0a50db74cef23026b2",
+        "bytes_per_atom": {"forward_desc": 1817.8, "forward_pair": 3278.7, "adjoint_jvp": 2979.4,
+                           "adjoint_cgrad": 2683.3},
     },
 }
 
