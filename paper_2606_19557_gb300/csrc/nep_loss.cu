@@ -115,25 +115,39 @@ struct TermsArgs {
 };
 
 // F_i = sum_{p in N(i)} G_p - sum_{p in N(i)} G_{rev(p)}: the second sum visits the pairs
-// (j, i, -S) of which i is the neighbour, through the reverse index (no atomics).  Warps
-// stride over the atoms; the block's squared force residuals go to fpart[block].
+// (j, i, -S) of which i is the neighbour, through the reverse index (no atomics).  Each
+// half-warp takes one atom (two atoms in flight per warp) and the half-warps stride over the
+// atoms; the next atom's list bounds are loaded while the current atom's rows are gathered.
+// The block's squared force residuals go to fpart[block].
 __device__ void gather_block(const TermsArgs &x, int blk) {
     __shared__ float2 wpart[32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t gw = (int64_t)blk * nw + wib, W = (int64_t)x.nG * nw;
+    const int hl = lane & 15;
+    const int64_t H = (int64_t)x.nG * nw * 2;
+    int64_t i = x.a0 + ((int64_t)blk * nw + wib) * 2 + (lane >> 4);
+    int64_t beg = 0, end = 0;
+    if (i < x.a1) {
+        beg = x.nbr_off[i];
+        end = x.nbr_off[i + 1];
+    }
     float ah = 0.0f, al = 0.0f;  // sum of d^2: each square exact as p + e (FMA), then TwoSum
-    for (int64_t i = x.a0 + gw; i < x.a1; i += W) {
-        const int64_t beg = x.nbr_off[i], end = x.nbr_off[i + 1];
+    while (__any_sync(FULL, i < x.a1)) {
+        const int64_t in = i + H;
+        int64_t nbeg = 0, nend = 0;
+        if (in < x.a1) {
+            nbeg = x.nbr_off[in];
+            nend = x.nbr_off[in + 1];
+        }
         float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-        for (int64_t p0 = beg; p0 < end; p0 += 128) {  // 4 index loads, then 4 gathers, in flight
-            int r[4];
+        for (int64_t p0 = beg; p0 < end; p0 += 128) {  // 8 index loads, then 8 gathers, in flight
+            int r[8];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t p = p0 + lane + 32 * k;
+            for (int k = 0; k < 8; ++k) {
+                const int64_t p = p0 + hl + 16 * k;
                 r[k] = p < end ? x.rev[p] : -1;
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 8; ++k) {
                 if (r[k] >= 0) {
                     const float4 g = x.G[r[k]];
                     sx += g.x;
@@ -142,26 +156,34 @@ __device__ void gather_block(const TermsArgs &x, int blk) {
                 }
             }
         }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        sz = warp_sum(sz);
-        if (lane < 3) {
-            const float own = x.F_own[i * 3 + lane];
-            const float F = own - (lane == 0 ? sx : lane == 1 ? sy : sz);
-            x.F_out[i * 3 + lane] = F;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {  // sums over each half-warp
+            sx += __shfl_xor_sync(FULL, sx, o);
+            sy += __shfl_xor_sync(FULL, sy, o);
+            sz += __shfl_xor_sync(FULL, sz, o);
+        }
+        if (hl < 3 && i < x.a1) {
+            const float own = x.F_own[i * 3 + hl];
+            const float F = own - (hl == 0 ? sx : hl == 1 ? sy : sz);
+            x.F_out[i * 3 + hl] = F;
             if (x.loss) {
-                const float d = F - x.F_ref[i * 3 + lane];
-                x.fbar[i * 4 + lane] = x.coefF * d;  // float4 rows (x, y, z, unused)
+                const float d = F - x.F_ref[i * 3 + hl];
+                x.fbar[i * 4 + hl] = x.coefF * d;  // float4 rows (x, y, z, unused)
                 const float p = d * d;
                 f2_add(ah, al, p);
                 al += fmaf(d, d, -p);
             }
         }
+        i = in;
+        beg = nbeg;
+        end = nend;
     }
     if (!x.loss) return;
-    // lanes 0..2 hold the sums (the others zero): lane 0 takes 1 and 2 in a fixed order
+    // lanes 0..2 and 16..18 hold the sums (the others zero): lanes 0 and 16 take their
+    // half's 1 and 2, then lane 0 takes lane 16, in a fixed order
     f2_merge(ah, al, __shfl_down_sync(FULL, ah, 1), __shfl_down_sync(FULL, al, 1));
     f2_merge(ah, al, __shfl_down_sync(FULL, ah, 2), __shfl_down_sync(FULL, al, 2));
+    f2_merge(ah, al, __shfl_down_sync(FULL, ah, 16), __shfl_down_sync(FULL, al, 16));
     if (lane == 0) wpart[wib] = make_float2(ah, al);
     __syncthreads();
     if (threadIdx.x == 0) {
