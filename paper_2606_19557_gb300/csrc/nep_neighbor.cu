@@ -592,7 +592,7 @@ __device__ __forceinline__ void pair_d0(const float *pi, const float *pj, const 
     }
 }
 
-// The predicate's displacement (c7's float) of the pair of key k from atom i.
+// The predicate's float displacement of the pair of key k from atom i.
 __device__ __forceinline__ void decode_key(uint64_t k, int64_t i, const float *pos, const SGeom &g, float *d32) {
     const int j = (int)((k >> 24) & ((1ull << 35) - 1));
     const uint32_t sp = (uint32_t)(k & 0xffffffull);
@@ -797,7 +797,7 @@ __global__ void k_max_disp(int64_t na, const float *pos, const float *ref, unsig
     if ((threadIdx.x & 31) == 0) atomicMax(out, b);
 }
 
-// Candidate filter, one warp per atom.  Pass 1 (WRITE = false): the pair predicate (c7) of
+// Candidate filter, one warp per atom.  Pass 1 (WRITE = false): the pair predicate (above) of
 // every candidate at the current positions, as flags (bit 0 within r_c^R, bit 1 within
 // r_c^A) and its pair record in crec, and the atom's radial and angular counts.  Pass 2:
 // the kept candidates' records at their list positions (angular ones first, each group in
@@ -1057,7 +1057,7 @@ int build_neighbors(Ctx *c, bool same_cells, bool host_lists) {
 // Position updates with the cells kept.  A candidate list holds, for reference positions R,
 // every pair within r_c + s (s the skin).  If no atom has moved more than d from R, a pair
 // within r_c at the new positions was within r_c + 2d at R, so for 2d < s the new lists are
-// the candidates that pass the pair predicate (c7) at the new positions: a filter instead
+// the candidates that pass the pair predicate at the new positions: a filter instead
 // of a scan.  The filter keeps the candidates' order, (t_j, j, S), and puts the angular
 // ones first, which is the order the scan's sort gives: the lists are the scan's, bit for
 // bit.  The reverse index follows from the candidates' own.
