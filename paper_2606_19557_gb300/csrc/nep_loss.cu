@@ -823,7 +823,8 @@ int launch_adjoint_sched(Ctx *c, const int *work, const DevBuf &rec, const DevBu
     return NEP_OK;
 }
 
-// 8-warp gather blocks: four per SM, fewer when the atoms give a warp less than one each
+// 8-warp gather blocks (two atoms in flight per warp): four per SM, and one block per 8 atoms
+// for batches too small to fill them
 static int gather_blocks(Ctx *c, int64_t n_atoms) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(c->n_sm * 4, (n_atoms + 7) / 8));
 }
